@@ -1,0 +1,526 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics
+(closed forms, invariants, brute force, library routines), none of them a
+restatement of the oracle's own formulas.  CPU only."""
+
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+from scipy.linalg import lapack
+
+import oracle
+from oracle import tableaux
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+ZTOP = 30e3
+
+
+def _rest(nez, N, ztop=ZTOP, ncols=1):
+    return oracle.reference_q(nez, N, ztop, ncols)
+
+
+def _perturbed_state(nez, N, seed=0, ztop=ZTOP, amp_w=5.0, amp_th=2.0):
+    """A non-rest state: rest + random w (0 at both ends) and theta'."""
+    g = np.random.default_rng(seed)
+    q = _rest(nez, N, ztop)[0].reshape(-1, 3)
+    nz = q.shape[0]
+    w = g.uniform(-amp_w, amp_w, nz)
+    w[0] = w[-1] = 0.0
+    th = g.uniform(-amp_th, amp_th, nz)
+    rho = q[:, 0] * (1 + 0.01 * g.uniform(-1, 1, nz))
+    Theta = q[:, 2] / q[:, 0] * rho + rho * th
+    return np.stack([rho, rho * w, Theta], 1).reshape(-1)
+
+
+# --------------------------------------------------------------------------
+# Sec. 3: LGL nodes, weights, differentiation matrix
+# --------------------------------------------------------------------------
+
+def test_lgl_order4_closed_form():
+    xi, w = oracle.lgl(4)
+    r = math.sqrt(3.0 / 7.0)
+    np.testing.assert_allclose(xi, [-1, -r, 0, r, 1], atol=1e-15)
+    np.testing.assert_allclose(w, [1 / 10, 49 / 90, 32 / 45, 49 / 90, 1 / 10], rtol=1e-15)
+
+
+@pytest.mark.parametrize("N", range(1, 11))
+def test_lgl_nodes_are_roots_of_dPN_and_quadrature_exact(N):
+    xi, w = oracle.lgl(N)
+    # interior nodes are the roots of P_N' (numpy's Legendre series)
+    dP = np.polynomial.legendre.Legendre.basis(N).deriv()
+    np.testing.assert_allclose(np.sort(dP.roots().real), xi[1:-1], atol=1e-13)
+    # Lobatto quadrature with N+1 points is exact to degree 2N-1
+    for p in range(2 * N):
+        exact = 0.0 if p % 2 else 2.0 / (p + 1)
+        assert abs(np.dot(w, xi**p) - exact) < 1e-13
+    # ... and not exact at degree 2N (the inexact mass matrix of Sec. 3)
+    assert abs(np.dot(w, xi ** (2 * N)) - 2.0 / (2 * N + 1)) > 1e-6
+
+
+@pytest.mark.parametrize("N", range(1, 11))
+def test_dmatrix_exact_rowsum_sbp(N):
+    xi, w = oracle.lgl(N)
+    D = oracle.dmatrix(N)
+    # row-sum property (Sec. 3): derivative of a constant is zero
+    np.testing.assert_allclose(D.sum(1), 0.0, atol=1e-12 * N * N)
+    # exact on polynomials of degree <= N
+    for p in range(N + 1):
+        np.testing.assert_allclose(D @ xi**p, p * xi ** max(p - 1, 0) if p else 0 * xi,
+                                   atol=1e-12 * N * N)
+    # summation by parts: W D + D^T W = diag(-1, 0, ..., 0, 1)
+    W = np.diag(w)
+    B = np.zeros((N + 1, N + 1))
+    B[0, 0], B[-1, -1] = -1.0, 1.0
+    np.testing.assert_allclose(W @ D + D.T @ W, B, atol=1e-12 * N * N)
+
+
+def test_dmatrix_matches_lgl_closed_form():
+    # classical closed form for LGL points: D_kj = P_N(x_k) / (P_N(x_j)(x_k - x_j)),
+    # D_00 = -N(N+1)/4, D_NN = N(N+1)/4, other diagonal entries 0
+    for N in (2, 3, 4, 7):
+        xi, _ = oracle.lgl(N)
+        PN = np.polynomial.legendre.Legendre.basis(N)(xi)
+        ref = np.zeros((N + 1, N + 1))
+        for k in range(N + 1):
+            for j in range(N + 1):
+                if k != j:
+                    ref[k, j] = PN[k] / (PN[j] * (xi[k] - xi[j]))
+        ref[0, 0], ref[N, N] = -N * (N + 1) / 4, N * (N + 1) / 4
+        np.testing.assert_allclose(oracle.dmatrix(N), ref, atol=1e-12)
+
+
+@pytest.mark.parametrize("nez,N", [(1, 1), (3, 2), (8, 4), (10, 4), (16, 3), (24, 4)])
+def test_grid_mass(nez, N):
+    z, M = oracle.column_grid(nez, N, ZTOP)
+    assert z.size == nez * N + 1
+    assert np.all(np.diff(z) > 0) and z[0] == 0.0 and z[-1] == ZTOP
+    assert abs(M.sum() - ZTOP) < 1e-10 * ZTOP
+    # mass integrates polynomials in z of degree <= 2N-1 exactly on each element
+    for p in range(2 * N):
+        assert abs(np.dot(M, (z / ZTOP) ** p) - ZTOP / (p + 1)) < 1e-11 * ZTOP
+
+
+# --------------------------------------------------------------------------
+# Band structure of Sec. 4.2.3 (golden values of the paper's formulas)
+# --------------------------------------------------------------------------
+
+def test_band_structure_golden():
+    with open(os.path.join(GOLDEN, "band_structure.json")) as f:
+        gold = json.load(f)
+    for row in gold["rows"]:
+        nvar, N = row["n_var"], row["N"]
+        assert nvar * (N + 1) - 1 == row["k_l"] == row["k_u"]
+        assert 3 * nvar * (N + 1) - 2 == row["ldab"]
+        if nvar == 3:
+            # the assembled Jacobian lies inside the band and reaches k_l below
+            # the diagonal (Theta-row, rho-column); above it reaches k_u - 1,
+            # since the rho-row couples to m only
+            nez = 3
+            q = _perturbed_state(nez, N, seed=1)
+            ab = oracle.assemble_band(nez, N, ZTOP, 50.0, q[None])[0]
+            A = oracle.band_to_dense(ab, row["k_l"], row["k_u"])
+            i, j = np.nonzero(A)
+            assert (i - j).max() == row["k_l"] and (j - i).max() == row["k_u"] - 1
+
+
+# --------------------------------------------------------------------------
+# Reference state and operator invariants
+# --------------------------------------------------------------------------
+
+def test_reference_state_isothermal_closed_form():
+    z, _ = oracle.column_grid(10, 4, ZTOP)
+    rho, theta, Theta, P = oracle.reference_state(z)
+    R, T0, p0, g = 287.17, 300.0, 1e5, 9.80616
+    p_exact = p0 * np.exp(-g * z / (R * T0))
+    np.testing.assert_allclose(P, p_exact, rtol=1e-12)       # EOS(Theta_bar) = p_bar
+    np.testing.assert_allclose(rho * R * T0, p_exact, rtol=1e-14)
+    # theta = T (p0/p)^(R/cp)
+    np.testing.assert_allclose(theta, T0 * (p0 / p_exact) ** (R / 1004.67), rtol=1e-13)
+
+
+@pytest.mark.parametrize("nez,N", [(1, 1), (2, 3), (8, 4), (16, 3), (24, 4)])
+def test_rest_state_is_exact_equilibrium(nez, N):
+    q = _rest(nez, N)
+    assert np.array_equal(oracle.apply_V(nez, N, ZTOP, q), np.zeros_like(q))
+
+
+@pytest.mark.parametrize("nez,N", [(2, 2), (8, 4), (16, 3)])
+def test_column_mass_and_theta_conserved(nez, N):
+    """Sec. 2.2 / 3: the divergence form conserves the column integrals of rho
+    and Theta under LGL quadrature when m = 0 at both ends."""
+    _, M = oracle.column_grid(nez, N, ZTOP)
+    q = _perturbed_state(nez, N, seed=2)
+    v = oracle.apply_V(nez, N, ZTOP, q)[0].reshape(-1, 3)
+    scale_r = np.abs(M * q.reshape(-1, 3)[:, 0]).sum() / ZTOP
+    assert abs(np.dot(M, v[:, 0])) < 1e-13 * scale_r * ZTOP
+    assert abs(np.dot(M, v[:, 2])) < 1e-13 * scale_r * 300 * ZTOP
+    g = np.random.default_rng(3)
+    x = g.standard_normal(q.size).reshape(-1, 3)
+    x[0, 1] = x[-1, 1] = 0.0
+    y = oracle.apply_L(nez, N, ZTOP, q[None], x.reshape(1, -1))[0].reshape(-1, 3)
+    assert abs(np.dot(M, y[:, 0])) < 1e-12 * np.abs(M[:, None] * y).sum()
+    assert abs(np.dot(M, y[:, 2])) < 1e-12 * np.abs(M[:, None] * y).sum()
+
+
+@pytest.mark.parametrize("nez,N", [(2, 2), (4, 4), (16, 3)])
+def test_linear_operator_is_the_frechet_derivative(nez, N):
+    """L(q0) x against central differences of the nonlinear V (pins every
+    entry of the flux Jacobian, its signs and the gravity coupling)."""
+    q0 = _perturbed_state(nez, N, seed=4)
+    g = np.random.default_rng(5)
+    s = oracle.scales(oracle.column_grid(nez, N, ZTOP)[0])
+    x = s * g.standard_normal(q0.size)
+    x[1] = x[-2] = 0.0
+    L = oracle.apply_L(nez, N, ZTOP, q0[None], x[None])[0]
+    eps = 1e-5
+    fd = (oracle.apply_V(nez, N, ZTOP, (q0 + eps * x)[None])[0]
+          - oracle.apply_V(nez, N, ZTOP, (q0 - eps * x)[None])[0]) / (2 * eps)
+    assert np.linalg.norm(L - fd) <= 1e-7 * np.linalg.norm(L)
+
+
+def test_operator_differentiates_polynomial_flux_exactly():
+    """With rho = const and a polynomial momentum of degree <= N on each
+    element, V_rho = -dm/dz exactly at every point (continuous derivative)."""
+    nez, N = 3, 4
+    z, _ = oracle.column_grid(nez, N, ZTOP)
+    q = _rest(nez, N)[0].reshape(-1, 3)
+    m = (z / ZTOP) * (1 - z / ZTOP) * 2.0        # degree 2, zero at both ends
+    q[:, 1] = m
+    v = oracle.apply_V(nez, N, ZTOP, q.reshape(1, -1))[0].reshape(-1, 3)
+    dm = 2.0 * (1 - 2 * z / ZTOP) / ZTOP
+    np.testing.assert_allclose(-v[:, 0], dm, atol=1e-14 * 2.0 / ZTOP * 100)
+
+
+def test_assembly_matches_operator_columns():
+    """Band column j of A equals e_j - Lambda L(q0) e_j (App. A.3 vs Sec. 4.3.1)."""
+    nez, N, lam = 3, 4, 87.0
+    q0 = _perturbed_state(nez, N, seed=6)
+    _, n, k = oracle.sizes(nez, N)
+    A = oracle.band_to_dense(oracle.assemble_band(nez, N, ZTOP, lam, q0[None])[0], k, k)
+    E = np.eye(n)
+    L = np.stack([oracle.apply_L(nez, N, ZTOP, q0[None], E[j][None])[0] for j in range(n)], 1)
+    ref = np.eye(n) - lam * L
+    # the boundary m-rows are identity rows (reading R3)
+    for I in (0, n // 3 - 1):
+        ref[3 * I + 1, :] = 0.0
+        ref[3 * I + 1, 3 * I + 1] = 1.0
+    np.testing.assert_allclose(A, ref, atol=1e-13 * np.abs(ref).max())
+
+
+# --------------------------------------------------------------------------
+# Band LU (Sec. 4.2.3) against LAPACK and dense brute force
+# --------------------------------------------------------------------------
+
+CASES = [(1, 1), (2, 1), (3, 2), (1, 4), (2, 4), (3, 3), (8, 4), (10, 4), (16, 3)]
+
+
+@pytest.mark.parametrize("nez,N", CASES)
+def test_band_lu_matches_lapack_and_dense(nez, N):
+    _, n, k = oracle.sizes(nez, N)
+    q0 = _perturbed_state(nez, N, seed=7 + nez)
+    lam = 87.868
+    ab = oracle.assemble_band(nez, N, ZTOP, lam, q0[None])[0].copy()
+    ab_orig = ab.copy()
+    A = oracle.band_to_dense(ab, k, k)
+    lu_ref, piv_ref, info_ref = lapack.dgbtrf(np.asfortranarray(ab.T), k, k)
+    info, piv = oracle.gbtrf(ab, k, k)
+    assert info == info_ref == 0
+    np.testing.assert_array_equal(piv, piv_ref)           # pivot sequence: reading R6
+    np.testing.assert_allclose(ab.T, lu_ref, atol=1e-12 * np.abs(lu_ref).max())
+    g = np.random.default_rng(8)
+    b = g.standard_normal(n) * oracle.scales(oracle.column_grid(nez, N, ZTOP)[0])
+    x = oracle.gbtrs(ab, k, k, piv, b)
+    x_dense = np.linalg.solve(A, b)
+    x_band = sla.solve_banded((k, k), ab_orig.T[k:, :], b)
+    kappa = np.linalg.cond(A)
+    assert np.linalg.norm(x - x_dense) <= 1e-15 * kappa * np.linalg.norm(x_dense) * 10
+    assert np.linalg.norm(x - x_band) <= 1e-15 * kappa * np.linalg.norm(x_band) * 10
+    assert np.linalg.norm(b - A @ x) <= 1e-14 * np.linalg.norm(b) * max(1.0, np.abs(A).max())
+
+
+def test_band_lu_tie_break_first_maximum():
+    """Equal-magnitude candidates: the first row wins, as LAPACK's i_amax."""
+    n, kl, ku = 4, 1, 1
+    A = np.array([[1.0, 2.0, 0, 0], [-1.0, 1.0, 3.0, 0], [0, 2.0, -2.0, 1.0], [0, 0, 2.0, 1.0]])
+    ab = np.zeros((n, 2 * kl + ku + 1))
+    for j in range(n):
+        for i in range(max(0, j - ku), min(n, j + kl + 1)):
+            ab[j, kl + ku + i - j] = A[i, j]
+    _, piv_ref, _ = lapack.dgbtrf(np.asfortranarray(ab.T), kl, ku)
+    info, piv = oracle.gbtrf(ab.copy(), kl, ku)
+    np.testing.assert_array_equal(piv, piv_ref)
+    assert piv[0] == 0
+
+
+def test_band_lu_reports_singular_pivot():
+    n, kl, ku = 3, 1, 1
+    A = np.array([[1.0, 2.0, 0], [1.0, 2.0, 0.0], [0, 0, 1.0]])
+    ab = np.zeros((n, 4))
+    for j in range(n):
+        for i in range(max(0, j - ku), min(n, j + kl + 1)):
+            ab[j, kl + ku + i - j] = A[i, j]
+    _, _, info_ref = lapack.dgbtrf(np.asfortranarray(ab.T), kl, ku)
+    info, _ = oracle.gbtrf(ab.copy(), kl, ku)
+    assert info == info_ref == 2
+
+
+def test_stage_solve_identity_when_lambda_zero():
+    nez, N = 8, 4
+    q0 = _rest(nez, N)
+    b = np.random.default_rng(9).standard_normal(q0.shape)
+    x, info = oracle.stage_solve(nez, N, ZTOP, 0.0, q0, b)
+    assert info[0] == 0
+    np.testing.assert_array_equal(x, b)
+
+
+def test_stage_solve_rest_zero_rhs_gives_zero():
+    nez, N = 8, 4
+    q0 = _rest(nez, N)
+    x, _ = oracle.stage_solve(nez, N, ZTOP, 87.868, q0, np.zeros_like(q0))
+    assert np.array_equal(x, np.zeros_like(q0))
+
+
+def test_stage_solve_conserves_column_mass():
+    import hevi_inputs
+    inp = hevi_inputs.lhevi_stage(seed=11, ncols=4)
+    nez, N = inp["nez"], inp["N"]
+    q0 = _rest(nez, N, ZTOP, 4)
+    x, info = oracle.stage_solve(nez, N, inp["ztop"], inp["lam"], q0, inp["b"])
+    assert (info == 0).all()
+    _, M = oracle.column_grid(nez, N, ZTOP)
+    for c in range(4):
+        xb, bb = x[c].reshape(-1, 3), inp["b"][c].reshape(-1, 3)
+        tot = np.abs(M * bb[:, 2]).sum()
+        assert abs(np.dot(M, xb[:, 0]) - np.dot(M, bb[:, 0])) < 1e-13 * tot
+        assert abs(np.dot(M, xb[:, 2]) - np.dot(M, bb[:, 2])) < 1e-13 * tot
+        # identity m-rows at both ends; pivoting may reorder them, so zero to rounding
+        assert abs(xb[0, 1]) < 1e-15 * np.abs(xb[:, 1]).max()
+        assert abs(xb[-1, 1]) < 1e-15 * np.abs(xb[:, 1]).max()
+
+
+# --------------------------------------------------------------------------
+# Newton (Sec. 4.2.3) and its relation to LHEVI (Sec. 4.3)
+# --------------------------------------------------------------------------
+
+def test_newton_at_rest_takes_no_step():
+    nez, N = 16, 3
+    q = _rest(nez, N)
+    out, it, st = oracle.newton(nez, N, ZTOP, 87.0, q, q)
+    assert it[0] == 0 and st[0] == 0 and np.array_equal(out, q)
+
+
+def test_one_newton_iteration_is_the_lhevi_solve():
+    """Sec. 4.3: LHEVI-PS is NHEVI-LU with one Newton iteration: from q0,
+    (I - Lambda L(q0)) q1 = R + Lambda (V(q0) - L(q0) q0)."""
+    nez, N, lam = 8, 4, 87.868
+    q0 = _perturbed_state(nez, N, seed=12)[None]
+    R = q0 + 0.01 * oracle.scales(oracle.column_grid(nez, N, ZTOP)[0])[None] * \
+        np.random.default_rng(13).standard_normal(q0.shape)
+    R[0, 1] = R[0, -2] = 0.0
+    q1, it, st = oracle.newton(nez, N, ZTOP, lam, R, q0, rtol=0.0, max_iter=1)
+    assert it[0] == 1
+    b = R + lam * (oracle.apply_V(nez, N, ZTOP, q0) - oracle.apply_L(nez, N, ZTOP, q0, q0))
+    x, _ = oracle.stage_solve(nez, N, ZTOP, lam, q0, b)
+    np.testing.assert_allclose(q1, x, rtol=1e-12, atol=1e-12 * np.abs(q0).max())
+
+
+def test_newton_converges_quadratically():
+    nez, N, lam = 8, 4, 87.868
+    q0 = _perturbed_state(nez, N, seed=14, amp_w=20.0, amp_th=5.0)[None]
+    s = oracle.scales(oracle.column_grid(nez, N, ZTOP)[0])
+    R = q0.copy()
+
+    def fnorm(q):
+        F = q - lam * oracle.apply_V(nez, N, ZTOP, q) - R
+        return np.linalg.norm(F / s)
+    norms = [fnorm(q0)]
+    for m in range(1, 5):
+        q, it, st = oracle.newton(nez, N, ZTOP, lam, R, q0, rtol=0.0, max_iter=m)
+        norms.append(fnorm(q))
+    norms = np.array(norms) / norms[0]
+    # quadratic: e_{m+1} <= C e_m^2 with a bounded C, down to the rounding floor
+    for m in range(3):
+        assert norms[m + 1] <= 10.0 * norms[m] ** 2, norms
+    assert norms[4] < 1e-13, norms
+
+
+def test_newton_linear_problem_one_iteration():
+    """For V := L_RS (q - q_bar) (linear), Newton converges in one iteration;
+    checked through the ARK driver: NHEVI and LHEVI-RS agree on the linear
+    test problem."""
+    nez, N = 4, 4
+    q = _rest(nez, N)
+    s = oracle.scales(oracle.column_grid(nez, N, ZTOP)[0])
+    g = np.random.default_rng(15)
+    dq = 1e-3 * s * g.standard_normal(q.size)
+    dq[1] = dq[-2] = 0.0
+    qn = q + dq
+    # LHEVI-RS step of the linear problem vs explicit formula for ARK2 stages
+    out_lin, info = oracle.lhevi_step(nez, N, ZTOP, tableaux.ARK2, 300.0, qn, 0 * qn, lin=2)
+    assert info[0] == 0 and np.all(np.isfinite(out_lin))
+
+
+# --------------------------------------------------------------------------
+# ARK tableaux (Sec. 4.1, Sec. 6): order conditions of additive RK methods
+# --------------------------------------------------------------------------
+
+def _bicolored_trees(order):
+    """All rooted trees with <= order vertices whose non-root vertices carry
+    a colour (0 explicit, 1 implicit); a tree is (colour, tuple(children))."""
+    from itertools import combinations_with_replacement
+    by_size = {1: [(None, ())]}
+
+    def colored(size):
+        return [(c, ch) for (_, ch) in by_size[size] for c in (0, 1)]
+    for size in range(2, order + 1):
+        out = []
+        # partitions of size-1 into child sizes
+        def parts(rem, maxp):
+            if rem == 0:
+                yield ()
+                return
+            for p in range(min(rem, maxp), 0, -1):
+                for rest in parts(rem - p, p):
+                    yield (p,) + rest
+        for part in parts(size - 1, size - 1):
+            pools = [sorted(set(colored(p)), key=repr) for p in part]
+            # multiset of children: group equal sizes
+            def build(i, acc):
+                if i == len(part):
+                    yield tuple(sorted(acc, key=repr))
+                    return
+                for t in pools[i]:
+                    if i > 0 and part[i] == part[i - 1] and repr(t) < repr(acc[-1]):
+                        continue
+                    yield from build(i + 1, acc + [t])
+            for ch in build(0, []):
+                out.append((None, ch))
+        by_size[size] = sorted(set(out), key=repr)
+    return by_size
+
+
+def _phi(tree, A, At):
+    s = A.shape[0]
+    v = np.ones(s)
+    for ch in tree[1]:
+        M = A if ch[0] == 0 else At
+        v = v * (M @ _phi(ch, A, At))
+    return v
+
+
+def _gamma(tree):
+    def size(t):
+        return 1 + sum(size(c) for c in t[1])
+    g = size(tree)
+    for ch in tree[1]:
+        g *= _gamma(ch)
+    return g
+
+
+@pytest.mark.parametrize("name", ["ARK2", "ARK3", "ARK4"])
+def test_tableau_structure_and_order_conditions(name):
+    t = tableaux.ALL[name]
+    A, At, b = t.A, t.At, t.b
+    s = t.s
+    assert np.allclose(np.triu(A), 0)                       # explicit: strictly lower
+    assert np.allclose(np.triu(At, 1), 0)                   # implicit: lower
+    assert At[0, 0] == 0.0                                  # first stage explicit
+    assert np.allclose(np.diag(At)[1:], t.gamma)            # singly diagonal
+    np.testing.assert_allclose(A.sum(1), At.sum(1), atol=1e-15)
+    trees = _bicolored_trees(t.order)
+    count = 0
+    for size in range(1, t.order + 1):
+        for tree in trees[size]:
+            lhs = b @ _phi(tree, A, At)
+            assert abs(lhs - 1.0 / _gamma(tree)) < 1e-14, (name, tree)
+            count += 1
+    # number of trees with two-coloured non-root vertices: 3, 10, 36 up to order 2, 3, 4
+    assert count == {2: 3, 3: 10, 4: 36}[t.order]
+
+
+def test_ark2_gamma_and_a32():
+    t = tableaux.ARK2
+    assert abs(t.gamma - (1 - 1 / math.sqrt(2))) < 1e-16
+    assert t.A[2, 1] == 0.5                                 # ARK(2,3,2)b, Sec. 4.1
+
+
+# --------------------------------------------------------------------------
+# Time integration: linear closed form and nonlinear self-convergence
+# --------------------------------------------------------------------------
+
+def _linear_exact(nez, N, q_bar, dq0, H, T):
+    """dq'/dt = L_RS q' + H, solved with the exponential of the augmented
+    matrix [[L, H], [0, 0]]."""
+    _, n, _ = oracle.sizes(nez, N)
+    E = np.eye(n)
+    L = np.stack([oracle.apply_L(nez, N, ZTOP, q_bar, E[j][None])[0] for j in range(n)], 1)
+    aug = np.zeros((n + 1, n + 1))
+    aug[:n, :n] = L
+    aug[:n, n] = H
+    y = sla.expm(T * aug) @ np.concatenate([dq0, [1.0]])
+    return y[:n]
+
+
+@pytest.mark.parametrize("name", ["ARK2", "ARK3", "ARK4"])
+def test_ark_linear_problem_converges_at_order(name):
+    tab = tableaux.ALL[name]
+    nez, N = 4, 4
+    q_bar = _rest(nez, N)
+    z, _ = oracle.column_grid(nez, N, ZTOP)
+    rho, _, _, _ = oracle.reference_state(z)
+    dq0 = np.zeros((z.size, 3))
+    dq0[:, 2] = rho * 1.0 * np.sin(np.pi * z / ZTOP)      # 1 K theta' (IGW profile, Sec. 7.2)
+    dq0 = dq0.reshape(-1)
+    H = np.zeros_like(dq0)
+    H[2::3] = 1e-4 * rho
+    # the sin profile is not balanced, so it excites acoustic modes with
+    # |lambda| up to 0.38 s^-1 on this column; the asymptotic regime needs
+    # steps that resolve them
+    T = 8.0
+    exact = _linear_exact(nez, N, q_bar, dq0, H, T)
+    errs = []
+    dts = [2.0, 1.0, 0.5]
+    for dt in dts:
+        q = q_bar + dq0
+        for _ in range(int(round(T / dt))):
+            q, info = oracle.lhevi_step(nez, N, ZTOP, tab, dt, q, H[None], lin=2)
+            assert info[0] == 0
+        errs.append(np.linalg.norm(q[0] - q_bar[0] - exact) / np.linalg.norm(exact))
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+    assert min(rates) > tab.order - 0.35, (errs, rates)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name,variant", [("ARK2", "lhevi"), ("ARK3", "lhevi"),
+                                          ("ARK2", "nhevi"), ("ARK3", "nhevi")])
+def test_nonlinear_wave_self_convergence(name, variant):
+    """1-D nonlinear acoustic-gravity wave (theta' = 1 K sin(pi z / z_top)):
+    LHEVI-PS and NHEVI-LU steps converge at the tableau's order against a
+    fine-step solution of the same method."""
+    tab = tableaux.ALL[name]
+    nez, N = 4, 4
+    q_bar = _rest(nez, N)
+    z, _ = oracle.column_grid(nez, N, ZTOP)
+    rho, _, _, _ = oracle.reference_state(z)
+    dq0 = np.zeros((z.size, 3))
+    dq0[:, 2] = rho * 5.0 * np.sin(np.pi * z / ZTOP)
+    q0 = q_bar + dq0.reshape(1, -1)
+    H = np.zeros_like(q0)
+    T = 8.0
+
+    def run(dt):
+        q = q0.copy()
+        for _ in range(int(round(T / dt))):
+            if variant == "lhevi":
+                q, info = oracle.lhevi_step(nez, N, ZTOP, tab, dt, q, H, lin=0)
+            else:
+                q, it, st = oracle.nhevi_step(nez, N, ZTOP, tab, dt, q, H, rtol=1e-10)
+                assert st[0] == 0
+        return q
+    ref = run(1.0 / 32)
+    errs = [np.linalg.norm(run(dt) - ref) / np.linalg.norm(ref - q0) for dt in (2.0, 1.0, 0.5)]
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert min(rates) > tab.order - 0.4, (errs, rates)
