@@ -1,0 +1,413 @@
+#!/usr/bin/env python
+"""Benchmark of the HEVI vertical column solve on GB300.
+
+Workload (one "step"): one LHEVI ARK3 time step (Sec. 4.3, Sec. 6) on
+86,402 columns of Nez = 10 elements of order N = 4 (41 points, 123 unknowns)
+with a 30 km top and dt = 300 s: one band factorisation linearised about q^n,
+three implicit stage solves (FP32 LU + FP64 iterative refinement), the
+vertical operator applies and the stage combinations, advancing the state in
+place from rest under a seeded horizontal tendency.  Metric: implicit column
+stage solves per second (3 x columns per step), whole job.
+
+Also reported: the same step with plain FP64 factors (one column per thread),
+an end-to-end number through the C ABI with host buffers, per-kernel times
+from CUDA events on the library's stream, the dominant kernel's roofline, SM
+clocks during the timed region, and the FP64 CPU oracle timed on the host
+cores on a bounded sample of the same workload.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NE, NEZ, ORDER, ZTOP, DT = 30, 10, 4, 30e3, 300.0
+NCOLS = 6 * (NE * 4) ** 2 + 2          # 86,402 cubed-sphere columns
+NZ = NEZ * ORDER + 1
+NUNK = 3 * NZ
+K_BAND = 3 * (ORDER + 1) - 1
+LDAB = 3 * K_BAND + 1
+STAGES = 3                              # implicit stages of ARK3
+WORKLOAD = (f"lhevi_ark3: {NCOLS} columns, Nez={NEZ}, N={ORDER}, ztop=30 km, dt=300 s, "
+            f"ARK3 (3 implicit stages), LHEVI-PS, seeded horizontal tendency")
+
+# Algorithmic bytes of one column stage solve: FP32 factors (ldab n 4), pivots
+# (n bytes) and b, x, q0 (3 n 8); FP64 plain: FP64 factors, int pivots, b, x.
+BYTES_SOLVE_FP32IR = LDAB * NUNK * 4 + NUNK + 3 * NUNK * 8
+BYTES_SOLVE_FP64 = LDAB * NUNK * 8 + NUNK * 4 + 2 * NUNK * 8
+
+
+def factor_flops(n=NUNK, k=K_BAND):
+    """FP32 flops of one band LU with partial pivoting (dgbtrf loop counts)."""
+    f = 0
+    for j in range(n):
+        nr = min(k, n - 1 - j)
+        nc = min(2 * k, n - 1 - j)
+        f += nr + 2 * nr * nc
+    return f
+
+
+def peaks():
+    p = {"hbm_gbs": 6777.0, "source": "fallback"}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            m = json.load(fh)
+        p["hbm_gbs"] = float(m["hbm_gbs"])
+        p["source"] = "measured"
+    except Exception:
+        pass
+    # FP32 ALU peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz
+    p["fp32_tflops"] = 152 * 128 * 2 * 2.07e9 / 1e12
+    return p
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (FP64, host cores)
+# ---------------------------------------------------------------------------
+
+def _oracle_chunk(args):
+    qn, H, ztop = args
+    import oracle
+    from oracle import tableaux
+    out, info = oracle.lhevi_step(NEZ, ORDER, ztop, tableaux.ARK3, DT, qn, H, lin=0)
+    return int((info != 0).sum())
+
+
+def oracle_sample_inputs(ncols):
+    import numpy as np
+    import hevi_inputs
+    import oracle
+    inp = hevi_inputs.lhevi_ark3(seed=2, ncols=ncols)
+    q = oracle.reference_q(NEZ, ORDER, ZTOP, ncols)
+    return q, inp["H"], np.full(ncols, ZTOP)
+
+
+def cpu_oracle_rate(pool, cores, target_s=12.0):
+    """Time the oracle's LHEVI ARK3 step on a bounded sample of the workload's
+    columns, spread over `cores` worker processes.  Returns (col-solves/s, dict)."""
+    import numpy as np
+    q, H, zt = oracle_sample_inputs(64)
+    t0 = time.perf_counter()
+    _oracle_chunk((q[:16], H[:16], zt[:16]))
+    per_col = (time.perf_counter() - t0) / 16
+    ncols = int(max(cores, min(NCOLS, target_s / per_col * cores)))
+    q, H, zt = oracle_sample_inputs(ncols)
+    chunks = [(q[i::cores], H[i::cores], zt[i::cores]) for i in range(cores)]
+    t0 = time.perf_counter()
+    bad = sum(pool.map(_oracle_chunk, chunks)) if pool else _oracle_chunk((q, H, zt))
+    wall = time.perf_counter() - t0
+    rate = STAGES * ncols / wall
+    return rate, {"value": rate, "unit": "column-solves/s", "cores": cores, "kind": "oracle",
+                  "sample": f"one FP64 oracle LHEVI ARK3 step on the first {ncols} of the "
+                            f"{NCOLS} columns ({wall:.1f} s wall over {cores} processes)",
+                  "failed_columns": bad}
+
+
+def make_pool(cores):
+    import multiprocessing as mp
+    if cores <= 1:
+        return None
+    return mp.get_context("spawn").Pool(cores)
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                   "-lms", "200"]
+            if self.uuid:
+                cmd += ["-i", self.uuid]
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        import statistics
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except Exception:
+                continue
+            for nm, val in zip(names, f[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_steps(ctx, tab, qa, qb, H, k):
+    for _ in range(k):
+        ctx.hevi_lhevi_step(tab, DT, qa, H, qb)
+        qa, qb = qb, qa
+    return qa, qb
+
+
+def gpu_arm(args, rank, world, local_rank, pool, cores):
+    import numpy as np
+    import torch
+    import hevi_inputs
+    import paper_2311_11425_gb300 as hv
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    hv.load(build=True)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream()
+    inp = hevi_inputs.lhevi_ark3(seed=2 + rank)
+    H = torch.from_numpy(inp["H"].reshape(-1)).to(dev)
+    tab = hv.tableau("ARK3")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if not dist:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    results = {}
+    for prec in (["FP32_IR", "FP64"] if not args.no_fp64 else ["FP32_IR"]):
+        ctx = hv.Context([(NEZ, ORDER)], ZTOP, ncols=NCOLS, precision=getattr(hv, prec),
+                         stream=stream)
+        qa = ctx.hevi_reference_state()
+        qb = torch.empty_like(qa)
+        qa, qb = run_steps(ctx, tab, qa, qb, H, args.warmup)
+        ctx.hevi_sync()
+        steps = args.steps if prec == "FP32_IR" else max(3, args.steps // 3)
+        barrier()
+        ctx.hevi_profile(True)
+        l0 = ctx.launch_count
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        uuid = None
+        try:
+            uuid = str(torch.cuda.get_device_properties(local_rank).uuid)
+            uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+        except Exception:
+            pass
+        with ClockSampler(uuid) as clk:
+            e0.record(stream)
+            qa, qb = run_steps(ctx, tab, qa, qb, H, steps)
+            e1.record(stream)
+            barrier()
+        ms = e0.elapsed_time(e1)
+        launches = ctx.launch_count - l0
+        kern = ctx.hevi_profile_read()
+        ctx.hevi_profile(False)
+        st = ctx.hevi_sync()
+        _, iters = ctx.hevi_column_status()
+        ms = max_over_ranks(ms)
+        results[prec] = dict(ms_per_step=ms / steps, steps=steps, launches=launches, kernels=kern,
+                             clocks=clk.summary(), ir_sweeps_last=float(iters.float().mean()),
+                             state_finite=bool(torch.isfinite(qa).all()))
+        if prec == "FP32_IR":
+            # end to end through the C ABI with host buffers: H2D of q^n and H
+            # from pinned memory, the step, D2H of q^{n+1}, every step
+            hq = qa.cpu().pin_memory()
+            hH = H.cpu().pin_memory()
+            hout = torch.empty_like(hq).pin_memory()
+            dq, dH = torch.empty_like(qa), torch.empty_like(H)
+            barrier()
+            e0.record(stream)
+            for _ in range(steps):
+                dq.copy_(hq, non_blocking=True)
+                dH.copy_(hH, non_blocking=True)
+                ctx.hevi_lhevi_step(tab, DT, dq, dH, qb)
+                hout.copy_(qb, non_blocking=True)
+            e1.record(stream)
+            barrier()
+            e2e_ms = max_over_ranks(e0.elapsed_time(e1))
+            results["e2e"] = dict(ms_per_step=e2e_ms / steps,
+                                  h2d=(hq.numel() + hH.numel()) * 8, d2h=hout.numel() * 8)
+        ctx.close()
+        del ctx
+        torch.cuda.empty_cache()
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    r = results["FP32_IR"]
+    value = world * STAGES * NCOLS / (r["ms_per_step"] * 1e-3)
+    # dominant kernel and its roofline
+    per = {k: v for k, v in r["kernels"].items() if v[1] > 0}
+    dom = max(per, key=lambda k: per[k][0])
+    pk = peaks()
+    avg_ms = per[dom][0] / per[dom][1]
+    if dom == "stage_solve":
+        ach = BYTES_SOLVE_FP32IR * NCOLS / (avg_ms * 1e-3) / 1e9
+        roof = {"kernel": "k_solve<IR> (stage_solve)", "bound": "hbm", "achieved": ach,
+                "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": ach / pk["hbm_gbs"],
+                "traffic": None, "peak_source": pk["source"],
+                "algorithmic_bytes_per_launch": BYTES_SOLVE_FP32IR * NCOLS}
+    elif dom == "factor":
+        ach = factor_flops() * NCOLS / (avg_ms * 1e-3) / 1e12
+        roof = {"kernel": "k_factor<float> (factor)", "bound": "alu", "achieved": ach,
+                "peak": pk["fp32_tflops"], "unit": "TFLOP/s", "frac": ach / pk["fp32_tflops"],
+                "traffic": None, "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz",
+                "algorithmic_flops_per_launch": factor_flops() * NCOLS}
+    else:
+        roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": None, "unit": None,
+                "frac": None, "traffic": None}
+    roof["avg_launch_ms"] = avg_ms
+    line = {
+        "metric": "columns solved/s (LHEVI ARK3 implicit stage solves, FP32 LU + FP64 refinement, "
+                  "1e-10 rel vs FP64 oracle)",
+        "value": value,
+        "unit": "column-solves/s",
+        "n_gpus": world,
+        "steps": r["steps"],
+        "warmup": args.warmup,
+        "ms_per_step": r["ms_per_step"],
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "columns_per_gpu": NCOLS, "nez": NEZ, "order": ORDER,
+                   "unknowns_per_column": NUNK, "implicit_stages": STAGES,
+                   "precision": "FP32 LU + FP64 refinement",
+                   "l2": "working set > L2 (factors 1.9 GB per step); no flush",
+                   "parallelism": f"{world} independent column shards, no collective"},
+        "e2e": None,
+        "gpu_launches": r["launches"],
+        "clocks": r["clocks"],
+        "roofline": roof,
+        "kernels": {k: {"total_ms": v[0], "launches": v[1], "avg_ms": v[0] / v[1]}
+                    for k, v in per.items()},
+        "ir_sweeps_mean": r["ir_sweeps_last"],
+        "state_finite": r["state_finite"],
+    }
+    if "e2e" in results:
+        e = results["e2e"]
+        line["e2e"] = {"value": world * STAGES * NCOLS / (e["ms_per_step"] * 1e-3),
+                       "unit": "column-solves/s", "h2d_bytes_per_step": e["h2d"],
+                       "d2h_bytes_per_step": e["d2h"], "ms_per_step": e["ms_per_step"]}
+    if "FP64" in results:
+        f = results["FP64"]
+        line["fp64_plain"] = {"value": world * STAGES * NCOLS / (f["ms_per_step"] * 1e-3),
+                              "unit": "column-solves/s", "ms_per_step": f["ms_per_step"],
+                              "kernels": {k: v[0] / max(1, v[1]) for k, v in f["kernels"].items()
+                                          if v[1]}}
+    if world == 1 and not args.no_cpu:
+        rate, cb = cpu_oracle_rate(pool, cores)
+        line["cpu_baseline"] = cb
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 CPU oracle on the host cores
+# ---------------------------------------------------------------------------
+
+def reference_arm(args, rank, world, pool, cores):
+    if rank != 0:
+        return
+    rates = []
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        cpu_oracle_rate(pool, cores, target_s=2.0)
+    samples = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        rate, cb = cpu_oracle_rate(pool, cores, target_s=6.0)
+        rates.append(rate)
+        samples.append(cb["sample"])
+    wall = time.perf_counter() - t0
+    import statistics
+    value = statistics.median(rates)
+    line = {"impl": "reference",
+            "metric": "columns solved/s (LHEVI ARK3 implicit stage solves, FP32 LU + FP64 "
+                      "refinement, 1e-10 rel vs FP64 oracle)",
+            "value": value, "unit": "column-solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": STAGES * NCOLS / value * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"value": value, "unit": "column-solves/s", "cores": cores,
+                             "kind": "oracle", "sample": samples[-1]},
+            "e2e": {"value": value, "unit": "column-solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "wall_s": wall}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    cores = os.cpu_count() or 1
+    # the oracle's process pool starts (spawn) before any GPU call
+    pool = make_pool(cores) if rank == 0 and (args.impl == "reference" or
+                                              (world == 1 and not args.no_cpu)) else None
+    try:
+        if args.impl == "reference":
+            reference_arm(args, rank, world, pool, cores)
+        else:
+            gpu_arm(args, rank, world, local_rank, pool, cores)
+    finally:
+        if pool:
+            pool.close()
+            pool.join()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,216 @@
+/*
+ * hevi.h -- C ABI of the GB300 (sm_103a) HEVI vertical column solver.
+ *
+ * The library solves, independently in every vertical atmospheric column,
+ * the vertically implicit stage problem of a horizontally explicit,
+ * vertically implicit (HEVI) IMEX Runge-Kutta integrator (Giraldo, Alves,
+ * Kelly, Kang & Reinecke, arXiv:2311.11425):
+ *
+ *   linear form (LHEVI, Sec. 4.3, Eq. lhevi-ark-final-2):
+ *       (I - Lambda L(q0)) x = b,   Lambda = gamma * dt,
+ *   Newton form (NHEVI-LU, Sec. 4.2.3, Eqs. nl_function, Newton-system):
+ *       F(q) = q - Lambda V(q) - R = 0,   J(q_m) dq = -F(q_m),
+ *
+ * where V is the vertical operator of set 2C (App. A.1-A.2) restricted to a
+ * flat column and discretised with continuous-Galerkin spectral elements on
+ * Legendre-Gauss-Lobatto points (Sec. 3), and L = dV/dq (Sec. 4.3.1, App.
+ * A.3).  Band half-widths are k_l = k_u = 3 (N + 1) - 1 (Sec. 4.2.3).
+ *
+ * State layout (caller-owned device buffers, FP64): columns are packed one
+ * after another (column c starts at offset hevi_column_offset(c)); within a
+ * column the unknowns are point-major and variable-fastest,
+ *   [point I = 0 .. n_z-1][v = rho, m = rho*w, Theta = rho*theta],
+ * n_z = Nez * N + 1.  Heights are measured from z = 0 to the column's top.
+ * w = 0 is imposed at the bottom and top point (the m-rows there are
+ * identity rows; V_m and (L x)_m are reported as 0 there).
+ *
+ * Every call is asynchronous on the context's CUDA stream unless stated
+ * otherwise.  Pointers marked (dev) are device pointers; (host) are host
+ * pointers.  No call allocates or frees caller memory.  Errors are returned
+ * as hevi_status values; nothing aborts or traps on the device.  Per-column
+ * failures (singular pivot, no convergence) are recorded in the context and
+ * read back with hevi_column_status.
+ */
+#ifndef HEVI_H
+#define HEVI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HEVI_OK = 0,
+  HEVI_ERR_INVALID_ARG = 1,  /* bad argument (null pointer, size, order) */
+  HEVI_ERR_CUDA = 2,         /* a CUDA runtime call failed */
+  HEVI_ERR_OOM = 3,          /* device allocation failed in setup */
+  HEVI_ERR_SINGULAR = 4,     /* some column met an exactly zero pivot */
+  HEVI_ERR_NOT_CONVERGED = 5, /* some column's refinement or Newton hit its limit */
+  HEVI_ERR_BAD_INPUT = 6      /* some column's state is non-physical (rho or Theta <= 0, NaN) */
+} hevi_status;
+
+/* One column size class: Nez elements of LGL order N (1 <= N <= 5). */
+typedef struct {
+  int32_t nez;
+  int32_t order;
+} hevi_size_class;
+
+/* The set of columns.  class_of_col (host, ncols entries, values in
+ * [0, nclasses)) may be NULL when nclasses == 1.  z_top (host, ncols
+ * entries, metres) gives each column's model top. */
+typedef struct {
+  int64_t ncols;
+  const hevi_size_class* classes;
+  int32_t nclasses;
+  const int32_t* class_of_col;
+  const double* z_top;
+} hevi_column_grid;
+
+/* Isothermal hydrostatic reference state and constants: T0 (K), p0 (Pa),
+ * R and cp (J kg^-1 K^-1), g (m s^-2).  NULL in hevi_setup selects
+ * 300, 1e5, 287.17, 1004.67, 9.80616. */
+typedef struct {
+  double T0, p0, R, cp, g;
+} hevi_ref_params;
+
+/* Precision of the band factorisation:
+ *   HEVI_FP64     plain FP64 band LU with partial pivoting (LAPACK dgbtrf
+ *                 semantics, Sec. 4.2.3), one column per thread;
+ *   HEVI_FP32_IR  the band is equilibrated with the reference-state scales,
+ *                 rounded to FP32 and LU-factored with partial pivoting in
+ *                 FP32; solves are refined with FP64 residuals. */
+typedef enum { HEVI_FP64 = 0, HEVI_FP32_IR = 1 } hevi_precision;
+
+typedef struct hevi_ctx hevi_ctx;
+
+/* Per-column status codes written by hevi_column_status. */
+#define HEVI_COL_OK 0
+#define HEVI_COL_SINGULAR 4
+#define HEVI_COL_NOT_CONVERGED 5
+#define HEVI_COL_BAD_INPUT 6
+
+/* Create a context: builds the LGL tables of each size class (Sec. 3) and
+ * the reference state of every column on the device, and allocates the
+ * factor, pivot, status and workspace buffers.  stream is a cudaStream_t
+ * (NULL = legacy default stream).  Synchronous.  Returns OOM if the device
+ * buffers do not fit. */
+hevi_status hevi_setup(hevi_ctx** out, const hevi_column_grid* grid,
+                       const hevi_ref_params* ref, hevi_precision precision,
+                       void* stream);
+
+/* Release every device buffer of the context.  Synchronous. */
+void hevi_destroy(hevi_ctx* ctx);
+
+/* Change the stream later calls launch on (cudaStream_t). */
+hevi_status hevi_set_stream(hevi_ctx* ctx, void* stream);
+
+/* Total number of FP64 entries of one state vector (sum of 3 n_z). */
+int64_t hevi_state_size(const hevi_ctx* ctx);
+/* Offset (in doubles) of column c within a state vector; -1 if out of range. */
+int64_t hevi_column_offset(const hevi_ctx* ctx, int64_t c);
+/* Device bytes held by the context. */
+int64_t hevi_device_bytes(const hevi_ctx* ctx);
+
+/* Write the rest state q_bar = (rho_bar, 0, Theta_bar) of every column
+ * (dev, state layout).  Reference state: isothermal, hydrostatic. */
+hevi_status hevi_reference_state(hevi_ctx* ctx, double* q_bar);
+
+/* Assemble A = I - Lambda L(q0) = I + Lambda Dcal K(q0) + Lambda G in band
+ * form (Sec. 4.2.3; App. A.3 with the gravity entry coupling the m-row to
+ * the rho-column) and LU-factor it with partial pivoting, for every column.
+ * lin_state (dev, state layout) is q0; NULL linearises about the rest state
+ * (LHEVI-RS, Sec. 4.3.1).  Lambda = gamma_dt.  The factors, pivots and the
+ * point coefficients of L(q0) stay in the context for later solves.  A column
+ * with an exactly zero pivot is marked SINGULAR. */
+hevi_status hevi_factor(hevi_ctx* ctx, double gamma_dt, const double* lin_state);
+
+/* Solve (I - Lambda L(q0)) x = rhs for every column with the factors of the
+ * last hevi_factor (Sec. 4.3, Eq. lhevi-ark-final-2).  rhs, x (dev, state
+ * layout, may not alias).  In HEVI_FP32_IR mode the FP32 solution is refined
+ * with FP64 residuals b - A x until the predicted relative error (scaled
+ * 2-norm) is below 1e-12, at most max_ir sweeps (hevi_set_refinement).
+ * Blocking: returns SINGULAR / NOT_CONVERGED if any column failed. */
+hevi_status hevi_stage_solve(hevi_ctx* ctx, const double* rhs, double* x);
+/* As hevi_stage_solve but does not wait: failures are only recorded for
+ * hevi_column_status. */
+hevi_status hevi_stage_solve_async(hevi_ctx* ctx, const double* rhs, double* x);
+
+/* Refinement controls for HEVI_FP32_IR solves: tolerance on the predicted
+ * relative error and the sweep limit (defaults 1e-12 and 10). */
+hevi_status hevi_set_refinement(hevi_ctx* ctx, double tol, int32_t max_sweeps);
+
+/* NHEVI-LU (Sec. 4.2.3): for every column, Newton-Raphson on
+ * F(q) = q - gamma_dt V(q) - R, rebuilding and LU-factoring the Jacobian at
+ * every iteration; state (dev) holds the initial guess on entry and the
+ * root on exit; R (dev).  Stops when ||S^-1 F(q_m)||_2 <= rtol ||S^-1 F(q_0)||_2
+ * (S = reference scales rho_bar, rho_bar c_s, Theta_bar) or after max_iter
+ * updates.  Blocking. */
+hevi_status hevi_newton_solve(hevi_ctx* ctx, double gamma_dt, double* state, const double* R,
+                              double rtol, int32_t max_iter);
+hevi_status hevi_newton_solve_async(hevi_ctx* ctx, double gamma_dt, double* state,
+                                    const double* R, double rtol, int32_t max_iter);
+
+/* Vertical operator apply (App. A.2 / Sec. 4.3.1), x, y (dev, state layout):
+ *   nonlinear != 0:  y = V(x);
+ *   nonlinear == 0:  y = L(q0) x with q0 of the last hevi_factor. */
+hevi_status hevi_apply_Lv(hevi_ctx* ctx, const double* x, double* y, int nonlinear);
+
+/* Copy the per-column status (HEVI_COL_*) and iteration count (refinement
+ * sweeps of the last solve, or Newton updates of the last Newton solve) of
+ * the last call into status and iters (dev, ncols int32 each; either may be
+ * NULL). */
+hevi_status hevi_column_status(hevi_ctx* ctx, int32_t* status, int32_t* iters);
+
+/* One IMEX ARK time step with the HEVI split (Sec. 4.1), ESDIRK tableau of
+ * s stages given row-major on the host: A (explicit, s x s), At (implicit,
+ * s x s, At[0][0] = 0, constant diagonal gamma), b (weights, shared).
+ * q_in, H, q_out (dev, state layout); H is the explicit (horizontal) tendency,
+ * held constant over the step; q_out may not alias q_in.
+ *   hevi_lhevi_step: LHEVI (Sec. 4.3): L linearised about q_in (LHEVI-PS) when
+ *     lin_about_rest == 0, about the rest state (LHEVI-RS) otherwise; one
+ *     factorisation for the step, one stage solve per implicit stage.
+ *   hevi_nhevi_step: NHEVI-LU (Sec. 4.2): one Newton solve per implicit stage
+ *     from the previous stage value.
+ * Asynchronous; per-column failures are recorded for hevi_column_status. */
+hevi_status hevi_lhevi_step(hevi_ctx* ctx, int32_t s, const double* A, const double* At,
+                            const double* b, double dt, const double* q_in, const double* H,
+                            double* q_out, int32_t lin_about_rest);
+hevi_status hevi_nhevi_step(hevi_ctx* ctx, int32_t s, const double* A, const double* At,
+                            const double* b, double dt, const double* q_in, const double* H,
+                            double* q_out, double rtol, int32_t max_iter);
+
+/* Named ESDIRK tableaux of Sec. 6 (the paper names them; the coefficients
+ * come from the cited constructions): "ARK2" = ARK(2,3,2)b with a32 = 1/2,
+ * "ARK3" = ARK3(2)4L[2]SA and "ARK4" = ARK4(3)6L[2]SA of Kennedy & Carpenter.
+ * Writes the stage count to *s and the row-major A, At (s x s) and b (s) to
+ * host arrays of at least 64, 64 and 8 doubles.  INVALID_ARG for an unknown
+ * name. */
+hevi_status hevi_tableau(const char* name, int32_t* s, double* A, double* At, double* b);
+
+/* Wait for the context's stream and return the aggregated status of the
+ * calls since the last wait (SINGULAR / NOT_CONVERGED if any column failed). */
+hevi_status hevi_sync(hevi_ctx* ctx);
+
+/* Per-kernel timing with CUDA events recorded around each launch on the
+ * context's stream (not while the stream is being captured into a graph).
+ * hevi_profile(ctx, 1) clears the totals and starts timing, 0 stops it.
+ * hevi_profile_read waits for the stream and returns the total milliseconds
+ * and launch count of one kernel kind; kinds are 0 .. hevi_profile_kinds()-1
+ * with names from hevi_profile_kind_name ("setup", "factor", "stage_solve",
+ * "apply", "apply_stage", "newton", "combine"). */
+hevi_status hevi_profile(hevi_ctx* ctx, int32_t enable);
+int32_t hevi_profile_kinds(void);
+const char* hevi_profile_kind_name(int32_t kind);
+hevi_status hevi_profile_read(hevi_ctx* ctx, int32_t kind, double* total_ms, int64_t* launches);
+
+/* Number of kernel launches issued by the context so far. */
+int64_t hevi_launch_count(const hevi_ctx* ctx);
+
+/* Human-readable name of a status code. */
+const char* hevi_status_string(hevi_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HEVI_H */

@@ -529,24 +529,28 @@ int or_newton(int ncols, int nez, int N, const double* ztop, double lam, const d
 /* H is the explicit tendency, held constant over the step.            */
 /* ------------------------------------------------------------------ */
 
-/* LHEVI (Sec. 4.3, linear implicit operator L): the direct stage form
- *   (I - gamma dt L) Q_i = q^n + dt sum_{j<i} [ a_ij E(Q_j) + at_ij L Q_j ],
- *   E(Q) = H + V(Q) - L Q,
- *   q^{n+1} = q^n + dt sum_i b_i [ E(Q_i) + L Q_i ].
+/* LHEVI (Sec. 4.3), in the ARK form of Eq. (lhevi-ark-final-3): with
+ * S(Q) = H + V(Q) the full right-hand side and w_ij = (at_ij - a_ij)/at_ii,
+ *   q^E   = q^n + dt sum_{j<i} a_ij S(Q_j),
+ *   q_hat = q^E + sum_{j<i} w_ij Q_j,
+ *   (I - gamma dt L) q_tt = q_hat                    (Eq. lhevi-ark-final-2),
+ *   Q_i   = q_tt - sum_{j<i} w_ij Q_j,
+ * and q^{n+1} = q^n + dt sum_i b_i S(Q_i) (Sec. 4.1 with b = bt).  Since the
+ * rows of A and At have equal sums, sum_j w_ij = -1 and q_tt is a difference
+ * of states.
  * lin = 0: L linearised about q^n (LHEVI-PS, Sec. 4.3.1); lin = 1: about
  * the reference state (LHEVI-RS); lin = 2: V itself replaced by the
  * reference-state linear operator V(q) := L_RS (q - q_bar), the linear test
- * problem.  info[c] = first nonzero band-LU info of the step. */
+ * problem.  info[c] = band-LU info of the step's factorisation. */
 int or_lhevi_step(int ncols, int nez, int N, const double* ztop, int s, const double* A,
                   const double* At, const double* b, double dt, int lin, const double* qn,
                   const double* H, double* qout, int* info) {
   int n = 3 * (nez * N + 1), kl = 3 * (N + 1) - 1, ldab = 3 * kl + 1;
-  double lam = At[1 * s + 1] * dt;
+  double gam = At[1 * s + 1], lam = gam * dt;
   double* ab = (double*)malloc(sizeof(double) * (size_t)ldab * n);
   int* ipiv = (int*)malloc(sizeof(int) * n);
-  double* Q = (double*)malloc(sizeof(double) * (size_t)n * (3 * s + 3));
-  double *E = Q + (size_t)n * s, *LQ = E + (size_t)n * s, *rhs = LQ + (size_t)n * s;
-  double *q0 = rhs + n, *qbar = q0 + n;
+  double* Q = (double*)malloc(sizeof(double) * (size_t)n * (2 * s + 3));
+  double *S = Q + (size_t)n * s, *q0 = S + (size_t)n * s, *qbar = q0 + n, *tmp = qbar + n;
   for (int c = 0; c < ncols; ++c) {
     column_t col;
     if (column_init(&col, nez, N, ztop[c])) return 1;
@@ -565,30 +569,36 @@ int or_lhevi_step(int ncols, int nez, int N, const double* ztop, int s, const do
       if (i == 0) {
         memcpy(Qi, qnc, sizeof(double) * n);
       } else {
+        /* q_hat = q^n + dt sum_j a_ij S_j + sum_j w_ij Q_j, solved in place */
         for (int r = 0; r < n; ++r) {
-          double acc = 0.0;
-          for (int j = 0; j < i; ++j)
-            acc += A[i * s + j] * E[(size_t)n * j + r] + At[i * s + j] * LQ[(size_t)n * j + r];
-          rhs[r] = qnc[r] + dt * acc;
+          double acc = 0.0, wq = 0.0;
+          for (int j = 0; j < i; ++j) {
+            acc += A[i * s + j] * S[(size_t)n * j + r];
+            wq += (At[i * s + j] - A[i * s + j]) / gam * Q[(size_t)n * j + r];
+          }
+          Qi[r] = qnc[r] + dt * acc + wq;
         }
-        memcpy(Qi, rhs, sizeof(double) * n);
         if (info[c] == 0) or_gbtrs(n, kl, kl, ab, ldab, ipiv, Qi);
+        /* Q_i = q_tt - sum_j w_ij Q_j */
+        for (int r = 0; r < n; ++r) {
+          double wq = 0.0;
+          for (int j = 0; j < i; ++j) wq += (At[i * s + j] - A[i * s + j]) / gam * Q[(size_t)n * j + r];
+          Qi[r] -= wq;
+        }
       }
-      /* E(Q_i) and L Q_i */
-      double* Ei = E + (size_t)n * i;
-      double* LQi = LQ + (size_t)n * i;
-      apply_L(&col, q0, Qi, LQi);
+      /* S(Q_i) = H + V(Q_i) */
+      double* Si = S + (size_t)n * i;
       if (lin == 2) {
-        for (int r = 0; r < n; ++r) rhs[r] = Qi[r] - qbar[r];
-        apply_L(&col, qbar, rhs, Ei);  /* V(Q) = L_RS (Q - q_bar) */
+        for (int r = 0; r < n; ++r) tmp[r] = Qi[r] - qbar[r];
+        apply_L(&col, qbar, tmp, Si);  /* V(Q) = L_RS (Q - q_bar) */
       } else {
-        apply_V(&col, Qi, Ei);
+        apply_V(&col, Qi, Si);
       }
-      for (int r = 0; r < n; ++r) Ei[r] = Hc[r] + Ei[r] - LQi[r];
+      for (int r = 0; r < n; ++r) Si[r] += Hc[r];
     }
     for (int r = 0; r < n; ++r) {
       double acc = 0.0;
-      for (int i = 0; i < s; ++i) acc += b[i] * (E[(size_t)n * i + r] + LQ[(size_t)n * i + r]);
+      for (int i = 0; i < s; ++i) acc += b[i] * S[(size_t)n * i + r];
       qout[o + r] = qnc[r] + dt * acc;
     }
     column_free(&col);

@@ -1,0 +1,814 @@
+// hevi_capi.cu -- host side of the C ABI declared in include/hevi.h.
+//
+// Setup (Sec. 3): LGL nodes and weights of each order and the derivative of
+// the cardinal Lagrange basis are built here in FP64; columns are grouped by
+// size class into tiles of 32; the reference state of every column is
+// computed on the device.  Calls launch kernels on the context's stream.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "hevi_internal.cuh"
+
+using hevi::Band;
+using hevi::DevView;
+using hevi::kMaxOrder;
+using hevi::kTile;
+using hevi::TileDesc;
+
+namespace {
+
+// Failure counters on the device: [0] any, [1] singular, [2] not converged,
+// [3] bad input.
+constexpr int kFailSlots = 4;
+
+int rl_of(int N) {  // record length per pivot step
+  const int K = 3 * (N + 1) - 1;
+  return ((K + 2) + 3) / 4 * 4 + ((2 * K) + 3) / 4 * 4;
+}
+int ur2_of(int N) {  // Newton scratch record {1/u_jj, u_j,j+1..j+2K}
+  const int K = 3 * (N + 1) - 1;
+  return ((2 * K + 1) + 3) / 4 * 4;
+}
+
+// Legendre P_n(x) by the three-term recurrence.
+double legendre_p(int n, double x) {
+  if (n == 0) return 1.0;
+  double a = 1.0, b = x;
+  for (int k = 2; k <= n; ++k) {
+    const double c = ((2.0 * k - 1.0) * x * b - (k - 1.0) * a) / k;
+    a = b;
+    b = c;
+  }
+  return b;
+}
+
+// LGL points of order N: the roots of P_{N+1} - P_{N-1} (which include +-1),
+// found by Newton's method with q' = (2N+1) P_N; weights 2/(N(N+1) P_N^2).
+void lgl_points(int N, double* x, double* w) {
+  for (int k = 0; k <= N; ++k) {
+    double t = -std::cos(M_PI * k / N);
+    if (k > 0 && k < N) {
+      for (int it = 0; it < 200; ++it) {
+        const double q = legendre_p(N + 1, t) - legendre_p(N - 1, t);
+        const double dq = (2.0 * N + 1.0) * legendre_p(N, t);
+        const double d = q / dq;
+        t -= d;
+        if (std::fabs(d) <= 1e-17) break;
+      }
+    }
+    x[k] = t;
+  }
+  for (int k = 0; k <= N; ++k) {
+    const double p = legendre_p(N, x[k]);
+    w[k] = 2.0 / (N * (N + 1.0) * p * p);
+  }
+}
+
+// Derivative of the cardinal Lagrange basis by barycentric weights:
+// Dhat_kj = h_j'(x_k) = (b_j / b_k) / (x_k - x_j), k != j; the diagonal makes
+// each row sum to zero.
+void lagrange_derivative(int N, const double* x, double* D) {
+  double b[kMaxOrder + 1];
+  for (int j = 0; j <= N; ++j) {
+    double p = 1.0;
+    for (int m = 0; m <= N; ++m)
+      if (m != j) p *= (x[j] - x[m]);
+    b[j] = 1.0 / p;
+  }
+  for (int k = 0; k <= N; ++k) {
+    double diag = 0.0;
+    for (int j = 0; j <= N; ++j) {
+      if (j == k) continue;
+      const double d = (b[j] / b[k]) / (x[k] - x[j]);
+      D[k * (N + 1) + j] = d;
+      diag -= d;
+    }
+    D[k * (N + 1) + k] = diag;
+  }
+}
+
+hevi::LglTables make_tables() {
+  hevi::LglTables t;
+  std::memset(&t, 0, sizeof(t));
+  for (int N = 1; N <= kMaxOrder; ++N) {
+    double D[(kMaxOrder + 1) * (kMaxOrder + 1)];
+    lgl_points(N, t.xi[N], t.w[N]);
+    lagrange_derivative(N, t.xi[N], D);
+    for (int k = 0; k <= N; ++k)
+      for (int j = 0; j <= N; ++j) {
+        const double v = t.w[N][k] * D[k * (N + 1) + j];
+        t.wD[N][k * (N + 1) + j] = v;
+        t.wDf[N][k * (N + 1) + j] = (float)v;
+      }
+  }
+  return t;
+}
+
+}  // namespace
+
+struct hevi_ctx {
+  DevView v{};
+  hevi_precision prec = HEVI_FP64;
+  cudaStream_t stream = nullptr;
+  int64_t ncols = 0, state_size = 0, ntiles = 0;
+  std::vector<int64_t> h_off;
+  std::vector<TileDesc> h_tiles;
+  int max_order = 0, max_ylen = 0;
+  double lam = 0.0;
+  bool factored = false;
+  double ir_tol = 1e-12;
+  int ir_max = 10;
+  int64_t scr_floats = 0;
+  int64_t fac_elems = 0;
+  // device allocations
+  std::vector<void*> allocs;
+  double* lin_newton = nullptr;
+  float* scr = nullptr;
+  double* work = nullptr;
+  int64_t work_vecs = 0;
+  int32_t* h_fail = nullptr;  // pinned mirror of the failure counters
+  int64_t launches = 0;
+  int64_t dev_bytes = 0;
+  // opt-in per-kernel timing with CUDA events on the context's stream
+  struct ProfRec {
+    int kind;
+    cudaEvent_t a, b;
+  };
+  bool prof = false;
+  std::vector<ProfRec> prof_recs;
+  std::vector<cudaEvent_t> ev_pool;
+  double prof_ms[8] = {0};
+  int64_t prof_n[8] = {0};
+
+  template <typename T>
+  hevi_status alloc(T** p, size_t count) {
+    void* q = nullptr;
+    if (count == 0) count = 1;
+    if (cudaMalloc(&q, count * sizeof(T)) != cudaSuccess) {
+      cudaGetLastError();
+      return HEVI_ERR_OOM;
+    }
+    allocs.push_back(q);
+    dev_bytes += (int64_t)(count * sizeof(T));
+    *p = static_cast<T*>(q);
+    return HEVI_OK;
+  }
+};
+
+namespace {
+
+enum Kind { kSetup = 0, kFactor, kSolve, kApply, kApplyStage, kNewton, kCombine, kNumKinds };
+const char* kKindNames[kNumKinds] = {"setup", "factor", "stage_solve", "apply",
+                                     "apply_stage", "newton", "combine"};
+
+cudaEvent_t get_event(hevi_ctx* c) {
+  if (!c->ev_pool.empty()) {
+    cudaEvent_t e = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Brackets one kernel launch with events when timing is on (and the stream is
+// not being captured into a graph).
+struct Scope {
+  hevi_ctx* c;
+  int kind;
+  cudaEvent_t a = nullptr;
+  Scope(hevi_ctx* ctx, int k) : c(ctx), kind(k) {
+    if (!c->prof) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(c->stream, &cs);
+    if (cs != cudaStreamCaptureStatusNone) return;
+    a = get_event(c);
+    cudaEventRecord(a, c->stream);
+  }
+  ~Scope() {
+    if (!a) return;
+    cudaEvent_t b = get_event(c);
+    cudaEventRecord(b, c->stream);
+    c->prof_recs.push_back({kind, a, b});
+  }
+};
+
+void fold_profile(hevi_ctx* c) {
+  if (c->prof_recs.empty()) return;
+  cudaStreamSynchronize(c->stream);
+  for (auto& r : c->prof_recs) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      c->prof_ms[r.kind] += ms;
+      c->prof_n[r.kind] += 1;
+    }
+    c->ev_pool.push_back(r.a);
+    c->ev_pool.push_back(r.b);
+  }
+  c->prof_recs.clear();
+  cudaGetLastError();
+}
+
+hevi_status check_launch(hevi_ctx* c, int n = 1) {
+  c->launches += n;
+  return cudaGetLastError() == cudaSuccess ? HEVI_OK : HEVI_ERR_CUDA;
+}
+
+void reset_fail(hevi_ctx* c) {
+  cudaMemsetAsync(c->v.fail_count, 0, kFailSlots * sizeof(int32_t), c->stream);
+}
+
+// Wait for the stream and turn the failure counters into a status.
+hevi_status wait_status(hevi_ctx* c) {
+  if (cudaMemcpyAsync(c->h_fail, c->v.fail_count, kFailSlots * sizeof(int32_t),
+                      cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+    return HEVI_ERR_CUDA;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return HEVI_ERR_CUDA;
+  if (c->h_fail[0] == 0) return HEVI_OK;
+  if (c->h_fail[3]) return HEVI_ERR_BAD_INPUT;
+  if (c->h_fail[1]) return HEVI_ERR_SINGULAR;
+  return HEVI_ERR_NOT_CONVERGED;
+}
+
+hevi_status ensure_work(hevi_ctx* c, int64_t vecs) {
+  if (c->work_vecs >= vecs) return HEVI_OK;
+  if (c->work) {
+    cudaStreamSynchronize(c->stream);
+    auto it = std::find(c->allocs.begin(), c->allocs.end(), (void*)c->work);
+    if (it != c->allocs.end()) c->allocs.erase(it);
+    cudaFree(c->work);
+    c->dev_bytes -= c->work_vecs * c->state_size * (int64_t)sizeof(double);
+    c->work = nullptr;
+    c->work_vecs = 0;
+  }
+  hevi_status s = c->alloc(&c->work, (size_t)(vecs * c->state_size));
+  if (s == HEVI_OK) c->work_vecs = vecs;
+  return s;
+}
+
+hevi_status ensure_newton(hevi_ctx* c) {
+  if (c->scr) return HEVI_OK;
+  hevi_status s = c->alloc(&c->lin_newton, (size_t)c->state_size);
+  if (s != HEVI_OK) return s;
+  s = c->alloc(&c->scr, (size_t)c->scr_floats);
+  if (s != HEVI_OK) return s;
+  c->v.scr = c->scr;
+  return HEVI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* hevi_status_string(hevi_status s) {
+  switch (s) {
+    case HEVI_OK: return "ok";
+    case HEVI_ERR_INVALID_ARG: return "invalid argument";
+    case HEVI_ERR_CUDA: return "CUDA error";
+    case HEVI_ERR_OOM: return "out of device memory";
+    case HEVI_ERR_SINGULAR: return "singular column";
+    case HEVI_ERR_NOT_CONVERGED: return "not converged";
+    case HEVI_ERR_BAD_INPUT: return "non-physical input state";
+  }
+  return "unknown status";
+}
+
+hevi_status hevi_setup(hevi_ctx** out, const hevi_column_grid* grid, const hevi_ref_params* ref,
+                       hevi_precision precision, void* stream) {
+  if (!out || !grid || grid->ncols <= 0 || !grid->classes || grid->nclasses <= 0 || !grid->z_top)
+    return HEVI_ERR_INVALID_ARG;
+  if (grid->nclasses > 1 && !grid->class_of_col) return HEVI_ERR_INVALID_ARG;
+  if (precision != HEVI_FP64 && precision != HEVI_FP32_IR) return HEVI_ERR_INVALID_ARG;
+  if (grid->ncols > (int64_t)INT32_MAX) return HEVI_ERR_INVALID_ARG;
+  for (int c = 0; c < grid->nclasses; ++c) {
+    const hevi_size_class& k = grid->classes[c];
+    if (k.order < 1 || k.order > kMaxOrder || k.nez < 1 || k.nez > 4096) return HEVI_ERR_INVALID_ARG;
+  }
+  const int64_t ncols = grid->ncols;
+  std::vector<int32_t> cls(ncols), order(ncols), nez(ncols);
+  std::vector<double> dz(ncols);
+  for (int64_t i = 0; i < ncols; ++i) {
+    const int32_t k = grid->class_of_col ? grid->class_of_col[i] : 0;
+    if (k < 0 || k >= grid->nclasses) return HEVI_ERR_INVALID_ARG;
+    const double zt = grid->z_top[i];
+    if (!(zt > 0.0) || !std::isfinite(zt)) return HEVI_ERR_INVALID_ARG;
+    cls[i] = k;
+    order[i] = grid->classes[k].order;
+    nez[i] = grid->classes[k].nez;
+    dz[i] = zt / nez[i];
+  }
+  hevi_ctx* c = new (std::nothrow) hevi_ctx();
+  if (!c) return HEVI_ERR_OOM;
+  c->prec = precision;
+  c->stream = static_cast<cudaStream_t>(stream);
+  c->ncols = ncols;
+  hevi::Phys ph;
+  ph.T0 = ref ? ref->T0 : 300.0;
+  ph.p0 = ref ? ref->p0 : 1.0e5;
+  ph.R = ref ? ref->R : 287.17;
+  ph.cp = ref ? ref->cp : 1004.67;
+  ph.g = ref ? ref->g : 9.80616;
+  ph.cv = ph.cp - ph.R;
+  ph.gamma = ph.cp / ph.cv;
+  ph.cs = std::sqrt(ph.gamma * ph.R * ph.T0);
+  c->v.ph = ph;
+  c->v.ncols = ncols;
+
+  // state offsets
+  c->h_off.resize(ncols + 1);
+  c->h_off[0] = 0;
+  for (int64_t i = 0; i < ncols; ++i) c->h_off[i + 1] = c->h_off[i] + 3 * ((int64_t)nez[i] * order[i] + 1);
+  c->state_size = c->h_off[ncols];
+
+  // class-sorted permutation and tiles of 32 columns of one class
+  std::vector<int32_t> perm(ncols);
+  for (int64_t i = 0; i < ncols; ++i) perm[i] = (int32_t)i;
+  std::stable_sort(perm.begin(), perm.end(), [&](int32_t a, int32_t b) { return cls[a] < cls[b]; });
+  int64_t fac_off = 0, scr_off = 0;
+  const int esz = precision == HEVI_FP64 ? 8 : 4;
+  for (int64_t i = 0; i < ncols;) {
+    const int32_t k = cls[perm[i]];
+    int64_t j = i;
+    while (j < ncols && j - i < kTile && cls[perm[j]] == k) ++j;
+    TileDesc t;
+    t.order = grid->classes[k].order;
+    t.nez = grid->classes[k].nez;
+    t.count = (int32_t)(j - i);
+    t.first = (int32_t)i;
+    t.fac_off = fac_off;
+    t.scr_off = scr_off;
+    const int64_t n = 3 * ((int64_t)t.nez * t.order + 1);
+    fac_off += n * rl_of(t.order) * kTile;
+    scr_off += n * ur2_of(t.order) * kTile;
+    c->h_tiles.push_back(t);
+    c->max_order = std::max(c->max_order, (int)t.order);
+    const int K = 3 * (t.order + 1) - 1;
+    c->max_ylen = std::max(c->max_ylen, (int)(n + 2 * K));
+    i = j;
+  }
+  c->ntiles = (int64_t)c->h_tiles.size();
+  c->fac_elems = fac_off;
+  c->scr_floats = scr_off;
+  (void)esz;
+
+  static bool tables_done = false;
+  static hevi::LglTables tables;
+  if (!tables_done) {
+    tables = make_tables();
+    tables_done = true;
+  }
+  hevi::upload_tables(tables);
+
+  hevi_status s = HEVI_OK;
+  int64_t* d_off;
+  int32_t *d_perm, *d_order, *d_nez;
+  double *d_dz, *d_ref;
+  TileDesc* d_tiles;
+  int32_t *d_fs, *d_cs, *d_it, *d_fail;
+  void* d_fac;
+  if ((s = c->alloc(&d_off, ncols + 1)) || (s = c->alloc(&d_perm, ncols)) ||
+      (s = c->alloc(&d_order, ncols)) || (s = c->alloc(&d_nez, ncols)) ||
+      (s = c->alloc(&d_dz, ncols)) || (s = c->alloc(&d_ref, c->state_size)) ||
+      (s = c->alloc(&c->v.lin, c->state_size)) || (s = c->alloc(&d_tiles, c->ntiles)) ||
+      (s = c->alloc(&d_fs, ncols)) || (s = c->alloc(&d_cs, ncols)) || (s = c->alloc(&d_it, ncols)) ||
+      (s = c->alloc(&d_fail, kFailSlots)) ||
+      (s = precision == HEVI_FP64 ? c->alloc((double**)&d_fac, c->fac_elems)
+                                  : c->alloc((float**)&d_fac, c->fac_elems))) {
+    hevi_destroy(c);
+    return s;
+  }
+  if (cudaMallocHost(&c->h_fail, kFailSlots * sizeof(int32_t)) != cudaSuccess) {
+    cudaGetLastError();
+    hevi_destroy(c);
+    return HEVI_ERR_OOM;
+  }
+  cudaMemcpy(d_off, c->h_off.data(), (ncols + 1) * sizeof(int64_t), cudaMemcpyHostToDevice);
+  cudaMemcpy(d_perm, perm.data(), ncols * sizeof(int32_t), cudaMemcpyHostToDevice);
+  cudaMemcpy(d_order, order.data(), ncols * sizeof(int32_t), cudaMemcpyHostToDevice);
+  cudaMemcpy(d_nez, nez.data(), ncols * sizeof(int32_t), cudaMemcpyHostToDevice);
+  cudaMemcpy(d_dz, dz.data(), ncols * sizeof(double), cudaMemcpyHostToDevice);
+  cudaMemcpy(d_tiles, c->h_tiles.data(), c->ntiles * sizeof(TileDesc), cudaMemcpyHostToDevice);
+  cudaMemset(d_fs, 0xff, ncols * sizeof(int32_t));  // no factorisation yet
+  cudaMemset(d_cs, 0, ncols * sizeof(int32_t));
+  cudaMemset(d_it, 0, ncols * sizeof(int32_t));
+  cudaMemset(d_fail, 0, kFailSlots * sizeof(int32_t));
+  c->v.col_off = d_off;
+  c->v.perm = d_perm;
+  c->v.col_dz = d_dz;
+  c->v.ref = d_ref;
+  c->v.tiles = d_tiles;
+  c->v.ntiles = (int32_t)c->ntiles;
+  c->v.fac = d_fac;
+  c->v.scr = nullptr;
+  c->v.fac_status = d_fs;
+  c->v.col_status = d_cs;
+  c->v.col_iters = d_it;
+  c->v.fail_count = d_fail;
+  hevi::launch_setup_ref(c->v, d_order, d_nez, c->stream);
+  c->launches += 1;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+    hevi_destroy(c);
+    return HEVI_ERR_CUDA;
+  }
+  *out = c;
+  return HEVI_OK;
+}
+
+void hevi_destroy(hevi_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  fold_profile(c);
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  for (void* p : c->allocs) cudaFree(p);
+  if (c->h_fail) cudaFreeHost(c->h_fail);
+  delete c;
+}
+
+hevi_status hevi_set_stream(hevi_ctx* c, void* stream) {
+  if (!c) return HEVI_ERR_INVALID_ARG;
+  c->stream = static_cast<cudaStream_t>(stream);
+  return HEVI_OK;
+}
+
+int64_t hevi_state_size(const hevi_ctx* c) { return c ? c->state_size : -1; }
+
+int64_t hevi_column_offset(const hevi_ctx* c, int64_t i) {
+  if (!c || i < 0 || i > c->ncols) return -1;
+  return c->h_off[i];
+}
+
+int64_t hevi_device_bytes(const hevi_ctx* c) { return c ? c->dev_bytes : -1; }
+
+int64_t hevi_launch_count(const hevi_ctx* c) { return c ? c->launches : -1; }
+
+hevi_status hevi_reference_state(hevi_ctx* c, double* q) {
+  if (!c || !q) return HEVI_ERR_INVALID_ARG;
+  hevi::launch_reference_state(c->v, q, c->stream);
+  return check_launch(c);
+}
+
+hevi_status hevi_set_refinement(hevi_ctx* c, double tol, int32_t max_sweeps) {
+  if (!c || !(tol > 0.0) || max_sweeps < 1 || max_sweeps > 100) return HEVI_ERR_INVALID_ARG;
+  c->ir_tol = tol;
+  c->ir_max = max_sweeps;
+  return HEVI_OK;
+}
+
+hevi_status hevi_factor(hevi_ctx* c, double gamma_dt, const double* lin_state) {
+  if (!c || !(gamma_dt >= 0.0) || !std::isfinite(gamma_dt)) return HEVI_ERR_INVALID_ARG;
+  {
+    Scope sc(c, kFactor);
+    hevi::launch_factor(c->v, c->prec, gamma_dt, lin_state, c->max_order, c->stream);
+  }
+  c->lam = gamma_dt;
+  c->factored = true;
+  return check_launch(c);
+}
+
+hevi_status hevi_stage_solve_async(hevi_ctx* c, const double* rhs, double* x) {
+  if (!c || !rhs || !x || rhs == x || !c->factored) return HEVI_ERR_INVALID_ARG;
+  {
+    Scope sc(c, kSolve);
+    hevi::launch_solve(c->v, c->prec, c->lam, rhs, x, c->ir_tol, c->ir_max, c->max_ylen, c->stream);
+  }
+  return check_launch(c);
+}
+
+hevi_status hevi_stage_solve(hevi_ctx* c, const double* rhs, double* x) {
+  if (!c) return HEVI_ERR_INVALID_ARG;
+  reset_fail(c);
+  hevi_status s = hevi_stage_solve_async(c, rhs, x);
+  if (s != HEVI_OK) return s;
+  return wait_status(c);
+}
+
+hevi_status hevi_newton_solve_async(hevi_ctx* c, double gamma_dt, double* state, const double* R,
+                                    double rtol, int32_t max_iter) {
+  if (!c || !state || !R || state == R || !(gamma_dt >= 0.0) || !(rtol >= 0.0) || max_iter < 0 ||
+      max_iter > 1000)
+    return HEVI_ERR_INVALID_ARG;
+  hevi_status s = ensure_newton(c);
+  if (s != HEVI_OK) return s;
+  DevView nv = c->v;
+  nv.lin = c->lin_newton;
+  {
+    Scope sc(c, kNewton);
+    hevi::launch_newton(nv, gamma_dt, state, R, rtol, max_iter, c->max_order, c->max_ylen, c->stream);
+  }
+  return check_launch(c);
+}
+
+hevi_status hevi_newton_solve(hevi_ctx* c, double gamma_dt, double* state, const double* R,
+                              double rtol, int32_t max_iter) {
+  if (!c) return HEVI_ERR_INVALID_ARG;
+  reset_fail(c);
+  hevi_status s = hevi_newton_solve_async(c, gamma_dt, state, R, rtol, max_iter);
+  if (s != HEVI_OK) return s;
+  return wait_status(c);
+}
+
+hevi_status hevi_apply_Lv(hevi_ctx* c, const double* x, double* y, int nonlinear) {
+  if (!c || !x || !y || x == y) return HEVI_ERR_INVALID_ARG;
+  if (!nonlinear && !c->factored) return HEVI_ERR_INVALID_ARG;
+  {
+    Scope sc(c, kApply);
+    hevi::launch_apply(c->v, x, y, nonlinear, c->stream);
+  }
+  return check_launch(c);
+}
+
+hevi_status hevi_column_status(hevi_ctx* c, int32_t* status, int32_t* iters) {
+  if (!c) return HEVI_ERR_INVALID_ARG;
+  if (status &&
+      cudaMemcpyAsync(status, c->v.col_status, c->ncols * sizeof(int32_t), cudaMemcpyDeviceToDevice,
+                      c->stream) != cudaSuccess)
+    return HEVI_ERR_CUDA;
+  if (iters &&
+      cudaMemcpyAsync(iters, c->v.col_iters, c->ncols * sizeof(int32_t), cudaMemcpyDeviceToDevice,
+                      c->stream) != cudaSuccess)
+    return HEVI_ERR_CUDA;
+  return HEVI_OK;
+}
+
+hevi_status hevi_sync(hevi_ctx* c) {
+  if (!c) return HEVI_ERR_INVALID_ARG;
+  hevi_status s = wait_status(c);
+  reset_fail(c);
+  cudaStreamSynchronize(c->stream);
+  return s;
+}
+
+hevi_status hevi_profile(hevi_ctx* c, int32_t enable) {
+  if (!c) return HEVI_ERR_INVALID_ARG;
+  fold_profile(c);
+  if (enable) {
+    for (int k = 0; k < kNumKinds; ++k) {
+      c->prof_ms[k] = 0.0;
+      c->prof_n[k] = 0;
+    }
+  }
+  c->prof = enable != 0;
+  return HEVI_OK;
+}
+
+int32_t hevi_profile_kinds(void) { return kNumKinds; }
+
+const char* hevi_profile_kind_name(int32_t kind) {
+  return (kind >= 0 && kind < kNumKinds) ? kKindNames[kind] : "";
+}
+
+hevi_status hevi_profile_read(hevi_ctx* c, int32_t kind, double* total_ms, int64_t* launches) {
+  if (!c || kind < 0 || kind >= kNumKinds || !total_ms || !launches) return HEVI_ERR_INVALID_ARG;
+  fold_profile(c);
+  *total_ms = c->prof_ms[kind];
+  *launches = c->prof_n[kind];
+  return HEVI_OK;
+}
+
+static bool tableau_ok(int32_t s, const double* A, const double* At, const double* b) {
+  if (s < 2 || s > 8 || !A || !At || !b) return false;
+  if (At[0] != 0.0) return false;
+  const double g = At[1 * s + 1];
+  if (!(g > 0.0)) return false;
+  for (int i = 1; i < s; ++i)
+    if (At[i * s + i] != g) return false;
+  for (int i = 0; i < s; ++i)
+    for (int j = i; j < s; ++j)
+      if (A[i * s + j] != 0.0 || (j > i && At[i * s + j] != 0.0)) return false;
+  return true;
+}
+
+hevi_status hevi_lhevi_step(hevi_ctx* c, int32_t s, const double* A, const double* At,
+                            const double* b, double dt, const double* q_in, const double* H,
+                            double* q_out, int32_t lin_about_rest) {
+  if (!c || !q_in || !H || !q_out || q_in == q_out || !(dt > 0.0) || !tableau_ok(s, A, At, b))
+    return HEVI_ERR_INVALID_ARG;
+  // ARK form of LHEVI (Sec. 4.3, Eq. lhevi-ark-final-3), S(Q) = H + V(Q),
+  // w_ij = (at_ij - a_ij) / gamma:
+  //   q_hat = q^n + dt sum_j a_ij S_j + sum_j w_ij Q_j;  (I - gamma dt L) q_tt = q_hat;
+  //   Q_i = q_tt - sum_j w_ij Q_j;  q^{n+1} = q^n + dt sum_i b_i S_i.
+  // The solve is for q_tt, a difference of states, so the refinement
+  // tolerance applies to the stage increment.
+  hevi_status st = ensure_work(c, 2 * s + 1);
+  if (st != HEVI_OK) return st;
+  const int64_t n = c->state_size;
+  double* Qb = c->work;            // stage values Q_1 .. Q_{s-1} (Q_0 = q_in)
+  double* S = c->work + s * n;     // s vectors
+  double* rhs = c->work + 2 * s * n;
+  const double gam = At[1 * s + 1], lam = gam * dt;
+  auto Qp = [&](int j) -> const double* { return j == 0 ? q_in : Qb + j * n; };
+  if ((st = hevi_factor(c, lam, lin_about_rest ? nullptr : q_in))) return st;
+  {
+    Scope sc(c, kApply);
+    hevi::launch_apply_rhs(c->v, q_in, H, S, c->stream);
+  }
+  c->launches += 1;
+  for (int i = 1; i < s; ++i) {
+    const double* vec[16];
+    double coef[16];
+    int nt = 0;
+    for (int j = 0; j < i; ++j) {
+      vec[nt] = S + j * n;
+      coef[nt++] = dt * A[i * s + j];
+      vec[nt] = Qp(j);
+      coef[nt++] = (At[i * s + j] - A[i * s + j]) / gam;
+    }
+    double* Qi = Qb + i * n;
+    {
+      Scope sc(c, kCombine);
+      hevi::launch_combine(n, q_in, nt, vec, coef, rhs, c->stream);
+    }
+    {
+      Scope sc(c, kSolve);
+      hevi::launch_solve(c->v, c->prec, lam, rhs, Qi, c->ir_tol, c->ir_max, c->max_ylen, c->stream);
+    }
+    nt = 0;
+    for (int j = 0; j < i; ++j) {
+      vec[nt] = Qp(j);
+      coef[nt++] = -(At[i * s + j] - A[i * s + j]) / gam;
+    }
+    {
+      Scope sc(c, kCombine);
+      hevi::launch_combine(n, Qi, nt, vec, coef, Qi, c->stream);
+    }
+    {
+      Scope sc(c, kApply);
+      hevi::launch_apply_rhs(c->v, Qi, H, S + i * n, c->stream);
+    }
+    c->launches += 4;
+  }
+  {
+    const double* vec[16];
+    double coef[16];
+    int nt = 0;
+    for (int i = 0; i < s; ++i) {
+      vec[nt] = S + i * n;
+      coef[nt++] = dt * b[i];
+    }
+    {
+      Scope sc(c, kCombine);
+      hevi::launch_combine(n, q_in, nt, vec, coef, q_out, c->stream);
+    }
+    c->launches += 1;
+  }
+  return cudaGetLastError() == cudaSuccess ? HEVI_OK : HEVI_ERR_CUDA;
+}
+
+hevi_status hevi_nhevi_step(hevi_ctx* c, int32_t s, const double* A, const double* At,
+                            const double* b, double dt, const double* q_in, const double* H,
+                            double* q_out, double rtol, int32_t max_iter) {
+  if (!c || !q_in || !H || !q_out || q_in == q_out || !(dt > 0.0) || !tableau_ok(s, A, At, b))
+    return HEVI_ERR_INVALID_ARG;
+  hevi_status st = ensure_work(c, s + 2);
+  if (st != HEVI_OK) return st;
+  if ((st = ensure_newton(c))) return st;
+  const int64_t n = c->state_size;
+  double* VQ = c->work;  // s vectors
+  double* R = c->work + s * n;
+  double* Q = R + n;
+  const double lam = At[1 * s + 1] * dt;
+  {
+    Scope sc(c, kApply);
+    hevi::launch_apply(c->v, q_in, VQ, 1, c->stream);
+  }
+  cudaMemcpyAsync(Q, q_in, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+  c->launches += 1;
+  DevView nv = c->v;
+  nv.lin = c->lin_newton;
+  for (int i = 1; i < s; ++i) {
+    const double* vec[16];
+    double coef[16];
+    int nt = 0;
+    double ah = 0.0;
+    for (int j = 0; j < i; ++j) {
+      ah += A[i * s + j];
+      vec[nt] = VQ + j * n;
+      coef[nt++] = dt * At[i * s + j];
+    }
+    vec[nt] = H;
+    coef[nt++] = dt * ah;
+    {
+      Scope sc(c, kCombine);
+      hevi::launch_combine(n, q_in, nt, vec, coef, R, c->stream);
+    }
+    {
+      Scope sc(c, kNewton);
+      hevi::launch_newton(nv, lam, Q, R, rtol, max_iter, c->max_order, c->max_ylen, c->stream);
+    }
+    {
+      Scope sc(c, kApply);
+      hevi::launch_apply(c->v, Q, VQ + i * n, 1, c->stream);
+    }
+    c->launches += 3;
+  }
+  {
+    const double* vec[16];
+    double coef[16];
+    int nt = 0;
+    double bs = 0.0;
+    for (int i = 0; i < s; ++i) {
+      bs += b[i];
+      vec[nt] = VQ + i * n;
+      coef[nt++] = dt * b[i];
+    }
+    vec[nt] = H;
+    coef[nt++] = dt * bs;
+    {
+      Scope sc(c, kCombine);
+      hevi::launch_combine(n, q_in, nt, vec, coef, q_out, c->stream);
+    }
+    c->launches += 1;
+  }
+  return cudaGetLastError() == cudaSuccess ? HEVI_OK : HEVI_ERR_CUDA;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Named ESDIRK tableaux (Sec. 6).  Coefficients of the cited constructions,
+// stored as ratios of integers.
+// ---------------------------------------------------------------------------
+namespace {
+struct Ratio {
+  double p, q;
+};
+double r(const Ratio& x) { return x.p / x.q; }
+}  // namespace
+
+extern "C" hevi_status hevi_tableau(const char* name, int32_t* s_out, double* A, double* At,
+                                    double* b) {
+  if (!name || !s_out || !A || !At || !b) return HEVI_ERR_INVALID_ARG;
+  std::string nm(name);
+  int s = 0;
+  std::fill(A, A + 64, 0.0);
+  std::fill(At, At + 64, 0.0);
+  std::fill(b, b + 8, 0.0);
+  auto a = [&](double* M, int i, int j) -> double& { return M[i * s + j]; };
+  if (nm == "ARK2") {
+    // ARK(2,3,2)b: gamma = 1 - 1/sqrt(2), a32 = 1/2 (Sec. 4.1)
+    s = 3;
+    const double g = 1.0 - 1.0 / std::sqrt(2.0), d = 1.0 / (2.0 * std::sqrt(2.0));
+    a(A, 1, 0) = 2.0 * g;
+    a(A, 2, 0) = 0.5;
+    a(A, 2, 1) = 0.5;
+    a(At, 1, 0) = g; a(At, 1, 1) = g;
+    a(At, 2, 0) = d; a(At, 2, 1) = d; a(At, 2, 2) = g;
+    b[0] = d; b[1] = d; b[2] = g;
+  } else if (nm == "ARK3") {
+    s = 4;
+    const double g = r({1767732205903.0, 4055673282236.0});
+    const double b0 = r({1471266399579.0, 7840856788654.0});
+    const double b1 = r({-4482444167858.0, 7529755066697.0});
+    const double b2 = r({11266239266428.0, 11593286722821.0});
+    a(At, 1, 0) = g; a(At, 1, 1) = g;
+    a(At, 2, 0) = r({2746238789719.0, 10658868560708.0});
+    a(At, 2, 1) = r({-640167445237.0, 6845629431997.0});
+    a(At, 2, 2) = g;
+    a(At, 3, 0) = b0; a(At, 3, 1) = b1; a(At, 3, 2) = b2; a(At, 3, 3) = g;
+    a(A, 1, 0) = r({1767732205903.0, 2027836641118.0});
+    a(A, 2, 0) = r({5535828885825.0, 10492691773637.0});
+    a(A, 2, 1) = r({788022342437.0, 10882634858940.0});
+    a(A, 3, 0) = r({6485989280629.0, 16251701735622.0});
+    a(A, 3, 1) = r({-4246266847089.0, 9704473918619.0});
+    a(A, 3, 2) = r({10755448449292.0, 10357097424841.0});
+    b[0] = b0; b[1] = b1; b[2] = b2; b[3] = g;
+  } else if (nm == "ARK4") {
+    s = 6;
+    const double g = 0.25;
+    const double bb[6] = {r({82889.0, 524892.0}), 0.0, r({15625.0, 83664.0}),
+                          r({69875.0, 102672.0}), r({-2260.0, 8211.0}), g};
+    a(At, 1, 0) = g; a(At, 1, 1) = g;
+    a(At, 2, 0) = r({8611.0, 62500.0}); a(At, 2, 1) = r({-1743.0, 31250.0}); a(At, 2, 2) = g;
+    a(At, 3, 0) = r({5012029.0, 34652500.0}); a(At, 3, 1) = r({-654441.0, 2922500.0});
+    a(At, 3, 2) = r({174375.0, 388108.0}); a(At, 3, 3) = g;
+    a(At, 4, 0) = r({15267082809.0, 155376265600.0}); a(At, 4, 1) = r({-71443401.0, 120774400.0});
+    a(At, 4, 2) = r({730878875.0, 902184768.0}); a(At, 4, 3) = r({2285395.0, 8070912.0});
+    a(At, 4, 4) = g;
+    for (int j = 0; j < 6; ++j) a(At, 5, j) = bb[j];
+    a(A, 1, 0) = 0.5;
+    a(A, 2, 0) = r({13861.0, 62500.0}); a(A, 2, 1) = r({6889.0, 62500.0});
+    a(A, 3, 0) = r({-116923316275.0, 2393684061468.0});
+    a(A, 3, 1) = r({-2731218467317.0, 15368042101831.0});
+    a(A, 3, 2) = r({9408046702089.0, 11113171139209.0});
+    a(A, 4, 0) = r({-451086348788.0, 2902428689909.0});
+    a(A, 4, 1) = r({-2682348792572.0, 7519795681897.0});
+    a(A, 4, 2) = r({12662868775082.0, 11960479115383.0});
+    a(A, 4, 3) = r({3355817975965.0, 11060851509271.0});
+    a(A, 5, 0) = r({647845179188.0, 3216320057751.0});
+    a(A, 5, 1) = r({73281519250.0, 8382639484533.0});
+    a(A, 5, 2) = r({552539513391.0, 3454668386233.0});
+    a(A, 5, 3) = r({3354512671639.0, 8306763924573.0});
+    a(A, 5, 4) = r({4040.0, 17871.0});
+    for (int j = 0; j < 6; ++j) b[j] = bb[j];
+  } else {
+    return HEVI_ERR_INVALID_ARG;
+  }
+  *s_out = s;
+  return HEVI_OK;
+}

@@ -1,0 +1,183 @@
+// hevi_internal.cuh -- device-side building blocks of the HEVI column solver.
+//
+// One column: Nez elements of LGL order N, n_z = Nez N + 1 points, n = 3 n_z
+// unknowns (rho, m = rho w, Theta = rho theta), point-major (Sec. 3; set 2C
+// of App. A.1 restricted to the vertical).  Band half-width K = 3(N+1) - 1
+// (Sec. 4.2.3).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/hevi.h"
+
+namespace hevi {
+
+constexpr int kMaxOrder = 5;
+constexpr int kTile = 32;  // columns per tile (one warp, one column per lane)
+
+// Band sizes and factor record layout for order N.  Per pivot step j a
+// column stores an L record {l_1..l_K, 1/u_jj, pivot offset} padded to a
+// multiple of 4 and a U record {u_j,j+1 .. u_j,j+2K} padded to a multiple of
+// 4 (partial pivoting fills U to k_l + k_u super-diagonals).
+template <int N>
+struct Band {
+  static constexpr int K = 3 * (N + 1) - 1;
+  static constexpr int WR = K + 1;          // active window rows
+  static constexpr int WC = 2 * K + 1;      // active window columns
+  static constexpr int LR = ((K + 2) + 3) / 4 * 4;
+  static constexpr int UR = ((2 * K) + 3) / 4 * 4;
+  static constexpr int RL = LR + UR;        // record length per pivot step
+};
+
+// Physical constants of the isothermal reference atmosphere.
+struct Phys {
+  double T0, p0, R, cp, g;
+  double cv, gamma, cs;  // cp - R, cp / cv, sqrt(gamma R T0)
+};
+
+// One tile = up to 32 columns of the same size class.
+struct TileDesc {
+  int32_t order;      // N
+  int32_t nez;        // elements
+  int32_t count;      // columns in this tile (<= 32)
+  int32_t first;      // index into the class-sorted column permutation
+  int64_t fac_off;    // offset of the tile's factor records (elements of T)
+  int64_t scr_off;    // offset of the tile's Newton scratch (floats)
+};
+
+// LGL tables per order (host fills them at setup): weights w_k, Dhat_kj =
+// h_j'(xi_k), and wD_kj = w_k Dhat_kj, in FP64 and FP32.
+struct LglTables {
+  double xi[kMaxOrder + 1][kMaxOrder + 1];
+  double w[kMaxOrder + 1][kMaxOrder + 1];
+  double wD[kMaxOrder + 1][(kMaxOrder + 1) * (kMaxOrder + 1)];
+  float wDf[kMaxOrder + 1][(kMaxOrder + 1) * (kMaxOrder + 1)];
+};
+
+// Device view of a context's buffers (passed to kernels by value).
+struct DevView {
+  Phys ph;
+  int64_t ncols;
+  const int64_t* col_off;   // [ncols + 1] state offsets
+  const int32_t* perm;      // [ncols] class-sorted column index
+  const double* col_dz;     // [ncols] element height
+  const double* ref;        // state layout: (rho_bar, P_bar, Theta_bar) per point
+  double* lin;              // state layout: (w0, theta0, c0 = gamma P0 / Theta0)
+  const TileDesc* tiles;
+  int32_t ntiles;
+  void* fac;                // factor records (float or double)
+  float* scr;               // Newton scratch (U records)
+  int32_t* fac_status;      // [ncols] status of the last factorisation
+  int32_t* col_status;      // [ncols] status of the last call
+  int32_t* col_iters;       // [ncols]
+  int32_t* fail_count;      // [1]
+};
+
+// Per-column geometry in a kernel.
+struct Col {
+  int64_t col;
+  int64_t off;
+  int nez, nz, n;
+  double s;  // 2 / dz: d(xi)/dz of every element
+};
+
+// Point weight sum W_I: M_I = (dz/2) W_I (DSS of the diagonal LGL mass).
+template <int N>
+__device__ __forceinline__ double wsum(const double* w, int I, int nz) {
+  if (I == 0 || I == nz - 1) return w[0];
+  int k = I % N;
+  return k == 0 ? 2.0 * w[0] : w[k];
+}
+
+// Element pass: visits the elements of a column bottom to top, asks `flux`
+// for the 3 flux components at every point (once per point, in increasing
+// order), forms the strong-form element derivative weighted by the LGL
+// weights, sums the two contributions of shared points (DSS), and hands each
+// completed point I to `out` with D_I = (Dcal f)_I =
+// (1/M_I) sum_{(e,k)->I} w_k J_e (dxi/dz) sum_j Dhat_kj f_(e,j)   (Sec. 3).
+// `out(I, D)` is called in increasing I, always after flux(J) for every J
+// of the element holding I.
+template <int N, class FluxF, class OutF>
+__device__ __forceinline__ void element_pass(const Col& c, const double* w, const double* wD,
+                                             FluxF&& flux, OutF&& out) {
+  double f[N + 1][3];
+  double carry[3] = {0.0, 0.0, 0.0};
+  flux(0, f[0]);
+  for (int e = 0; e < c.nez; ++e) {
+    const int I0 = e * N;
+#pragma unroll
+    for (int k = 1; k <= N; ++k) flux(I0 + k, f[k]);
+    double cc[N + 1][3];
+#pragma unroll
+    for (int k = 0; k <= N; ++k) {
+#pragma unroll
+      for (int v = 0; v < 3; ++v) {
+        double a = 0.0;
+#pragma unroll
+        for (int j = 0; j <= N; ++j) a = fma(wD[k * (N + 1) + j], f[j][v], a);
+        cc[k][v] = a;
+      }
+    }
+    {
+      double D[3];
+      const double sc = c.s / (e == 0 ? w[0] : 2.0 * w[0]);
+#pragma unroll
+      for (int v = 0; v < 3; ++v) D[v] = (carry[v] + cc[0][v]) * sc;
+      out(I0, D);
+    }
+#pragma unroll
+    for (int k = 1; k < N; ++k) {
+      double D[3];
+      const double sc = c.s / w[k];
+#pragma unroll
+      for (int v = 0; v < 3; ++v) D[v] = cc[k][v] * sc;
+      out(I0 + k, D);
+    }
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+      carry[v] = cc[N][v];
+      f[0][v] = f[N][v];
+    }
+  }
+  double D[3];
+  const double sc = c.s / w[0];
+#pragma unroll
+  for (int v = 0; v < 3; ++v) D[v] = carry[v] * sc;
+  out(c.nz - 1, D);
+}
+
+// Equation of state of set 2C (App. A.1): P = p0 (R Theta / p0)^gamma.
+__device__ __forceinline__ double eos(const Phys& ph, double Theta) {
+  return ph.p0 * pow(ph.R * Theta / ph.p0, ph.gamma);
+}
+
+// Pressure perturbation about the reference state, from the same equation of
+// state: P(Theta) - P_bar = P_bar ((Theta / Theta_bar)^gamma - 1), evaluated as
+// P_bar expm1(gamma log1p((Theta - Theta_bar) / Theta_bar)) so that it is
+// exactly zero at Theta = Theta_bar and free of the cancellation of two
+// O(1e5 Pa) numbers.
+__device__ __forceinline__ double eos_perturbation(const Phys& ph, double Theta, double Theta_bar,
+                                                   double P_bar) {
+  return P_bar * expm1(ph.gamma * log1p((Theta - Theta_bar) / Theta_bar));
+}
+
+// Launch helpers (host side, defined in hevi_kernels.cu).
+void launch_setup_ref(const DevView& v, const int32_t* col_order, const int32_t* col_nez,
+                      cudaStream_t st);
+void launch_factor(const DevView& v, hevi_precision prec, double lam, const double* q0,
+                   int max_order_present, cudaStream_t st);
+void launch_solve(const DevView& v, hevi_precision prec, double lam, const double* b, double* x,
+                  double tol, int max_sweeps, int max_ylen, cudaStream_t st);
+void launch_apply(const DevView& v, const double* x, double* y, int nonlinear, cudaStream_t st);
+void launch_apply_stage(const DevView& v, const double* Q, const double* H, double* E, double* LQ,
+                        int lin_rest, cudaStream_t st);
+void launch_apply_rhs(const DevView& v, const double* Q, const double* H, double* S,
+                      cudaStream_t st);
+void launch_newton(const DevView& v, double lam, double* q, const double* R, double rtol,
+                   int max_iter, int max_order, int max_ylen, cudaStream_t st);
+void launch_combine(int64_t count, const double* base, int nterms, const double* const* vec,
+                    const double* coef, double* out, cudaStream_t st);
+void launch_reference_state(const DevView& v, double* q, cudaStream_t st);
+void upload_tables(const LglTables& t);
+
+}  // namespace hevi

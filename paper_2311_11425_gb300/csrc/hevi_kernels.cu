@@ -1,0 +1,1046 @@
+// hevi_kernels.cu -- CUDA kernels of the HEVI vertical column solver (sm_103a).
+//
+// Work decomposition: one column per thread, 32 columns of one size class per
+// warp ("tile").  Factor records are interleaved per tile
+//   [step j][record vector][lane][vector lane]
+// so that the 32 lanes of a warp read or write one contiguous 512-byte line
+// (float4 / double2) per record vector.  The active window of the band LU,
+// (K+1) rows x (2K+1) columns (Sec. 4.2.3: partial pivoting fills U to
+// k_l + k_u super-diagonals), lives in shared memory, slot-major with the
+// thread index fastest so that a warp's accesses are bank-conflict free.
+#include <cstdio>
+
+#include "hevi_internal.cuh"
+
+namespace hevi {
+
+__constant__ LglTables c_tab;
+
+void upload_tables(const LglTables& t) { cudaMemcpyToSymbol(c_tab, &t, sizeof(LglTables)); }
+
+// ---------------------------------------------------------------------------
+// Record addressing
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Vec;
+template <>
+struct Vec<float> {
+  using type = float4;
+  static constexpr int W = 4;
+};
+template <>
+struct Vec<double> {
+  using type = double2;
+  static constexpr int W = 2;
+};
+
+template <int N, typename T>
+__device__ __forceinline__ T* record_vec(T* tile_base, int j, int e, int lane) {
+  constexpr int W = Vec<T>::W;
+  constexpr int NV = Band<N>::RL / W;
+  return tile_base + ((int64_t)(j * NV + e / W) * kTile + lane) * W;
+}
+
+template <int N, typename T>
+__device__ __forceinline__ const T* record_ptr(const T* tile_base, int j, int e, int lane) {
+  return record_vec<N, T>(const_cast<T*>(tile_base), j, e, lane) + (e % Vec<T>::W);
+}
+
+// Record a per-column failure; counters: [0] any, [1] singular, [2] not
+// converged, [3] bad input.
+__device__ __forceinline__ void fail(const DevView& v, int64_t col, int code) {
+  v.col_status[col] = code;
+  atomicAdd(v.fail_count, 1);
+  atomicAdd(v.fail_count + (code == HEVI_COL_SINGULAR ? 1 : code == HEVI_COL_NOT_CONVERGED ? 2 : 3), 1);
+}
+
+__device__ __forceinline__ Col make_col(const DevView& v, const TileDesc& t, int lane, int N) {
+  Col c;
+  c.col = v.perm[t.first + lane];
+  c.off = v.col_off[c.col];
+  c.nez = t.nez;
+  c.nz = t.nez * N + 1;
+  c.n = 3 * c.nz;
+  c.s = 2.0 / v.col_dz[c.col];
+  return c;
+}
+
+// ---------------------------------------------------------------------------
+// Setup: reference state per point (isothermal, hydrostatic) and rest state
+// ---------------------------------------------------------------------------
+__global__ void k_setup_ref(DevView v, const int32_t* col_order, const int32_t* col_nez) {
+  int64_t col = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (col >= v.ncols) return;
+  const int N = col_order[col], nez = col_nez[col], nz = nez * N + 1;
+  const double dz = v.col_dz[col];
+  const Phys ph = v.ph;
+  const double Hs = ph.R * ph.T0 / ph.g;
+  double* r = const_cast<double*>(v.ref) + v.col_off[col];
+  for (int I = 0; I < nz; ++I) {
+    int e = I / N;
+    if (e == nez) e = nez - 1;
+    const int k = I - e * N;
+    double z = e * dz + (c_tab.xi[N][k] + 1.0) * 0.5 * dz;
+    if (I == 0) z = 0.0;
+    if (I == nz - 1) z = nez * dz;
+    const double rho = ph.p0 / (ph.R * ph.T0) * exp(-z / Hs);
+    const double th = ph.T0 * exp(ph.g * z / (ph.cp * ph.T0));
+    const double Th = rho * th;
+    r[3 * I + 0] = rho;
+    r[3 * I + 1] = eos(ph, Th);
+    r[3 * I + 2] = Th;
+  }
+}
+
+void launch_setup_ref(const DevView& v, const int32_t* col_order, const int32_t* col_nez,
+                      cudaStream_t st) {
+  int blk = 128;
+  k_setup_ref<<<(unsigned)((v.ncols + blk - 1) / blk), blk, 0, st>>>(v, col_order, col_nez);
+}
+
+__global__ void k_reference_state(DevView v, double* q) {
+  int64_t col = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (col >= v.ncols) return;
+  const int64_t a = v.col_off[col], b = v.col_off[col + 1];
+  for (int64_t i = a; i < b; i += 3) {
+    q[i] = v.ref[i];
+    q[i + 1] = 0.0;
+    q[i + 2] = v.ref[i + 2];
+  }
+}
+
+void launch_reference_state(const DevView& v, double* q, cudaStream_t st) {
+  int blk = 128;
+  k_reference_state<<<(unsigned)((v.ncols + blk - 1) / blk), blk, 0, st>>>(v, q);
+}
+
+// ---------------------------------------------------------------------------
+// Linearisation coefficients per point: w = m/rho, theta = Theta/rho and
+// c = dP/dTheta = gamma P / Theta; these are the entries of the flux
+// Jacobian K (App. A.3 restricted to the vertical):
+//   rho-flux (0, 1, 0);  m-flux (-w^2, 2w, c);  Theta-flux (-theta w, theta, w)
+// Returns false on a non-physical state.
+// ---------------------------------------------------------------------------
+// dP receives P(Theta) - P_bar.
+__device__ __forceinline__ bool lin_coefs(const Phys& ph, double rho, double m, double Th,
+                                          double Th_bar, double P_bar, double* w, double* th,
+                                          double* c, double* dP) {
+  if (!(rho > 0.0) || !(Th > 0.0) || !isfinite(m)) return false;
+  const double ir = 1.0 / rho;
+  *w = m * ir;
+  *th = Th * ir;
+  *dP = eos_perturbation(ph, Th, Th_bar, P_bar);
+  *c = ph.gamma * (P_bar + *dP) / Th;
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Band assembly of one row of A = I + Lambda Dcal K(q0) + Lambda G into the
+// shared-memory window (Sec. 4.2.3, App. A.3):
+//   A[(I,v),(J,u)] = delta + Lambda (2/dz)/W_I sum_{e containing I and J}
+//                    w_k(I) Dhat_k(I),j(J) K_vu(J) + Lambda g [v=m, u=rho, I=J],
+// m-rows of the two end points replaced by identity rows (w = 0).
+// With SCALED the row is equilibrated: A_hat = S^-1 A S with the reference
+// scales S = (rho_bar, rho_bar c_s, Theta_bar).
+// ---------------------------------------------------------------------------
+template <int N, typename T, bool SCALED>
+__device__ __forceinline__ void assemble_row(const DevView& v, const Col& c, double lam, int i,
+                                             T* win, int stride, int rs, int col0, int cs0) {
+  constexpr int K = Band<N>::K, WC = Band<N>::WC;
+  T* row = win + (rs * WC) * stride;
+#pragma unroll
+  for (int s = 0; s < WC; ++s) row[s * stride] = T(0);
+  auto slot = [&](int col) {
+    int s = cs0 + (col - col0);
+    return s >= WC ? s - WC : s;
+  };
+  const int I = i / 3, vv = i - 3 * I;
+  if (vv == 1 && (I == 0 || I == c.nz - 1)) {
+    row[slot(i) * stride] = T(1);
+    return;
+  }
+  const double* w = c_tab.w[N];
+  const double* lin = v.lin + c.off;
+  const double* ref = v.ref + c.off;
+  const double cs = v.ph.cs;
+  auto scale = [&](int idx) -> double {  // S entry of unknown idx
+    const int P = idx / 3, u = idx - 3 * P;
+    const double rb = ref[3 * P];
+    return u == 0 ? rb : (u == 1 ? rb * cs : ref[3 * P + 2]);
+  };
+  const T inv_si = SCALED ? T(1.0 / scale(i)) : T(1);
+  const T fac = T(lam * c.s / wsum<N>(w, I, c.nz));
+  // elements containing point I and I's local index in each
+  int e_lo, e_hi;
+  if (I % N == 0) {
+    e_lo = I / N - 1;
+    e_hi = I / N;
+  } else {
+    e_lo = e_hi = I / N;
+  }
+  if (e_lo < 0) e_lo = 0;
+  if (e_hi > c.nez - 1) e_hi = c.nez - 1;
+  for (int e = e_lo; e <= e_hi; ++e) {
+    const int kI = I - e * N;
+#pragma unroll
+    for (int j = 0; j <= N; ++j) {
+      const int J = e * N + j;
+      T g;
+      if constexpr (sizeof(T) == 4)
+        g = fac * c_tab.wDf[N][kI * (N + 1) + j];
+      else
+        g = fac * c_tab.wD[N][kI * (N + 1) + j];
+      const T wJ = T(lin[3 * J]), thJ = T(lin[3 * J + 1]), cJ = T(lin[3 * J + 2]);
+      T kv0, kv1, kv2;
+      if (vv == 0) {
+        kv0 = T(0); kv1 = T(1); kv2 = T(0);
+      } else if (vv == 1) {
+        kv0 = -wJ * wJ; kv1 = T(2) * wJ; kv2 = cJ;
+      } else {
+        kv0 = -thJ * wJ; kv1 = thJ; kv2 = wJ;
+      }
+      if (SCALED) {
+        kv0 *= T(scale(3 * J)) * inv_si;
+        kv1 *= T(scale(3 * J + 1)) * inv_si;
+        kv2 *= T(scale(3 * J + 2)) * inv_si;
+      }
+      const int b = 3 * J;
+      row[slot(b) * stride] += g * kv0;
+      row[slot(b + 1) * stride] += g * kv1;
+      row[slot(b + 2) * stride] += g * kv2;
+    }
+  }
+  row[slot(i) * stride] += T(1);
+  if (vv == 1) {
+    T gg = T(lam * v.ph.g);
+    if (SCALED) gg *= T(scale(i - 1)) * inv_si;
+    row[slot(i - 1) * stride] += gg;
+  }
+  (void)K;
+}
+
+// ---------------------------------------------------------------------------
+// Band LU with partial pivoting of one column in the shared-memory window
+// (LAPACK dgbtrf semantics: pivot = first row of maximal |a| among rows
+// j..j+k_l; swap over the fill extent; unit-lower multipliers; rank-1 update).
+// The assembly of row j+K+1 happens as the window advances.  `emit(j, l[],
+// invd, piv, u[])` receives the finished pivot step; with FWD the L part is
+// also applied right away to the right-hand side y (Newton).
+// Returns info (0, or 1 + first zero-pivot step).
+// ---------------------------------------------------------------------------
+template <int N, typename T, bool SCALED, class Emit>
+__device__ int band_lu(const DevView& v, const Col& c, double lam, T* win, int stride,
+                       Emit&& emit) {
+  constexpr int K = Band<N>::K, WR = Band<N>::WR, WC = Band<N>::WC;
+  const int n = c.n;
+  for (int i = 0; i <= K && i < n; ++i) assemble_row<N, T, SCALED>(v, c, lam, i, win, stride, i, 0, 0);
+  for (int i = n; i <= K; ++i) {  // rows past the end of a tiny column
+    T* row = win + (i * WC) * stride;
+    for (int s = 0; s < WC; ++s) row[s * stride] = T(0);
+  }
+  int info = 0;
+  int rb = 0, cb = 0;
+  auto W = [&](int r, int cc) -> T& {
+    int rs = rb + r;
+    rs = rs >= WR ? rs - WR : rs;
+    int cs = cb + cc;
+    cs = cs >= WC ? cs - WC : cs;
+    return win[(rs * WC + cs) * stride];
+  };
+  for (int j = 0; j < n; ++j) {
+    const int nr = min(K, n - 1 - j);
+    const int ncol = min(2 * K, n - 1 - j);
+    // pivot search: first maximal |a|
+    int p = 0;
+    T amax = fabs(W(0, 0));
+#pragma unroll
+    for (int r = 1; r <= K; ++r) {
+      if (r <= nr) {
+        const T a = fabs(W(r, 0));
+        if (a > amax) {
+          amax = a;
+          p = r;
+        }
+      }
+    }
+    T l[K];
+    T invd;
+    if (amax == T(0)) {
+      if (info == 0) info = j + 1;
+      invd = T(0);
+#pragma unroll
+      for (int r = 0; r < K; ++r) l[r] = T(0);
+    } else {
+      if (p != 0) {
+#pragma unroll
+        for (int cc = 0; cc <= 2 * K; ++cc) {
+          if (cc <= ncol) {
+            T t = W(0, cc);
+            W(0, cc) = W(p, cc);
+            W(p, cc) = t;
+          }
+        }
+      }
+      invd = T(1) / W(0, 0);
+#pragma unroll
+      for (int r = 1; r <= K; ++r) l[r - 1] = (r <= nr) ? W(r, 0) * invd : T(0);
+#pragma unroll 4
+      for (int cc = 1; cc <= 2 * K; ++cc) {
+        if (cc <= ncol) {
+          const T u = W(0, cc);
+#pragma unroll
+          for (int r = 1; r <= K; ++r)
+            if (r <= nr) W(r, cc) -= l[r - 1] * u;
+        }
+      }
+    }
+    emit(j, l, invd, p, [&](int cc) -> T { return cc <= ncol ? W(0, cc) : T(0); });
+    // advance: column j leaves, column j+2K+1 enters (zero fill for rows
+    // j+1..j+K); row j leaves, row j+K+1 enters (assembled).
+#pragma unroll
+    for (int r = 1; r <= K; ++r) W(r, 0) = T(0);
+    const int inew = j + K + 1;
+    const int rs_new = rb, cs_next = (cb + 1 == WC) ? 0 : cb + 1;
+    if (inew < n) {
+      assemble_row<N, T, SCALED>(v, c, lam, inew, win, stride, rs_new, j + 1, cs_next);
+    } else {
+      T* row = win + (rs_new * WC) * stride;
+      for (int s = 0; s < WC; ++s) row[s * stride] = T(0);
+    }
+    rb = (rb + 1 == WR) ? 0 : rb + 1;
+    cb = cs_next;
+  }
+  return info;
+}
+
+// ---------------------------------------------------------------------------
+// Factor kernel: linearisation coefficients, assembly, band LU, records out.
+// ---------------------------------------------------------------------------
+template <int N, typename T, bool SCALED>
+__device__ void factor_column(const DevView& v, const TileDesc& t, int lane, double lam,
+                              const double* q0, T* win, int stride) {
+  constexpr int K = Band<N>::K, LR = Band<N>::LR, UR = Band<N>::UR;
+  constexpr int W = Vec<T>::W;
+  using V = typename Vec<T>::type;
+  const Col c = make_col(v, t, lane, N);
+  const Phys ph = v.ph;
+  bool ok = true;
+  for (int I = 0; I < c.nz; ++I) {
+    const int64_t a = c.off + 3 * I;
+    double rho, m, Th;
+    if (q0) {
+      rho = q0[a]; m = q0[a + 1]; Th = q0[a + 2];
+    } else {
+      rho = v.ref[a]; m = 0.0; Th = v.ref[a + 2];
+    }
+    double w, th, cc, dP;
+    if (!lin_coefs(ph, rho, m, Th, v.ref[a + 2], v.ref[a + 1], &w, &th, &cc, &dP)) {
+      ok = false;
+      w = 0.0; th = 0.0; cc = 0.0;
+    }
+    v.lin[a] = w;
+    v.lin[a + 1] = th;
+    v.lin[a + 2] = cc;
+  }
+  T* base = reinterpret_cast<T*>(v.fac) + t.fac_off;
+  const int info = band_lu<N, T, SCALED>(
+      v, c, lam, win, stride, [&](int j, const T* l, T invd, int p, auto&& U) {
+        T rec[LR];
+#pragma unroll
+        for (int r = 0; r < K; ++r) rec[r] = l[r];
+        rec[K] = invd;
+        rec[K + 1] = T(p);
+#pragma unroll
+        for (int r = K + 2; r < LR; ++r) rec[r] = T(0);
+#pragma unroll
+        for (int q = 0; q < LR; q += W) {
+          V* dst = reinterpret_cast<V*>(record_vec<N, T>(base, j, q, lane));
+          if constexpr (W == 4)
+            *dst = make_float4(rec[q], rec[q + 1], rec[q + 2], rec[q + 3]);
+          else
+            *dst = make_double2(rec[q], rec[q + 1]);
+        }
+        T ur[UR];
+#pragma unroll
+        for (int cc = 0; cc < UR; ++cc) ur[cc] = (cc < 2 * K) ? U(cc + 1) : T(0);
+#pragma unroll
+        for (int q = 0; q < UR; q += W) {
+          V* dst = reinterpret_cast<V*>(record_vec<N, T>(base, j, LR + q, lane));
+          if constexpr (W == 4)
+            *dst = make_float4(ur[q], ur[q + 1], ur[q + 2], ur[q + 3]);
+          else
+            *dst = make_double2(ur[q], ur[q + 1]);
+        }
+      });
+  int st = HEVI_COL_OK;
+  if (!ok)
+    st = HEVI_COL_BAD_INPUT;
+  else if (info)
+    st = HEVI_COL_SINGULAR;
+  v.fac_status[c.col] = st;
+  if (st != HEVI_COL_OK)
+    fail(v, c.col, st);
+  else
+    v.col_status[c.col] = HEVI_COL_OK;
+  v.col_iters[c.col] = 0;
+}
+
+template <typename T, bool SCALED>
+__global__ void __launch_bounds__(64) k_factor(DevView v, double lam, const double* q0) {
+  extern __shared__ unsigned char smem_raw[];
+  T* smem = reinterpret_cast<T*>(smem_raw);
+  const int warp = threadIdx.x / kTile, lane = threadIdx.x % kTile;
+  const int64_t tile = (int64_t)blockIdx.x * (blockDim.x / kTile) + warp;
+  if (tile >= v.ntiles) return;
+  const TileDesc t = v.tiles[tile];
+  if (lane >= t.count) return;
+  T* win = smem + threadIdx.x;
+  const int stride = blockDim.x;
+  switch (t.order) {
+    case 1: factor_column<1, T, SCALED>(v, t, lane, lam, q0, win, stride); break;
+    case 2: factor_column<2, T, SCALED>(v, t, lane, lam, q0, win, stride); break;
+    case 3: factor_column<3, T, SCALED>(v, t, lane, lam, q0, win, stride); break;
+    case 4: factor_column<4, T, SCALED>(v, t, lane, lam, q0, win, stride); break;
+    case 5: factor_column<5, T, SCALED>(v, t, lane, lam, q0, win, stride); break;
+    default: break;
+  }
+}
+
+static int pick_block(int bytes, int max_blk);
+static int window_slots(int N) {
+  const int K = 3 * (N + 1) - 1;
+  return (K + 1) * (2 * K + 1);
+}
+
+void launch_factor(const DevView& v, hevi_precision prec, double lam, const double* q0,
+                   int max_order, cudaStream_t st) {
+  const int esz = prec == HEVI_FP64 ? (int)sizeof(double) : (int)sizeof(float);
+  const int blk = pick_block(window_slots(max_order) * esz, 64), tiles_per_blk = blk / kTile;
+  const unsigned grid = (unsigned)((v.ntiles + tiles_per_blk - 1) / tiles_per_blk);
+  if (prec == HEVI_FP64) {
+    const int smem = window_slots(max_order) * blk * (int)sizeof(double);
+    cudaFuncSetAttribute(k_factor<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    k_factor<double, false><<<grid, blk, smem, st>>>(v, lam, q0);
+  } else {
+    const int smem = window_slots(max_order) * blk * (int)sizeof(float);
+    cudaFuncSetAttribute(k_factor<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    k_factor<float, true><<<grid, blk, smem, st>>>(v, lam, q0);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Triangular solves with the records of one column (dgbtrs semantics:
+// interchanges and unit-lower multipliers in factorisation order, then the
+// upper triangle with 2K super-diagonals).  y is the thread's slice of shared
+// memory (stride = threads per block), length n + 2K (tail kept at zero).
+// ---------------------------------------------------------------------------
+template <int N, typename T, typename Y>
+__device__ __forceinline__ void forward_sweep(const T* base, int lane, int n, Y* y, int stride) {
+  constexpr int K = Band<N>::K, LR = Band<N>::LR;
+  constexpr int W = Vec<T>::W;
+  using V = typename Vec<T>::type;
+  for (int j = 0; j < n; ++j) {
+    T rec[LR];
+#pragma unroll
+    for (int q = 0; q < LR; q += W) {
+      const V x = *reinterpret_cast<const V*>(record_vec<N, T>(const_cast<T*>(base), j, q, lane));
+      if constexpr (W == 4) {
+        rec[q] = x.x; rec[q + 1] = x.y; rec[q + 2] = x.z; rec[q + 3] = x.w;
+      } else {
+        rec[q] = x.x; rec[q + 1] = x.y;
+      }
+    }
+    const int p = (int)rec[K + 1];
+    Y yj = y[j * stride];
+    if (p) {
+      const Y t = y[(j + p) * stride];
+      y[(j + p) * stride] = yj;
+      yj = t;
+      y[j * stride] = yj;
+    }
+#pragma unroll
+    for (int r = 1; r <= K; ++r) y[(j + r) * stride] -= Y(rec[r - 1]) * yj;
+  }
+}
+
+// Backward substitution; returns sum of squares of the solution (for IR).
+template <int N, typename T, typename Y>
+__device__ __forceinline__ Y backward_sweep(const T* base, int lane, int n, Y* y, int stride) {
+  constexpr int K = Band<N>::K, LR = Band<N>::LR, UR = Band<N>::UR;
+  constexpr int W = Vec<T>::W;
+  using V = typename Vec<T>::type;
+  Y ss = Y(0);
+  for (int j = n - 1; j >= 0; --j) {
+    T u[UR];
+#pragma unroll
+    for (int q = 0; q < UR; q += W) {
+      const V x = *reinterpret_cast<const V*>(record_vec<N, T>(const_cast<T*>(base), j, LR + q, lane));
+      if constexpr (W == 4) {
+        u[q] = x.x; u[q + 1] = x.y; u[q + 2] = x.z; u[q + 3] = x.w;
+      } else {
+        u[q] = x.x; u[q + 1] = x.y;
+      }
+    }
+    const T invd = *record_ptr<N, T>(base, j, K, lane);
+    Y s = y[j * stride];
+#pragma unroll
+    for (int cc = 1; cc <= 2 * K; ++cc) s -= Y(u[cc - 1]) * y[(j + cc) * stride];
+    s *= Y(invd);
+    y[j * stride] = s;
+    ss += s * s;
+  }
+  return ss;
+}
+
+// Plain FP64 solve (K = one column per thread, FP64 factors).
+template <int N>
+__device__ void solve_fp64_column(const DevView& v, const TileDesc& t, int lane, const double* b,
+                                  double* x, double* y, int stride) {
+  constexpr int K = Band<N>::K;
+  const Col c = make_col(v, t, lane, N);
+  const double* base = reinterpret_cast<const double*>(v.fac) + t.fac_off;
+  if (v.fac_status[c.col] != HEVI_COL_OK) {  // no usable factors for this column
+    for (int i = 0; i < c.n; ++i) x[c.off + i] = __longlong_as_double(0x7ff8000000000000LL);
+    v.col_iters[c.col] = 0;
+    fail(v, c.col, v.fac_status[c.col]);
+    return;
+  }
+  v.col_status[c.col] = HEVI_COL_OK;
+  for (int i = 0; i < c.n; ++i) y[i * stride] = b[c.off + i];
+  for (int i = c.n; i < c.n + 2 * K; ++i) y[i * stride] = 0.0;
+  forward_sweep<N, double, double>(base, lane, c.n, y, stride);
+  backward_sweep<N, double, double>(base, lane, c.n, y, stride);
+  for (int i = 0; i < c.n; ++i) x[c.off + i] = y[i * stride];
+  v.col_iters[c.col] = 1;
+}
+
+// Scales S = (rho_bar, rho_bar c_s, Theta_bar) of unknown (I, u).
+__device__ __forceinline__ double ref_scale(const double* ref, double cs, int64_t a, int u) {
+  return u == 0 ? ref[a] : (u == 1 ? ref[a] * cs : ref[a + 2]);
+}
+
+// FP32 factors + FP64 iterative refinement.
+//   y0 = S^-1 b (FP32), solve; then repeat: x += S y; r = b - A x (FP64,
+//   matrix-free from the point coefficients of L(q0)); y = S^-1 r (FP32);
+//   solve; until the predicted relative error |d_k|^2/|d_{k-1}| / |x| (plain
+//   2-norms) is below tol, or max_sweeps.
+template <int N>
+__device__ void solve_ir_column(const DevView& v, const TileDesc& t, int lane, double lam,
+                                const double* b, double* x, float* y, int stride, double tol,
+                                int max_sweeps) {
+  constexpr int K = Band<N>::K;
+  const Col c = make_col(v, t, lane, N);
+  const float* base = reinterpret_cast<const float*>(v.fac) + t.fac_off;
+  const double* ref = v.ref + c.off;
+  const double* lin = v.lin + c.off;
+  const double* bc = b + c.off;
+  double* xc = x + c.off;
+  const double cs = v.ph.cs, g = v.ph.g;
+  const double* w = c_tab.w[N];
+  const double* wD = c_tab.wD[N];
+  if (v.fac_status[c.col] != HEVI_COL_OK) {  // no usable factors for this column
+    for (int i = 0; i < c.n; ++i) xc[i] = __longlong_as_double(0x7ff8000000000000LL);
+    v.col_iters[c.col] = 0;
+    fail(v, c.col, v.fac_status[c.col]);
+    return;
+  }
+  for (int I = 0; I < c.nz; ++I)
+#pragma unroll
+    for (int u = 0; u < 3; ++u)
+      y[(3 * I + u) * stride] = (float)(bc[3 * I + u] / ref_scale(ref, cs, 3 * I, u));
+  for (int i = c.n; i < c.n + 2 * K; ++i) y[i * stride] = 0.0f;
+
+  int sweeps = 0, status = HEVI_COL_NOT_CONVERGED;
+  double dprev = 0.0, xnorm = 0.0;
+  bool first = true;
+  while (true) {
+    forward_sweep<N, float, float>(base, lane, c.n, y, stride);
+    backward_sweep<N, float, float>(base, lane, c.n, y, stride);
+    ++sweeps;
+    // size of the correction d = S y in the caller's (unscaled) norm
+    float d2 = 0.0f;
+    for (int I = 0; I < c.nz; ++I)
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        const float d = y[(3 * I + u) * stride] * (float)ref_scale(ref, cs, 3 * I, u);
+        d2 = fmaf(d, d, d2);
+      }
+    const double dn = sqrt((double)d2);
+    const double xref = first ? dn : xnorm;
+    bool stop = false;
+    if (dn <= tol * xref) {
+      stop = true;
+      status = HEVI_COL_OK;
+    } else if (!first) {
+      const double pred = dn * (dn / dprev);  // error left after applying d
+      if (pred <= tol * xref) {
+        stop = true;
+        status = HEVI_COL_OK;
+      } else if (dn > 0.5 * dprev) {
+        stop = true;  // refinement is not contracting
+      }
+    }
+    if (sweeps >= max_sweeps) stop = true;
+    if (stop) {
+      for (int I = 0; I < c.nz; ++I)
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+          const int i = 3 * I + u;
+          const double d = (double)y[i * stride] * ref_scale(ref, cs, 3 * I, u);
+          xc[i] = first ? d : xc[i] + d;
+        }
+      break;
+    }
+    // fused pass: x += S y, r = b - A x, y = S^-1 r, |S^-1 x|
+    double xs = 0.0;
+    const bool fst = first;
+    auto flux = [&](int I, double* f) {
+      double xi[3];
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        const int i = 3 * I + u;
+        const double d = (double)y[i * stride] * ref_scale(ref, cs, 3 * I, u);
+        xi[u] = fst ? d : xc[i] + d;
+        xc[i] = xi[u];
+        xs = fma(xi[u], xi[u], xs);
+      }
+      const double wI = lin[3 * I], thI = lin[3 * I + 1], cI = lin[3 * I + 2];
+      f[0] = xi[1];
+      f[1] = fma(-wI * wI, xi[0], fma(2.0 * wI, xi[1], cI * xi[2]));
+      f[2] = fma(-thI * wI, xi[0], fma(thI, xi[1], wI * xi[2]));
+    };
+    auto out = [&](int I, const double* D) {
+      // A x = x + Lambda (Dcal[K x] + G x);  r = b - A x
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        const int i = 3 * I + u;
+        double r;
+        if (u == 1 && (I == 0 || I == c.nz - 1)) {
+          r = bc[i] - xc[i];
+        } else {
+          double ax = D[u];
+          if (u == 1) ax = fma(g, xc[3 * I], ax);
+          r = bc[i] - fma(lam, ax, xc[i]);
+        }
+        y[i * stride] = (float)(r / ref_scale(ref, cs, 3 * I, u));
+      }
+    };
+    element_pass<N>(c, w, wD, flux, out);
+    xnorm = sqrt(xs);
+    dprev = dn;
+    first = false;
+  }
+  v.col_iters[c.col] = sweeps;
+  if (status != HEVI_COL_OK)
+    fail(v, c.col, status);
+  else
+    v.col_status[c.col] = HEVI_COL_OK;
+}
+
+template <bool IR>
+__global__ void __launch_bounds__(128) k_solve(DevView v, double lam, const double* b, double* x,
+                                               double tol, int max_sweeps) {
+  extern __shared__ unsigned char smem_raw[];
+  const int warp = threadIdx.x / kTile, lane = threadIdx.x % kTile;
+  const int64_t tile = (int64_t)blockIdx.x * (blockDim.x / kTile) + warp;
+  if (tile >= v.ntiles) return;
+  const TileDesc t = v.tiles[tile];
+  if (lane >= t.count) return;
+  const int stride = blockDim.x;
+  if (IR) {
+    float* y = reinterpret_cast<float*>(smem_raw) + threadIdx.x;
+    switch (t.order) {
+      case 1: solve_ir_column<1>(v, t, lane, lam, b, x, y, stride, tol, max_sweeps); break;
+      case 2: solve_ir_column<2>(v, t, lane, lam, b, x, y, stride, tol, max_sweeps); break;
+      case 3: solve_ir_column<3>(v, t, lane, lam, b, x, y, stride, tol, max_sweeps); break;
+      case 4: solve_ir_column<4>(v, t, lane, lam, b, x, y, stride, tol, max_sweeps); break;
+      case 5: solve_ir_column<5>(v, t, lane, lam, b, x, y, stride, tol, max_sweeps); break;
+      default: break;
+    }
+  } else {
+    double* y = reinterpret_cast<double*>(smem_raw) + threadIdx.x;
+    switch (t.order) {
+      case 1: solve_fp64_column<1>(v, t, lane, b, x, y, stride); break;
+      case 2: solve_fp64_column<2>(v, t, lane, b, x, y, stride); break;
+      case 3: solve_fp64_column<3>(v, t, lane, b, x, y, stride); break;
+      case 4: solve_fp64_column<4>(v, t, lane, b, x, y, stride); break;
+      case 5: solve_fp64_column<5>(v, t, lane, b, x, y, stride); break;
+      default: break;
+    }
+  }
+}
+
+// Threads per block for a per-thread shared-memory footprint of `bytes`.
+static int pick_block(int bytes, int max_blk) {
+  int blk = max_blk;
+  while (blk > kTile && bytes * blk > 200 * 1024) blk /= 2;
+  return blk;
+}
+
+void launch_solve(const DevView& v, hevi_precision prec, double lam, const double* b, double* x,
+                  double tol, int max_sweeps, int max_ylen, cudaStream_t st) {
+  const int esz = prec == HEVI_FP64 ? (int)sizeof(double) : (int)sizeof(float);
+  const int blk = pick_block(max_ylen * esz, 128), tiles_per_blk = blk / kTile;
+  const unsigned grid = (unsigned)((v.ntiles + tiles_per_blk - 1) / tiles_per_blk);
+  if (prec == HEVI_FP64) {
+    const int smem = max_ylen * blk * (int)sizeof(double);
+    cudaFuncSetAttribute(k_solve<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    k_solve<false><<<grid, blk, smem, st>>>(v, lam, b, x, tol, max_sweeps);
+  } else {
+    const int smem = max_ylen * blk * (int)sizeof(float);
+    cudaFuncSetAttribute(k_solve<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    k_solve<true><<<grid, blk, smem, st>>>(v, lam, b, x, tol, max_sweeps);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Operator applies (FP64): V(x) (App. A.2 with the reference subtracted) and
+// L(q0) x (Sec. 4.3.1).
+// ---------------------------------------------------------------------------
+template <int N>
+__device__ void apply_V_column(const DevView& v, const Col& c, const double* q, double* out,
+                               double scale_lq, const double* add, const double* sub) {
+  // out = add + V(q) - sub (add / sub may be null)
+  const Phys ph = v.ph;
+  const double* ref = v.ref + c.off;
+  const double* qc = q + c.off;
+  bool ok = true;
+  auto flux = [&](int I, double* f) {
+    const double rho = qc[3 * I], m = qc[3 * I + 1], Th = qc[3 * I + 2];
+    if (!(rho > 0.0) || !(Th > 0.0)) ok = false;
+    const double ir = 1.0 / rho;
+    f[0] = m;
+    f[1] = fma(m * m, ir, eos_perturbation(ph, Th, ref[3 * I + 2], ref[3 * I + 1]));
+    f[2] = Th * m * ir;
+  };
+  auto o = [&](int I, const double* D) {
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      const int64_t i = c.off + 3 * I + u;
+      double val;
+      if (u == 1 && (I == 0 || I == c.nz - 1))
+        val = 0.0;
+      else
+        val = (u == 1) ? -D[1] - ph.g * (qc[3 * I] - ref[3 * I]) : -D[u];
+      if (add) val += add[i];
+      if (sub) val -= sub[i];
+      out[i] = val;
+    }
+  };
+  element_pass<N>(c, c_tab.w[N], c_tab.wD[N], flux, o);
+  if (!ok) fail(v, c.col, HEVI_COL_BAD_INPUT);
+  (void)scale_lq;
+}
+
+template <int N>
+__device__ void apply_L_column(const DevView& v, const Col& c, const double* x, double* out) {
+  const double* lin = v.lin + c.off;
+  const double* xc = x + c.off;
+  const double g = v.ph.g;
+  auto flux = [&](int I, double* f) {
+    const double x0 = xc[3 * I], x1 = xc[3 * I + 1], x2 = xc[3 * I + 2];
+    const double wI = lin[3 * I], thI = lin[3 * I + 1], cI = lin[3 * I + 2];
+    f[0] = x1;
+    f[1] = fma(-wI * wI, x0, fma(2.0 * wI, x1, cI * x2));
+    f[2] = fma(-thI * wI, x0, fma(thI, x1, wI * x2));
+  };
+  auto o = [&](int I, const double* D) {
+    const int64_t a = c.off + 3 * I;
+    out[a] = -D[0];
+    out[a + 1] = (I == 0 || I == c.nz - 1) ? 0.0 : -D[1] - g * xc[3 * I];
+    out[a + 2] = -D[2];
+  };
+  element_pass<N>(c, c_tab.w[N], c_tab.wD[N], flux, o);
+}
+
+template <int N>
+__device__ void apply_dispatch(const DevView& v, const TileDesc& t, int lane, const double* x,
+                               double* y, int nonlinear) {
+  const Col c = make_col(v, t, lane, N);
+  if (nonlinear)
+    apply_V_column<N>(v, c, x, y, 0.0, nullptr, nullptr);
+  else
+    apply_L_column<N>(v, c, x, y);
+}
+
+__global__ void __launch_bounds__(128) k_apply(DevView v, const double* x, double* y, int nonlinear) {
+  const int warp = threadIdx.x / kTile, lane = threadIdx.x % kTile;
+  const int64_t tile = (int64_t)blockIdx.x * (blockDim.x / kTile) + warp;
+  if (tile >= v.ntiles) return;
+  const TileDesc t = v.tiles[tile];
+  if (lane >= t.count) return;
+  switch (t.order) {
+    case 1: apply_dispatch<1>(v, t, lane, x, y, nonlinear); break;
+    case 2: apply_dispatch<2>(v, t, lane, x, y, nonlinear); break;
+    case 3: apply_dispatch<3>(v, t, lane, x, y, nonlinear); break;
+    case 4: apply_dispatch<4>(v, t, lane, x, y, nonlinear); break;
+    case 5: apply_dispatch<5>(v, t, lane, x, y, nonlinear); break;
+    default: break;
+  }
+}
+
+void launch_apply(const DevView& v, const double* x, double* y, int nonlinear, cudaStream_t st) {
+  const int blk = 128, tiles_per_blk = blk / kTile;
+  k_apply<<<(unsigned)((v.ntiles + tiles_per_blk - 1) / tiles_per_blk), blk, 0, st>>>(v, x, y, nonlinear);
+}
+
+// Full right-hand side S(Q) = H + V(Q) of a stage value (Sec. 4.1, 4.3).
+template <int N>
+__device__ void apply_rhs_dispatch(const DevView& v, const TileDesc& t, int lane, const double* Q,
+                                   const double* H, double* S) {
+  const Col c = make_col(v, t, lane, N);
+  apply_V_column<N>(v, c, Q, S, 0.0, H, nullptr);
+}
+
+__global__ void __launch_bounds__(128) k_apply_rhs(DevView v, const double* Q, const double* H,
+                                                   double* S) {
+  const int warp = threadIdx.x / kTile, lane = threadIdx.x % kTile;
+  const int64_t tile = (int64_t)blockIdx.x * (blockDim.x / kTile) + warp;
+  if (tile >= v.ntiles) return;
+  const TileDesc t = v.tiles[tile];
+  if (lane >= t.count) return;
+  switch (t.order) {
+    case 1: apply_rhs_dispatch<1>(v, t, lane, Q, H, S); break;
+    case 2: apply_rhs_dispatch<2>(v, t, lane, Q, H, S); break;
+    case 3: apply_rhs_dispatch<3>(v, t, lane, Q, H, S); break;
+    case 4: apply_rhs_dispatch<4>(v, t, lane, Q, H, S); break;
+    case 5: apply_rhs_dispatch<5>(v, t, lane, Q, H, S); break;
+    default: break;
+  }
+}
+
+void launch_apply_rhs(const DevView& v, const double* Q, const double* H, double* S,
+                      cudaStream_t st) {
+  const int blk = 128, tiles_per_blk = blk / kTile;
+  k_apply_rhs<<<(unsigned)((v.ntiles + tiles_per_blk - 1) / tiles_per_blk), blk, 0, st>>>(v, Q, H, S);
+}
+
+// ARK stage tendencies of the LHEVI split (Sec. 4.3):
+//   LQ = L(q0) Q,   E = H + V(Q) - L Q.
+template <int N>
+__device__ void apply_stage_dispatch(const DevView& v, const TileDesc& t, int lane,
+                                     const double* Q, const double* H, double* E, double* LQ) {
+  const Col c = make_col(v, t, lane, N);
+  apply_L_column<N>(v, c, Q, LQ);
+  apply_V_column<N>(v, c, Q, E, 0.0, H, LQ);
+}
+
+__global__ void __launch_bounds__(128) k_apply_stage(DevView v, const double* Q, const double* H,
+                                                     double* E, double* LQ) {
+  const int warp = threadIdx.x / kTile, lane = threadIdx.x % kTile;
+  const int64_t tile = (int64_t)blockIdx.x * (blockDim.x / kTile) + warp;
+  if (tile >= v.ntiles) return;
+  const TileDesc t = v.tiles[tile];
+  if (lane >= t.count) return;
+  switch (t.order) {
+    case 1: apply_stage_dispatch<1>(v, t, lane, Q, H, E, LQ); break;
+    case 2: apply_stage_dispatch<2>(v, t, lane, Q, H, E, LQ); break;
+    case 3: apply_stage_dispatch<3>(v, t, lane, Q, H, E, LQ); break;
+    case 4: apply_stage_dispatch<4>(v, t, lane, Q, H, E, LQ); break;
+    case 5: apply_stage_dispatch<5>(v, t, lane, Q, H, E, LQ); break;
+    default: break;
+  }
+}
+
+void launch_apply_stage(const DevView& v, const double* Q, const double* H, double* E, double* LQ,
+                        int lin_rest, cudaStream_t st) {
+  const int blk = 128, tiles_per_blk = blk / kTile;
+  (void)lin_rest;
+  k_apply_stage<<<(unsigned)((v.ntiles + tiles_per_blk - 1) / tiles_per_blk), blk, 0, st>>>(
+      v, Q, H, E, LQ);
+}
+
+// ---------------------------------------------------------------------------
+// NHEVI-LU Newton solve (Sec. 4.2.3), one column per thread, fused:
+//   F(q) = q - Lambda V(q) - R (FP64), y = -S^-1 F (FP32);
+//   J(q) assembled from FP64 point coefficients, equilibrated, LU-factored in
+//   FP32 with the L part applied to y on the fly; U records to scratch;
+//   backward sweep; q += S y (FP64); repeat until
+//   |S^-1 F(q_m)| <= rtol |S^-1 F(q_0)| or max_iter updates.
+// ---------------------------------------------------------------------------
+template <int N>
+__device__ void newton_column(const DevView& v, const TileDesc& t, int lane, double lam, double* q,
+                              const double* R, double rtol, int max_iter, float* win, float* y,
+                              int stride) {
+  constexpr int K = Band<N>::K;
+  constexpr int UR2 = ((2 * K + 1) + 3) / 4 * 4;  // {1/u_jj, u_j,j+1 .. u_j,j+2K}
+  const Col c = make_col(v, t, lane, N);
+  const Phys ph = v.ph;
+  const double* ref = v.ref + c.off;
+  double* lin = v.lin + c.off;
+  double* qc = q + c.off;
+  const double* Rc = R + c.off;
+  const double cs = ph.cs;
+  float* scr = v.scr + t.scr_off;
+  auto urec = [&](int j, int e) -> float* {
+    return scr + ((int64_t)(j * (UR2 / 4) + e / 4) * kTile + lane) * 4 + (e & 3);
+  };
+  bool ok = true;
+
+  // F pass with the pending update q += S y (when `update`); returns |S^-1 F|.
+  auto fpass = [&](bool update) -> double {
+    double fn = 0.0;
+    auto flux = [&](int I, double* f) {
+      double qi[3];
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        const int i = 3 * I + u;
+        qi[u] = qc[i];
+        if (update) {
+          qi[u] += (double)y[i * stride] * ref_scale(ref, cs, 3 * I, u);
+          qc[i] = qi[u];
+        }
+      }
+      double w, th, cc, dP;
+      if (!lin_coefs(ph, qi[0], qi[1], qi[2], ref[3 * I + 2], ref[3 * I + 1], &w, &th, &cc, &dP)) {
+        ok = false;
+        w = th = cc = dP = 0.0;
+      }
+      lin[3 * I] = w;
+      lin[3 * I + 1] = th;
+      lin[3 * I + 2] = cc;
+      f[0] = qi[1];
+      f[1] = fma(qi[1], w, dP);
+      f[2] = qi[2] * w;
+    };
+    auto out = [&](int I, const double* D) {
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        const int i = 3 * I + u;
+        double F;
+        if (u == 1 && (I == 0 || I == c.nz - 1)) {
+          F = qc[i] - Rc[i];
+        } else {
+          // F = q - Lambda V - R,  V = -D - g (rho - rho_bar) e_m
+          double vterm = D[u];
+          if (u == 1) vterm = fma(ph.g, qc[3 * I] - ref[3 * I], vterm);
+          F = fma(lam, vterm, qc[i]) - Rc[i];
+        }
+        const double sF = F / ref_scale(ref, cs, 3 * I, u);
+        fn += sF * sF;
+        y[i * stride] = (float)(-sF);
+      }
+    };
+    element_pass<N>(c, c_tab.w[N], c_tab.wD[N], flux, out);
+    return sqrt(fn);
+  };
+
+  for (int i = c.n; i < c.n + 2 * K; ++i) y[i * stride] = 0.0f;
+  const double f0 = fpass(false);
+  int it = 0, status = HEVI_COL_OK;
+  if (!ok) status = HEVI_COL_BAD_INPUT;
+  if (ok && f0 > 0.0 && max_iter > 0) {
+    status = HEVI_COL_NOT_CONVERGED;
+    for (it = 1; it <= max_iter; ++it) {
+      // factor J(q_m) with the forward substitution applied to y on the fly
+      const int info = band_lu<N, float, true>(
+          v, c, lam, win, stride, [&](int j, const float* l, float invd, int p, auto&& U) {
+            float yj = y[j * stride];
+            if (p) {
+              const float tt = y[(j + p) * stride];
+              y[(j + p) * stride] = yj;
+              yj = tt;
+              y[j * stride] = yj;
+            }
+#pragma unroll
+            for (int r = 1; r <= K; ++r) y[(j + r) * stride] -= l[r - 1] * yj;
+            *urec(j, 0) = invd;
+#pragma unroll
+            for (int cc = 1; cc <= 2 * K; ++cc) *urec(j, cc) = U(cc);
+          });
+      if (info) {
+        status = HEVI_COL_SINGULAR;
+        break;
+      }
+      for (int j = c.n - 1; j >= 0; --j) {
+        float s = y[j * stride];
+#pragma unroll
+        for (int cc = 1; cc <= 2 * K; ++cc) s -= *urec(j, cc) * y[(j + cc) * stride];
+        y[j * stride] = s * *urec(j, 0);
+      }
+      const double fn = fpass(true);
+      if (!ok) {
+        status = HEVI_COL_BAD_INPUT;
+        break;
+      }
+      if (fn <= rtol * f0) {
+        status = HEVI_COL_OK;
+        break;
+      }
+    }
+    if (it > max_iter) it = max_iter;
+  }
+  v.col_iters[c.col] = it;
+  if (status != HEVI_COL_OK)
+    fail(v, c.col, status);
+  else
+    v.col_status[c.col] = HEVI_COL_OK;
+}
+
+__global__ void __launch_bounds__(64) k_newton(DevView v, double lam, double* q, const double* R,
+                                               double rtol, int max_iter, int win_slots) {
+  extern __shared__ unsigned char smem_raw[];
+  float* smem = reinterpret_cast<float*>(smem_raw);
+  const int warp = threadIdx.x / kTile, lane = threadIdx.x % kTile;
+  const int64_t tile = (int64_t)blockIdx.x * (blockDim.x / kTile) + warp;
+  if (tile >= v.ntiles) return;
+  const TileDesc t = v.tiles[tile];
+  if (lane >= t.count) return;
+  const int stride = blockDim.x;
+  float* win = smem + threadIdx.x;
+  float* y = smem + (int64_t)win_slots * stride + threadIdx.x;
+  switch (t.order) {
+    case 1: newton_column<1>(v, t, lane, lam, q, R, rtol, max_iter, win, y, stride); break;
+    case 2: newton_column<2>(v, t, lane, lam, q, R, rtol, max_iter, win, y, stride); break;
+    case 3: newton_column<3>(v, t, lane, lam, q, R, rtol, max_iter, win, y, stride); break;
+    case 4: newton_column<4>(v, t, lane, lam, q, R, rtol, max_iter, win, y, stride); break;
+    case 5: newton_column<5>(v, t, lane, lam, q, R, rtol, max_iter, win, y, stride); break;
+    default: break;
+  }
+}
+
+void launch_newton(const DevView& v, double lam, double* q, const double* R, double rtol,
+                   int max_iter, int max_order, int max_ylen, cudaStream_t st) {
+  const int slots = window_slots(max_order);
+  const int blk = pick_block((slots + max_ylen) * (int)sizeof(float), 64), tiles_per_blk = blk / kTile;
+  const int smem = (slots + max_ylen) * blk * (int)sizeof(float);
+  cudaFuncSetAttribute(k_newton, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  k_newton<<<(unsigned)((v.ntiles + tiles_per_blk - 1) / tiles_per_blk), blk, smem, st>>>(
+      v, lam, q, R, rtol, max_iter, slots);
+}
+
+// ---------------------------------------------------------------------------
+// out = base + sum_t coef[t] vec[t]  (ARK stage right-hand sides and update)
+// ---------------------------------------------------------------------------
+constexpr int kMaxTerms = 16;
+struct CombineArgs {
+  const double* vec[kMaxTerms];
+  double coef[kMaxTerms];
+  int n;
+};
+
+__global__ void k_combine(int64_t count, const double* base, CombineArgs a, double* out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double s = base ? base[i] : 0.0;
+    for (int t = 0; t < a.n; ++t) s = fma(a.coef[t], a.vec[t][i], s);
+    out[i] = s;
+  }
+}
+
+void launch_combine(int64_t count, const double* base, int nterms, const double* const* vec,
+                    const double* coef, double* out, cudaStream_t st) {
+  CombineArgs a;
+  a.n = nterms;
+  for (int t = 0; t < nterms && t < kMaxTerms; ++t) {
+    a.vec[t] = vec[t];
+    a.coef[t] = coef[t];
+  }
+  const int blk = 256;
+  int64_t grid = (count + blk - 1) / blk;
+  if (grid > 152 * 16) grid = 152 * 16;
+  if (grid < 1) grid = 1;
+  k_combine<<<(unsigned)grid, blk, 0, st>>>(count, base, a, out);
+}
+
+}  // namespace hevi

@@ -524,3 +524,32 @@ def test_nonlinear_wave_self_convergence(name, variant):
     errs = [np.linalg.norm(run(dt) - ref) / np.linalg.norm(ref - q0) for dt in (2.0, 1.0, 0.5)]
     rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
     assert min(rates) > tab.order - 0.4, (errs, rates)
+
+
+@pytest.mark.parametrize("name", ["ARK2", "ARK3"])
+def test_lhevi_ark_form_equals_direct_stage_form(name):
+    """Sec. 4.3: the ARK form (Eq. lhevi-ark-final-3, solving for q_tt) and the
+    direct stage form (I - gamma dt L) Q_i = q^n + dt sum_j [a_ij E(Q_j) +
+    at_ij L Q_j], E = H + V - L, give the same step (built here from the
+    oracle's stage solve and operator applies)."""
+    tab = tableaux.ALL[name]
+    nez, N, dt = 4, 4, 300.0
+    s = tab.s
+    qn = _perturbed_state(nez, N, seed=21, amp_w=3.0, amp_th=1.0)[None]
+    sc = oracle.scales(oracle.column_grid(nez, N, ZTOP)[0])
+    H = 1e-6 * sc[None] * np.random.default_rng(22).standard_normal(qn.shape)
+    H[0, 1] = H[0, -2] = 0.0
+    lam = tab.gamma * dt
+    Q, E, LQ = [qn], [], []
+    for i in range(s):
+        if i > 0:
+            rhs = qn + dt * sum(tab.A[i, j] * E[j] + tab.At[i, j] * LQ[j] for j in range(i))
+            Qi, info = oracle.stage_solve(nez, N, ZTOP, lam, qn, rhs)
+            Q.append(Qi)
+        LQ.append(oracle.apply_L(nez, N, ZTOP, qn, Q[i]))
+        E.append(H + oracle.apply_V(nez, N, ZTOP, Q[i]) - LQ[i])
+    direct = qn + dt * sum(tab.b[i] * (E[i] + LQ[i]) for i in range(s))
+    ark, info = oracle.lhevi_step(nez, N, ZTOP, tab, dt, qn, H, lin=0)
+    assert info[0] == 0
+    d = np.linalg.norm(ark - direct) / np.linalg.norm(direct - qn)
+    assert d < 1e-10, d
