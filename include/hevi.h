@@ -151,6 +151,39 @@ hevi_status hevi_newton_solve(hevi_ctx* ctx, double gamma_dt, double* state, con
 hevi_status hevi_newton_solve_async(hevi_ctx* ctx, double gamma_dt, double* state,
                                     const double* R, double rtol, int32_t max_iter);
 
+/* Newton solve for callers that cannot allocate device memory.
+ *
+ * Code that runs inside another framework's memory pool, holds an allocator
+ * lock, or lives in a plugin that must not touch the device heap cannot call
+ * cudaMalloc, and hevi_setup allocates.  This entry point needs no context
+ * and allocates nothing: it runs the Newton kernel of hevi_newton_solve on
+ * ncols uniform columns (nez elements of order `order`, model top z_top in
+ * metres, default reference constants) with every piece of scratch -- column
+ * table, reference state, linearisation coefficients and factor rows -- in
+ * one file-scope device array of 64 MiB that every GPU which loads this
+ * library holds until the process exits.  The paper has no counterpart; it
+ * is a deployment variant of NHEVI-LU (hevi_newton_solve).
+ *
+ * state (dev, in/out) and R (dev) use the state layout with columns packed
+ * back to back (column c at offset 3 (nez order + 1) c); status and iters
+ * (dev, ncols int32 each) receive the per-column status (HEVI_COL_*) and the
+ * number of Newton updates.  stream is a cudaStream_t (NULL = legacy default
+ * stream).  The call is blocking and returns the aggregated status.
+ *
+ * Limit: the scratch per column is about 3 n doubles plus n (2K+1) floats
+ * (n = 3 (nez order + 1), K = 3 (order + 1) - 1), e.g. about 4,000 columns
+ * of (16, 3) or (10, 4); larger ncols returns HEVI_ERR_INVALID_ARG.
+ *
+ * The first call on a device looks up the array's device address and copies
+ * the LGL tables to the device; make that first call before any stream
+ * capture.  All calls share the array and it keeps the last call's contents:
+ * calls that overlap on the GPU (other streams, other threads) race.  The
+ * failure counters in it are cleared by every call. */
+hevi_status hevi_newton_solve_noalloc(int32_t nez, int32_t order, double z_top, int64_t ncols,
+                                      double gamma_dt, double* state, const double* R,
+                                      double rtol, int32_t max_iter, int32_t* status,
+                                      int32_t* iters, void* stream);
+
 /* Vertical operator apply (App. A.2 / Sec. 4.3.1), x, y (dev, state layout):
  *   nonlinear != 0:  y = V(x);
  *   nonlinear == 0:  y = L(q0) x with q0 of the last hevi_factor. */

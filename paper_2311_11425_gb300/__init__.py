@@ -87,6 +87,8 @@ def load(build: bool = False):
         "hevi_launch_count": (_I64, [_P]),
         "hevi_status_string": (ctypes.c_char_p, [_I32]),
         "hevi_tableau": (_I32, [ctypes.c_char_p, ctypes.POINTER(_I32), DP, DP, DP]),
+        "hevi_newton_solve_noalloc": (_I32, [_I32, _I32, _D, _I64, _D, _P, _P, _D, _I32, _P, _P,
+                                             _P]),
         "hevi_profile": (_I32, [_P, _I32]),
         "hevi_profile_kinds": (_I32, []),
         "hevi_profile_kind_name": (ctypes.c_char_p, [_I32]),
@@ -149,6 +151,33 @@ def _darr(x):
     import numpy as np
     a = np.ascontiguousarray(x, dtype=np.float64).reshape(-1)
     return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def hevi_newton_solve_noalloc(nez, order, z_top, ncols, gamma_dt, state, R, status, iters,
+                              rtol=1e-10, max_iter=20, stream=None):
+    """Newton solve (NHEVI-LU) of `ncols` uniform columns that allocates no device
+    memory, for callers that cannot call cudaMalloc (inside another framework's
+    memory pool, under an allocator lock, or in a plugin that must not touch the
+    device heap).  All scratch lives in a fixed 64 MiB device array of the
+    library, shared by every call: calls that overlap on the GPU race.  state
+    (in/out), R: float64 CUDA tensors of 3 (nez order + 1) ncols entries; status,
+    iters: int32 CUDA tensors of ncols entries (outputs).  Raises HeviError
+    (INVALID_ARG) when the columns do not fit the scratch (about 4,000 columns
+    of (16, 3) or (10, 4))."""
+    import torch
+    lib = load()
+    n = 3 * (int(nez) * int(order) + 1) * int(ncols)
+    st = torch.cuda.current_stream() if stream is None else stream
+    code = lib.hevi_newton_solve_noalloc(
+        int(nez), int(order), float(z_top), int(ncols), float(gamma_dt),
+        _ptr(state, n, torch.float64), _ptr(R, n, torch.float64), float(rtol), int(max_iter),
+        _ptr(status, int(ncols), torch.int32), _ptr(iters, int(ncols), torch.int32),
+        ctypes.c_void_p(st.cuda_stream))
+    if code == 1:
+        raise HeviError(1, "hevi_newton_solve_noalloc (bad argument, or the columns do not fit "
+                           "the 64 MiB scratch array)")
+    _check(code, "hevi_newton_solve_noalloc")
+    return state
 
 
 class Context:

@@ -111,6 +111,13 @@ hevi::LglTables make_tables() {
 
 }  // namespace
 
+namespace hevi {
+const LglTables& lgl_tables() {
+  static const LglTables t = make_tables();
+  return t;
+}
+}  // namespace hevi
+
 struct hevi_ctx {
   DevView v{};
   hevi_precision prec = HEVI_FP64;

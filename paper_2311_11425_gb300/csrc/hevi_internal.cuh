@@ -179,5 +179,7 @@ void launch_combine(int64_t count, const double* base, int nterms, const double*
                     const double* coef, double* out, cudaStream_t st);
 void launch_reference_state(const DevView& v, double* q, cudaStream_t st);
 void upload_tables(const LglTables& t);
+// The LGL tables of every order (built once on the host, FP64).
+const LglTables& lgl_tables();
 
 }  // namespace hevi

@@ -1044,3 +1044,168 @@ void launch_combine(int64_t count, const double* base, int nterms, const double*
 }
 
 }  // namespace hevi
+
+// ---------------------------------------------------------------------------
+// Newton solve without any device allocation.
+//
+// For callers that cannot call cudaMalloc (code running inside another
+// framework's memory pool or allocator lock, or plugins that must not touch
+// the device heap), hevi_newton_solve_noalloc runs the same Newton kernel as
+// hevi_newton_solve with all of its scratch -- column table, reference
+// state, linearisation coefficients and the U records of the factorisation --
+// in one file-scope device array of kNoAllocBytes.  Every GPU that loads this
+// library holds that array until the process exits.  All calls share it and
+// it keeps the last call's contents, so calls that overlap on the GPU race;
+// the failure counters are cleared by every call.
+// ---------------------------------------------------------------------------
+namespace hevi {
+namespace {
+
+constexpr size_t kNoAllocBytes = 64ull << 20;  // 64 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kMaxDevices = 64;
+void* g_noalloc_ptr[kMaxDevices] = {nullptr};
+bool g_noalloc_tables[kMaxDevices] = {false};
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Fill the column table, tiles and reference state of `ncols` uniform
+// columns inside the scratch array, and clear the failure counters.
+__global__ void k_noalloc_init(DevView v, int order, int nez, double dz, int64_t n,
+                               TileDesc* tiles, int64_t* col_off, int32_t* perm, double* col_dz,
+                               int32_t* col_order, int32_t* col_nez) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i == 0) {
+    for (int k = 0; k < 4; ++k) v.fail_count[k] = 0;
+  }
+  if (i <= v.ncols) col_off[i] = i * n;
+  if (i < v.ncols) {
+    perm[i] = (int32_t)i;
+    col_dz[i] = dz;
+    col_order[i] = order;
+    col_nez[i] = nez;
+  }
+  if (i < v.ntiles) {
+    const int K = 3 * (order + 1) - 1;
+    const int ur2 = ((2 * K + 1) + 3) / 4 * 4;
+    TileDesc t;
+    t.order = order;
+    t.nez = nez;
+    t.first = (int32_t)(i * kTile);
+    t.count = (int32_t)min((int64_t)kTile, v.ncols - i * kTile);
+    t.fac_off = 0;
+    t.scr_off = i * n * ur2 * kTile;
+    tiles[i] = t;
+  }
+}
+
+}  // namespace
+}  // namespace hevi
+
+extern "C" hevi_status hevi_newton_solve_noalloc(int32_t nez, int32_t order, double z_top,
+                                                 int64_t ncols, double gamma_dt, double* state,
+                                                 const double* R, double rtol, int32_t max_iter,
+                                                 int32_t* status, int32_t* iters, void* stream) {
+  using namespace hevi;
+  if (nez < 1 || nez > 4096 || order < 1 || order > kMaxOrder || !(z_top > 0.0) || ncols < 1 ||
+      !state || !R || state == R || !status || !iters || !(gamma_dt >= 0.0) || !(rtol >= 0.0) ||
+      max_iter < 0 || max_iter > 1000)
+    return HEVI_ERR_INVALID_ARG;
+  const int64_t nz = (int64_t)nez * order + 1, n = 3 * nz;
+  const int K = 3 * (order + 1) - 1, ur2 = ((2 * K + 1) + 3) / 4 * 4;
+  const int64_t ntiles = (ncols + kTile - 1) / kTile;
+  // scratch layout: fail counters | tiles | col_off | perm | col_dz | order | nez | ref | lin |
+  // U records
+  size_t off = 0;
+  const size_t o_fail = off;
+  off = align256(off + 4 * sizeof(int32_t));
+  const size_t o_tiles = off;
+  off = align256(off + ntiles * sizeof(TileDesc));
+  const size_t o_off = off;
+  off = align256(off + (ncols + 1) * sizeof(int64_t));
+  const size_t o_perm = off;
+  off = align256(off + ncols * sizeof(int32_t));
+  const size_t o_dz = off;
+  off = align256(off + ncols * sizeof(double));
+  const size_t o_ord = off;
+  off = align256(off + ncols * sizeof(int32_t));
+  const size_t o_nez = off;
+  off = align256(off + ncols * sizeof(int32_t));
+  const size_t o_ref = off;
+  off = align256(off + ncols * n * sizeof(double));
+  const size_t o_lin = off;
+  off = align256(off + ncols * n * sizeof(double));
+  const size_t o_scr = off;
+  off = align256(off + ntiles * n * ur2 * kTile * sizeof(float));
+  if (off > kNoAllocBytes) return HEVI_ERR_INVALID_ARG;  // columns do not fit the scratch array
+
+  // once per device, with that device current: the device address of the
+  // scratch array and the LGL tables in constant memory
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return HEVI_ERR_CUDA;
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return HEVI_ERR_CUDA;
+    }
+    g_noalloc_ptr[dev] = p;
+  }
+  if (!g_noalloc_tables[dev]) {
+    upload_tables(lgl_tables());
+    if (cudaGetLastError() != cudaSuccess) return HEVI_ERR_CUDA;
+    g_noalloc_tables[dev] = true;
+  }
+  unsigned char* base = static_cast<unsigned char*>(g_noalloc_ptr[dev]);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+
+  DevView v{};
+  Phys ph;
+  ph.T0 = 300.0;
+  ph.p0 = 1.0e5;
+  ph.R = 287.17;
+  ph.cp = 1004.67;
+  ph.g = 9.80616;
+  ph.cv = ph.cp - ph.R;
+  ph.gamma = ph.cp / ph.cv;
+  ph.cs = sqrt(ph.gamma * ph.R * ph.T0);
+  v.ph = ph;
+  v.ncols = ncols;
+  v.ntiles = (int32_t)ntiles;
+  v.fail_count = reinterpret_cast<int32_t*>(base + o_fail);
+  TileDesc* tiles = reinterpret_cast<TileDesc*>(base + o_tiles);
+  int64_t* col_off = reinterpret_cast<int64_t*>(base + o_off);
+  int32_t* perm = reinterpret_cast<int32_t*>(base + o_perm);
+  double* col_dz = reinterpret_cast<double*>(base + o_dz);
+  v.tiles = tiles;
+  v.col_off = col_off;
+  v.perm = perm;
+  v.col_dz = col_dz;
+  v.ref = reinterpret_cast<double*>(base + o_ref);
+  v.lin = reinterpret_cast<double*>(base + o_lin);
+  v.scr = reinterpret_cast<float*>(base + o_scr);
+  v.fac = nullptr;
+  v.fac_status = nullptr;  // not used by the Newton kernel
+  v.col_status = status;
+  v.col_iters = iters;
+  const double dz = z_top / nez;
+  const int64_t items = ncols + 1 > ntiles ? ncols + 1 : ntiles;
+  int32_t* col_order = reinterpret_cast<int32_t*>(base + o_ord);
+  int32_t* col_nez = reinterpret_cast<int32_t*>(base + o_nez);
+  k_noalloc_init<<<(unsigned)((items + 127) / 128), 128, 0, st>>>(v, order, nez, dz, n, tiles,
+                                                                   col_off, perm, col_dz,
+                                                                   col_order, col_nez);
+  launch_setup_ref(v, col_order, col_nez, st);
+  launch_newton(v, gamma_dt, state, R, rtol, max_iter, order, (int)(n + 2 * K), st);
+  int32_t h_fail[4] = {0, 0, 0, 0};
+  if (cudaMemcpyAsync(h_fail, v.fail_count, sizeof(h_fail), cudaMemcpyDeviceToHost, st) !=
+      cudaSuccess)
+    return HEVI_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+    return HEVI_ERR_CUDA;
+  if (h_fail[0] == 0) return HEVI_OK;
+  if (h_fail[3]) return HEVI_ERR_BAD_INPUT;
+  if (h_fail[1]) return HEVI_ERR_SINGULAR;
+  return HEVI_ERR_NOT_CONVERGED;
+}
