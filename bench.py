@@ -382,15 +382,61 @@ def reference_arm(args, rank, world, pool, cores):
     print(json.dumps(line), flush=True)
 
 
+def ncu_case(args):
+    """A short run of one operation on the benchmark workload for targeted
+    ncu captures: setup, one warm-up step, then `--ncu-reps` launches of the
+    chosen operation (factor, solve, apply, newton or step)."""
+    import torch
+    import hevi_inputs
+    import paper_2311_11425_gb300 as hv
+    hv.load(build=True)
+    case = args.ncu_case
+    prec = hv.FP64 if args.ncu_fp64 else hv.FP32_IR
+    if case == "newton":
+        inp = hevi_inputs.nhevi_ark2(seed=3)
+        ctx = hv.Context([(inp["nez"], inp["N"])], inp["ztop"], precision=prec)
+        q0 = ctx.hevi_reference_state() + torch.from_numpy(inp["dq"].reshape(-1)).cuda()
+        for _ in range(args.ncu_reps):
+            q = q0.clone()
+            ctx.hevi_newton_solve(87.868, q, q0, blocking=False)
+        ctx.hevi_sync()
+        return
+    inp = hevi_inputs.lhevi_ark3(seed=2)
+    ctx = hv.Context([(NEZ, ORDER)], ZTOP, ncols=NCOLS, precision=prec)
+    tab = hv.tableau("ARK3")
+    H = torch.from_numpy(inp["H"].reshape(-1)).cuda()
+    qa = ctx.hevi_reference_state()
+    qb = torch.empty_like(qa)
+    ctx.hevi_lhevi_step(tab, DT, qa, H, qb)
+    lam = tab.gamma * DT
+    for _ in range(args.ncu_reps):
+        if case == "factor":
+            ctx.hevi_factor(lam, qb)
+        elif case == "solve":
+            ctx.hevi_stage_solve(H, qa, blocking=False)
+        elif case == "apply":
+            ctx.hevi_apply_Lv(qb, qa, nonlinear=True)
+        elif case == "step":
+            ctx.hevi_lhevi_step(tab, DT, qb, H, qa)
+    ctx.hevi_sync()
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--ncu-case", choices=["factor", "solve", "apply", "newton", "step"],
+                    help="run only a few launches of one operation (for ncu captures)")
+    ap.add_argument("--ncu-reps", type=int, default=2)
+    ap.add_argument("--ncu-fp64", action="store_true")
     args = ap.parse_args()
+    if args.ncu_case:
+        ncu_case(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

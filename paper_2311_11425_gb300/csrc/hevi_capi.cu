@@ -126,6 +126,9 @@ struct hevi_ctx {
   std::vector<int64_t> h_off;
   std::vector<TileDesc> h_tiles;
   int max_order = 0, max_ylen = 0;
+  // tiles of each order N occupy [order_begin[N], order_begin[N] + order_count[N])
+  int32_t order_begin[kMaxOrder + 1] = {0}, order_count[kMaxOrder + 1] = {0};
+  int order_ylen[kMaxOrder + 1] = {0};
   double lam = 0.0;
   bool factored = false;
   double ir_tol = 1e-12;
@@ -222,9 +225,23 @@ void fold_profile(hevi_ctx* c) {
   cudaGetLastError();
 }
 
-hevi_status check_launch(hevi_ctx* c, int n = 1) {
+hevi_status check_launch(hevi_ctx* c, int n = 0) {
   c->launches += n;
   return cudaGetLastError() == cudaSuccess ? HEVI_OK : HEVI_ERR_CUDA;
+}
+
+// Run f(view, order, ylen) for every order present, with the view's tile
+// range set to that order's tiles.
+template <class F>
+void for_orders(hevi_ctx* c, const DevView& base, F&& f) {
+  for (int N = 1; N <= kMaxOrder; ++N) {
+    if (!c->order_count[N]) continue;
+    DevView v = base;
+    v.tile_begin = c->order_begin[N];
+    v.tile_count = c->order_count[N];
+    f(v, N, c->order_ylen[N]);
+    c->launches += 1;
+  }
 }
 
 void reset_fail(hevi_ctx* c) {
@@ -336,7 +353,9 @@ hevi_status hevi_setup(hevi_ctx** out, const hevi_column_grid* grid, const hevi_
   // class-sorted permutation and tiles of 32 columns of one class
   std::vector<int32_t> perm(ncols);
   for (int64_t i = 0; i < ncols; ++i) perm[i] = (int32_t)i;
-  std::stable_sort(perm.begin(), perm.end(), [&](int32_t a, int32_t b) { return cls[a] < cls[b]; });
+  std::stable_sort(perm.begin(), perm.end(), [&](int32_t a, int32_t b) {
+    return order[a] != order[b] ? order[a] < order[b] : cls[a] < cls[b];
+  });
   int64_t fac_off = 0, scr_off = 0;
   const int esz = precision == HEVI_FP64 ? 8 : 4;
   for (int64_t i = 0; i < ncols;) {
@@ -353,10 +372,13 @@ hevi_status hevi_setup(hevi_ctx** out, const hevi_column_grid* grid, const hevi_
     const int64_t n = 3 * ((int64_t)t.nez * t.order + 1);
     fac_off += n * rl_of(t.order) * kTile;
     scr_off += n * ur2_of(t.order) * kTile;
+    if (c->order_count[t.order] == 0) c->order_begin[t.order] = (int32_t)c->h_tiles.size();
+    c->order_count[t.order] += 1;
     c->h_tiles.push_back(t);
     c->max_order = std::max(c->max_order, (int)t.order);
     const int K = 3 * (t.order + 1) - 1;
     c->max_ylen = std::max(c->max_ylen, (int)(n + 2 * K));
+    c->order_ylen[t.order] = std::max(c->order_ylen[t.order], (int)(n + 2 * K));
     i = j;
   }
   c->ntiles = (int64_t)c->h_tiles.size();
@@ -457,7 +479,7 @@ int64_t hevi_launch_count(const hevi_ctx* c) { return c ? c->launches : -1; }
 hevi_status hevi_reference_state(hevi_ctx* c, double* q) {
   if (!c || !q) return HEVI_ERR_INVALID_ARG;
   hevi::launch_reference_state(c->v, q, c->stream);
-  return check_launch(c);
+  return check_launch(c, 1);
 }
 
 hevi_status hevi_set_refinement(hevi_ctx* c, double tol, int32_t max_sweeps) {
@@ -471,7 +493,9 @@ hevi_status hevi_factor(hevi_ctx* c, double gamma_dt, const double* lin_state) {
   if (!c || !(gamma_dt >= 0.0) || !std::isfinite(gamma_dt)) return HEVI_ERR_INVALID_ARG;
   {
     Scope sc(c, kFactor);
-    hevi::launch_factor(c->v, c->prec, gamma_dt, lin_state, c->max_order, c->stream);
+    for_orders(c, c->v, [&](const DevView& v, int N, int) {
+      hevi::launch_factor(v, N, c->prec, gamma_dt, lin_state, c->stream);
+    });
   }
   c->lam = gamma_dt;
   c->factored = true;
@@ -482,7 +506,9 @@ hevi_status hevi_stage_solve_async(hevi_ctx* c, const double* rhs, double* x) {
   if (!c || !rhs || !x || rhs == x || !c->factored) return HEVI_ERR_INVALID_ARG;
   {
     Scope sc(c, kSolve);
-    hevi::launch_solve(c->v, c->prec, c->lam, rhs, x, c->ir_tol, c->ir_max, c->max_ylen, c->stream);
+    for_orders(c, c->v, [&](const DevView& v, int N, int ylen) {
+      hevi::launch_solve(v, N, c->prec, c->lam, rhs, x, c->ir_tol, c->ir_max, ylen, c->stream);
+    });
   }
   return check_launch(c);
 }
@@ -506,7 +532,9 @@ hevi_status hevi_newton_solve_async(hevi_ctx* c, double gamma_dt, double* state,
   nv.lin = c->lin_newton;
   {
     Scope sc(c, kNewton);
-    hevi::launch_newton(nv, gamma_dt, state, R, rtol, max_iter, c->max_order, c->max_ylen, c->stream);
+    for_orders(c, nv, [&](const DevView& v, int N, int ylen) {
+      hevi::launch_newton(v, N, gamma_dt, state, R, rtol, max_iter, ylen, c->stream);
+    });
   }
   return check_launch(c);
 }
@@ -525,7 +553,9 @@ hevi_status hevi_apply_Lv(hevi_ctx* c, const double* x, double* y, int nonlinear
   if (!nonlinear && !c->factored) return HEVI_ERR_INVALID_ARG;
   {
     Scope sc(c, kApply);
-    hevi::launch_apply(c->v, x, y, nonlinear, c->stream);
+    for_orders(c, c->v, [&](const DevView& v, int N, int) {
+      hevi::launch_apply(v, N, x, y, nonlinear, c->stream);
+    });
   }
   return check_launch(c);
 }
@@ -613,9 +643,10 @@ hevi_status hevi_lhevi_step(hevi_ctx* c, int32_t s, const double* A, const doubl
   if ((st = hevi_factor(c, lam, lin_about_rest ? nullptr : q_in))) return st;
   {
     Scope sc(c, kApply);
-    hevi::launch_apply_rhs(c->v, q_in, H, S, c->stream);
+    for_orders(c, c->v, [&](const DevView& v, int N, int) {
+      hevi::launch_apply_rhs(v, N, q_in, H, S, c->stream);
+    });
   }
-  c->launches += 1;
   for (int i = 1; i < s; ++i) {
     const double* vec[16];
     double coef[16];
@@ -633,7 +664,9 @@ hevi_status hevi_lhevi_step(hevi_ctx* c, int32_t s, const double* A, const doubl
     }
     {
       Scope sc(c, kSolve);
-      hevi::launch_solve(c->v, c->prec, lam, rhs, Qi, c->ir_tol, c->ir_max, c->max_ylen, c->stream);
+      for_orders(c, c->v, [&](const DevView& v, int N, int ylen) {
+        hevi::launch_solve(v, N, c->prec, lam, rhs, Qi, c->ir_tol, c->ir_max, ylen, c->stream);
+      });
     }
     nt = 0;
     for (int j = 0; j < i; ++j) {
@@ -646,9 +679,11 @@ hevi_status hevi_lhevi_step(hevi_ctx* c, int32_t s, const double* A, const doubl
     }
     {
       Scope sc(c, kApply);
-      hevi::launch_apply_rhs(c->v, Qi, H, S + i * n, c->stream);
+      for_orders(c, c->v, [&](const DevView& v, int N, int) {
+        hevi::launch_apply_rhs(v, N, Qi, H, S + i * n, c->stream);
+      });
     }
-    c->launches += 4;
+    c->launches += 2;  // the two combines
   }
   {
     const double* vec[16];
@@ -682,10 +717,11 @@ hevi_status hevi_nhevi_step(hevi_ctx* c, int32_t s, const double* A, const doubl
   const double lam = At[1 * s + 1] * dt;
   {
     Scope sc(c, kApply);
-    hevi::launch_apply(c->v, q_in, VQ, 1, c->stream);
+    for_orders(c, c->v, [&](const DevView& v, int N, int) {
+      hevi::launch_apply(v, N, q_in, VQ, 1, c->stream);
+    });
   }
   cudaMemcpyAsync(Q, q_in, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
-  c->launches += 1;
   DevView nv = c->v;
   nv.lin = c->lin_newton;
   for (int i = 1; i < s; ++i) {
@@ -706,13 +742,17 @@ hevi_status hevi_nhevi_step(hevi_ctx* c, int32_t s, const double* A, const doubl
     }
     {
       Scope sc(c, kNewton);
-      hevi::launch_newton(nv, lam, Q, R, rtol, max_iter, c->max_order, c->max_ylen, c->stream);
+      for_orders(c, nv, [&](const DevView& v, int N, int ylen) {
+        hevi::launch_newton(v, N, lam, Q, R, rtol, max_iter, ylen, c->stream);
+      });
     }
     {
       Scope sc(c, kApply);
-      hevi::launch_apply(c->v, Q, VQ + i * n, 1, c->stream);
+      for_orders(c, c->v, [&](const DevView& v, int N, int) {
+        hevi::launch_apply(v, N, Q, VQ + i * n, 1, c->stream);
+      });
     }
-    c->launches += 3;
+    c->launches += 1;  // the combine
   }
   {
     const double* vec[16];

@@ -16,17 +16,19 @@ constexpr int kMaxOrder = 5;
 constexpr int kTile = 32;  // columns per tile (one warp, one column per lane)
 
 // Band sizes and factor record layout for order N.  Per pivot step j a
-// column stores an L record {l_1..l_K, 1/u_jj, pivot offset} padded to a
-// multiple of 4 and a U record {u_j,j+1 .. u_j,j+2K} padded to a multiple of
-// 4 (partial pivoting fills U to k_l + k_u super-diagonals).
+// column stores a forward record F_j = {l_1..l_K, pivot offset, 1/u_jj}
+// (unit-lower multipliers of Sec. 4.2.3's band LU, dgbtrf semantics) and a
+// backward record B_j = {U[j-1][j], U[j-2][j], .., U[j-2K][j]}, column j of U
+// above the diagonal (partial pivoting fills U to k_l + k_u = 2K
+// super-diagonals); both padded to a multiple of 4.
 template <int N>
 struct Band {
   static constexpr int K = 3 * (N + 1) - 1;
-  static constexpr int WR = K + 1;          // active window rows
-  static constexpr int WC = 2 * K + 1;      // active window columns
-  static constexpr int LR = ((K + 2) + 3) / 4 * 4;
-  static constexpr int UR = ((2 * K) + 3) / 4 * 4;
-  static constexpr int RL = LR + UR;        // record length per pivot step
+  static constexpr int WR = K + 1;          // active window rows (forward window)
+  static constexpr int WC = 2 * K + 1;      // active window columns (backward window)
+  static constexpr int FR = ((K + 2) + 3) / 4 * 4;
+  static constexpr int BR = ((2 * K) + 3) / 4 * 4;
+  static constexpr int RL = FR + BR;        // record length per pivot step
 };
 
 // Physical constants of the isothermal reference atmosphere.
@@ -65,6 +67,8 @@ struct DevView {
   double* lin;              // state layout: (w0, theta0, c0 = gamma P0 / Theta0)
   const TileDesc* tiles;
   int32_t ntiles;
+  int32_t tile_begin;       // tiles [tile_begin, tile_begin + tile_count) of one order
+  int32_t tile_count;
   void* fac;                // factor records (float or double)
   float* scr;               // Newton scratch (U records)
   int32_t* fac_status;      // [ncols] status of the last factorisation
@@ -164,17 +168,20 @@ __device__ __forceinline__ double eos_perturbation(const Phys& ph, double Theta,
 // Launch helpers (host side, defined in hevi_kernels.cu).
 void launch_setup_ref(const DevView& v, const int32_t* col_order, const int32_t* col_nez,
                       cudaStream_t st);
-void launch_factor(const DevView& v, hevi_precision prec, double lam, const double* q0,
-                   int max_order_present, cudaStream_t st);
-void launch_solve(const DevView& v, hevi_precision prec, double lam, const double* b, double* x,
-                  double tol, int max_sweeps, int max_ylen, cudaStream_t st);
-void launch_apply(const DevView& v, const double* x, double* y, int nonlinear, cudaStream_t st);
-void launch_apply_stage(const DevView& v, const double* Q, const double* H, double* E, double* LQ,
-                        int lin_rest, cudaStream_t st);
-void launch_apply_rhs(const DevView& v, const double* Q, const double* H, double* S,
+// The column launchers below process the tiles [v.tile_begin, v.tile_begin +
+// v.tile_count), all of order `order`; ylen is the longest n + 2K among them.
+void launch_factor(const DevView& v, int order, hevi_precision prec, double lam, const double* q0,
+                   cudaStream_t st);
+void launch_solve(const DevView& v, int order, hevi_precision prec, double lam, const double* b,
+                  double* x, double tol, int max_sweeps, int ylen, cudaStream_t st);
+void launch_apply(const DevView& v, int order, const double* x, double* y, int nonlinear,
+                  cudaStream_t st);
+void launch_apply_stage(const DevView& v, int order, const double* Q, const double* H, double* E,
+                        double* LQ, cudaStream_t st);
+void launch_apply_rhs(const DevView& v, int order, const double* Q, const double* H, double* S,
                       cudaStream_t st);
-void launch_newton(const DevView& v, double lam, double* q, const double* R, double rtol,
-                   int max_iter, int max_order, int max_ylen, cudaStream_t st);
+void launch_newton(const DevView& v, int order, double lam, double* q, const double* R,
+                   double rtol, int max_iter, int ylen, cudaStream_t st);
 void launch_combine(int64_t count, const double* base, int nterms, const double* const* vec,
                     const double* coef, double* out, cudaStream_t st);
 void launch_reference_state(const DevView& v, double* q, cudaStream_t st);

@@ -34,16 +34,19 @@ struct Vec<double> {
   static constexpr int W = 2;
 };
 
+// A tile's records: the F block (n steps x FR values x 32 lanes) followed by
+// the B block (n steps x BR values x 32 lanes), each [j][vector][lane][W].
 template <int N, typename T>
-__device__ __forceinline__ T* record_vec(T* tile_base, int j, int e, int lane) {
+__device__ __forceinline__ T* frec_vec(T* tile_base, int j, int e, int lane) {
   constexpr int W = Vec<T>::W;
-  constexpr int NV = Band<N>::RL / W;
+  constexpr int NV = Band<N>::FR / W;
   return tile_base + ((int64_t)(j * NV + e / W) * kTile + lane) * W;
 }
-
 template <int N, typename T>
-__device__ __forceinline__ const T* record_ptr(const T* tile_base, int j, int e, int lane) {
-  return record_vec<N, T>(const_cast<T*>(tile_base), j, e, lane) + (e % Vec<T>::W);
+__device__ __forceinline__ T* brec_vec(T* tile_base, int n, int j, int e, int lane) {
+  constexpr int W = Vec<T>::W;
+  constexpr int NV = Band<N>::BR / W;
+  return tile_base + (int64_t)n * Band<N>::FR * kTile + ((int64_t)(j * NV + e / W) * kTile + lane) * W;
 }
 
 // Record a per-column failure; counters: [0] any, [1] singular, [2] not
@@ -319,7 +322,7 @@ __device__ int band_lu(const DevView& v, const Col& c, double lam, T* win, int s
 template <int N, typename T, bool SCALED>
 __device__ void factor_column(const DevView& v, const TileDesc& t, int lane, double lam,
                               const double* q0, T* win, int stride) {
-  constexpr int K = Band<N>::K, LR = Band<N>::LR, UR = Band<N>::UR;
+  constexpr int K = Band<N>::K;
   constexpr int W = Vec<T>::W;
   using V = typename Vec<T>::type;
   const Col c = make_col(v, t, lane, N);
@@ -343,33 +346,35 @@ __device__ void factor_column(const DevView& v, const TileDesc& t, int lane, dou
     v.lin[a + 2] = cc;
   }
   T* base = reinterpret_cast<T*>(v.fac) + t.fac_off;
+  constexpr int FR = Band<N>::FR;
+  const int n = c.n;
   const int info = band_lu<N, T, SCALED>(
       v, c, lam, win, stride, [&](int j, const T* l, T invd, int p, auto&& U) {
-        T rec[LR];
+        // forward record {l_1..l_K, p, 1/u_jj}
+        T rec[FR];
 #pragma unroll
         for (int r = 0; r < K; ++r) rec[r] = l[r];
-        rec[K] = invd;
-        rec[K + 1] = T(p);
+        rec[K] = T(p);
+        rec[K + 1] = invd;
 #pragma unroll
-        for (int r = K + 2; r < LR; ++r) rec[r] = T(0);
+        for (int r = K + 2; r < FR; ++r) rec[r] = T(0);
 #pragma unroll
-        for (int q = 0; q < LR; q += W) {
-          V* dst = reinterpret_cast<V*>(record_vec<N, T>(base, j, q, lane));
+        for (int q = 0; q < FR; q += W) {
+          V* dst = reinterpret_cast<V*>(frec_vec<N, T>(base, j, q, lane));
           if constexpr (W == 4)
             *dst = make_float4(rec[q], rec[q + 1], rec[q + 2], rec[q + 3]);
           else
             *dst = make_double2(rec[q], rec[q + 1]);
         }
-        T ur[UR];
+        // row j of U goes to the backward records of columns j+1..j+2K
 #pragma unroll
-        for (int cc = 0; cc < UR; ++cc) ur[cc] = (cc < 2 * K) ? U(cc + 1) : T(0);
+        for (int cc = 1; cc <= 2 * K; ++cc) {
+          if (j + cc < n) brec_vec<N, T>(base, n, j + cc, cc - 1, lane)[(cc - 1) % W] = U(cc);
+        }
+        // entries of B_j that no row reaches (rows j-c < 0) and the padding
 #pragma unroll
-        for (int q = 0; q < UR; q += W) {
-          V* dst = reinterpret_cast<V*>(record_vec<N, T>(base, j, LR + q, lane));
-          if constexpr (W == 4)
-            *dst = make_float4(ur[q], ur[q + 1], ur[q + 2], ur[q + 3]);
-          else
-            *dst = make_double2(ur[q], ur[q + 1]);
+        for (int cc = 1; cc <= Band<N>::BR; ++cc) {
+          if (cc > j || cc > 2 * K) brec_vec<N, T>(base, n, j, cc - 1, lane)[(cc - 1) % W] = T(0);
         }
       });
   int st = HEVI_COL_OK;
@@ -385,110 +390,148 @@ __device__ void factor_column(const DevView& v, const TileDesc& t, int lane, dou
   v.col_iters[c.col] = 0;
 }
 
-template <typename T, bool SCALED>
+template <int N, typename T, bool SCALED>
 __global__ void __launch_bounds__(64) k_factor(DevView v, double lam, const double* q0) {
   extern __shared__ unsigned char smem_raw[];
   T* smem = reinterpret_cast<T*>(smem_raw);
   const int warp = threadIdx.x / kTile, lane = threadIdx.x % kTile;
-  const int64_t tile = (int64_t)blockIdx.x * (blockDim.x / kTile) + warp;
-  if (tile >= v.ntiles) return;
+  const int64_t tile = v.tile_begin + (int64_t)blockIdx.x * (blockDim.x / kTile) + warp;
+  if (tile >= (int64_t)v.tile_begin + v.tile_count) return;
   const TileDesc t = v.tiles[tile];
   if (lane >= t.count) return;
   T* win = smem + threadIdx.x;
   const int stride = blockDim.x;
-  switch (t.order) {
-    case 1: factor_column<1, T, SCALED>(v, t, lane, lam, q0, win, stride); break;
-    case 2: factor_column<2, T, SCALED>(v, t, lane, lam, q0, win, stride); break;
-    case 3: factor_column<3, T, SCALED>(v, t, lane, lam, q0, win, stride); break;
-    case 4: factor_column<4, T, SCALED>(v, t, lane, lam, q0, win, stride); break;
-    case 5: factor_column<5, T, SCALED>(v, t, lane, lam, q0, win, stride); break;
-    default: break;
-  }
+  factor_column<N, T, SCALED>(v, t, lane, lam, q0, win, stride);
 }
 
 static int pick_block(int bytes, int max_blk);
+static unsigned col_grid(const DevView& v, int blk);
 static int window_slots(int N) {
   const int K = 3 * (N + 1) - 1;
   return (K + 1) * (2 * K + 1);
 }
 
-void launch_factor(const DevView& v, hevi_precision prec, double lam, const double* q0,
-                   int max_order, cudaStream_t st) {
+template <int N>
+static void launch_factor_n(const DevView& v, hevi_precision prec, double lam, const double* q0,
+                            cudaStream_t st) {
   const int esz = prec == HEVI_FP64 ? (int)sizeof(double) : (int)sizeof(float);
-  const int blk = pick_block(window_slots(max_order) * esz, 64), tiles_per_blk = blk / kTile;
-  const unsigned grid = (unsigned)((v.ntiles + tiles_per_blk - 1) / tiles_per_blk);
+  const int blk = pick_block(window_slots(N) * esz, 64), tiles_per_blk = blk / kTile;
+  const unsigned grid = (unsigned)((v.tile_count + tiles_per_blk - 1) / tiles_per_blk);
+  const int smem = window_slots(N) * blk * esz;
   if (prec == HEVI_FP64) {
-    const int smem = window_slots(max_order) * blk * (int)sizeof(double);
-    cudaFuncSetAttribute(k_factor<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    k_factor<double, false><<<grid, blk, smem, st>>>(v, lam, q0);
+    cudaFuncSetAttribute(k_factor<N, double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    k_factor<N, double, false><<<grid, blk, smem, st>>>(v, lam, q0);
   } else {
-    const int smem = window_slots(max_order) * blk * (int)sizeof(float);
-    cudaFuncSetAttribute(k_factor<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    k_factor<float, true><<<grid, blk, smem, st>>>(v, lam, q0);
+    cudaFuncSetAttribute(k_factor<N, float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    k_factor<N, float, true><<<grid, blk, smem, st>>>(v, lam, q0);
+  }
+}
+
+void launch_factor(const DevView& v, int order, hevi_precision prec, double lam, const double* q0,
+                   cudaStream_t st) {
+  switch (order) {
+    case 1: launch_factor_n<1>(v, prec, lam, q0, st); break;
+    case 2: launch_factor_n<2>(v, prec, lam, q0, st); break;
+    case 3: launch_factor_n<3>(v, prec, lam, q0, st); break;
+    case 4: launch_factor_n<4>(v, prec, lam, q0, st); break;
+    case 5: launch_factor_n<5>(v, prec, lam, q0, st); break;
+    default: break;
   }
 }
 
 // ---------------------------------------------------------------------------
 // Triangular solves with the records of one column (dgbtrs semantics:
 // interchanges and unit-lower multipliers in factorisation order, then the
-// upper triangle with 2K super-diagonals).  y is the thread's slice of shared
-// memory (stride = threads per block), length n + 2K (tail kept at zero).
+// upper triangle with 2K super-diagonals, column by column).  The active
+// window of the sweep lives in registers: the loop over pivot steps is
+// unrolled by the window length so that every ring position is a
+// compile-time register.  y is the thread's slice of shared memory (stride =
+// threads per block), length n + 2K with a zero tail; the forward sweep
+// leaves the intermediate vector in y, the backward sweep the solution.
 // ---------------------------------------------------------------------------
-template <int N, typename T, typename Y>
-__device__ __forceinline__ void forward_sweep(const T* base, int lane, int n, Y* y, int stride) {
-  constexpr int K = Band<N>::K, LR = Band<N>::LR;
+template <int N, typename T>
+__device__ __forceinline__ void load_vecs(const T* src, T* dst, int count) {
   constexpr int W = Vec<T>::W;
   using V = typename Vec<T>::type;
-  for (int j = 0; j < n; ++j) {
-    T rec[LR];
 #pragma unroll
-    for (int q = 0; q < LR; q += W) {
-      const V x = *reinterpret_cast<const V*>(record_vec<N, T>(const_cast<T*>(base), j, q, lane));
-      if constexpr (W == 4) {
-        rec[q] = x.x; rec[q + 1] = x.y; rec[q + 2] = x.z; rec[q + 3] = x.w;
-      } else {
-        rec[q] = x.x; rec[q + 1] = x.y;
-      }
+  for (int q = 0; q < count; q += W) {
+    const V x = *reinterpret_cast<const V*>(src + (int64_t)(q / W) * kTile * W);
+    if constexpr (W == 4) {
+      dst[q] = x.x; dst[q + 1] = x.y; dst[q + 2] = x.z; dst[q + 3] = x.w;
+    } else {
+      dst[q] = x.x; dst[q + 1] = x.y;
     }
-    const int p = (int)rec[K + 1];
-    Y yj = y[j * stride];
-    if (p) {
-      const Y t = y[(j + p) * stride];
-      y[(j + p) * stride] = yj;
-      yj = t;
-      y[j * stride] = yj;
-    }
-#pragma unroll
-    for (int r = 1; r <= K; ++r) y[(j + r) * stride] -= Y(rec[r - 1]) * yj;
   }
 }
 
-// Backward substitution; returns sum of squares of the solution (for IR).
 template <int N, typename T, typename Y>
-__device__ __forceinline__ Y backward_sweep(const T* base, int lane, int n, Y* y, int stride) {
-  constexpr int K = Band<N>::K, LR = Band<N>::LR, UR = Band<N>::UR;
-  constexpr int W = Vec<T>::W;
-  using V = typename Vec<T>::type;
-  Y ss = Y(0);
-  for (int j = n - 1; j >= 0; --j) {
-    T u[UR];
+__device__ __forceinline__ void forward_sweep(const T* base, int lane, int n, Y* y, int stride) {
+  constexpr int K = Band<N>::K, WR = Band<N>::WR, FR = Band<N>::FR;
+  Y w[WR];
 #pragma unroll
-    for (int q = 0; q < UR; q += W) {
-      const V x = *reinterpret_cast<const V*>(record_vec<N, T>(const_cast<T*>(base), j, LR + q, lane));
-      if constexpr (W == 4) {
-        u[q] = x.x; u[q + 1] = x.y; u[q + 2] = x.z; u[q + 3] = x.w;
-      } else {
-        u[q] = x.x; u[q + 1] = x.y;
+  for (int r = 0; r < WR; ++r) w[r] = y[r * stride];
+  for (int j0 = 0; j0 < n; j0 += WR) {
+#pragma unroll
+    for (int t = 0; t < WR; ++t) {
+      const int j = j0 + t;
+      if (j < n) {
+        T f[FR];
+        load_vecs<N, T>(frec_vec<N, T>(const_cast<T*>(base), j, 0, lane), f, FR);
+        const int p = (int)f[K];
+        // interchange rows j and j+p, then eliminate below the pivot
+        Y yp = w[t];
+#pragma unroll
+        for (int r = 1; r <= K; ++r)
+          if (p == r) yp = w[(t + r) % WR];
+#pragma unroll
+        for (int r = 1; r <= K; ++r)
+          if (p == r) w[(t + r) % WR] = w[t];
+        y[j * stride] = yp;
+#pragma unroll
+        for (int r = 1; r <= K; ++r) w[(t + r) % WR] -= Y(f[r - 1]) * yp;
+        w[t] = y[(j + WR) * stride];
       }
     }
-    const T invd = *record_ptr<N, T>(base, j, K, lane);
-    Y s = y[j * stride];
-#pragma unroll
-    for (int cc = 1; cc <= 2 * K; ++cc) s -= Y(u[cc - 1]) * y[(j + cc) * stride];
-    s *= Y(invd);
-    y[j * stride] = s;
-    ss += s * s;
   }
+}
+
+// Backward substitution; returns the sum of squares of the solution.
+template <int N, typename T, typename Y>
+__device__ __forceinline__ Y backward_sweep(const T* base, int lane, int n, Y* y, int stride) {
+  constexpr int K = Band<N>::K, WB = Band<N>::WC, BR = Band<N>::BR, FR = Band<N>::FR;
+  constexpr int W = Vec<T>::W;
+  using V = typename Vec<T>::type;
+  Y w[WB];
+#pragma unroll
+  for (int cc = 0; cc < WB; ++cc) {
+    const int i = n - 1 - cc;
+    w[cc] = i >= 0 ? y[i * stride] : Y(0);
+  }
+  Y ss = Y(0);
+  for (int j0 = n - 1; j0 >= 0; j0 -= WB) {
+#pragma unroll
+    for (int t = 0; t < WB; ++t) {
+      const int j = j0 - t;
+      if (j >= 0) {
+        T u[BR];
+        load_vecs<N, T>(brec_vec<N, T>(const_cast<T*>(base), n, j, 0, lane), u, BR);
+        const V dv = *reinterpret_cast<const V*>(frec_vec<N, T>(const_cast<T*>(base), j, K + 1, lane));
+        T invd;
+        if constexpr (W == 4)
+          invd = ((K + 1) % 4 == 0) ? dv.x : ((K + 1) % 4 == 1) ? dv.y : ((K + 1) % 4 == 2) ? dv.z : dv.w;
+        else
+          invd = ((K + 1) % 2 == 0) ? dv.x : dv.y;
+        const Y x = w[t] * Y(invd);
+        y[j * stride] = x;
+        ss += x * x;
+#pragma unroll
+        for (int cc = 1; cc <= 2 * K; ++cc) w[(t + cc) % WB] -= Y(u[cc - 1]) * x;
+        const int jn = j - WB;
+        w[t] = jn >= 0 ? y[jn * stride] : Y(0);
+      }
+    }
+  }
+  (void)FR;
   return ss;
 }
 
@@ -637,36 +680,22 @@ __device__ void solve_ir_column(const DevView& v, const TileDesc& t, int lane, d
     v.col_status[c.col] = HEVI_COL_OK;
 }
 
-template <bool IR>
+template <int N, bool IR>
 __global__ void __launch_bounds__(128) k_solve(DevView v, double lam, const double* b, double* x,
                                                double tol, int max_sweeps) {
   extern __shared__ unsigned char smem_raw[];
   const int warp = threadIdx.x / kTile, lane = threadIdx.x % kTile;
-  const int64_t tile = (int64_t)blockIdx.x * (blockDim.x / kTile) + warp;
-  if (tile >= v.ntiles) return;
+  const int64_t tile = v.tile_begin + (int64_t)blockIdx.x * (blockDim.x / kTile) + warp;
+  if (tile >= (int64_t)v.tile_begin + v.tile_count) return;
   const TileDesc t = v.tiles[tile];
   if (lane >= t.count) return;
   const int stride = blockDim.x;
   if (IR) {
     float* y = reinterpret_cast<float*>(smem_raw) + threadIdx.x;
-    switch (t.order) {
-      case 1: solve_ir_column<1>(v, t, lane, lam, b, x, y, stride, tol, max_sweeps); break;
-      case 2: solve_ir_column<2>(v, t, lane, lam, b, x, y, stride, tol, max_sweeps); break;
-      case 3: solve_ir_column<3>(v, t, lane, lam, b, x, y, stride, tol, max_sweeps); break;
-      case 4: solve_ir_column<4>(v, t, lane, lam, b, x, y, stride, tol, max_sweeps); break;
-      case 5: solve_ir_column<5>(v, t, lane, lam, b, x, y, stride, tol, max_sweeps); break;
-      default: break;
-    }
+    solve_ir_column<N>(v, t, lane, lam, b, x, y, stride, tol, max_sweeps);
   } else {
     double* y = reinterpret_cast<double*>(smem_raw) + threadIdx.x;
-    switch (t.order) {
-      case 1: solve_fp64_column<1>(v, t, lane, b, x, y, stride); break;
-      case 2: solve_fp64_column<2>(v, t, lane, b, x, y, stride); break;
-      case 3: solve_fp64_column<3>(v, t, lane, b, x, y, stride); break;
-      case 4: solve_fp64_column<4>(v, t, lane, b, x, y, stride); break;
-      case 5: solve_fp64_column<5>(v, t, lane, b, x, y, stride); break;
-      default: break;
-    }
+    solve_fp64_column<N>(v, t, lane, b, x, y, stride);
   }
 }
 
@@ -677,19 +706,31 @@ static int pick_block(int bytes, int max_blk) {
   return blk;
 }
 
-void launch_solve(const DevView& v, hevi_precision prec, double lam, const double* b, double* x,
-                  double tol, int max_sweeps, int max_ylen, cudaStream_t st) {
+template <int N>
+static void launch_solve_n(const DevView& v, hevi_precision prec, double lam, const double* b,
+                           double* x, double tol, int max_sweeps, int ylen, cudaStream_t st) {
   const int esz = prec == HEVI_FP64 ? (int)sizeof(double) : (int)sizeof(float);
-  const int blk = pick_block(max_ylen * esz, 128), tiles_per_blk = blk / kTile;
-  const unsigned grid = (unsigned)((v.ntiles + tiles_per_blk - 1) / tiles_per_blk);
+  const int blk = pick_block(ylen * esz, 128), tiles_per_blk = blk / kTile;
+  const unsigned grid = (unsigned)((v.tile_count + tiles_per_blk - 1) / tiles_per_blk);
+  const int smem = ylen * blk * esz;
   if (prec == HEVI_FP64) {
-    const int smem = max_ylen * blk * (int)sizeof(double);
-    cudaFuncSetAttribute(k_solve<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    k_solve<false><<<grid, blk, smem, st>>>(v, lam, b, x, tol, max_sweeps);
+    cudaFuncSetAttribute(k_solve<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    k_solve<N, false><<<grid, blk, smem, st>>>(v, lam, b, x, tol, max_sweeps);
   } else {
-    const int smem = max_ylen * blk * (int)sizeof(float);
-    cudaFuncSetAttribute(k_solve<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    k_solve<true><<<grid, blk, smem, st>>>(v, lam, b, x, tol, max_sweeps);
+    cudaFuncSetAttribute(k_solve<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    k_solve<N, true><<<grid, blk, smem, st>>>(v, lam, b, x, tol, max_sweeps);
+  }
+}
+
+void launch_solve(const DevView& v, int order, hevi_precision prec, double lam, const double* b,
+                  double* x, double tol, int max_sweeps, int ylen, cudaStream_t st) {
+  switch (order) {
+    case 1: launch_solve_n<1>(v, prec, lam, b, x, tol, max_sweeps, ylen, st); break;
+    case 2: launch_solve_n<2>(v, prec, lam, b, x, tol, max_sweeps, ylen, st); break;
+    case 3: launch_solve_n<3>(v, prec, lam, b, x, tol, max_sweeps, ylen, st); break;
+    case 4: launch_solve_n<4>(v, prec, lam, b, x, tol, max_sweeps, ylen, st); break;
+    case 5: launch_solve_n<5>(v, prec, lam, b, x, tol, max_sweeps, ylen, st); break;
+    default: break;
   }
 }
 
@@ -763,25 +804,36 @@ __device__ void apply_dispatch(const DevView& v, const TileDesc& t, int lane, co
     apply_L_column<N>(v, c, x, y);
 }
 
+template <int N>
 __global__ void __launch_bounds__(128) k_apply(DevView v, const double* x, double* y, int nonlinear) {
   const int warp = threadIdx.x / kTile, lane = threadIdx.x % kTile;
-  const int64_t tile = (int64_t)blockIdx.x * (blockDim.x / kTile) + warp;
-  if (tile >= v.ntiles) return;
+  const int64_t tile = v.tile_begin + (int64_t)blockIdx.x * (blockDim.x / kTile) + warp;
+  if (tile >= (int64_t)v.tile_begin + v.tile_count) return;
   const TileDesc t = v.tiles[tile];
   if (lane >= t.count) return;
-  switch (t.order) {
-    case 1: apply_dispatch<1>(v, t, lane, x, y, nonlinear); break;
-    case 2: apply_dispatch<2>(v, t, lane, x, y, nonlinear); break;
-    case 3: apply_dispatch<3>(v, t, lane, x, y, nonlinear); break;
-    case 4: apply_dispatch<4>(v, t, lane, x, y, nonlinear); break;
-    case 5: apply_dispatch<5>(v, t, lane, x, y, nonlinear); break;
-    default: break;
-  }
+  apply_dispatch<N>(v, t, lane, x, y, nonlinear);
 }
 
-void launch_apply(const DevView& v, const double* x, double* y, int nonlinear, cudaStream_t st) {
-  const int blk = 128, tiles_per_blk = blk / kTile;
-  k_apply<<<(unsigned)((v.ntiles + tiles_per_blk - 1) / tiles_per_blk), blk, 0, st>>>(v, x, y, nonlinear);
+#define HEVI_ORDER_SWITCH(order, CALL) \
+  switch (order) {                       \
+    case 1: CALL(1); break;              \
+    case 2: CALL(2); break;              \
+    case 3: CALL(3); break;              \
+    case 4: CALL(4); break;              \
+    case 5: CALL(5); break;              \
+    default: break;                      \
+  }
+
+static unsigned col_grid(const DevView& v, int blk) {
+  const int tiles_per_blk = blk / kTile;
+  return (unsigned)((v.tile_count + tiles_per_blk - 1) / tiles_per_blk);
+}
+
+void launch_apply(const DevView& v, int order, const double* x, double* y, int nonlinear,
+                  cudaStream_t st) {
+#define HEVI_CALL(NN) k_apply<NN><<<col_grid(v, 128), 128, 0, st>>>(v, x, y, nonlinear)
+  HEVI_ORDER_SWITCH(order, HEVI_CALL)
+#undef HEVI_CALL
 }
 
 // Full right-hand side S(Q) = H + V(Q) of a stage value (Sec. 4.1, 4.3).
@@ -792,27 +844,22 @@ __device__ void apply_rhs_dispatch(const DevView& v, const TileDesc& t, int lane
   apply_V_column<N>(v, c, Q, S, 0.0, H, nullptr);
 }
 
+template <int N>
 __global__ void __launch_bounds__(128) k_apply_rhs(DevView v, const double* Q, const double* H,
                                                    double* S) {
   const int warp = threadIdx.x / kTile, lane = threadIdx.x % kTile;
-  const int64_t tile = (int64_t)blockIdx.x * (blockDim.x / kTile) + warp;
-  if (tile >= v.ntiles) return;
+  const int64_t tile = v.tile_begin + (int64_t)blockIdx.x * (blockDim.x / kTile) + warp;
+  if (tile >= (int64_t)v.tile_begin + v.tile_count) return;
   const TileDesc t = v.tiles[tile];
   if (lane >= t.count) return;
-  switch (t.order) {
-    case 1: apply_rhs_dispatch<1>(v, t, lane, Q, H, S); break;
-    case 2: apply_rhs_dispatch<2>(v, t, lane, Q, H, S); break;
-    case 3: apply_rhs_dispatch<3>(v, t, lane, Q, H, S); break;
-    case 4: apply_rhs_dispatch<4>(v, t, lane, Q, H, S); break;
-    case 5: apply_rhs_dispatch<5>(v, t, lane, Q, H, S); break;
-    default: break;
-  }
+  apply_rhs_dispatch<N>(v, t, lane, Q, H, S);
 }
 
-void launch_apply_rhs(const DevView& v, const double* Q, const double* H, double* S,
+void launch_apply_rhs(const DevView& v, int order, const double* Q, const double* H, double* S,
                       cudaStream_t st) {
-  const int blk = 128, tiles_per_blk = blk / kTile;
-  k_apply_rhs<<<(unsigned)((v.ntiles + tiles_per_blk - 1) / tiles_per_blk), blk, 0, st>>>(v, Q, H, S);
+#define HEVI_CALL(NN) k_apply_rhs<NN><<<col_grid(v, 128), 128, 0, st>>>(v, Q, H, S)
+  HEVI_ORDER_SWITCH(order, HEVI_CALL)
+#undef HEVI_CALL
 }
 
 // ARK stage tendencies of the LHEVI split (Sec. 4.3):
@@ -825,29 +872,22 @@ __device__ void apply_stage_dispatch(const DevView& v, const TileDesc& t, int la
   apply_V_column<N>(v, c, Q, E, 0.0, H, LQ);
 }
 
+template <int N>
 __global__ void __launch_bounds__(128) k_apply_stage(DevView v, const double* Q, const double* H,
                                                      double* E, double* LQ) {
   const int warp = threadIdx.x / kTile, lane = threadIdx.x % kTile;
-  const int64_t tile = (int64_t)blockIdx.x * (blockDim.x / kTile) + warp;
-  if (tile >= v.ntiles) return;
+  const int64_t tile = v.tile_begin + (int64_t)blockIdx.x * (blockDim.x / kTile) + warp;
+  if (tile >= (int64_t)v.tile_begin + v.tile_count) return;
   const TileDesc t = v.tiles[tile];
   if (lane >= t.count) return;
-  switch (t.order) {
-    case 1: apply_stage_dispatch<1>(v, t, lane, Q, H, E, LQ); break;
-    case 2: apply_stage_dispatch<2>(v, t, lane, Q, H, E, LQ); break;
-    case 3: apply_stage_dispatch<3>(v, t, lane, Q, H, E, LQ); break;
-    case 4: apply_stage_dispatch<4>(v, t, lane, Q, H, E, LQ); break;
-    case 5: apply_stage_dispatch<5>(v, t, lane, Q, H, E, LQ); break;
-    default: break;
-  }
+  apply_stage_dispatch<N>(v, t, lane, Q, H, E, LQ);
 }
 
-void launch_apply_stage(const DevView& v, const double* Q, const double* H, double* E, double* LQ,
-                        int lin_rest, cudaStream_t st) {
-  const int blk = 128, tiles_per_blk = blk / kTile;
-  (void)lin_rest;
-  k_apply_stage<<<(unsigned)((v.ntiles + tiles_per_blk - 1) / tiles_per_blk), blk, 0, st>>>(
-      v, Q, H, E, LQ);
+void launch_apply_stage(const DevView& v, int order, const double* Q, const double* H, double* E,
+                        double* LQ, cudaStream_t st) {
+#define HEVI_CALL(NN) k_apply_stage<NN><<<col_grid(v, 128), 128, 0, st>>>(v, Q, H, E, LQ)
+  HEVI_ORDER_SWITCH(order, HEVI_CALL)
+#undef HEVI_CALL
 }
 
 // ---------------------------------------------------------------------------
@@ -977,36 +1017,37 @@ __device__ void newton_column(const DevView& v, const TileDesc& t, int lane, dou
     v.col_status[c.col] = HEVI_COL_OK;
 }
 
+template <int N>
 __global__ void __launch_bounds__(64) k_newton(DevView v, double lam, double* q, const double* R,
                                                double rtol, int max_iter, int win_slots) {
   extern __shared__ unsigned char smem_raw[];
   float* smem = reinterpret_cast<float*>(smem_raw);
   const int warp = threadIdx.x / kTile, lane = threadIdx.x % kTile;
-  const int64_t tile = (int64_t)blockIdx.x * (blockDim.x / kTile) + warp;
-  if (tile >= v.ntiles) return;
+  const int64_t tile = v.tile_begin + (int64_t)blockIdx.x * (blockDim.x / kTile) + warp;
+  if (tile >= (int64_t)v.tile_begin + v.tile_count) return;
   const TileDesc t = v.tiles[tile];
   if (lane >= t.count) return;
   const int stride = blockDim.x;
   float* win = smem + threadIdx.x;
   float* y = smem + (int64_t)win_slots * stride + threadIdx.x;
-  switch (t.order) {
-    case 1: newton_column<1>(v, t, lane, lam, q, R, rtol, max_iter, win, y, stride); break;
-    case 2: newton_column<2>(v, t, lane, lam, q, R, rtol, max_iter, win, y, stride); break;
-    case 3: newton_column<3>(v, t, lane, lam, q, R, rtol, max_iter, win, y, stride); break;
-    case 4: newton_column<4>(v, t, lane, lam, q, R, rtol, max_iter, win, y, stride); break;
-    case 5: newton_column<5>(v, t, lane, lam, q, R, rtol, max_iter, win, y, stride); break;
-    default: break;
-  }
+  newton_column<N>(v, t, lane, lam, q, R, rtol, max_iter, win, y, stride);
 }
 
-void launch_newton(const DevView& v, double lam, double* q, const double* R, double rtol,
-                   int max_iter, int max_order, int max_ylen, cudaStream_t st) {
-  const int slots = window_slots(max_order);
-  const int blk = pick_block((slots + max_ylen) * (int)sizeof(float), 64), tiles_per_blk = blk / kTile;
-  const int smem = (slots + max_ylen) * blk * (int)sizeof(float);
-  cudaFuncSetAttribute(k_newton, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  k_newton<<<(unsigned)((v.ntiles + tiles_per_blk - 1) / tiles_per_blk), blk, smem, st>>>(
-      v, lam, q, R, rtol, max_iter, slots);
+template <int N>
+static void launch_newton_n(const DevView& v, double lam, double* q, const double* R, double rtol,
+                            int max_iter, int ylen, cudaStream_t st) {
+  const int slots = window_slots(N);
+  const int blk = pick_block((slots + ylen) * (int)sizeof(float), 64);
+  const int smem = (slots + ylen) * blk * (int)sizeof(float);
+  cudaFuncSetAttribute(k_newton<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  k_newton<N><<<col_grid(v, blk), blk, smem, st>>>(v, lam, q, R, rtol, max_iter, slots);
+}
+
+void launch_newton(const DevView& v, int order, double lam, double* q, const double* R,
+                   double rtol, int max_iter, int ylen, cudaStream_t st) {
+#define HEVI_CALL(NN) launch_newton_n<NN>(v, lam, q, R, rtol, max_iter, ylen, st)
+  HEVI_ORDER_SWITCH(order, HEVI_CALL)
+#undef HEVI_CALL
 }
 
 // ---------------------------------------------------------------------------
@@ -1173,6 +1214,8 @@ extern "C" hevi_status hevi_newton_solve_noalloc(int32_t nez, int32_t order, dou
   v.ph = ph;
   v.ncols = ncols;
   v.ntiles = (int32_t)ntiles;
+  v.tile_begin = 0;
+  v.tile_count = (int32_t)ntiles;
   v.fail_count = reinterpret_cast<int32_t*>(base + o_fail);
   TileDesc* tiles = reinterpret_cast<TileDesc*>(base + o_tiles);
   int64_t* col_off = reinterpret_cast<int64_t*>(base + o_off);
@@ -1197,7 +1240,7 @@ extern "C" hevi_status hevi_newton_solve_noalloc(int32_t nez, int32_t order, dou
                                                                    col_off, perm, col_dz,
                                                                    col_order, col_nez);
   launch_setup_ref(v, col_order, col_nez, st);
-  launch_newton(v, gamma_dt, state, R, rtol, max_iter, order, (int)(n + 2 * K), st);
+  launch_newton(v, order, gamma_dt, state, R, rtol, max_iter, (int)(n + 2 * K), st);
   int32_t h_fail[4] = {0, 0, 0, 0};
   if (cudaMemcpyAsync(h_fail, v.fail_count, sizeof(h_fail), cudaMemcpyDeviceToHost, st) !=
       cudaSuccess)
