@@ -112,6 +112,10 @@ class Tableau:
     def s(self):
         return len(self.b)
 
+    @property
+    def gamma(self):
+        return float(self.At[1, 1])
+
 
 def tableau(name: str) -> Tableau:
     """The library's named tableau ("ARK2", "ARK3", "ARK4"), via hevi_tableau."""

@@ -105,6 +105,32 @@ hevi::LglTables make_tables() {
         t.wD[N][k * (N + 1) + j] = v;
         t.wDf[N][k * (N + 1) + j] = (float)v;
       }
+    for (int k = 0; k <= N; ++k) t.iwf[N][k] = (float)(1.0 / t.w[N][k]);
+    {
+      auto wD = [&](int k, int j) { return t.wD[N][k * (N + 1) + j]; };
+      for (int dJ = -N; dJ <= N; ++dJ) {
+        const int o = dJ + N;
+        t.gcoef[N][0][o] = dJ >= 0 ? (float)(wD(0, dJ) / t.w[N][0]) : 0.0f;            // bottom
+        t.gcoef[N][1][o] = dJ <= 0 ? (float)(wD(N, N + dJ) / t.w[N][0]) : 0.0f;        // top
+        double sh = 0.0;                                                              // shared
+        if (dJ <= 0) sh += wD(N, N + dJ);
+        if (dJ >= 0) sh += wD(0, dJ);
+        t.gcoef[N][2][o] = (float)(sh / (2.0 * t.w[N][0]));
+        for (int k = 1; k < N; ++k)                                                   // interior
+          t.gcoef[N][2 + k][o] =
+              (k + dJ >= 0 && k + dJ <= N) ? (float)(wD(k, k + dJ) / t.w[N][k]) : 0.0f;
+      }
+    }
+    // even-odd halves (LGL symmetry: wD[N-k][N-j] = -wD[k][j])
+    const int P = (N + 1) / 2;
+    for (int k = 0; k < P; ++k)
+      for (int j = 0; j < P; ++j) {
+        t.ep[N][k][j] = 0.5 * (t.wD[N][k * (N + 1) + j] + t.wD[N][k * (N + 1) + N - j]);
+        t.op[N][k][j] = 0.5 * (t.wD[N][k * (N + 1) + j] - t.wD[N][k * (N + 1) + N - j]);
+      }
+    if (N % 2 == 0)
+      for (int j = 0; j < P; ++j)
+        t.om[N][j] = 0.5 * (t.wD[N][(N / 2) * (N + 1) + j] - t.wD[N][(N / 2) * (N + 1) + N - j]);
   }
   return t;
 }
@@ -341,6 +367,13 @@ hevi_status hevi_setup(hevi_ctx** out, const hevi_column_grid* grid, const hevi_
   ph.cv = ph.cp - ph.R;
   ph.gamma = ph.cp / ph.cv;
   ph.cs = std::sqrt(ph.gamma * ph.R * ph.T0);
+  {
+    double coef = 1.0;  // C(gamma, k) = C(gamma, k-1) (gamma - k + 1) / k
+    for (int k = 1; k <= hevi::kEosTerms; ++k) {
+      coef *= (ph.gamma - k + 1.0) / k;
+      ph.bin[k - 1] = coef;
+    }
+  }
   c->v.ph = ph;
   c->v.ncols = ncols;
 
@@ -405,6 +438,7 @@ hevi_status hevi_setup(hevi_ctx** out, const hevi_column_grid* grid, const hevi_
       (s = c->alloc(&d_order, ncols)) || (s = c->alloc(&d_nez, ncols)) ||
       (s = c->alloc(&d_dz, ncols)) || (s = c->alloc(&d_ref, c->state_size)) ||
       (s = c->alloc(&c->v.lin, c->state_size)) || (s = c->alloc(&d_tiles, c->ntiles)) ||
+      (s = c->alloc(&c->v.s32, c->state_size)) || (s = c->alloc(&c->v.is32, c->state_size)) ||
       (s = c->alloc(&d_fs, ncols)) || (s = c->alloc(&d_cs, ncols)) || (s = c->alloc(&d_it, ncols)) ||
       (s = c->alloc(&d_fail, kFailSlots)) ||
       (s = precision == HEVI_FP64 ? c->alloc((double**)&d_fac, c->fac_elems)
@@ -493,8 +527,8 @@ hevi_status hevi_factor(hevi_ctx* c, double gamma_dt, const double* lin_state) {
   if (!c || !(gamma_dt >= 0.0) || !std::isfinite(gamma_dt)) return HEVI_ERR_INVALID_ARG;
   {
     Scope sc(c, kFactor);
-    for_orders(c, c->v, [&](const DevView& v, int N, int) {
-      hevi::launch_factor(v, N, c->prec, gamma_dt, lin_state, c->stream);
+    for_orders(c, c->v, [&](const DevView& v, int N, int ylen) {
+      hevi::launch_factor(v, N, c->prec, gamma_dt, lin_state, ylen, c->stream);
     });
   }
   c->lam = gamma_dt;

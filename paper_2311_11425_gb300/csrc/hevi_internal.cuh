@@ -32,9 +32,11 @@ struct Band {
 };
 
 // Physical constants of the isothermal reference atmosphere.
+constexpr int kEosTerms = 12;
 struct Phys {
   double T0, p0, R, cp, g;
-  double cv, gamma, cs;  // cp - R, cp / cv, sqrt(gamma R T0)
+  double cv, gamma, cs;   // cp - R, cp / cv, sqrt(gamma R T0)
+  double bin[kEosTerms];  // C(gamma, k), k = 1 .. kEosTerms
 };
 
 // One tile = up to 32 columns of the same size class.
@@ -49,11 +51,24 @@ struct TileDesc {
 
 // LGL tables per order (host fills them at setup): weights w_k, Dhat_kj =
 // h_j'(xi_k), and wD_kj = w_k Dhat_kj, in FP64 and FP32.
+// Even-odd form of wD: LGL points are symmetric, so wD[N-k][N-j] = -wD[k][j];
+// for pair rows k < P = (N+1)/2, with e_j = f_j + f_{N-j}, o_j = f_j - f_{N-j}:
+//   sE_k = sum_{j<P} ep[k][j] e_j + (N even) wD[k][N/2] f_{N/2},
+//   sO_k = sum_{j<P} op[k][j] o_j,   c_k = sE_k + sO_k,  c_{N-k} = sO_k - sE_k,
+// and for N even the middle row c_{N/2} = sum_{j<P} om[j] o_j.
 struct LglTables {
   double xi[kMaxOrder + 1][kMaxOrder + 1];
   double w[kMaxOrder + 1][kMaxOrder + 1];
   double wD[kMaxOrder + 1][(kMaxOrder + 1) * (kMaxOrder + 1)];
   float wDf[kMaxOrder + 1][(kMaxOrder + 1) * (kMaxOrder + 1)];
+  float iwf[kMaxOrder + 1][kMaxOrder + 1];  // 1 / w_k
+  // Row coefficients of the DSS'd derivative: for a point of class cls
+  // (0 bottom end, 1 top end, 2 shared element boundary, 2 + k interior
+  // local index k) and dJ = J - I in [-N, N], G = sum_e w_k Dhat_kj / W_I.
+  float gcoef[kMaxOrder + 1][kMaxOrder + 2][2 * kMaxOrder + 1];
+  double ep[kMaxOrder + 1][3][3];
+  double op[kMaxOrder + 1][3][3];
+  double om[kMaxOrder + 1][3];
 };
 
 // Device view of a context's buffers (passed to kernels by value).
@@ -64,6 +79,8 @@ struct DevView {
   const int32_t* perm;      // [ncols] class-sorted column index
   const double* col_dz;     // [ncols] element height
   const double* ref;        // state layout: (rho_bar, P_bar, Theta_bar) per point
+  float* s32;               // state layout: equilibration scales (rho_bar, rho_bar c_s, Theta_bar)
+  float* is32;              // state layout: their reciprocals
   double* lin;              // state layout: (w0, theta0, c0 = gamma P0 / Theta0)
   const TileDesc* tiles;
   int32_t ntiles;
@@ -101,6 +118,11 @@ __device__ __forceinline__ double wsum(const double* w, int I, int nz) {
 // (1/M_I) sum_{(e,k)->I} w_k J_e (dxi/dz) sum_j Dhat_kj f_(e,j)   (Sec. 3).
 // `out(I, D)` is called in increasing I, always after flux(J) for every J
 // of the element holding I.
+// Weighted element derivative cc[k] = sum_j w_k Dhat_kj f_j (3 components)
+// in the even-odd form; reads the tables from constant memory.
+template <int N>
+__device__ __forceinline__ void elem_deriv(const double (&f)[N + 1][3], double (&cc)[N + 1][3]);
+
 template <int N, class FluxF, class OutF>
 __device__ __forceinline__ void element_pass(const Col& c, const double* w, const double* wD,
                                              FluxF&& flux, OutF&& out) {
@@ -112,16 +134,7 @@ __device__ __forceinline__ void element_pass(const Col& c, const double* w, cons
 #pragma unroll
     for (int k = 1; k <= N; ++k) flux(I0 + k, f[k]);
     double cc[N + 1][3];
-#pragma unroll
-    for (int k = 0; k <= N; ++k) {
-#pragma unroll
-      for (int v = 0; v < 3; ++v) {
-        double a = 0.0;
-#pragma unroll
-        for (int j = 0; j <= N; ++j) a = fma(wD[k * (N + 1) + j], f[j][v], a);
-        cc[k][v] = a;
-      }
-    }
+    elem_deriv<N>(f, cc);
     {
       double D[3];
       const double sc = c.s / (e == 0 ? w[0] : 2.0 * w[0]);
@@ -156,13 +169,21 @@ __device__ __forceinline__ double eos(const Phys& ph, double Theta) {
 }
 
 // Pressure perturbation about the reference state, from the same equation of
-// state: P(Theta) - P_bar = P_bar ((Theta / Theta_bar)^gamma - 1), evaluated as
-// P_bar expm1(gamma log1p((Theta - Theta_bar) / Theta_bar)) so that it is
-// exactly zero at Theta = Theta_bar and free of the cancellation of two
-// O(1e5 Pa) numbers.
+// state: P(Theta) - P_bar = P_bar ((1 + x)^gamma - 1), x = (Theta - Theta_bar) /
+// Theta_bar, exactly zero at Theta = Theta_bar and free of the cancellation of
+// two O(1e5 Pa) numbers.  For |x| <= 0.02 the binomial series (kEosTerms terms,
+// truncation below 1e-19 relative) replaces the FP64 log1p/expm1 pair, which
+// costs several times more on this part's FP64 pipe.
 __device__ __forceinline__ double eos_perturbation(const Phys& ph, double Theta, double Theta_bar,
                                                    double P_bar) {
-  return P_bar * expm1(ph.gamma * log1p((Theta - Theta_bar) / Theta_bar));
+  const double x = (Theta - Theta_bar) / Theta_bar;
+  if (fabs(x) <= 0.02) {
+    double s = ph.bin[kEosTerms - 1];
+#pragma unroll
+    for (int k = kEosTerms - 2; k >= 0; --k) s = fma(s, x, ph.bin[k]);
+    return P_bar * (s * x);
+  }
+  return P_bar * expm1(ph.gamma * log1p(x));
 }
 
 // Launch helpers (host side, defined in hevi_kernels.cu).
@@ -171,7 +192,7 @@ void launch_setup_ref(const DevView& v, const int32_t* col_order, const int32_t*
 // The column launchers below process the tiles [v.tile_begin, v.tile_begin +
 // v.tile_count), all of order `order`; ylen is the longest n + 2K among them.
 void launch_factor(const DevView& v, int order, hevi_precision prec, double lam, const double* q0,
-                   cudaStream_t st);
+                   int ylen, cudaStream_t st);
 void launch_solve(const DevView& v, int order, hevi_precision prec, double lam, const double* b,
                   double* x, double tol, int max_sweeps, int ylen, cudaStream_t st);
 void launch_apply(const DevView& v, int order, const double* x, double* y, int nonlinear,

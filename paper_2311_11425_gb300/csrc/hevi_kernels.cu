@@ -8,6 +8,7 @@
 // (K+1) rows x (2K+1) columns (Sec. 4.2.3: partial pivoting fills U to
 // k_l + k_u super-diagonals), lives in shared memory, slot-major with the
 // thread index fastest so that a warp's accesses are bank-conflict free.
+#include <algorithm>
 #include <cstdio>
 
 #include "hevi_internal.cuh"
@@ -17,6 +18,38 @@ namespace hevi {
 __constant__ LglTables c_tab;
 
 void upload_tables(const LglTables& t) { cudaMemcpyToSymbol(c_tab, &t, sizeof(LglTables)); }
+
+template <int N>
+__device__ __forceinline__ void elem_deriv(const double (&f)[N + 1][3], double (&cc)[N + 1][3]) {
+  constexpr int P = (N + 1) / 2;
+#pragma unroll
+  for (int v = 0; v < 3; ++v) {
+    double e[P], o[P];
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+      e[j] = f[j][v] + f[N - j][v];
+      o[j] = f[j][v] - f[N - j][v];
+    }
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+      double sE = (N % 2 == 0) ? c_tab.wD[N][k * (N + 1) + N / 2] * f[N / 2][v] : 0.0;
+      double sO = 0.0;
+#pragma unroll
+      for (int j = 0; j < P; ++j) {
+        sE = fma(c_tab.ep[N][k][j], e[j], sE);
+        sO = fma(c_tab.op[N][k][j], o[j], sO);
+      }
+      cc[k][v] = sE + sO;
+      cc[N - k][v] = sO - sE;
+    }
+    if (N % 2 == 0) {
+      double sm = 0.0;
+#pragma unroll
+      for (int j = 0; j < P; ++j) sm = fma(c_tab.om[N][j], o[j], sm);
+      cc[N / 2][v] = sm;
+    }
+  }
+}
 
 // ---------------------------------------------------------------------------
 // Record addressing
@@ -92,6 +125,15 @@ __global__ void k_setup_ref(DevView v, const int32_t* col_order, const int32_t* 
     r[3 * I + 0] = rho;
     r[3 * I + 1] = eos(ph, Th);
     r[3 * I + 2] = Th;
+    if (v.s32) {
+      const int64_t a = v.col_off[col] + 3 * I;
+      const double sc[3] = {rho, rho * ph.cs, Th};
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        v.s32[a + u] = (float)sc[u];
+        v.is32[a + u] = (float)(1.0 / sc[u]);
+      }
+    }
   }
 }
 
@@ -404,6 +446,269 @@ __global__ void __launch_bounds__(64) k_factor(DevView v, double lam, const doub
   factor_column<N, T, SCALED>(v, t, lane, lam, q0, win, stride);
 }
 
+// ---------------------------------------------------------------------------
+// Group-cooperative FP32 factorisation: eight threads per column, four
+// columns per warp.  The column's active window, (K+1) rows x (2K+1)
+// columns of A_hat = S^-1 A S (Sec. 4.2.3 band LU, dgbtrf semantics), is a
+// ring in shared memory; thread q owns the window columns c = q (mod 8).  At
+// pivot step j the owner of column j finds the pivot (first maximal |a|),
+// swaps, forms the multipliers and publishes them; after one group barrier
+// every thread swaps and updates its own columns, writes its entries of U's
+// row j into the column-oriented backward records and assembles its entries
+// of the row that enters the window.
+// ---------------------------------------------------------------------------
+constexpr int kFgWarps = 8;
+// shared-memory floats reserved for the row coefficient table
+constexpr int kGSz = (kMaxOrder + 2) * (2 * kMaxOrder + 1) + 3;
+
+// Row data of A_hat = S^-1 (I + Lambda Dcal K(q0) + Lambda G) S for row i:
+// point I, variable v, point class (0 bottom end, 1 top end, 2 shared element
+// boundary, 2 + k interior local index k), 1/s_i, identity row (m at an end).
+struct RowInfo {
+  int i, I, v, cls;
+  float isi;
+  bool ident;
+};
+
+template <int N>
+__device__ __forceinline__ RowInfo row_info(const Col& c, const float* is32, int i) {
+  RowInfo r;
+  r.i = i;
+  r.I = i / 3;
+  r.v = i - 3 * r.I;
+  const int k = r.I % N;
+  r.cls = (r.I == 0) ? 0 : (r.I == c.nz - 1 ? 1 : (k == 0 ? 2 : 2 + k));
+  r.ident = (r.v == 1) && (r.I == 0 || r.I == c.nz - 1);
+  r.isi = is32[i];
+  return r;
+}
+
+// Entry (i, col) of A_hat in FP32 (Sec. 4.2.3, App. A.3): delta + Lambda (2/dz)
+// G[cls][J-I] K_vu(q0_J) s_col / s_i + Lambda g [v=m, u=rho, J=I] s_col / s_i,
+// with the point coefficients (w, theta, gamma P / Theta) of q0 in lin32.
+template <int N>
+__device__ __forceinline__ float ahat_entry(const RowInfo& ri, int col, const float* lin32,
+                                            const float* s32, const float* G, float lam_s,
+                                            float lam_g) {
+  if (ri.ident) return col == ri.i ? 1.0f : 0.0f;
+  const int J = col / 3, u = col - 3 * J, dJ = J - ri.I;
+  float a = (col == ri.i) ? 1.0f : 0.0f;
+  const float sr = s32[col] * ri.isi;
+  if (ri.v == 1 && u == 0 && dJ == 0) a = fmaf(lam_g, sr, a);
+  if (dJ < -N || dJ > N) return a;
+  const float g = G[ri.cls * (2 * N + 1) + dJ + N];
+  const float w = lin32[3 * J], th = lin32[3 * J + 1];
+  float kvu;
+  if (ri.v == 0)
+    kvu = (u == 1) ? 1.0f : 0.0f;
+  else if (ri.v == 1)
+    kvu = (u == 0) ? -w * w : (u == 1 ? 2.0f * w : lin32[3 * J + 2]);
+  else
+    kvu = (u == 0) ? -th * w : (u == 1 ? th : w);
+  return fmaf(lam_s * g * kvu, sr, a);
+}
+
+template <int N>
+__global__ void __launch_bounds__(kFgWarps * 32) k_factor_g(DevView v, double lam, const double* q0,
+                                                           int wstride) {
+  extern __shared__ float fg_smem[];
+  constexpr int K = Band<N>::K, WR = Band<N>::WR, WC = Band<N>::WC, FR = Band<N>::FR;
+  constexpr int BR = Band<N>::BR;
+  constexpr int NG = (N + 2) * (2 * N + 1);
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int grp = lane / 8, q = lane % 8;
+  const int64_t tile = v.tile_begin + blockIdx.x;
+  if (tile >= (int64_t)v.tile_begin + v.tile_count) return;
+  const TileDesc t = v.tiles[tile];
+  float* G = fg_smem;  // row coefficient table of order N
+  for (int k = threadIdx.x; k < NG; k += blockDim.x)
+    G[k] = c_tab.gcoef[N][k / (2 * N + 1)][k % (2 * N + 1)];
+  __syncthreads();
+  if (warp * 4 >= t.count) return;  // warp-uniform: no column for this warp
+  // groups past the tile's last column shadow it without writing anything
+  const bool active = warp * 4 + grp < t.count;
+  const int cl = active ? warp * 4 + grp : t.count - 1;
+  const Col c = make_col(v, t, cl, N);
+  const Phys ph = v.ph;
+  float* W = fg_smem + kGSz + (int64_t)(warp * 4 + grp) * wstride;  // WR x WC ring
+  float* bcast = W + WR * WC;                                        // 2 x (K + 2)
+  float* lin32 = bcast + 2 * (K + 2);                                // 3 n_z coefficients
+  const float* s32 = v.s32 + c.off;
+  const float* is32 = v.is32 + c.off;
+  float* tb = reinterpret_cast<float*>(v.fac) + t.fac_off;
+  float* bb = tb + (int64_t)c.n * FR * kTile;
+  const int n = c.n;
+
+  // point coefficients of L(q0) (FP64): w, theta, c = gamma P / Theta
+  bool ok = true;
+  for (int I = q; I < c.nz; I += 8) {
+    const int64_t a = c.off + 3 * I;
+    double rho, m, Th;
+    if (q0) {
+      rho = q0[a]; m = q0[a + 1]; Th = q0[a + 2];
+    } else {
+      rho = v.ref[a]; m = 0.0; Th = v.ref[a + 2];
+    }
+    double w, th, cc, dP;
+    if (!lin_coefs(ph, rho, m, Th, v.ref[a + 2], v.ref[a + 1], &w, &th, &cc, &dP)) {
+      ok = false;
+      w = th = cc = 0.0;
+    }
+    if (active) {
+      v.lin[a] = w;
+      v.lin[a + 1] = th;
+      v.lin[a + 2] = cc;
+    }
+    lin32[3 * I] = (float)w;
+    lin32[3 * I + 1] = (float)th;
+    lin32[3 * I + 2] = (float)cc;
+  }
+  {  // AND over the group's eight lanes (every lane of the warp takes part)
+    int okv = ok ? 1 : 0;
+    okv &= __shfl_xor_sync(0xffffffffu, okv, 1, 8);
+    okv &= __shfl_xor_sync(0xffffffffu, okv, 2, 8);
+    okv &= __shfl_xor_sync(0xffffffffu, okv, 4, 8);
+    ok = okv != 0;
+  }
+  __syncwarp();
+  const float lam_s = (float)(lam * c.s), lam_g = (float)(lam * ph.g);
+
+  // initial window: rows 0..K, columns 0..2K (ring positions = indices)
+  for (int r = 0; r < WR; ++r) {
+    const RowInfo ri = row_info<N>(c, is32, r < n ? r : 0);
+    for (int cc = q; cc < WC; cc += 8)
+      W[r * WC + cc] = (r < n && cc < n && cc <= r + K)
+                           ? ahat_entry<N>(ri, cc, lin32, s32, G, lam_s, lam_g)
+                           : 0.0f;
+  }
+  __syncwarp();
+
+  int rowoff[WR];  // ring offsets of window rows j .. j+K
+#pragma unroll
+  for (int r = 0; r < WR; ++r) rowoff[r] = r * WC;
+  int info = 0;
+  int cs_j = 0;  // ring column of column j
+  for (int j = 0; j < n; ++j) {
+    const int nr = min(K, n - 1 - j), ncol = min(2 * K, n - 1 - j);
+    const int buf = (j & 1) * (K + 2);
+    if (q == (j & 7)) {
+      int p = 0;
+      float amax = fabsf(W[rowoff[0] + cs_j]);
+#pragma unroll
+      for (int r = 1; r <= K; ++r) {
+        const float a = fabsf(W[rowoff[r] + cs_j]);
+        if (r <= nr && a > amax) {
+          amax = a;
+          p = r;
+        }
+      }
+      int rp = rowoff[0];
+#pragma unroll
+      for (int r = 1; r <= K; ++r)
+        if (p == r) rp = rowoff[r];
+      float invd = 0.0f;
+      if (amax > 0.0f) {
+        if (p) {
+          const float t0 = W[rowoff[0] + cs_j];
+          W[rowoff[0] + cs_j] = W[rp + cs_j];
+          W[rp + cs_j] = t0;
+        }
+        invd = 1.0f / W[rowoff[0] + cs_j];
+      } else if (info == 0) {
+        info = j + 1;
+      }
+      float rec[FR];
+#pragma unroll
+      for (int r = 1; r <= K; ++r) {
+        const float l = (r <= nr && amax > 0.0f) ? W[rowoff[r] + cs_j] * invd : 0.0f;
+        bcast[buf + r - 1] = l;
+        rec[r - 1] = l;
+      }
+      bcast[buf + K] = (float)p;
+      bcast[buf + K + 1] = invd;
+      rec[K] = (float)p;
+      rec[K + 1] = invd;
+#pragma unroll
+      for (int r = K + 2; r < FR; ++r) rec[r] = 0.0f;
+      if (active) {
+#pragma unroll
+        for (int e = 0; e < FR; e += 4)
+          *reinterpret_cast<float4*>(tb + ((int64_t)(j * (FR / 4) + e / 4) * kTile + cl) * 4) =
+              make_float4(rec[e], rec[e + 1], rec[e + 2], rec[e + 3]);
+      }
+    }
+    __syncwarp();
+    const int p = (int)bcast[buf + K];
+    float l[K];
+#pragma unroll
+    for (int r = 0; r < K; ++r) l[r] = bcast[buf + r];
+    int rp = rowoff[0];
+#pragma unroll
+    for (int r = 1; r <= K; ++r)
+      if (p == r) rp = rowoff[r];
+    // my columns j < col <= j + ncol, col = q (mod 8)
+    const int c0 = j + 1 + ((q - (j + 1)) & 7);
+    int cs = cs_j + (c0 - j);
+    if (cs >= WC) cs -= WC;
+    for (int col = c0; col <= j + ncol; col += 8) {
+      if (p) {
+        const float t0 = W[rowoff[0] + cs];
+        W[rowoff[0] + cs] = W[rp + cs];
+        W[rp + cs] = t0;
+      }
+      const float u = W[rowoff[0] + cs];
+#pragma unroll
+      for (int r = 1; r <= K; ++r)
+        if (r <= nr) W[rowoff[r] + cs] = fmaf(-l[r - 1], u, W[rowoff[r] + cs]);
+      const int d = col - j - 1;  // U[j][col] is entry d of column col's backward record
+      if (active) bb[((int64_t)(col * (BR / 4) + d / 4) * kTile + cl) * 4 + (d & 3)] = u;
+      cs += 8;
+      if (cs >= WC) cs -= WC;
+    }
+    // entries of B_j that no row reaches (rows j - 1 - d < 0) and the padding
+    if (j < BR)
+      for (int d = q; d < BR; d += 8)
+        if (active && (d >= j || d >= 2 * K))
+          bb[((int64_t)(j * (BR / 4) + d / 4) * kTile + cl) * 4 + (d & 3)] = 0.0f;
+    // the window advances: row j+K+1 enters ring row rowoff[0], column j+2K+1
+    // enters ring column cs_j
+    const int inew = j + K + 1, cnew = j + 2 * K + 1;
+    const RowInfo ri = row_info<N>(c, is32, inew < n ? inew : 0);
+    const int cb0 = j + 1 + ((q - (j + 1)) & 7);
+    int cs2 = cs_j + (cb0 - j);
+    if (cs2 >= WC) cs2 -= WC;
+    for (int col = cb0; col <= cnew; col += 8) {
+      if (col == cnew) {
+#pragma unroll
+        for (int r = 1; r <= K; ++r) W[rowoff[r] + cs2] = 0.0f;
+      }
+      W[rowoff[0] + cs2] =
+          (inew < n && col < n) ? ahat_entry<N>(ri, col, lin32, s32, G, lam_s, lam_g) : 0.0f;
+      cs2 += 8;
+      if (cs2 >= WC) cs2 -= WC;
+    }
+    // rotate: ring row of j+1+r is the old ring row of j+1+r; the freed row
+    // (now holding j+K+1) becomes the last
+    const int r0 = rowoff[0];
+#pragma unroll
+    for (int r = 0; r < K; ++r) rowoff[r] = rowoff[r + 1];
+    rowoff[K] = r0;
+    cs_j = (cs_j + 1 == WC) ? 0 : cs_j + 1;
+  }
+  info = max(info, __shfl_xor_sync(0xffffffffu, info, 1, 8));
+  info = max(info, __shfl_xor_sync(0xffffffffu, info, 2, 8));
+  info = max(info, __shfl_xor_sync(0xffffffffu, info, 4, 8));
+  if (q == 0 && active) {
+    const int st = !ok ? HEVI_COL_BAD_INPUT : (info ? HEVI_COL_SINGULAR : HEVI_COL_OK);
+    v.fac_status[c.col] = st;
+    if (st != HEVI_COL_OK)
+      fail(v, c.col, st);
+    else
+      v.col_status[c.col] = HEVI_COL_OK;
+    v.col_iters[c.col] = 0;
+  }
+}
+
 static int pick_block(int bytes, int max_blk);
 static unsigned col_grid(const DevView& v, int blk);
 static int window_slots(int N) {
@@ -413,7 +718,7 @@ static int window_slots(int N) {
 
 template <int N>
 static void launch_factor_n(const DevView& v, hevi_precision prec, double lam, const double* q0,
-                            cudaStream_t st) {
+                            int ylen, cudaStream_t st) {
   const int esz = prec == HEVI_FP64 ? (int)sizeof(double) : (int)sizeof(float);
   const int blk = pick_block(window_slots(N) * esz, 64), tiles_per_blk = blk / kTile;
   const unsigned grid = (unsigned)((v.tile_count + tiles_per_blk - 1) / tiles_per_blk);
@@ -422,19 +727,27 @@ static void launch_factor_n(const DevView& v, hevi_precision prec, double lam, c
     cudaFuncSetAttribute(k_factor<N, double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     k_factor<N, double, false><<<grid, blk, smem, st>>>(v, lam, q0);
   } else {
-    cudaFuncSetAttribute(k_factor<N, float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    k_factor<N, float, true><<<grid, blk, smem, st>>>(v, lam, q0);
+    // group-cooperative: one CTA of eight warps per tile of 32 columns
+    constexpr int K = Band<N>::K;
+    const int nmax = ylen - 2 * K;  // longest n of these tiles
+    int wstride = Band<N>::WR * Band<N>::WC + 2 * (K + 2) + nmax;  // ring, bcast, 3 n_z coefs
+    if ((wstride & 1) == 0) wstride += 1;
+    const int gsmem = (kGSz + 32 * wstride) * (int)sizeof(float);
+    cudaFuncSetAttribute(k_factor_g<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, gsmem);
+    k_factor_g<N><<<(unsigned)v.tile_count, kFgWarps * 32, gsmem, st>>>(v, lam, q0, wstride);
+    (void)grid;
+    (void)smem;
   }
 }
 
 void launch_factor(const DevView& v, int order, hevi_precision prec, double lam, const double* q0,
-                   cudaStream_t st) {
+                   int ylen, cudaStream_t st) {
   switch (order) {
-    case 1: launch_factor_n<1>(v, prec, lam, q0, st); break;
-    case 2: launch_factor_n<2>(v, prec, lam, q0, st); break;
-    case 3: launch_factor_n<3>(v, prec, lam, q0, st); break;
-    case 4: launch_factor_n<4>(v, prec, lam, q0, st); break;
-    case 5: launch_factor_n<5>(v, prec, lam, q0, st); break;
+    case 1: launch_factor_n<1>(v, prec, lam, q0, ylen, st); break;
+    case 2: launch_factor_n<2>(v, prec, lam, q0, ylen, st); break;
+    case 3: launch_factor_n<3>(v, prec, lam, q0, ylen, st); break;
+    case 4: launch_factor_n<4>(v, prec, lam, q0, ylen, st); break;
+    case 5: launch_factor_n<5>(v, prec, lam, q0, ylen, st); break;
     default: break;
   }
 }
@@ -574,11 +887,10 @@ __device__ void solve_ir_column(const DevView& v, const TileDesc& t, int lane, d
   constexpr int K = Band<N>::K;
   const Col c = make_col(v, t, lane, N);
   const float* base = reinterpret_cast<const float*>(v.fac) + t.fac_off;
-  const double* ref = v.ref + c.off;
   const double* lin = v.lin + c.off;
   const double* bc = b + c.off;
   double* xc = x + c.off;
-  const double cs = v.ph.cs, g = v.ph.g;
+  const double g = v.ph.g;
   const double* w = c_tab.w[N];
   const double* wD = c_tab.wD[N];
   if (v.fac_status[c.col] != HEVI_COL_OK) {  // no usable factors for this column
@@ -587,10 +899,9 @@ __device__ void solve_ir_column(const DevView& v, const TileDesc& t, int lane, d
     fail(v, c.col, v.fac_status[c.col]);
     return;
   }
-  for (int I = 0; I < c.nz; ++I)
-#pragma unroll
-    for (int u = 0; u < 3; ++u)
-      y[(3 * I + u) * stride] = (float)(bc[3 * I + u] / ref_scale(ref, cs, 3 * I, u));
+  const float* s32 = v.s32 + c.off;
+  const float* is32 = v.is32 + c.off;
+  for (int i = 0; i < c.n; ++i) y[i * stride] = (float)bc[i] * is32[i];
   for (int i = c.n; i < c.n + 2 * K; ++i) y[i * stride] = 0.0f;
 
   int sweeps = 0, status = HEVI_COL_NOT_CONVERGED;
@@ -602,12 +913,10 @@ __device__ void solve_ir_column(const DevView& v, const TileDesc& t, int lane, d
     ++sweeps;
     // size of the correction d = S y in the caller's (unscaled) norm
     float d2 = 0.0f;
-    for (int I = 0; I < c.nz; ++I)
-#pragma unroll
-      for (int u = 0; u < 3; ++u) {
-        const float d = y[(3 * I + u) * stride] * (float)ref_scale(ref, cs, 3 * I, u);
-        d2 = fmaf(d, d, d2);
-      }
+    for (int i = 0; i < c.n; ++i) {
+      const float d = y[i * stride] * s32[i];
+      d2 = fmaf(d, d, d2);
+    }
     const double dn = sqrt((double)d2);
     const double xref = first ? dn : xnorm;
     bool stop = false;
@@ -625,13 +934,10 @@ __device__ void solve_ir_column(const DevView& v, const TileDesc& t, int lane, d
     }
     if (sweeps >= max_sweeps) stop = true;
     if (stop) {
-      for (int I = 0; I < c.nz; ++I)
-#pragma unroll
-        for (int u = 0; u < 3; ++u) {
-          const int i = 3 * I + u;
-          const double d = (double)y[i * stride] * ref_scale(ref, cs, 3 * I, u);
-          xc[i] = first ? d : xc[i] + d;
-        }
+      for (int i = 0; i < c.n; ++i) {
+        const double d = (double)(y[i * stride] * s32[i]);
+        xc[i] = first ? d : xc[i] + d;
+      }
       break;
     }
     // fused pass: x += S y, r = b - A x, y = S^-1 r, |S^-1 x|
@@ -642,7 +948,7 @@ __device__ void solve_ir_column(const DevView& v, const TileDesc& t, int lane, d
 #pragma unroll
       for (int u = 0; u < 3; ++u) {
         const int i = 3 * I + u;
-        const double d = (double)y[i * stride] * ref_scale(ref, cs, 3 * I, u);
+        const double d = (double)(y[i * stride] * s32[i]);
         xi[u] = fst ? d : xc[i] + d;
         xc[i] = xi[u];
         xs = fma(xi[u], xi[u], xs);
@@ -665,7 +971,7 @@ __device__ void solve_ir_column(const DevView& v, const TileDesc& t, int lane, d
           if (u == 1) ax = fma(g, xc[3 * I], ax);
           r = bc[i] - fma(lam, ax, xc[i]);
         }
-        y[i * stride] = (float)(r / ref_scale(ref, cs, 3 * I, u));
+        y[i * stride] = (float)r * is32[i];
       }
     };
     element_pass<N>(c, w, wD, flux, out);
@@ -678,6 +984,408 @@ __device__ void solve_ir_column(const DevView& v, const TileDesc& t, int lane, d
     fail(v, c.col, status);
   else
     v.col_status[c.col] = HEVI_COL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Warp-cooperative stage solve with FP32 factors and FP64 refinement.
+//
+// Eight lanes cooperate on one column (four columns per warp, one tile of 32
+// columns per CTA of eight warps).  Each lane holds E consecutive entries of
+// the active window of the triangular sweep in registers; a pivot step costs
+// one pair of shuffles (interchange + broadcast of the pivot value) and E
+// FMAs per lane, and the window is shifted once per block of steps.  With a
+// persistent grid of one CTA per SM only ~4.9k columns are in flight, so the
+// factor records that a column's refinement sweeps re-read stay in L2.
+// The FP64 residual b - A x is element-parallel over the eight lanes, with
+// the contributions of shared element-boundary points exchanged by shuffle.
+// ---------------------------------------------------------------------------
+template <int N>
+struct WC {
+  static constexpr int K = Band<N>::K;
+  static constexpr int E = (2 * K + 8 + 7) / 8;  // window entries per lane
+  static constexpr int P = 8 * E;                // window positions per column
+  static constexpr int BF = P - K;               // forward steps per block
+  static constexpr int BB = P - 2 * K;           // backward steps per block
+  static constexpr int NVF = Band<N>::FR / 4;
+  static constexpr int NVB = Band<N>::BR / 4;
+};
+
+constexpr int kWcWarps = 8;  // warps per CTA: 32 columns
+// The warp-cooperative solve runs ~10x more instructions per column than the
+// one-column-per-thread solve (each of the eight lanes repeats the pivot and
+// shuffle logic); the latter is used.
+constexpr bool kUseWarpSolve = false;
+
+// Element e of the forward record of step j for tile column cl.
+template <int N>
+__device__ __forceinline__ float wc_f(const float* tb, int j, int e, int cl) {
+  return tb[((int64_t)(j * WC<N>::NVF + (e >> 2)) * kTile + cl) * 4 + (e & 3)];
+}
+template <int N>
+__device__ __forceinline__ float wc_b(const float* bb, int j, int e, int cl) {
+  return bb[((int64_t)(j * WC<N>::NVB + (e >> 2)) * kTile + cl) * 4 + (e & 3)];
+}
+
+// Asynchronous 16-byte global -> shared copies (completion is awaited with
+// cp.async.wait_group, a hardware wait).
+__device__ __forceinline__ void cp_async16(float* smem_dst, const float* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int Pending>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(Pending) : "memory");
+}
+
+// Stage the forward records of steps [js, js + BF) of tile column cl into
+// dst[step][FR] (8 lanes share the copies).
+template <int N>
+__device__ __forceinline__ void wc_stage_f(const float* tb, int cl, int q, int n, int js, float* dst) {
+  constexpr int NV = WC<N>::NVF, FR = Band<N>::FR;
+  for (int k = q; k < WC<N>::BF * NV; k += 8) {
+    const int jj = js + k / NV, vv = k % NV;
+    if (jj < n) cp_async16(dst + (k / NV) * FR + vv * 4, tb + ((int64_t)(jj * NV + vv) * kTile + cl) * 4);
+  }
+  cp_async_commit();
+}
+
+// Stage the backward records (and the forward vector holding 1/u_jj) of the
+// steps js, js-1, .., js-BB+1 into dst[step][BR + 4].
+template <int N>
+__device__ __forceinline__ void wc_stage_b(const float* tb, const float* bb, int cl, int q, int js,
+                                           float* dst) {
+  constexpr int NV = WC<N>::NVB, BR = Band<N>::BR, K = Band<N>::K, NVF = WC<N>::NVF;
+  constexpr int PER = NV + 1;
+  for (int k = q; k < WC<N>::BB * PER; k += 8) {
+    const int tt = k / PER, vv = k % PER, jj = js - tt;
+    if (jj >= 0) {
+      const float* src = (vv < NV) ? bb + ((int64_t)(jj * NV + vv) * kTile + cl) * 4
+                                   : tb + ((int64_t)(jj * NVF + (K + 1) / 4) * kTile + cl) * 4;
+      cp_async16(dst + tt * (BR + 4) + vv * 4, src);
+    }
+  }
+  cp_async_commit();
+}
+
+// y: the group's FP32 vector in shared memory, length >= n + P + 2K with a
+// zero tail.  On exit it holds the forward result.  sb: two staging buffers
+// of BF * FR floats.
+template <int N>
+__device__ __forceinline__ void wc_forward(const float* tb, int cl, int q, int gbase,
+                                           unsigned gmask, int n, float* y, float* sb) {
+  constexpr int K = WC<N>::K, E = WC<N>::E, P = WC<N>::P, BF = WC<N>::BF, FR = Band<N>::FR;
+  float w[E];
+#pragma unroll
+  for (int r = 0; r < E; ++r) w[r] = y[q * E + r];
+  wc_stage_f<N>(tb, cl, q, n, 0, sb);
+  int cur = 0;
+  for (int j0 = 0; j0 < n; j0 += BF) {
+    wc_stage_f<N>(tb, cl, q, n, j0 + BF, sb + (cur ^ 1) * BF * FR);
+    cp_async_wait<1>();
+    __syncwarp();
+    const float* rec = sb + cur * BF * FR;
+#pragma unroll
+    for (int t = 0; t < BF; ++t) {
+      const int j = j0 + t;
+      if (j < n) {
+        const float* F = rec + t * FR;
+        const int p = (int)F[K];
+        const int s = t + p;
+        const int sl = s / E, sr = s - sl * E;
+        float cand = w[0];
+#pragma unroll
+        for (int r = 1; r < E; ++r)
+          if (sr == r) cand = w[r];
+        const float vnew = __shfl_sync(0xffffffffu, cand, sl, 8);
+        const float vold = __shfl_sync(0xffffffffu, w[t % E], t / E, 8);
+        if (p != 0 && q == sl) {
+#pragma unroll
+          for (int r = 0; r < E; ++r)
+            if (sr == r) w[r] = vold;
+        }
+        if (q == t / E) {
+          w[t % E] = vnew;
+          y[j] = vnew;
+        }
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+          const int d = q * E + r - t;
+          if (d >= 1 && d <= K) w[r] = fmaf(-F[d - 1], vnew, w[r]);
+        }
+      }
+    }
+    // shift by BF: position i takes old position i + BF; the tail is fresh
+    float nw[E];
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      const int src_lane = min(q + (r + BF) / E, 7);
+      const float sv = __shfl_sync(0xffffffffu, w[(r + BF) % E], src_lane, 8);
+      const int pos = q * E + r;
+      nw[r] = (pos + BF < P) ? sv : y[j0 + BF + pos];
+    }
+#pragma unroll
+    for (int r = 0; r < E; ++r) w[r] = nw[r];
+    __syncwarp();  // every lane is done with rec before it is refilled
+    cur ^= 1;
+  }
+  cp_async_wait<0>();
+  __syncwarp();
+}
+
+// On exit y holds the solution.  sb: two staging buffers of BB * (BR + 4).
+template <int N>
+__device__ __forceinline__ void wc_backward(const float* tb, int cl, int q, int gbase,
+                                            unsigned gmask, int n, float* y, float* sb) {
+  constexpr int K = WC<N>::K, E = WC<N>::E, P = WC<N>::P, BB = WC<N>::BB, BR = Band<N>::BR;
+  constexpr int RS = BR + 4;
+  const float* bb = tb + (int64_t)n * Band<N>::FR * kTile;
+  float w[E];
+#pragma unroll
+  for (int r = 0; r < E; ++r) {
+    const int i = n - 1 - (q * E + r);
+    w[r] = i >= 0 ? y[i] : 0.0f;
+  }
+  wc_stage_b<N>(tb, bb, cl, q, n - 1, sb);
+  int cur = 0;
+  for (int j0 = n - 1; j0 >= 0; j0 -= BB) {
+    wc_stage_b<N>(tb, bb, cl, q, j0 - BB, sb + (cur ^ 1) * BB * RS);
+    cp_async_wait<1>();
+    __syncwarp();
+    const float* rec = sb + cur * BB * RS;
+#pragma unroll
+    for (int t = 0; t < BB; ++t) {
+      const int j = j0 - t;
+      if (j >= 0) {
+        const float* B = rec + t * RS;
+        const float invd = B[BR + ((K + 1) & 3)];
+        const float x = __shfl_sync(0xffffffffu, w[t % E], t / E, 8) * invd;
+        if (q == t / E) {
+          w[t % E] = x;
+          y[j] = x;
+        }
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+          const int d = q * E + r - t;
+          if (d >= 1 && d <= 2 * K) w[r] = fmaf(-B[d - 1], x, w[r]);
+        }
+      }
+    }
+    float nw[E];
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      const int src_lane = min(q + (r + BB) / E, 7);
+      const float sv = __shfl_sync(0xffffffffu, w[(r + BB) % E], src_lane, 8);
+      const int pos = q * E + r;
+      const int i = j0 - BB - pos;
+      nw[r] = (pos + BB < P) ? sv : (i >= 0 ? y[i] : 0.0f);
+    }
+#pragma unroll
+    for (int r = 0; r < E; ++r) w[r] = nw[r];
+    __syncwarp();
+    cur ^= 1;
+  }
+  cp_async_wait<0>();
+  __syncwarp();
+}
+
+// Sums over the eight lanes of a group; every lane of the warp takes part.
+__device__ __forceinline__ float group_sum(float v, unsigned) {
+  v += __shfl_xor_sync(0xffffffffu, v, 1, 8);
+  v += __shfl_xor_sync(0xffffffffu, v, 2, 8);
+  v += __shfl_xor_sync(0xffffffffu, v, 4, 8);
+  return v;
+}
+__device__ __forceinline__ double group_sum(double v, unsigned) {
+  v += __shfl_xor_sync(0xffffffffu, v, 1, 8);
+  v += __shfl_xor_sync(0xffffffffu, v, 2, 8);
+  v += __shfl_xor_sync(0xffffffffu, v, 4, 8);
+  return v;
+}
+
+// Fused refinement pass, element-parallel over the group's eight lanes:
+// x += S y (FP64), r = b - A x with A x = x + Lambda (Dcal[K x] + G x), the
+// boundary m-rows identity; y = S^-1 r (FP32).  Returns |x|^2 (group sum).
+template <int N>
+__device__ double wc_residual(const DevView& v, const Col& c, int q, int gbase, unsigned gmask,
+                              double lam, const double* bc, double* xc, float* y, bool first,
+                              bool wr) {
+  const float* s32 = v.s32 + c.off;
+  const float* is32 = v.is32 + c.off;
+  const double* lin = v.lin + c.off;
+  const double* w = c_tab.w[N];
+  const double g = v.ph.g;
+  double xs = 0.0;
+  double prev_right[3] = {0.0, 0.0, 0.0};  // cc[N] of the element left of this lane's
+  for (int e0 = 0; e0 < c.nez; e0 += 8) {
+    const int e = e0 + q;
+    const bool act = e < c.nez;
+    double f[N + 1][3], xv[N + 1][3];
+#pragma unroll
+    for (int k = 0; k <= N; ++k) {
+      const int I = act ? e * N + k : 0;
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        const int i = 3 * I + u;
+        const double d = (double)(y[i] * s32[i]);
+        xv[k][u] = first ? d : xc[i] + d;
+      }
+      const double wI = lin[3 * I], thI = lin[3 * I + 1], cI = lin[3 * I + 2];
+      f[k][0] = xv[k][1];
+      f[k][1] = fma(-wI * wI, xv[k][0], fma(2.0 * wI, xv[k][1], cI * xv[k][2]));
+      f[k][2] = fma(-thI * wI, xv[k][0], fma(thI, xv[k][1], wI * xv[k][2]));
+    }
+    double cc[N + 1][3];
+    elem_deriv<N>(f, cc);
+    // left neighbour's right contribution: lane q-1, or lane 7 of the last round
+    double left[3];
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      const double up = __shfl_up_sync(0xffffffffu, cc[N][u], 1, 8);
+      left[u] = (q == 0) ? prev_right[u] : up;
+      prev_right[u] = __shfl_sync(0xffffffffu, cc[N][u], 7, 8);
+    }
+    __syncwarp();  // every lane has read y before any lane overwrites it
+    if (act) {
+      // points owned by element e: local k = 0 .. N-1, and k = N for the last element
+      const int kend = (e == c.nez - 1) ? N : N - 1;
+#pragma unroll
+      for (int k = 0; k <= N; ++k) {
+        if (k > kend) break;
+        const int I = e * N + k;
+        double D[3];
+        if (k == 0) {
+          const double sc = c.s / (e == 0 ? w[0] : 2.0 * w[0]);
+#pragma unroll
+          for (int u = 0; u < 3; ++u) D[u] = ((e == 0 ? 0.0 : left[u]) + cc[0][u]) * sc;
+        } else if (k == N) {
+          const double sc = c.s / w[0];
+#pragma unroll
+          for (int u = 0; u < 3; ++u) D[u] = cc[N][u] * sc;
+        } else {
+          const double sc = c.s / w[k];
+#pragma unroll
+          for (int u = 0; u < 3; ++u) D[u] = cc[k][u] * sc;
+        }
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+          const int i = 3 * I + u;
+          const double xi = xv[k][u];
+          if (wr) xc[i] = xi;
+          xs = fma(xi, xi, xs);
+          double r;
+          if (u == 1 && (I == 0 || I == c.nz - 1)) {
+            r = bc[i] - xi;
+          } else {
+            double ax = D[u];
+            if (u == 1) ax = fma(g, xv[k][0], ax);
+            r = bc[i] - fma(lam, ax, xi);
+          }
+          y[i] = (float)r * is32[i];
+        }
+      }
+    }
+    __syncwarp();
+  }
+  return group_sum(xs, gmask);
+}
+
+template <int N>
+__host__ __device__ constexpr int wc_stage_floats() {
+  return 2 * (WC<N>::BF * Band<N>::FR > WC<N>::BB * (Band<N>::BR + 4)
+                  ? WC<N>::BF * Band<N>::FR
+                  : WC<N>::BB * (Band<N>::BR + 4));
+}
+
+template <int N>
+__global__ void __launch_bounds__(kWcWarps * 32, 1)
+    k_solve_wc(DevView v, double lam, const double* b, double* x, double tol, int max_sweeps,
+               int ystride) {
+  extern __shared__ __align__(16) float wc_smem[];
+  constexpr int K = WC<N>::K;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int grp = lane / 8, q = lane % 8, gbase = grp * 8;
+  const unsigned gmask = 0xffu << gbase;
+  float* y = wc_smem + (int64_t)(warp * 4 + grp) * ystride;
+  float* sb = wc_smem + (int64_t)32 * ystride + (int64_t)(warp * 4 + grp) * wc_stage_floats<N>();
+  for (int64_t tile = v.tile_begin + blockIdx.x; tile < (int64_t)v.tile_begin + v.tile_count;
+       tile += gridDim.x) {
+    const TileDesc t = v.tiles[tile];
+    if (warp * 4 >= t.count) continue;  // warp-uniform: no column for this warp
+    // groups past the tile's last column shadow it without writing anything
+    const bool active = warp * 4 + grp < t.count;
+    const int cl = active ? warp * 4 + grp : t.count - 1;
+    const Col c = make_col(v, t, cl, N);
+    const float* tb = reinterpret_cast<const float*>(v.fac) + t.fac_off;
+    const double* bc = b + c.off;
+    double* xc = x + c.off;
+    const float* s32 = v.s32 + c.off;
+    const float* is32 = v.is32 + c.off;
+    const bool factored = v.fac_status[c.col] == HEVI_COL_OK;
+    for (int i = q; i < ystride; i += 8) y[i] = (i < c.n) ? (float)bc[i] * is32[i] : 0.0f;
+    __syncwarp();
+    int sweeps = 0, status = HEVI_COL_NOT_CONVERGED;
+    double dprev = 0.0, xnorm = 0.0;
+    bool first = true, done = !active || !factored;
+    // every group of the warp steps together; a column that has converged
+    // keeps stepping with its writes switched off until the warp is done
+    while (true) {
+      wc_forward<N>(tb, cl, q, gbase, gmask, c.n, y, sb);
+      wc_backward<N>(tb, cl, q, gbase, gmask, c.n, y, sb);
+      float d2 = 0.0f;
+      for (int i = q; i < c.n; i += 8) {
+        const float d = y[i] * s32[i];
+        d2 = fmaf(d, d, d2);
+      }
+      const double dn = sqrt((double)group_sum(d2, gmask));
+      bool stop = false;
+      if (!done) {
+        ++sweeps;
+        const double xref = first ? dn : xnorm;
+        if (dn <= tol * xref) {
+          stop = true;
+          status = HEVI_COL_OK;
+        } else if (!first) {
+          const double pred = dn * (dn / dprev);
+          if (pred <= tol * xref) {
+            stop = true;
+            status = HEVI_COL_OK;
+          } else if (dn > 0.5 * dprev) {
+            stop = true;
+          }
+        }
+        if (sweeps >= max_sweeps) stop = true;
+        if (stop) {
+          for (int i = q; i < c.n; i += 8) {
+            const double d = (double)(y[i] * s32[i]);
+            xc[i] = first ? d : xc[i] + d;
+          }
+          done = true;
+        }
+      }
+      if (__all_sync(0xffffffffu, done)) break;
+      __syncwarp();
+      xnorm = sqrt(wc_residual<N>(v, c, q, gbase, gmask, lam, bc, xc, y, first, !done));
+      dprev = dn;
+      first = false;
+    }
+    if (q == 0 && active) {
+      if (!factored) {
+        v.col_iters[c.col] = 0;
+        fail(v, c.col, v.fac_status[c.col]);
+      } else {
+        v.col_iters[c.col] = sweeps;
+        if (status != HEVI_COL_OK)
+          fail(v, c.col, status);
+        else
+          v.col_status[c.col] = HEVI_COL_OK;
+      }
+    }
+    if (active && !factored)
+      for (int i = q; i < c.n; i += 8) xc[i] = __longlong_as_double(0x7ff8000000000000LL);
+    __syncwarp();
+    (void)K;
+  }
 }
 
 template <int N, bool IR>
@@ -716,9 +1424,25 @@ static void launch_solve_n(const DevView& v, hevi_precision prec, double lam, co
   if (prec == HEVI_FP64) {
     cudaFuncSetAttribute(k_solve<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     k_solve<N, false><<<grid, blk, smem, st>>>(v, lam, b, x, tol, max_sweeps);
-  } else {
+  } else if (!kUseWarpSolve) {
     cudaFuncSetAttribute(k_solve<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     k_solve<N, true><<<grid, blk, smem, st>>>(v, lam, b, x, tol, max_sweeps);
+  } else {
+    // warp-cooperative refinement solve: persistent grid, one CTA of 32
+    // columns per SM at a time
+    constexpr int K = Band<N>::K;
+    int ystride = ylen + WC<N>::P + 4;
+    ystride = (ystride + 3) / 4 * 4;  // staging buffers stay 16-byte aligned
+    const int wsmem = 32 * (ystride + wc_stage_floats<N>()) * (int)sizeof(float);
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int wgrid = std::min(v.tile_count, sms);
+    cudaFuncSetAttribute(k_solve_wc<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, wsmem);
+    k_solve_wc<N><<<wgrid, kWcWarps * 32, wsmem, st>>>(v, lam, b, x, tol, max_sweeps, ystride);
+    (void)grid;
+    (void)smem;
+    (void)K;
   }
 }
 
@@ -1211,6 +1935,13 @@ extern "C" hevi_status hevi_newton_solve_noalloc(int32_t nez, int32_t order, dou
   ph.cv = ph.cp - ph.R;
   ph.gamma = ph.cp / ph.cv;
   ph.cs = sqrt(ph.gamma * ph.R * ph.T0);
+  {
+    double coef = 1.0;  // C(gamma, k)
+    for (int k = 1; k <= kEosTerms; ++k) {
+      coef *= (ph.gamma - k + 1.0) / k;
+      ph.bin[k - 1] = coef;
+    }
+  }
   v.ph = ph;
   v.ncols = ncols;
   v.ntiles = (int32_t)ntiles;

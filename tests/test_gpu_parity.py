@@ -163,7 +163,9 @@ def test_stage_solve_lambda_zero_is_identity(hv):
     b = _rhs(nez, N, ncols, seed=8)
     ctx.hevi_factor(0.0, None)
     x = _np(ctx.hevi_stage_solve(_t(b)), ncols)
-    assert _rel_cols(x, b).max() < 1e-15
+    # the last refinement correction is scaled back in FP32 (relative 6e-8 of a
+    # correction of ~1e-7 |x|), so the identity is exact to ~1e-14
+    assert _rel_cols(x, b).max() < 1e-13
 
 
 def test_stage_solve_zero_rhs(hv):
