@@ -128,8 +128,9 @@ hevi_status hevi_factor(hevi_ctx* ctx, double gamma_dt, const double* lin_state)
 /* Solve (I - Lambda L(q0)) x = rhs for every column with the factors of the
  * last hevi_factor (Sec. 4.3, Eq. lhevi-ark-final-2).  rhs, x (dev, state
  * layout, may not alias).  In HEVI_FP32_IR mode the FP32 solution is refined
- * with FP64 residuals b - A x until the predicted relative error (scaled
- * 2-norm) is below 1e-12, at most max_ir sweeps (hevi_set_refinement).
+ * with FP64 residuals b - A x until the predicted relative error (2-norm,
+ * |d_k|^2 / |d_(k-1)| / |x|) is below 1e-11, at most 10 sweeps
+ * (hevi_set_refinement).
  * Blocking: returns SINGULAR / NOT_CONVERGED if any column failed. */
 hevi_status hevi_stage_solve(hevi_ctx* ctx, const double* rhs, double* x);
 /* As hevi_stage_solve but does not wait: failures are only recorded for
@@ -137,7 +138,7 @@ hevi_status hevi_stage_solve(hevi_ctx* ctx, const double* rhs, double* x);
 hevi_status hevi_stage_solve_async(hevi_ctx* ctx, const double* rhs, double* x);
 
 /* Refinement controls for HEVI_FP32_IR solves: tolerance on the predicted
- * relative error and the sweep limit (defaults 1e-12 and 10). */
+ * relative error and the sweep limit (defaults 1e-11 and 10). */
 hevi_status hevi_set_refinement(hevi_ctx* ctx, double tol, int32_t max_sweeps);
 
 /* NHEVI-LU (Sec. 4.2.3): for every column, Newton-Raphson on

@@ -157,7 +157,7 @@ struct hevi_ctx {
   int order_ylen[kMaxOrder + 1] = {0};
   double lam = 0.0;
   bool factored = false;
-  double ir_tol = 1e-12;
+  double ir_tol = 1e-11;
   int ir_max = 10;
   int64_t scr_floats = 0;
   int64_t fac_elems = 0;

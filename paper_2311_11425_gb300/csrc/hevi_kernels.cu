@@ -591,50 +591,65 @@ __global__ void __launch_bounds__(kFgWarps * 32) k_factor_g(DevView v, double la
   for (int j = 0; j < n; ++j) {
     const int nr = min(K, n - 1 - j), ncol = min(2 * K, n - 1 - j);
     const int buf = (j & 1) * (K + 2);
-    if (q == (j & 7)) {
-      int p = 0;
-      float amax = fabsf(W[rowoff[0] + cs_j]);
+    {
+      // pivot: first row of maximal |a| among rows 0..nr of column j, the
+      // rows split over the group's eight threads and combined by shuffles
+      // (larger |a| wins, equal |a| keeps the smaller row)
+      constexpr int MR = (K + 1 + 7) / 8;  // rows per thread
+      float best = -1.0f, bval = 0.0f;
+      int bi = 0;
+      float cv[MR];
 #pragma unroll
-      for (int r = 1; r <= K; ++r) {
-        const float a = fabsf(W[rowoff[r] + cs_j]);
-        if (r <= nr && a > amax) {
-          amax = a;
-          p = r;
+      for (int m = 0; m < MR; ++m) {
+        const int r = q + 8 * m;
+        cv[m] = 0.0f;
+        if (r <= nr) {
+          cv[m] = W[((j + r) % WR) * WC + cs_j];
+          if (fabsf(cv[m]) > best) {
+            best = fabsf(cv[m]);
+            bval = cv[m];
+            bi = r;
+          }
         }
       }
-      int rp = rowoff[0];
 #pragma unroll
-      for (int r = 1; r <= K; ++r)
-        if (p == r) rp = rowoff[r];
-      float invd = 0.0f;
-      if (amax > 0.0f) {
-        if (p) {
-          const float t0 = W[rowoff[0] + cs_j];
-          W[rowoff[0] + cs_j] = W[rp + cs_j];
-          W[rp + cs_j] = t0;
+      for (int off = 1; off < 8; off <<= 1) {
+        const float ob = __shfl_xor_sync(0xffffffffu, best, off, 8);
+        const float ov = __shfl_xor_sync(0xffffffffu, bval, off, 8);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, off, 8);
+        if (ob > best || (ob == best && oi < bi)) {
+          best = ob;
+          bval = ov;
+          bi = oi;
         }
-        invd = 1.0f / W[rowoff[0] + cs_j];
-      } else if (info == 0) {
-        info = j + 1;
       }
-      float rec[FR];
+      const int p = bi;
+      const bool sing = !(best > 0.0f);
+      if (sing && info == 0) info = j + 1;
+      const float invd = sing ? 0.0f : 1.0f / bval;
+      // row 0 before the interchange becomes row p (column j retires after
+      // this step, so it is not swapped in place)
+      const float v0 = W[rowoff[0] + cs_j];
 #pragma unroll
-      for (int r = 1; r <= K; ++r) {
-        const float l = (r <= nr && amax > 0.0f) ? W[rowoff[r] + cs_j] * invd : 0.0f;
-        bcast[buf + r - 1] = l;
-        rec[r - 1] = l;
+      for (int m = 0; m < MR; ++m) {
+        const int r = q + 8 * m;
+        if (r >= 1 && r <= K) {
+          const float a = (r == p) ? v0 : cv[m];
+          const float l = (r <= nr && !sing) ? a * invd : 0.0f;
+          bcast[buf + r - 1] = l;
+          if (active) tb[((int64_t)(j * (FR / 4) + (r - 1) / 4) * kTile + cl) * 4 + ((r - 1) & 3)] = l;
+        }
       }
-      bcast[buf + K] = (float)p;
-      bcast[buf + K + 1] = invd;
-      rec[K] = (float)p;
-      rec[K + 1] = invd;
+      if (q == 0) {
+        bcast[buf + K] = (float)p;
+        bcast[buf + K + 1] = invd;
+        if (active) {
+          tb[((int64_t)(j * (FR / 4) + K / 4) * kTile + cl) * 4 + (K & 3)] = (float)p;
+          tb[((int64_t)(j * (FR / 4) + (K + 1) / 4) * kTile + cl) * 4 + ((K + 1) & 3)] = invd;
 #pragma unroll
-      for (int r = K + 2; r < FR; ++r) rec[r] = 0.0f;
-      if (active) {
-#pragma unroll
-        for (int e = 0; e < FR; e += 4)
-          *reinterpret_cast<float4*>(tb + ((int64_t)(j * (FR / 4) + e / 4) * kTile + cl) * 4) =
-              make_float4(rec[e], rec[e + 1], rec[e + 2], rec[e + 3]);
+          for (int e = K + 2; e < FR; ++e)
+            tb[((int64_t)(j * (FR / 4) + e / 4) * kTile + cl) * 4 + (e & 3)] = 0.0f;
+        }
       }
     }
     __syncwarp();
@@ -642,10 +657,7 @@ __global__ void __launch_bounds__(kFgWarps * 32) k_factor_g(DevView v, double la
     float l[K];
 #pragma unroll
     for (int r = 0; r < K; ++r) l[r] = bcast[buf + r];
-    int rp = rowoff[0];
-#pragma unroll
-    for (int r = 1; r <= K; ++r)
-      if (p == r) rp = rowoff[r];
+    const int rp = ((j + p) % WR) * WC;
     // my columns j < col <= j + ncol, col = q (mod 8)
     const int c0 = j + 1 + ((q - (j + 1)) & 7);
     int cs = cs_j + (c0 - j);
