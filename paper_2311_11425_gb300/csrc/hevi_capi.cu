@@ -161,6 +161,7 @@ struct hevi_ctx {
   int ir_max = 10;
   int64_t scr_floats = 0;
   int64_t fac_elems = 0;
+  int64_t ysc_floats = 0;
   // device allocations
   std::vector<void*> allocs;
   double* lin_newton = nullptr;
@@ -389,7 +390,7 @@ hevi_status hevi_setup(hevi_ctx** out, const hevi_column_grid* grid, const hevi_
   std::stable_sort(perm.begin(), perm.end(), [&](int32_t a, int32_t b) {
     return order[a] != order[b] ? order[a] < order[b] : cls[a] < cls[b];
   });
-  int64_t fac_off = 0, scr_off = 0;
+  int64_t fac_off = 0, scr_off = 0, y_off = 0;
   const int esz = precision == HEVI_FP64 ? 8 : 4;
   for (int64_t i = 0; i < ncols;) {
     const int32_t k = cls[perm[i]];
@@ -402,7 +403,9 @@ hevi_status hevi_setup(hevi_ctx** out, const hevi_column_grid* grid, const hevi_
     t.first = (int32_t)i;
     t.fac_off = fac_off;
     t.scr_off = scr_off;
+    t.y_off = y_off;
     const int64_t n = 3 * ((int64_t)t.nez * t.order + 1);
+    y_off += (n + 2 * (3 * (t.order + 1) - 1) + 4) * kTile;
     fac_off += n * rl_of(t.order) * kTile;
     scr_off += n * ur2_of(t.order) * kTile;
     if (c->order_count[t.order] == 0) c->order_begin[t.order] = (int32_t)c->h_tiles.size();
@@ -417,6 +420,7 @@ hevi_status hevi_setup(hevi_ctx** out, const hevi_column_grid* grid, const hevi_
   c->ntiles = (int64_t)c->h_tiles.size();
   c->fac_elems = fac_off;
   c->scr_floats = scr_off;
+  c->ysc_floats = y_off;
   (void)esz;
 
   static bool tables_done = false;
@@ -439,6 +443,8 @@ hevi_status hevi_setup(hevi_ctx** out, const hevi_column_grid* grid, const hevi_
       (s = c->alloc(&d_dz, ncols)) || (s = c->alloc(&d_ref, c->state_size)) ||
       (s = c->alloc(&c->v.lin, c->state_size)) || (s = c->alloc(&d_tiles, c->ntiles)) ||
       (s = c->alloc(&c->v.s32, c->state_size)) || (s = c->alloc(&c->v.is32, c->state_size)) ||
+      (s = c->alloc(&c->v.ithb, c->state_size / 3)) ||
+      (s = precision == HEVI_FP32_IR ? c->alloc(&c->v.ysc, c->ysc_floats) : HEVI_OK) ||
       (s = c->alloc(&d_fs, ncols)) || (s = c->alloc(&d_cs, ncols)) || (s = c->alloc(&d_it, ncols)) ||
       (s = c->alloc(&d_fail, kFailSlots)) ||
       (s = precision == HEVI_FP64 ? c->alloc((double**)&d_fac, c->fac_elems)

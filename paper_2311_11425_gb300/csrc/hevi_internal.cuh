@@ -47,6 +47,7 @@ struct TileDesc {
   int32_t first;      // index into the class-sorted column permutation
   int64_t fac_off;    // offset of the tile's factor records (elements of T)
   int64_t scr_off;    // offset of the tile's Newton scratch (floats)
+  int64_t y_off;      // offset of the tile's solve vectors (floats, (n + 2K) x 32)
 };
 
 // LGL tables per order (host fills them at setup): weights w_k, Dhat_kj =
@@ -79,6 +80,7 @@ struct DevView {
   const int32_t* perm;      // [ncols] class-sorted column index
   const double* col_dz;     // [ncols] element height
   const double* ref;        // state layout: (rho_bar, P_bar, Theta_bar) per point
+  double* ithb;             // per point (index off/3 + I): 1 / Theta_bar, or null
   float* s32;               // state layout: equilibration scales (rho_bar, rho_bar c_s, Theta_bar)
   float* is32;              // state layout: their reciprocals
   double* lin;              // state layout: (w0, theta0, c0 = gamma P0 / Theta0)
@@ -88,6 +90,7 @@ struct DevView {
   int32_t tile_count;
   void* fac;                // factor records (float or double)
   float* scr;               // Newton scratch (U records)
+  float* ysc;               // per tile: the FP32 work vectors of the refinement solve
   int32_t* fac_status;      // [ncols] status of the last factorisation
   int32_t* col_status;      // [ncols] status of the last call
   int32_t* col_iters;       // [ncols]
@@ -175,8 +178,8 @@ __device__ __forceinline__ double eos(const Phys& ph, double Theta) {
 // truncation below 1e-19 relative) replaces the FP64 log1p/expm1 pair, which
 // costs several times more on this part's FP64 pipe.
 __device__ __forceinline__ double eos_perturbation(const Phys& ph, double Theta, double Theta_bar,
-                                                   double P_bar) {
-  const double x = (Theta - Theta_bar) / Theta_bar;
+                                                   double P_bar, const double* inv_theta_bar = nullptr) {
+  const double x = inv_theta_bar ? (Theta - Theta_bar) * *inv_theta_bar : (Theta - Theta_bar) / Theta_bar;
   if (fabs(x) <= 0.02) {
     double s = ph.bin[kEosTerms - 1];
 #pragma unroll

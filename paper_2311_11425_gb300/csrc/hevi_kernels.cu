@@ -125,6 +125,7 @@ __global__ void k_setup_ref(DevView v, const int32_t* col_order, const int32_t* 
     r[3 * I + 0] = rho;
     r[3 * I + 1] = eos(ph, Th);
     r[3 * I + 2] = Th;
+    if (v.ithb) v.ithb[v.col_off[col] / 3 + I] = 1.0 / Th;
     if (v.s32) {
       const int64_t a = v.col_off[col] + 3 * I;
       const double sc[3] = {rho, rho * ph.cs, Th};
@@ -166,15 +167,15 @@ void launch_reference_state(const DevView& v, double* q, cudaStream_t st) {
 //   rho-flux (0, 1, 0);  m-flux (-w^2, 2w, c);  Theta-flux (-theta w, theta, w)
 // Returns false on a non-physical state.
 // ---------------------------------------------------------------------------
-// dP receives P(Theta) - P_bar.
+// dP receives P(Theta) - P_bar; ithb (optional) points at 1 / Theta_bar.
 __device__ __forceinline__ bool lin_coefs(const Phys& ph, double rho, double m, double Th,
                                           double Th_bar, double P_bar, double* w, double* th,
-                                          double* c, double* dP) {
+                                          double* c, double* dP, const double* ithb = nullptr) {
   if (!(rho > 0.0) || !(Th > 0.0) || !isfinite(m)) return false;
   const double ir = 1.0 / rho;
   *w = m * ir;
   *th = Th * ir;
-  *dP = eos_perturbation(ph, Th, Th_bar, P_bar);
+  *dP = eos_perturbation(ph, Th, Th_bar, P_bar, ithb);
   *c = ph.gamma * (P_bar + *dP) / Th;
   return true;
 }
@@ -550,7 +551,8 @@ __global__ void __launch_bounds__(kFgWarps * 32) k_factor_g(DevView v, double la
       rho = v.ref[a]; m = 0.0; Th = v.ref[a + 2];
     }
     double w, th, cc, dP;
-    if (!lin_coefs(ph, rho, m, Th, v.ref[a + 2], v.ref[a + 1], &w, &th, &cc, &dP)) {
+    if (!lin_coefs(ph, rho, m, Th, v.ref[a + 2], v.ref[a + 1], &w, &th, &cc, &dP,
+                   v.ithb ? v.ithb + c.off / 3 + I : nullptr)) {
       ok = false;
       w = th = cc = 0.0;
     }
@@ -770,9 +772,12 @@ void launch_factor(const DevView& v, int order, hevi_precision prec, double lam,
 // upper triangle with 2K super-diagonals, column by column).  The active
 // window of the sweep lives in registers: the loop over pivot steps is
 // unrolled by the window length so that every ring position is a
-// compile-time register.  y is the thread's slice of shared memory (stride =
-// threads per block), length n + 2K with a zero tail; the forward sweep
-// leaves the intermediate vector in y, the backward sweep the solution.
+// compile-time register.  y is the column's work vector with element stride
+// `stride` (shared memory, or the tile's interleaved global scratch), length
+// n + 2K with a zero tail; the forward sweep leaves the intermediate vector
+// in y, the backward sweep the solution.  PD > 0 prefetches the records of
+// step j +/- PD into L1 while step j computes: the sweep is a dependent chain
+// of n steps per thread, and without it every step waits for its record.
 // ---------------------------------------------------------------------------
 template <int N, typename T>
 __device__ __forceinline__ void load_vecs(const T* src, T* dst, int count) {
@@ -789,9 +794,20 @@ __device__ __forceinline__ void load_vecs(const T* src, T* dst, int count) {
   }
 }
 
-template <int N, typename T, typename Y>
+// Cache-line prefetch of one 16-byte record vector (no registers held).
+__device__ __forceinline__ void prefetch_line(const void* p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
+template <int N, typename T, typename Y, int PD = 0>
 __device__ __forceinline__ void forward_sweep(const T* base, int lane, int n, Y* y, int stride) {
   constexpr int K = Band<N>::K, WR = Band<N>::WR, FR = Band<N>::FR;
+  constexpr int NVF = FR / Vec<T>::W;
+  if constexpr (PD > 0) {
+    for (int jj = 0; jj < PD && jj < n; ++jj)
+#pragma unroll
+      for (int vv = 0; vv < NVF; ++vv) prefetch_line(frec_vec<N, T>(const_cast<T*>(base), jj, vv * Vec<T>::W, lane));
+  }
   Y w[WR];
 #pragma unroll
   for (int r = 0; r < WR; ++r) w[r] = y[r * stride];
@@ -800,6 +816,13 @@ __device__ __forceinline__ void forward_sweep(const T* base, int lane, int n, Y*
     for (int t = 0; t < WR; ++t) {
       const int j = j0 + t;
       if (j < n) {
+        if constexpr (PD > 0) {
+          if (j + PD < n) {
+#pragma unroll
+            for (int vv = 0; vv < NVF; ++vv)
+              prefetch_line(frec_vec<N, T>(const_cast<T*>(base), j + PD, vv * Vec<T>::W, lane));
+          }
+        }
         T f[FR];
         load_vecs<N, T>(frec_vec<N, T>(const_cast<T*>(base), j, 0, lane), f, FR);
         const int p = (int)f[K];
@@ -821,11 +844,20 @@ __device__ __forceinline__ void forward_sweep(const T* base, int lane, int n, Y*
 }
 
 // Backward substitution; returns the sum of squares of the solution.
-template <int N, typename T, typename Y>
+template <int N, typename T, typename Y, int PD = 0>
 __device__ __forceinline__ Y backward_sweep(const T* base, int lane, int n, Y* y, int stride) {
   constexpr int K = Band<N>::K, WB = Band<N>::WC, BR = Band<N>::BR, FR = Band<N>::FR;
   constexpr int W = Vec<T>::W;
+  constexpr int NVB = BR / W;
   using V = typename Vec<T>::type;
+  auto prefetch_step = [&](int jj) {
+#pragma unroll
+    for (int vv = 0; vv < NVB; ++vv) prefetch_line(brec_vec<N, T>(const_cast<T*>(base), n, jj, vv * W, lane));
+    prefetch_line(frec_vec<N, T>(const_cast<T*>(base), jj, K + 1, lane));
+  };
+  if constexpr (PD > 0) {
+    for (int jj = n - 1; jj > n - 1 - PD && jj >= 0; --jj) prefetch_step(jj);
+  }
   Y w[WB];
 #pragma unroll
   for (int cc = 0; cc < WB; ++cc) {
@@ -838,6 +870,9 @@ __device__ __forceinline__ Y backward_sweep(const T* base, int lane, int n, Y* y
     for (int t = 0; t < WB; ++t) {
       const int j = j0 - t;
       if (j >= 0) {
+        if constexpr (PD > 0) {
+          if (j - PD >= 0) prefetch_step(j - PD);
+        }
         T u[BR];
         load_vecs<N, T>(brec_vec<N, T>(const_cast<T*>(base), n, j, 0, lane), u, BR);
         const V dv = *reinterpret_cast<const V*>(frec_vec<N, T>(const_cast<T*>(base), j, K + 1, lane));
@@ -920,8 +955,9 @@ __device__ void solve_ir_column(const DevView& v, const TileDesc& t, int lane, d
   double dprev = 0.0, xnorm = 0.0;
   bool first = true;
   while (true) {
-    forward_sweep<N, float, float>(base, lane, c.n, y, stride);
-    backward_sweep<N, float, float>(base, lane, c.n, y, stride);
+    // records of step j+2 are prefetched into L1 while step j computes
+    forward_sweep<N, float, float, 2>(base, lane, c.n, y, stride);
+    backward_sweep<N, float, float, 2>(base, lane, c.n, y, stride);
     ++sweeps;
     // size of the correction d = S y in the caller's (unscaled) norm
     float d2 = 0.0f;
@@ -998,425 +1034,32 @@ __device__ void solve_ir_column(const DevView& v, const TileDesc& t, int lane, d
     v.col_status[c.col] = HEVI_COL_OK;
 }
 
-// ---------------------------------------------------------------------------
-// Warp-cooperative stage solve with FP32 factors and FP64 refinement.
-//
-// Eight lanes cooperate on one column (four columns per warp, one tile of 32
-// columns per CTA of eight warps).  Each lane holds E consecutive entries of
-// the active window of the triangular sweep in registers; a pivot step costs
-// one pair of shuffles (interchange + broadcast of the pivot value) and E
-// FMAs per lane, and the window is shifted once per block of steps.  With a
-// persistent grid of one CTA per SM only ~4.9k columns are in flight, so the
-// factor records that a column's refinement sweeps re-read stay in L2.
-// The FP64 residual b - A x is element-parallel over the eight lanes, with
-// the contributions of shared element-boundary points exchanged by shuffle.
-// ---------------------------------------------------------------------------
+// FP32 + refinement solve: one warp per block, one column per thread, the
+// work vector in the tile's interleaved global scratch.  The solve is latency
+// bound per thread (two dependent passes of n pivot steps), so what matters is
+// that every column is resident at once: with 96 registers 20 one-warp blocks
+// fit an SM, i.e. 97k columns in one wave on 152 SMs.
 template <int N>
-struct WC {
-  static constexpr int K = Band<N>::K;
-  static constexpr int E = (2 * K + 8 + 7) / 8;  // window entries per lane
-  static constexpr int P = 8 * E;                // window positions per column
-  static constexpr int BF = P - K;               // forward steps per block
-  static constexpr int BB = P - 2 * K;           // backward steps per block
-  static constexpr int NVF = Band<N>::FR / 4;
-  static constexpr int NVB = Band<N>::BR / 4;
-};
+__global__ void __launch_bounds__(32, 20) k_solve_ir(DevView v, double lam, const double* b,
+                                                     double* x, double tol, int max_sweeps) {
+  const int lane = threadIdx.x;
+  const TileDesc t = v.tiles[v.tile_begin + blockIdx.x];
+  if (lane >= t.count) return;
+  float* y = v.ysc + t.y_off + lane;
+  solve_ir_column<N>(v, t, lane, lam, b, x, y, kTile, tol, max_sweeps);
+}
 
-constexpr int kWcWarps = 8;  // warps per CTA: 32 columns
-// The warp-cooperative solve runs ~10x more instructions per column than the
-// one-column-per-thread solve (each of the eight lanes repeats the pivot and
-// shuffle logic); the latter is used.
-constexpr bool kUseWarpSolve = false;
-
-// Element e of the forward record of step j for tile column cl.
+// Plain FP64 solve; the work vectors live in shared memory.
 template <int N>
-__device__ __forceinline__ float wc_f(const float* tb, int j, int e, int cl) {
-  return tb[((int64_t)(j * WC<N>::NVF + (e >> 2)) * kTile + cl) * 4 + (e & 3)];
-}
-template <int N>
-__device__ __forceinline__ float wc_b(const float* bb, int j, int e, int cl) {
-  return bb[((int64_t)(j * WC<N>::NVB + (e >> 2)) * kTile + cl) * 4 + (e & 3)];
-}
-
-// Asynchronous 16-byte global -> shared copies (completion is awaited with
-// cp.async.wait_group, a hardware wait).
-__device__ __forceinline__ void cp_async16(float* smem_dst, const float* gsrc) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int Pending>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(Pending) : "memory");
-}
-
-// Stage the forward records of steps [js, js + BF) of tile column cl into
-// dst[step][FR] (8 lanes share the copies).
-template <int N>
-__device__ __forceinline__ void wc_stage_f(const float* tb, int cl, int q, int n, int js, float* dst) {
-  constexpr int NV = WC<N>::NVF, FR = Band<N>::FR;
-  for (int k = q; k < WC<N>::BF * NV; k += 8) {
-    const int jj = js + k / NV, vv = k % NV;
-    if (jj < n) cp_async16(dst + (k / NV) * FR + vv * 4, tb + ((int64_t)(jj * NV + vv) * kTile + cl) * 4);
-  }
-  cp_async_commit();
-}
-
-// Stage the backward records (and the forward vector holding 1/u_jj) of the
-// steps js, js-1, .., js-BB+1 into dst[step][BR + 4].
-template <int N>
-__device__ __forceinline__ void wc_stage_b(const float* tb, const float* bb, int cl, int q, int js,
-                                           float* dst) {
-  constexpr int NV = WC<N>::NVB, BR = Band<N>::BR, K = Band<N>::K, NVF = WC<N>::NVF;
-  constexpr int PER = NV + 1;
-  for (int k = q; k < WC<N>::BB * PER; k += 8) {
-    const int tt = k / PER, vv = k % PER, jj = js - tt;
-    if (jj >= 0) {
-      const float* src = (vv < NV) ? bb + ((int64_t)(jj * NV + vv) * kTile + cl) * 4
-                                   : tb + ((int64_t)(jj * NVF + (K + 1) / 4) * kTile + cl) * 4;
-      cp_async16(dst + tt * (BR + 4) + vv * 4, src);
-    }
-  }
-  cp_async_commit();
-}
-
-// y: the group's FP32 vector in shared memory, length >= n + P + 2K with a
-// zero tail.  On exit it holds the forward result.  sb: two staging buffers
-// of BF * FR floats.
-template <int N>
-__device__ __forceinline__ void wc_forward(const float* tb, int cl, int q, int gbase,
-                                           unsigned gmask, int n, float* y, float* sb) {
-  constexpr int K = WC<N>::K, E = WC<N>::E, P = WC<N>::P, BF = WC<N>::BF, FR = Band<N>::FR;
-  float w[E];
-#pragma unroll
-  for (int r = 0; r < E; ++r) w[r] = y[q * E + r];
-  wc_stage_f<N>(tb, cl, q, n, 0, sb);
-  int cur = 0;
-  for (int j0 = 0; j0 < n; j0 += BF) {
-    wc_stage_f<N>(tb, cl, q, n, j0 + BF, sb + (cur ^ 1) * BF * FR);
-    cp_async_wait<1>();
-    __syncwarp();
-    const float* rec = sb + cur * BF * FR;
-#pragma unroll
-    for (int t = 0; t < BF; ++t) {
-      const int j = j0 + t;
-      if (j < n) {
-        const float* F = rec + t * FR;
-        const int p = (int)F[K];
-        const int s = t + p;
-        const int sl = s / E, sr = s - sl * E;
-        float cand = w[0];
-#pragma unroll
-        for (int r = 1; r < E; ++r)
-          if (sr == r) cand = w[r];
-        const float vnew = __shfl_sync(0xffffffffu, cand, sl, 8);
-        const float vold = __shfl_sync(0xffffffffu, w[t % E], t / E, 8);
-        if (p != 0 && q == sl) {
-#pragma unroll
-          for (int r = 0; r < E; ++r)
-            if (sr == r) w[r] = vold;
-        }
-        if (q == t / E) {
-          w[t % E] = vnew;
-          y[j] = vnew;
-        }
-#pragma unroll
-        for (int r = 0; r < E; ++r) {
-          const int d = q * E + r - t;
-          if (d >= 1 && d <= K) w[r] = fmaf(-F[d - 1], vnew, w[r]);
-        }
-      }
-    }
-    // shift by BF: position i takes old position i + BF; the tail is fresh
-    float nw[E];
-#pragma unroll
-    for (int r = 0; r < E; ++r) {
-      const int src_lane = min(q + (r + BF) / E, 7);
-      const float sv = __shfl_sync(0xffffffffu, w[(r + BF) % E], src_lane, 8);
-      const int pos = q * E + r;
-      nw[r] = (pos + BF < P) ? sv : y[j0 + BF + pos];
-    }
-#pragma unroll
-    for (int r = 0; r < E; ++r) w[r] = nw[r];
-    __syncwarp();  // every lane is done with rec before it is refilled
-    cur ^= 1;
-  }
-  cp_async_wait<0>();
-  __syncwarp();
-}
-
-// On exit y holds the solution.  sb: two staging buffers of BB * (BR + 4).
-template <int N>
-__device__ __forceinline__ void wc_backward(const float* tb, int cl, int q, int gbase,
-                                            unsigned gmask, int n, float* y, float* sb) {
-  constexpr int K = WC<N>::K, E = WC<N>::E, P = WC<N>::P, BB = WC<N>::BB, BR = Band<N>::BR;
-  constexpr int RS = BR + 4;
-  const float* bb = tb + (int64_t)n * Band<N>::FR * kTile;
-  float w[E];
-#pragma unroll
-  for (int r = 0; r < E; ++r) {
-    const int i = n - 1 - (q * E + r);
-    w[r] = i >= 0 ? y[i] : 0.0f;
-  }
-  wc_stage_b<N>(tb, bb, cl, q, n - 1, sb);
-  int cur = 0;
-  for (int j0 = n - 1; j0 >= 0; j0 -= BB) {
-    wc_stage_b<N>(tb, bb, cl, q, j0 - BB, sb + (cur ^ 1) * BB * RS);
-    cp_async_wait<1>();
-    __syncwarp();
-    const float* rec = sb + cur * BB * RS;
-#pragma unroll
-    for (int t = 0; t < BB; ++t) {
-      const int j = j0 - t;
-      if (j >= 0) {
-        const float* B = rec + t * RS;
-        const float invd = B[BR + ((K + 1) & 3)];
-        const float x = __shfl_sync(0xffffffffu, w[t % E], t / E, 8) * invd;
-        if (q == t / E) {
-          w[t % E] = x;
-          y[j] = x;
-        }
-#pragma unroll
-        for (int r = 0; r < E; ++r) {
-          const int d = q * E + r - t;
-          if (d >= 1 && d <= 2 * K) w[r] = fmaf(-B[d - 1], x, w[r]);
-        }
-      }
-    }
-    float nw[E];
-#pragma unroll
-    for (int r = 0; r < E; ++r) {
-      const int src_lane = min(q + (r + BB) / E, 7);
-      const float sv = __shfl_sync(0xffffffffu, w[(r + BB) % E], src_lane, 8);
-      const int pos = q * E + r;
-      const int i = j0 - BB - pos;
-      nw[r] = (pos + BB < P) ? sv : (i >= 0 ? y[i] : 0.0f);
-    }
-#pragma unroll
-    for (int r = 0; r < E; ++r) w[r] = nw[r];
-    __syncwarp();
-    cur ^= 1;
-  }
-  cp_async_wait<0>();
-  __syncwarp();
-}
-
-// Sums over the eight lanes of a group; every lane of the warp takes part.
-__device__ __forceinline__ float group_sum(float v, unsigned) {
-  v += __shfl_xor_sync(0xffffffffu, v, 1, 8);
-  v += __shfl_xor_sync(0xffffffffu, v, 2, 8);
-  v += __shfl_xor_sync(0xffffffffu, v, 4, 8);
-  return v;
-}
-__device__ __forceinline__ double group_sum(double v, unsigned) {
-  v += __shfl_xor_sync(0xffffffffu, v, 1, 8);
-  v += __shfl_xor_sync(0xffffffffu, v, 2, 8);
-  v += __shfl_xor_sync(0xffffffffu, v, 4, 8);
-  return v;
-}
-
-// Fused refinement pass, element-parallel over the group's eight lanes:
-// x += S y (FP64), r = b - A x with A x = x + Lambda (Dcal[K x] + G x), the
-// boundary m-rows identity; y = S^-1 r (FP32).  Returns |x|^2 (group sum).
-template <int N>
-__device__ double wc_residual(const DevView& v, const Col& c, int q, int gbase, unsigned gmask,
-                              double lam, const double* bc, double* xc, float* y, bool first,
-                              bool wr) {
-  const float* s32 = v.s32 + c.off;
-  const float* is32 = v.is32 + c.off;
-  const double* lin = v.lin + c.off;
-  const double* w = c_tab.w[N];
-  const double g = v.ph.g;
-  double xs = 0.0;
-  double prev_right[3] = {0.0, 0.0, 0.0};  // cc[N] of the element left of this lane's
-  for (int e0 = 0; e0 < c.nez; e0 += 8) {
-    const int e = e0 + q;
-    const bool act = e < c.nez;
-    double f[N + 1][3], xv[N + 1][3];
-#pragma unroll
-    for (int k = 0; k <= N; ++k) {
-      const int I = act ? e * N + k : 0;
-#pragma unroll
-      for (int u = 0; u < 3; ++u) {
-        const int i = 3 * I + u;
-        const double d = (double)(y[i] * s32[i]);
-        xv[k][u] = first ? d : xc[i] + d;
-      }
-      const double wI = lin[3 * I], thI = lin[3 * I + 1], cI = lin[3 * I + 2];
-      f[k][0] = xv[k][1];
-      f[k][1] = fma(-wI * wI, xv[k][0], fma(2.0 * wI, xv[k][1], cI * xv[k][2]));
-      f[k][2] = fma(-thI * wI, xv[k][0], fma(thI, xv[k][1], wI * xv[k][2]));
-    }
-    double cc[N + 1][3];
-    elem_deriv<N>(f, cc);
-    // left neighbour's right contribution: lane q-1, or lane 7 of the last round
-    double left[3];
-#pragma unroll
-    for (int u = 0; u < 3; ++u) {
-      const double up = __shfl_up_sync(0xffffffffu, cc[N][u], 1, 8);
-      left[u] = (q == 0) ? prev_right[u] : up;
-      prev_right[u] = __shfl_sync(0xffffffffu, cc[N][u], 7, 8);
-    }
-    __syncwarp();  // every lane has read y before any lane overwrites it
-    if (act) {
-      // points owned by element e: local k = 0 .. N-1, and k = N for the last element
-      const int kend = (e == c.nez - 1) ? N : N - 1;
-#pragma unroll
-      for (int k = 0; k <= N; ++k) {
-        if (k > kend) break;
-        const int I = e * N + k;
-        double D[3];
-        if (k == 0) {
-          const double sc = c.s / (e == 0 ? w[0] : 2.0 * w[0]);
-#pragma unroll
-          for (int u = 0; u < 3; ++u) D[u] = ((e == 0 ? 0.0 : left[u]) + cc[0][u]) * sc;
-        } else if (k == N) {
-          const double sc = c.s / w[0];
-#pragma unroll
-          for (int u = 0; u < 3; ++u) D[u] = cc[N][u] * sc;
-        } else {
-          const double sc = c.s / w[k];
-#pragma unroll
-          for (int u = 0; u < 3; ++u) D[u] = cc[k][u] * sc;
-        }
-#pragma unroll
-        for (int u = 0; u < 3; ++u) {
-          const int i = 3 * I + u;
-          const double xi = xv[k][u];
-          if (wr) xc[i] = xi;
-          xs = fma(xi, xi, xs);
-          double r;
-          if (u == 1 && (I == 0 || I == c.nz - 1)) {
-            r = bc[i] - xi;
-          } else {
-            double ax = D[u];
-            if (u == 1) ax = fma(g, xv[k][0], ax);
-            r = bc[i] - fma(lam, ax, xi);
-          }
-          y[i] = (float)r * is32[i];
-        }
-      }
-    }
-    __syncwarp();
-  }
-  return group_sum(xs, gmask);
-}
-
-template <int N>
-__host__ __device__ constexpr int wc_stage_floats() {
-  return 2 * (WC<N>::BF * Band<N>::FR > WC<N>::BB * (Band<N>::BR + 4)
-                  ? WC<N>::BF * Band<N>::FR
-                  : WC<N>::BB * (Band<N>::BR + 4));
-}
-
-template <int N>
-__global__ void __launch_bounds__(kWcWarps * 32, 1)
-    k_solve_wc(DevView v, double lam, const double* b, double* x, double tol, int max_sweeps,
-               int ystride) {
-  extern __shared__ __align__(16) float wc_smem[];
-  constexpr int K = WC<N>::K;
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int grp = lane / 8, q = lane % 8, gbase = grp * 8;
-  const unsigned gmask = 0xffu << gbase;
-  float* y = wc_smem + (int64_t)(warp * 4 + grp) * ystride;
-  float* sb = wc_smem + (int64_t)32 * ystride + (int64_t)(warp * 4 + grp) * wc_stage_floats<N>();
-  for (int64_t tile = v.tile_begin + blockIdx.x; tile < (int64_t)v.tile_begin + v.tile_count;
-       tile += gridDim.x) {
-    const TileDesc t = v.tiles[tile];
-    if (warp * 4 >= t.count) continue;  // warp-uniform: no column for this warp
-    // groups past the tile's last column shadow it without writing anything
-    const bool active = warp * 4 + grp < t.count;
-    const int cl = active ? warp * 4 + grp : t.count - 1;
-    const Col c = make_col(v, t, cl, N);
-    const float* tb = reinterpret_cast<const float*>(v.fac) + t.fac_off;
-    const double* bc = b + c.off;
-    double* xc = x + c.off;
-    const float* s32 = v.s32 + c.off;
-    const float* is32 = v.is32 + c.off;
-    const bool factored = v.fac_status[c.col] == HEVI_COL_OK;
-    for (int i = q; i < ystride; i += 8) y[i] = (i < c.n) ? (float)bc[i] * is32[i] : 0.0f;
-    __syncwarp();
-    int sweeps = 0, status = HEVI_COL_NOT_CONVERGED;
-    double dprev = 0.0, xnorm = 0.0;
-    bool first = true, done = !active || !factored;
-    // every group of the warp steps together; a column that has converged
-    // keeps stepping with its writes switched off until the warp is done
-    while (true) {
-      wc_forward<N>(tb, cl, q, gbase, gmask, c.n, y, sb);
-      wc_backward<N>(tb, cl, q, gbase, gmask, c.n, y, sb);
-      float d2 = 0.0f;
-      for (int i = q; i < c.n; i += 8) {
-        const float d = y[i] * s32[i];
-        d2 = fmaf(d, d, d2);
-      }
-      const double dn = sqrt((double)group_sum(d2, gmask));
-      bool stop = false;
-      if (!done) {
-        ++sweeps;
-        const double xref = first ? dn : xnorm;
-        if (dn <= tol * xref) {
-          stop = true;
-          status = HEVI_COL_OK;
-        } else if (!first) {
-          const double pred = dn * (dn / dprev);
-          if (pred <= tol * xref) {
-            stop = true;
-            status = HEVI_COL_OK;
-          } else if (dn > 0.5 * dprev) {
-            stop = true;
-          }
-        }
-        if (sweeps >= max_sweeps) stop = true;
-        if (stop) {
-          for (int i = q; i < c.n; i += 8) {
-            const double d = (double)(y[i] * s32[i]);
-            xc[i] = first ? d : xc[i] + d;
-          }
-          done = true;
-        }
-      }
-      if (__all_sync(0xffffffffu, done)) break;
-      __syncwarp();
-      xnorm = sqrt(wc_residual<N>(v, c, q, gbase, gmask, lam, bc, xc, y, first, !done));
-      dprev = dn;
-      first = false;
-    }
-    if (q == 0 && active) {
-      if (!factored) {
-        v.col_iters[c.col] = 0;
-        fail(v, c.col, v.fac_status[c.col]);
-      } else {
-        v.col_iters[c.col] = sweeps;
-        if (status != HEVI_COL_OK)
-          fail(v, c.col, status);
-        else
-          v.col_status[c.col] = HEVI_COL_OK;
-      }
-    }
-    if (active && !factored)
-      for (int i = q; i < c.n; i += 8) xc[i] = __longlong_as_double(0x7ff8000000000000LL);
-    __syncwarp();
-    (void)K;
-  }
-}
-
-template <int N, bool IR>
-__global__ void __launch_bounds__(128) k_solve(DevView v, double lam, const double* b, double* x,
-                                               double tol, int max_sweeps) {
+__global__ void __launch_bounds__(128) k_solve_fp64(DevView v, const double* b, double* x) {
   extern __shared__ unsigned char smem_raw[];
   const int warp = threadIdx.x / kTile, lane = threadIdx.x % kTile;
   const int64_t tile = v.tile_begin + (int64_t)blockIdx.x * (blockDim.x / kTile) + warp;
   if (tile >= (int64_t)v.tile_begin + v.tile_count) return;
   const TileDesc t = v.tiles[tile];
   if (lane >= t.count) return;
-  const int stride = blockDim.x;
-  if (IR) {
-    float* y = reinterpret_cast<float*>(smem_raw) + threadIdx.x;
-    solve_ir_column<N>(v, t, lane, lam, b, x, y, stride, tol, max_sweeps);
-  } else {
-    double* y = reinterpret_cast<double*>(smem_raw) + threadIdx.x;
-    solve_fp64_column<N>(v, t, lane, b, x, y, stride);
-  }
+  double* y = reinterpret_cast<double*>(smem_raw) + threadIdx.x;
+  solve_fp64_column<N>(v, t, lane, b, x, y, blockDim.x);
 }
 
 // Threads per block for a per-thread shared-memory footprint of `bytes`.
@@ -1429,32 +1072,15 @@ static int pick_block(int bytes, int max_blk) {
 template <int N>
 static void launch_solve_n(const DevView& v, hevi_precision prec, double lam, const double* b,
                            double* x, double tol, int max_sweeps, int ylen, cudaStream_t st) {
-  const int esz = prec == HEVI_FP64 ? (int)sizeof(double) : (int)sizeof(float);
-  const int blk = pick_block(ylen * esz, 128), tiles_per_blk = blk / kTile;
-  const unsigned grid = (unsigned)((v.tile_count + tiles_per_blk - 1) / tiles_per_blk);
-  const int smem = ylen * blk * esz;
   if (prec == HEVI_FP64) {
-    cudaFuncSetAttribute(k_solve<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    k_solve<N, false><<<grid, blk, smem, st>>>(v, lam, b, x, tol, max_sweeps);
-  } else if (!kUseWarpSolve) {
-    cudaFuncSetAttribute(k_solve<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    k_solve<N, true><<<grid, blk, smem, st>>>(v, lam, b, x, tol, max_sweeps);
+    const int esz = (int)sizeof(double);
+    const int blk = pick_block(ylen * esz, 128), tiles_per_blk = blk / kTile;
+    const unsigned grid = (unsigned)((v.tile_count + tiles_per_blk - 1) / tiles_per_blk);
+    const int smem = ylen * blk * esz;
+    cudaFuncSetAttribute(k_solve_fp64<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    k_solve_fp64<N><<<grid, blk, smem, st>>>(v, b, x);
   } else {
-    // warp-cooperative refinement solve: persistent grid, one CTA of 32
-    // columns per SM at a time
-    constexpr int K = Band<N>::K;
-    int ystride = ylen + WC<N>::P + 4;
-    ystride = (ystride + 3) / 4 * 4;  // staging buffers stay 16-byte aligned
-    const int wsmem = 32 * (ystride + wc_stage_floats<N>()) * (int)sizeof(float);
-    int dev = 0, sms = 152;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int wgrid = std::min(v.tile_count, sms);
-    cudaFuncSetAttribute(k_solve_wc<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, wsmem);
-    k_solve_wc<N><<<wgrid, kWcWarps * 32, wsmem, st>>>(v, lam, b, x, tol, max_sweeps, ystride);
-    (void)grid;
-    (void)smem;
-    (void)K;
+    k_solve_ir<N><<<(unsigned)v.tile_count, kTile, 0, st>>>(v, lam, b, x, tol, max_sweeps);
   }
 }
 
@@ -1487,7 +1113,8 @@ __device__ void apply_V_column(const DevView& v, const Col& c, const double* q, 
     if (!(rho > 0.0) || !(Th > 0.0)) ok = false;
     const double ir = 1.0 / rho;
     f[0] = m;
-    f[1] = fma(m * m, ir, eos_perturbation(ph, Th, ref[3 * I + 2], ref[3 * I + 1]));
+    f[1] = fma(m * m, ir, eos_perturbation(ph, Th, ref[3 * I + 2], ref[3 * I + 1],
+                                           v.ithb ? v.ithb + c.off / 3 + I : nullptr));
     f[2] = Th * m * ir;
   };
   auto o = [&](int I, const double* D) {
@@ -1668,7 +1295,8 @@ __device__ void newton_column(const DevView& v, const TileDesc& t, int lane, dou
         }
       }
       double w, th, cc, dP;
-      if (!lin_coefs(ph, qi[0], qi[1], qi[2], ref[3 * I + 2], ref[3 * I + 1], &w, &th, &cc, &dP)) {
+      if (!lin_coefs(ph, qi[0], qi[1], qi[2], ref[3 * I + 2], ref[3 * I + 1], &w, &th, &cc, &dP,
+                     v.ithb ? v.ithb + c.off / 3 + I : nullptr)) {
         ok = false;
         w = th = cc = dP = 0.0;
       }
