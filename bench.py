@@ -198,10 +198,15 @@ def gpu_arm(args, rank, world, local_rank, pool, cores):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    from paper_2311_11425_gb300.shard import shard_of
     hv.load(build=True)
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream()
-    inp = hevi_inputs.lhevi_ark3(seed=2 + rank)
+    # weak scaling: a global grid of world x 86,402 columns, one contiguous
+    # shard per rank (each shard a seeded copy of the cubed-sphere workload)
+    start, stop = shard_of(world * NCOLS, rank, world)
+    assert stop - start == NCOLS
+    inp = hevi_inputs.lhevi_ark3(seed=2 + start // NCOLS)
     H = torch.from_numpy(inp["H"].reshape(-1)).to(dev)
     tab = hv.tableau("ARK3")
 
