@@ -33,11 +33,20 @@
  *   R6  pivot tie-break: the first row of maximal |a| (LAPACK semantics);
  *   R7  Newton: initial guess supplied by the caller, stop when
  *       ||S^-1 F(q_m)||_2 <= rtol ||S^-1 F(q_0)||_2 with S the reference
- *       scales (rho_bar, rho_bar*c_s, Theta_bar); F(q_0) = 0 stops at m = 0.
+ *       scales (rho_bar, rho_bar*c_s, Theta_bar), or when
+ *       ||S^-1 F(q_m)||_2 <= 512 eps ||S^-1 q_m||_2 (eps = 2^-52): the
+ *       residual is then at the rounding level of its own FP64 evaluation and
+ *       the relative test cannot be met when ||F(q_0)|| is itself within
+ *       1/rtol of that level (a column already near its stage solution).
+ *       Both tests are applied to q_0 as well (m = 0 updates).
  */
+#include <float.h>
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+
+/* reading R7: rounding floor of the Newton stop */
+#define OR_NEWTON_FLOOR (512.0 * DBL_EPSILON)
 
 /* physical constants of the isothermal reference atmosphere */
 #define OR_T0 300.0
@@ -501,7 +510,7 @@ int or_newton(int ncols, int nez, int N, const double* ztop, double lam, const d
     double f0 = scaled_norm(&col, F);
     iters[c] = 0;
     status[c] = 0;
-    if (f0 > 0.0) {
+    if (f0 > OR_NEWTON_FLOOR * scaled_norm(&col, qc)) {
       status[c] = 5;
       for (int m = 1; m <= max_iter; ++m) {
         assemble_band(&col, lam, qc, ab, ldab);
@@ -511,7 +520,11 @@ int or_newton(int ncols, int nez, int N, const double* ztop, double lam, const d
         for (int i = 0; i < n; ++i) qc[i] += F[i];
         iters[c] = m;
         residual_F(&col, lam, qc, R + o, F);
-        if (scaled_norm(&col, F) <= rtol * f0) { status[c] = 0; break; }
+        double fn = scaled_norm(&col, F);
+        if (fn <= rtol * f0 || fn <= OR_NEWTON_FLOOR * scaled_norm(&col, qc)) {
+          status[c] = 0;
+          break;
+        }
       }
     }
     column_free(&col);

@@ -1253,13 +1253,18 @@ void launch_apply_stage(const DevView& v, int order, const double* Q, const doub
 #undef HEVI_CALL
 }
 
+// Rounding floor of the Newton stop: |S^-1 F| <= 512 eps |S^-1 q|, eps = 2^-52
+// (a residual evaluated in FP64 stalls at 60-90 eps |S^-1 q| on the stiffest
+// columns of the workloads, acoustic Courant number ~500).
+constexpr double kNewtonFloor = 512.0 * 2.220446049250313e-16;
+
 // ---------------------------------------------------------------------------
 // NHEVI-LU Newton solve (Sec. 4.2.3), one column per thread, fused:
 //   F(q) = q - Lambda V(q) - R (FP64), y = -S^-1 F (FP32);
 //   J(q) assembled from FP64 point coefficients, equilibrated, LU-factored in
 //   FP32 with the L part applied to y on the fly; U records to scratch;
 //   backward sweep; q += S y (FP64); repeat until
-//   |S^-1 F(q_m)| <= rtol |S^-1 F(q_0)| or max_iter updates.
+//   |S^-1 F(q_m)| <= max(rtol |S^-1 F(q_0)|, 512 eps |S^-1 q_m|) or max_iter updates.
 // ---------------------------------------------------------------------------
 template <int N>
 __device__ void newton_column(const DevView& v, const TileDesc& t, int lane, double lam, double* q,
@@ -1280,9 +1285,11 @@ __device__ void newton_column(const DevView& v, const TileDesc& t, int lane, dou
   };
   bool ok = true;
 
-  // F pass with the pending update q += S y (when `update`); returns |S^-1 F|.
+  // F pass with the pending update q += S y (when `update`); returns |S^-1 F|
+  // and leaves |S^-1 q| in qnorm.
+  double qnorm = 0.0;
   auto fpass = [&](bool update) -> double {
-    double fn = 0.0;
+    double fn = 0.0, qn = 0.0;
     auto flux = [&](int I, double* f) {
       double qi[3];
 #pragma unroll
@@ -1320,20 +1327,29 @@ __device__ void newton_column(const DevView& v, const TileDesc& t, int lane, dou
           if (u == 1) vterm = fma(ph.g, qc[3 * I] - ref[3 * I], vterm);
           F = fma(lam, vterm, qc[i]) - Rc[i];
         }
-        const double sF = F / ref_scale(ref, cs, 3 * I, u);
+        const double sc = ref_scale(ref, cs, 3 * I, u);
+        const double sF = F / sc, sq = qc[i] / sc;
         fn += sF * sF;
+        qn += sq * sq;
         y[i * stride] = (float)(-sF);
       }
     };
     element_pass<N>(c, c_tab.w[N], c_tab.wD[N], flux, out);
+    qnorm = sqrt(qn);
     return sqrt(fn);
+  };
+  // converged: the relative test of Sec. 4.2.3, or the residual at the
+  // rounding level of its own FP64 evaluation (where the relative test cannot
+  // be met: |F(q_0)| itself within 1/rtol of that level)
+  auto converged = [&](double fn, double f0) {
+    return fn <= rtol * f0 || fn <= kNewtonFloor * qnorm;
   };
 
   for (int i = c.n; i < c.n + 2 * K; ++i) y[i * stride] = 0.0f;
   const double f0 = fpass(false);
   int it = 0, status = HEVI_COL_OK;
   if (!ok) status = HEVI_COL_BAD_INPUT;
-  if (ok && f0 > 0.0 && max_iter > 0) {
+  if (ok && !converged(f0, f0) && max_iter > 0) {
     status = HEVI_COL_NOT_CONVERGED;
     for (it = 1; it <= max_iter; ++it) {
       // factor J(q_m) with the forward substitution applied to y on the fly
@@ -1367,7 +1383,7 @@ __device__ void newton_column(const DevView& v, const TileDesc& t, int lane, dou
         status = HEVI_COL_BAD_INPUT;
         break;
       }
-      if (fn <= rtol * f0) {
+      if (converged(fn, f0)) {
         status = HEVI_COL_OK;
         break;
       }

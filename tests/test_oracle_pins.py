@@ -347,6 +347,29 @@ def test_newton_converges_quadratically():
     assert norms[4] < 1e-13, norms
 
 
+def test_newton_restart_from_root_stops_at_rounding_floor():
+    """Reading R7: restarted from its own root, Newton has |F(q_0)| at the
+    rounding level of the FP64 residual, where the relative test
+    |F(q_m)| <= rtol |F(q_0)| cannot be met; the rounding floor
+    |S^-1 F| <= 512 eps |S^-1 q| stops it at once, converged.  Stiffest
+    class of the workloads (Nez = 24, N = 4, 30 km top: acoustic Courant
+    number ~480 at dt = 300 s)."""
+    nez, N, lam = 24, 4, 87.868
+    q0 = _perturbed_state(nez, N, seed=16, amp_w=1.0, amp_th=0.5)[None]
+    R = q0.copy()
+    root, it, st = oracle.newton(nez, N, ZTOP, lam, R, q0, rtol=1e-10, max_iter=20)
+    assert st[0] == 0 and 1 <= it[0] <= 8
+    s = oracle.scales(oracle.column_grid(nez, N, ZTOP)[0])
+    F = root - lam * oracle.apply_V(nez, N, ZTOP, root) - R
+    assert np.linalg.norm(F / s) <= 512 * np.finfo(float).eps * np.linalg.norm(root / s)
+    again, it2, st2 = oracle.newton(nez, N, ZTOP, lam, R, root, rtol=1e-10, max_iter=20)
+    assert st2[0] == 0 and it2[0] == 0 and np.array_equal(again, root)
+    # with the relative test alone (floor below rounding) it would not stop:
+    # one more update moves the root by no more than rounding
+    moved, it3, _ = oracle.newton(nez, N, ZTOP, lam, R, root, rtol=0.0, max_iter=1)
+    assert it3[0] == 0 or np.linalg.norm((moved - root) / s) < 1e-12
+
+
 def test_newton_linear_problem_one_iteration():
     """For V := L_RS (q - q_bar) (linear), Newton converges in one iteration;
     checked through the ARK driver: NHEVI and LHEVI-RS agree on the linear
