@@ -345,12 +345,103 @@ def gpu_arm(args, rank, world, local_rank, pool, cores):
                               "unit": "column-solves/s", "ms_per_step": f["ms_per_step"],
                               "kernels": {k: v[0] / max(1, v[1]) for k, v in f["kernels"].items()
                                           if v[1]}}
+    if world == 1 and not args.no_extra:
+        line["batched"] = batched_run(args)
+        line["serving"] = serving_run(args)
     if world == 1 and not args.no_cpu:
         rate, cb = cpu_oracle_rate(pool, cores)
         line["cpu_baseline"] = cb
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# secondary workloads (reported inside the main line, rank 0, one GPU)
+# ---------------------------------------------------------------------------
+
+def batched_run(args):
+    """Uneven columns: 200,000 columns of four size classes with tops uniform
+    in 30-100 km, LHEVI-PS ARK4 steps replayed from a captured graph (two
+    steps per replay) and, for comparison, the same steps called one by one."""
+    import torch
+    import hevi_inputs
+    import paper_2311_11425_gb300 as hv
+    inp = hevi_inputs.batched(seed=4)
+    classes = hevi_inputs.SIZE_CLASSES
+    ctx = hv.Context(classes, inp["ztop"], class_of_col=inp["class_of_col"],
+                     precision=hv.FP32_IR)
+    off = ctx.offsets()
+    import numpy as np
+    H = np.zeros(ctx.n)
+    for blk in inp["blocks"]:
+        n = 3 * (blk["nez"] * blk["N"] + 1)
+        H[(off[blk["cols"]][:, None] + np.arange(n)[None, :]).reshape(-1)] = blk["H"].reshape(-1)
+    H = torch.from_numpy(H).cuda()
+    tab = hv.tableau("ARK4")
+    stream = torch.cuda.current_stream()
+    qa = ctx.hevi_reference_state()
+    qb = torch.empty_like(qa)
+    g = ctx.hevi_lhevi_graph(tab, inp["dt"], qa, qb, H, nsteps=2)
+    reps = max(2, min(10, args.steps // 5))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(2):
+        g.launch()
+    torch.cuda.synchronize()
+    l0 = ctx.launch_count
+    e0.record(stream)
+    for _ in range(reps):
+        g.launch()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_graph = e0.elapsed_time(e1) / (2 * reps)
+    launches = (ctx.launch_count - l0) / (2 * reps)
+    e0.record(stream)
+    for _ in range(reps):
+        ctx.hevi_lhevi_step(tab, inp["dt"], qa, H, qb)
+        ctx.hevi_lhevi_step(tab, inp["dt"], qb, H, qa)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_calls = e0.elapsed_time(e1) / (2 * reps)
+    try:
+        ctx.hevi_sync()
+        st = "ok"
+    except hv.HeviError as e:
+        st = str(e)
+    finite = bool(torch.isfinite(qa).all())
+    g.close()
+    ctx.close()
+    torch.cuda.empty_cache()
+    implicit = tab.s - 1
+    return {"workload": f"batched: {inp['ncols']} columns, classes {list(classes)} uniform, "
+                        f"ztop U(30, 100) km, LHEVI-PS ARK4 ({implicit} implicit stages), "
+                        f"dt={inp['dt']} s, graph of 2 steps per replay",
+            "value": implicit * inp["ncols"] / (ms_graph * 1e-3), "unit": "column-solves/s",
+            "ms_per_step_graph": ms_graph, "ms_per_step_calls": ms_calls,
+            "kernel_launches_per_step": launches, "steps_timed": 2 * reps,
+            "status": st, "state_finite": finite}
+
+
+def serving_run(args):
+    """Poisson arrivals at 50/s; per request U{2000..86402} columns of the four
+    classes, U{1..20} ARK3 steps, LHEVI or NHEVI-LU with probability 1/2;
+    150 GB device budget; latency from arrival to completion."""
+    import torch
+    import hevi_inputs
+    from paper_2311_11425_gb300.serve import Request, Server, latency_stats
+    raw = hevi_inputs.serve_requests(seed=5, count=args.serve_requests, rate=50.0)
+    reqs = [Request(**r) for r in raw]
+    server = Server(hbm_budget=150 * 10**9, tab="ARK3")
+    res = server.run(reqs, realtime=True)
+    torch.cuda.empty_cache()
+    out = {"workload": f"serving: {len(reqs)} requests, Poisson 50/s, columns U(2000, 86402) of "
+                       f"4 classes, steps U(1, 20), LHEVI-PS or NHEVI-LU ARK3, budget 150 GB",
+           "peak_bytes": server.peak_bytes}
+    out.update(latency_stats(res))
+    errs = [r.error for r in res if r.error]
+    if errs:
+        out["errors"] = errs[:3]
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -434,6 +525,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the batched-columns and serving sub-measurements")
+    ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--ncu-case", choices=["factor", "solve", "apply", "newton", "step"],
                     help="run only a few launches of one operation (for ncu captures)")
     ap.add_argument("--ncu-reps", type=int, default=2)

@@ -133,23 +133,34 @@ def lhevi_ark3(seed: int = 2, ne: int = 30, nez: int = 10, N: int = 4, ztop: flo
                 dq=np.zeros((len(pts), n)), H=horizontal_tendency(g, pts, nez, N, zt))
 
 
+def state_increment(g: np.random.Generator, nez: int, N: int, ztop: np.ndarray,
+                    amp: float = 1.0) -> np.ndarray:
+    """Increment on the rest state for NHEVI inputs: m = density_like * w with
+    w ~ U(-amp, amp) m/s at interior points; Theta = density_like * theta' with
+    theta' an amp K Gaussian (centre U(0.25, 0.75) of the column, width 1/15)
+    as in ``lhevi_stage``.  Returns [ncols, n]."""
+    ztop = np.asarray(ztop, dtype=np.float64)
+    count = ztop.size
+    nz, n = sizes(nez, N)
+    s = _s(nz)
+    a = density_like(s, ztop)
+    centre = g.uniform(0.25, 0.75, count)
+    dq = np.zeros((count, nz, 3))
+    dq[:, 1:-1, 1] = a[:, 1:-1] * amp * g.uniform(-1.0, 1.0, (count, nz - 2))
+    dq[:, :, 2] = a * amp * gaussian_bump(s, centre, 1.0 / 15.0)
+    return dq.reshape(count, n)
+
+
 def nhevi_ark2(seed: int = 3, ne: int = 30, nez: int = 16, N: int = 3, ztop: float = 30e3,
                dt: float = 300.0, ncols: int | None = None) -> dict:
-    """One NHEVI-LU ARK2 step with H = 0 from the rest state plus an increment
-    dq: m = density_like * w, w ~ U(-1, 1) m/s at interior points; Theta =
-    density_like * theta', theta' a 1 K Gaussian as in ``lhevi_stage``."""
+    """One NHEVI-LU ARK2 step with H = 0 from the rest state plus the
+    increment of ``state_increment``."""
     g = rng(seed)
     count = 6 * (ne * 4) ** 2 + 2 if ncols is None else ncols
     nz, n = sizes(nez, N)
-    s = _s(nz)
     zt = np.full(count, ztop)
-    a = density_like(s, zt)
-    centre = g.uniform(0.25, 0.75, count)
-    dq = np.zeros((count, nz, 3))
-    dq[:, 1:-1, 1] = a[:, 1:-1] * g.uniform(-1.0, 1.0, (count, nz - 2))
-    dq[:, :, 2] = a * 1.0 * gaussian_bump(s, centre, 1.0 / 15.0)
-    return dict(nez=nez, N=N, ncols=count, ztop=zt, dt=dt, dq=dq.reshape(count, n),
-                H=np.zeros((count, n)))
+    dq = state_increment(g, nez, N, zt)
+    return dict(nez=nez, N=N, ncols=count, ztop=zt, dt=dt, dq=dq, H=np.zeros((count, n)))
 
 
 def batched(seed: int = 4, ncols: int = 200_000, classes=SIZE_CLASSES,
@@ -178,3 +189,46 @@ def pack(blocks, ncols: int):
     off = np.zeros(ncols + 1, dtype=np.int64)
     np.cumsum(n_of, out=off[1:])
     return n_of, off
+
+
+def serve_requests(seed: int = 5, count: int = 2000, rate: float = 50.0,
+                   cols_range=(2000, 86402), steps_range=(1, 20), classes=SIZE_CLASSES,
+                   ztop_range=(30e3, 100e3)) -> list:
+    """A stream of serving requests: Poisson arrivals at `rate` per second;
+    per request a column count and a step count uniform in their ranges, the
+    variant LHEVI or NHEVI with probability 1/2, and columns as in ``batched``
+    (class uniform, top uniform, tendency from uniform sphere positions),
+    packed in column order.  NHEVI requests also start from the rest state
+    plus the increment of ``state_increment`` at amplitude 0.1 (dq; at full
+    amplitude a few coarse, tall columns go non-physical within a few steps).  Returns a list of dicts
+    (rid, arrival, classes, class_of_col, ztop, steps, variant, H, dq)."""
+    g = rng(seed)
+    t = 0.0
+    out = []
+    for i in range(count):
+        t += float(g.exponential(1.0 / rate))
+        ncols = int(g.integers(cols_range[0], cols_range[1] + 1))
+        steps = int(g.integers(steps_range[0], steps_range[1] + 1))
+        variant = "LHEVI" if g.random() < 0.5 else "NHEVI"
+        cls = g.integers(0, len(classes), ncols).astype(np.int32)
+        zt = g.uniform(*ztop_range, ncols)
+        pts = sphere_points_uniform(g, ncols)
+        blocks = []
+        for c, (nez, N) in enumerate(classes):
+            idx = np.nonzero(cls == c)[0]
+            blocks.append(dict(nez=nez, N=N, cols=idx,
+                               H=horizontal_tendency(g, pts[idx], nez, N, zt[idx])))
+        n_of, off = pack(blocks, ncols)
+        H = np.zeros(int(off[-1]))
+        dq = np.zeros(int(off[-1])) if variant == "NHEVI" else None
+        for blk in blocks:
+            n = 3 * (blk["nez"] * blk["N"] + 1)
+            if len(blk["cols"]):
+                pos = (off[blk["cols"]][:, None] + np.arange(n)[None, :]).reshape(-1)
+                H[pos] = blk["H"].reshape(-1)
+                if dq is not None:
+                    dq[pos] = state_increment(g, blk["nez"], blk["N"], zt[blk["cols"]],
+                                              amp=0.1).reshape(-1)
+        out.append(dict(rid=i, arrival=t, classes=list(classes), class_of_col=cls, ztop=zt,
+                        steps=steps, variant=variant, H=H, dq=dq))
+    return out

@@ -214,6 +214,43 @@ hevi_status hevi_nhevi_step(hevi_ctx* ctx, int32_t s, const double* A, const dou
                             const double* b, double dt, const double* q_in, const double* H,
                             double* q_out, double rtol, int32_t max_iter);
 
+/* A time loop of nsteps LHEVI or NHEVI-LU steps captured once into a CUDA
+ * graph and replayed with one launch (the stage loop of Sec. 4.2/4.3 with the
+ * same kernels and arithmetic as hevi_lhevi_step / hevi_nhevi_step, so a
+ * replay gives bit-identical results to the same steps called one by one).
+ * The steps ping-pong between two caller buffers: step k reads q_a and writes
+ * q_b for even k, the reverse for odd k, so after a replay the state is in
+ * q_b when nsteps is odd and in q_a when it is even.  H is read at every
+ * replay (its contents may change between replays, its address may not);
+ * the tableau arrays are copied at creation.  Capture runs on a private
+ * stream, so ctx's stream may be any stream including the legacy default;
+ * the workspace the steps need is allocated before capture.  Replays run on
+ * ctx's stream at the time of hevi_graph_launch.  The context must outlive
+ * the graph; hevi_graph_destroy frees it (NULL is a no-op).
+ * INVALID_ARG for bad arguments (as the step calls, nsteps < 1, q_a == q_b);
+ * CUDA if capture or instantiation fails. */
+typedef struct hevi_graph hevi_graph;
+hevi_status hevi_lhevi_graph_create(hevi_ctx* ctx, int32_t s, const double* A, const double* At,
+                                    const double* b, double dt, double* q_a, double* q_b,
+                                    const double* H, int32_t nsteps, int32_t lin_about_rest,
+                                    hevi_graph** out);
+hevi_status hevi_nhevi_graph_create(hevi_ctx* ctx, int32_t s, const double* A, const double* At,
+                                    const double* b, double dt, double* q_a, double* q_b,
+                                    const double* H, int32_t nsteps, double rtol,
+                                    int32_t max_iter, hevi_graph** out);
+hevi_status hevi_graph_launch(hevi_graph* g);
+void hevi_graph_destroy(hevi_graph* g);
+
+/* Device bytes that hevi_setup(grid, precision) allocates, plus the
+ * workspace of the first step call of one kind: kind 0 = setup only, 1 = an
+ * LHEVI step (hevi_lhevi_step / hevi_lhevi_graph_create) with `stages`
+ * stages, 2 = an NHEVI-LU step (hevi_nhevi_step / hevi_nhevi_graph_create,
+ * Newton scratch included).  Equal to hevi_device_bytes() after those calls.
+ * Host arithmetic only (no device call, z_top not read); -1 for invalid
+ * arguments (as hevi_setup, or kind outside 0..2, stages outside 2..8). */
+int64_t hevi_estimate_bytes(const hevi_column_grid* grid, hevi_precision precision, int32_t kind,
+                            int32_t stages);
+
 /* Named ESDIRK tableaux of Sec. 6 (the paper names them; the coefficients
  * come from the cited constructions): "ARK2" = ARK(2,3,2)b with a32 = 1/2,
  * "ARK3" = ARK3(2)4L[2]SA and "ARK4" = ARK4(3)6L[2]SA of Kennedy & Carpenter.

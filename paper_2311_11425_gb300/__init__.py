@@ -14,6 +14,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import weakref
 
 from . import build as _build_mod
 
@@ -93,6 +94,13 @@ def load(build: bool = False):
         "hevi_profile_kinds": (_I32, []),
         "hevi_profile_kind_name": (ctypes.c_char_p, [_I32]),
         "hevi_profile_read": (_I32, [_P, _I32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64)]),
+        "hevi_lhevi_graph_create": (_I32, [_P, _I32, DP, DP, DP, _D, _P, _P, _P, _I32, _I32,
+                                           ctypes.POINTER(_P)]),
+        "hevi_nhevi_graph_create": (_I32, [_P, _I32, DP, DP, DP, _D, _P, _P, _P, _I32, _D, _I32,
+                                           ctypes.POINTER(_P)]),
+        "hevi_graph_launch": (_I32, [_P]),
+        "hevi_estimate_bytes": (_I64, [ctypes.POINTER(_Grid), _I32, _I32, _I32]),
+        "hevi_graph_destroy": (None, [_P]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -100,6 +108,30 @@ def load(build: bool = False):
         f.argtypes = args
     _lib = lib
     return lib
+
+
+class Graph:
+    """A captured step loop (hevi_graph); keeps its context and buffers alive."""
+
+    def __init__(self, ctx, handle, keep):
+        self._ctx, self._h, self._keep = ctx, handle, keep
+
+    def launch(self):
+        """hevi_graph_launch: one replay on the context's stream (asynchronous)."""
+        if not self._h:
+            raise HeviError("graph is closed")
+        _check(self._ctx._lib.hevi_graph_launch(self._h), "hevi_graph_launch")
+
+    def close(self):
+        if self._h:
+            self._ctx._lib.hevi_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Tableau:
@@ -184,6 +216,31 @@ def hevi_newton_solve_noalloc(nez, order, z_top, ncols, gamma_dt, state, R, stat
     return state
 
 
+LHEVI, NHEVI = 1, 2  # step kinds of hevi_estimate_bytes
+
+
+def hevi_estimate_bytes(classes, class_of_col=None, ncols=None, precision=FP32_IR, kind=0,
+                        stages=2) -> int:
+    """Device bytes of a context over this column set plus the workspace of its
+    first step of `kind` (0 none, LHEVI, NHEVI) with `stages` stages
+    (hevi_estimate_bytes); host arithmetic only, no device needed."""
+    import numpy as np
+    lib = load()
+    classes = [tuple(int(v) for v in c) for c in classes]
+    if ncols is None:
+        ncols = 1 if class_of_col is None else len(class_of_col)
+    arr = (_SizeClass * len(classes))(*[_SizeClass(nez, order) for nez, order in classes])
+    cptr, cc = None, None
+    if class_of_col is not None:
+        cc = np.ascontiguousarray(class_of_col, dtype=np.int32)
+        cptr = cc.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    grid = _Grid(int(ncols), arr, len(classes), cptr, None)
+    b = int(lib.hevi_estimate_bytes(ctypes.byref(grid), int(precision), int(kind), int(stages)))
+    if b < 0:
+        raise HeviError(1, "hevi_estimate_bytes: invalid arguments")
+    return b
+
+
 class Context:
     """A set of columns on the current CUDA device (wraps ``hevi_ctx``).
 
@@ -229,9 +286,12 @@ class Context:
         self.precision = precision
         self.n = int(lib.hevi_state_size(h))
         self.device = torch.device("cuda", torch.cuda.current_device())
+        self._graphs = weakref.WeakSet()
 
     # -- housekeeping ---------------------------------------------------------
     def close(self):
+        for g in list(getattr(self, "_graphs", ())):
+            g.close()  # a graph must not outlive its context
         if getattr(self, "_h", None):
             self._lib.hevi_destroy(self._h)
             self._h = None
@@ -332,6 +392,33 @@ class Context:
                                          self._v(H), self._v(q_out), float(rtol), int(max_iter)),
                "hevi_nhevi_step")
         return q_out
+
+    def hevi_lhevi_graph(self, tab, dt, q_a, q_b, H, nsteps=1, lin_about_rest=False):
+        """nsteps LHEVI steps captured into one CUDA graph (hevi_lhevi_graph_create);
+        replays ping-pong between q_a and q_b (result in q_b for odd nsteps)."""
+        A, pA = _darr(tab.A)
+        At, pAt = _darr(tab.At)
+        b, pb = _darr(tab.b)
+        h = _P()
+        _check(self._lib.hevi_lhevi_graph_create(
+            self._h, len(b), pA, pAt, pb, float(dt), self._v(q_a), self._v(q_b), self._v(H),
+            int(nsteps), int(bool(lin_about_rest)), ctypes.byref(h)), "hevi_lhevi_graph_create")
+        g = Graph(self, h, (q_a, q_b, H))
+        self._graphs.add(g)
+        return g
+
+    def hevi_nhevi_graph(self, tab, dt, q_a, q_b, H, nsteps=1, rtol=1e-10, max_iter=20):
+        """nsteps NHEVI-LU steps captured into one CUDA graph (hevi_nhevi_graph_create)."""
+        A, pA = _darr(tab.A)
+        At, pAt = _darr(tab.At)
+        b, pb = _darr(tab.b)
+        h = _P()
+        _check(self._lib.hevi_nhevi_graph_create(
+            self._h, len(b), pA, pAt, pb, float(dt), self._v(q_a), self._v(q_b), self._v(H),
+            int(nsteps), float(rtol), int(max_iter), ctypes.byref(h)), "hevi_nhevi_graph_create")
+        g = Graph(self, h, (q_a, q_b, H))
+        self._graphs.add(g)
+        return g
 
     def hevi_profile(self, enable: bool):
         _check(self._lib.hevi_profile(self._h, int(bool(enable))), "hevi_profile")

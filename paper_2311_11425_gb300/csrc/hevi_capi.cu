@@ -181,6 +181,12 @@ struct hevi_ctx {
   std::vector<cudaEvent_t> ev_pool;
   double prof_ms[8] = {0};
   int64_t prof_n[8] = {0};
+  // fork/join of per-order launches when several orders are present: the
+  // kernels of each order run on their own stream, concurrently
+  int norders = 0;
+  cudaStream_t aux[kMaxOrder + 1] = {nullptr};
+  cudaEvent_t fork_ev = nullptr;
+  cudaEvent_t join_ev[kMaxOrder + 1] = {nullptr};
 
   template <typename T>
   hevi_status alloc(T** p, size_t count) {
@@ -257,16 +263,32 @@ hevi_status check_launch(hevi_ctx* c, int n = 0) {
   return cudaGetLastError() == cudaSuccess ? HEVI_OK : HEVI_ERR_CUDA;
 }
 
-// Run f(view, order, ylen) for every order present, with the view's tile
-// range set to that order's tiles.
+// Run f(view, order, ylen, stream) for every order present, with the view's
+// tile range set to that order's tiles.  With one order the launch goes to
+// the context's stream.  With several, each order's launch goes to its own
+// stream, forked from and joined back into the context's stream by events,
+// so that the orders' kernels share the GPU instead of running one after
+// the other (each with its own partial last wave).  Fork and join are plain
+// event record/wait pairs and so are also valid under stream capture.
 template <class F>
 void for_orders(hevi_ctx* c, const DevView& base, F&& f) {
+  const bool fork = c->norders > 1;
+  if (fork) cudaEventRecord(c->fork_ev, c->stream);
   for (int N = 1; N <= kMaxOrder; ++N) {
     if (!c->order_count[N]) continue;
     DevView v = base;
     v.tile_begin = c->order_begin[N];
     v.tile_count = c->order_count[N];
-    f(v, N, c->order_ylen[N]);
+    cudaStream_t sk = c->stream;
+    if (fork) {
+      sk = c->aux[N];
+      cudaStreamWaitEvent(sk, c->fork_ev, 0);
+    }
+    f(v, N, c->order_ylen[N], sk);
+    if (fork) {
+      cudaEventRecord(c->join_ev[N], sk);
+      cudaStreamWaitEvent(c->stream, c->join_ev[N], 0);
+    }
     c->launches += 1;
   }
 }
@@ -457,6 +479,20 @@ hevi_status hevi_setup(hevi_ctx** out, const hevi_column_grid* grid, const hevi_
     hevi_destroy(c);
     return HEVI_ERR_OOM;
   }
+  for (int N = 1; N <= kMaxOrder; ++N) c->norders += c->order_count[N] ? 1 : 0;
+  if (c->norders > 1) {
+    bool ok = cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming) == cudaSuccess;
+    for (int N = 1; N <= kMaxOrder && ok; ++N) {
+      if (!c->order_count[N]) continue;
+      ok = cudaStreamCreateWithFlags(&c->aux[N], cudaStreamNonBlocking) == cudaSuccess &&
+           cudaEventCreateWithFlags(&c->join_ev[N], cudaEventDisableTiming) == cudaSuccess;
+    }
+    if (!ok) {
+      cudaGetLastError();
+      hevi_destroy(c);
+      return HEVI_ERR_CUDA;
+    }
+  }
   cudaMemcpy(d_off, c->h_off.data(), (ncols + 1) * sizeof(int64_t), cudaMemcpyHostToDevice);
   cudaMemcpy(d_perm, perm.data(), ncols * sizeof(int32_t), cudaMemcpyHostToDevice);
   cudaMemcpy(d_order, order.data(), ncols * sizeof(int32_t), cudaMemcpyHostToDevice);
@@ -494,9 +530,58 @@ void hevi_destroy(hevi_ctx* c) {
   cudaStreamSynchronize(c->stream);
   fold_profile(c);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  for (int N = 0; N <= kMaxOrder; ++N) {
+    if (c->aux[N]) {
+      cudaStreamSynchronize(c->aux[N]);
+      cudaStreamDestroy(c->aux[N]);
+    }
+    if (c->join_ev[N]) cudaEventDestroy(c->join_ev[N]);
+  }
+  if (c->fork_ev) cudaEventDestroy(c->fork_ev);
   for (void* p : c->allocs) cudaFree(p);
   if (c->h_fail) cudaFreeHost(c->h_fail);
   delete c;
+}
+
+int64_t hevi_estimate_bytes(const hevi_column_grid* grid, hevi_precision precision, int32_t kind,
+                            int32_t stages) {
+  if (!grid || grid->ncols <= 0 || !grid->classes || grid->nclasses <= 0 ||
+      grid->ncols > (int64_t)INT32_MAX || (grid->nclasses > 1 && !grid->class_of_col))
+    return -1;
+  if (precision != HEVI_FP64 && precision != HEVI_FP32_IR) return -1;
+  if (kind < 0 || kind > 2 || (kind > 0 && (stages < 2 || stages > 8))) return -1;
+  std::vector<int64_t> count(grid->nclasses, 0);
+  for (int c = 0; c < grid->nclasses; ++c) {
+    const hevi_size_class& k = grid->classes[c];
+    if (k.order < 1 || k.order > kMaxOrder || k.nez < 1 || k.nez > 4096) return -1;
+  }
+  for (int64_t i = 0; i < grid->ncols; ++i) {
+    const int32_t k = grid->class_of_col ? grid->class_of_col[i] : 0;
+    if (k < 0 || k >= grid->nclasses) return -1;
+    count[k] += 1;
+  }
+  // the same sizes as hevi_setup: tiles of up to 32 columns of one class
+  const int64_t ncols = grid->ncols;
+  int64_t state = 0, ntiles = 0, fac = 0, scr = 0, ysc = 0;
+  for (int c = 0; c < grid->nclasses; ++c) {
+    if (!count[c]) continue;
+    const int N = grid->classes[c].order;
+    const int64_t n = 3 * ((int64_t)grid->classes[c].nez * N + 1);
+    const int64_t tiles = (count[c] + kTile - 1) / kTile;
+    state += n * count[c];
+    ntiles += tiles;
+    ysc += tiles * (n + 2 * (3 * (N + 1) - 1) + 4) * kTile;
+    fac += tiles * n * rl_of(N) * kTile;
+    scr += tiles * n * ur2_of(N) * kTile;
+  }
+  const int64_t esz = precision == HEVI_FP64 ? 8 : 4;
+  int64_t b = (ncols + 1) * 8 + 3 * ncols * 4 + ncols * 8 + 2 * state * 8 +
+              ntiles * (int64_t)sizeof(TileDesc) + 2 * state * 4 + (state / 3) * 8 +
+              (precision == HEVI_FP32_IR ? ysc * 4 : 0) + 3 * ncols * 4 + kFailSlots * 4 +
+              fac * esz;
+  if (kind == 1) b += (2 * (int64_t)stages + 1) * state * 8;
+  if (kind == 2) b += ((int64_t)stages + 2) * state * 8 + state * 8 + scr * 4;
+  return b;
 }
 
 hevi_status hevi_set_stream(hevi_ctx* c, void* stream) {
@@ -533,8 +618,8 @@ hevi_status hevi_factor(hevi_ctx* c, double gamma_dt, const double* lin_state) {
   if (!c || !(gamma_dt >= 0.0) || !std::isfinite(gamma_dt)) return HEVI_ERR_INVALID_ARG;
   {
     Scope sc(c, kFactor);
-    for_orders(c, c->v, [&](const DevView& v, int N, int ylen) {
-      hevi::launch_factor(v, N, c->prec, gamma_dt, lin_state, ylen, c->stream);
+    for_orders(c, c->v, [&](const DevView& v, int N, int ylen, cudaStream_t sk) {
+      hevi::launch_factor(v, N, c->prec, gamma_dt, lin_state, ylen, sk);
     });
   }
   c->lam = gamma_dt;
@@ -546,8 +631,8 @@ hevi_status hevi_stage_solve_async(hevi_ctx* c, const double* rhs, double* x) {
   if (!c || !rhs || !x || rhs == x || !c->factored) return HEVI_ERR_INVALID_ARG;
   {
     Scope sc(c, kSolve);
-    for_orders(c, c->v, [&](const DevView& v, int N, int ylen) {
-      hevi::launch_solve(v, N, c->prec, c->lam, rhs, x, c->ir_tol, c->ir_max, ylen, c->stream);
+    for_orders(c, c->v, [&](const DevView& v, int N, int ylen, cudaStream_t sk) {
+      hevi::launch_solve(v, N, c->prec, c->lam, rhs, x, c->ir_tol, c->ir_max, ylen, sk);
     });
   }
   return check_launch(c);
@@ -572,8 +657,8 @@ hevi_status hevi_newton_solve_async(hevi_ctx* c, double gamma_dt, double* state,
   nv.lin = c->lin_newton;
   {
     Scope sc(c, kNewton);
-    for_orders(c, nv, [&](const DevView& v, int N, int ylen) {
-      hevi::launch_newton(v, N, gamma_dt, state, R, rtol, max_iter, ylen, c->stream);
+    for_orders(c, nv, [&](const DevView& v, int N, int ylen, cudaStream_t sk) {
+      hevi::launch_newton(v, N, gamma_dt, state, R, rtol, max_iter, ylen, sk);
     });
   }
   return check_launch(c);
@@ -593,8 +678,8 @@ hevi_status hevi_apply_Lv(hevi_ctx* c, const double* x, double* y, int nonlinear
   if (!nonlinear && !c->factored) return HEVI_ERR_INVALID_ARG;
   {
     Scope sc(c, kApply);
-    for_orders(c, c->v, [&](const DevView& v, int N, int) {
-      hevi::launch_apply(v, N, x, y, nonlinear, c->stream);
+    for_orders(c, c->v, [&](const DevView& v, int N, int, cudaStream_t sk) {
+      hevi::launch_apply(v, N, x, y, nonlinear, sk);
     });
   }
   return check_launch(c);
@@ -670,8 +755,9 @@ hevi_status hevi_lhevi_step(hevi_ctx* c, int32_t s, const double* A, const doubl
   // w_ij = (at_ij - a_ij) / gamma:
   //   q_hat = q^n + dt sum_j a_ij S_j + sum_j w_ij Q_j;  (I - gamma dt L) q_tt = q_hat;
   //   Q_i = q_tt - sum_j w_ij Q_j;  q^{n+1} = q^n + dt sum_i b_i S_i.
-  // The solve is for q_tt, a difference of states, so the refinement
-  // tolerance applies to the stage increment.
+  // The solve is for q_tt, a difference of states (sum_j w_ij = -1 when the
+  // two tableaux share their stage times), so the refinement tolerance
+  // applies to the stage increment.
   hevi_status st = ensure_work(c, 2 * s + 1);
   if (st != HEVI_OK) return st;
   const int64_t n = c->state_size;
@@ -683,8 +769,8 @@ hevi_status hevi_lhevi_step(hevi_ctx* c, int32_t s, const double* A, const doubl
   if ((st = hevi_factor(c, lam, lin_about_rest ? nullptr : q_in))) return st;
   {
     Scope sc(c, kApply);
-    for_orders(c, c->v, [&](const DevView& v, int N, int) {
-      hevi::launch_apply_rhs(v, N, q_in, H, S, c->stream);
+    for_orders(c, c->v, [&](const DevView& v, int N, int, cudaStream_t sk) {
+      hevi::launch_apply_rhs(v, N, q_in, H, S, sk);
     });
   }
   for (int i = 1; i < s; ++i) {
@@ -704,8 +790,8 @@ hevi_status hevi_lhevi_step(hevi_ctx* c, int32_t s, const double* A, const doubl
     }
     {
       Scope sc(c, kSolve);
-      for_orders(c, c->v, [&](const DevView& v, int N, int ylen) {
-        hevi::launch_solve(v, N, c->prec, lam, rhs, Qi, c->ir_tol, c->ir_max, ylen, c->stream);
+      for_orders(c, c->v, [&](const DevView& v, int N, int ylen, cudaStream_t sk) {
+        hevi::launch_solve(v, N, c->prec, lam, rhs, Qi, c->ir_tol, c->ir_max, ylen, sk);
       });
     }
     nt = 0;
@@ -719,8 +805,8 @@ hevi_status hevi_lhevi_step(hevi_ctx* c, int32_t s, const double* A, const doubl
     }
     {
       Scope sc(c, kApply);
-      for_orders(c, c->v, [&](const DevView& v, int N, int) {
-        hevi::launch_apply_rhs(v, N, Qi, H, S + i * n, c->stream);
+      for_orders(c, c->v, [&](const DevView& v, int N, int, cudaStream_t sk) {
+        hevi::launch_apply_rhs(v, N, Qi, H, S + i * n, sk);
       });
     }
     c->launches += 2;  // the two combines
@@ -757,8 +843,8 @@ hevi_status hevi_nhevi_step(hevi_ctx* c, int32_t s, const double* A, const doubl
   const double lam = At[1 * s + 1] * dt;
   {
     Scope sc(c, kApply);
-    for_orders(c, c->v, [&](const DevView& v, int N, int) {
-      hevi::launch_apply(v, N, q_in, VQ, 1, c->stream);
+    for_orders(c, c->v, [&](const DevView& v, int N, int, cudaStream_t sk) {
+      hevi::launch_apply(v, N, q_in, VQ, 1, sk);
     });
   }
   cudaMemcpyAsync(Q, q_in, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
@@ -782,14 +868,14 @@ hevi_status hevi_nhevi_step(hevi_ctx* c, int32_t s, const double* A, const doubl
     }
     {
       Scope sc(c, kNewton);
-      for_orders(c, nv, [&](const DevView& v, int N, int ylen) {
-        hevi::launch_newton(v, N, lam, Q, R, rtol, max_iter, ylen, c->stream);
+      for_orders(c, nv, [&](const DevView& v, int N, int ylen, cudaStream_t sk) {
+        hevi::launch_newton(v, N, lam, Q, R, rtol, max_iter, ylen, sk);
       });
     }
     {
       Scope sc(c, kApply);
-      for_orders(c, c->v, [&](const DevView& v, int N, int) {
-        hevi::launch_apply(v, N, Q, VQ + i * n, 1, c->stream);
+      for_orders(c, c->v, [&](const DevView& v, int N, int, cudaStream_t sk) {
+        hevi::launch_apply(v, N, Q, VQ + i * n, 1, sk);
       });
     }
     c->launches += 1;  // the combine
@@ -899,3 +985,118 @@ extern "C" hevi_status hevi_tableau(const char* name, int32_t* s_out, double* A,
   *s_out = s;
   return HEVI_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Step loops captured into CUDA graphs.
+// ---------------------------------------------------------------------------
+struct hevi_graph {
+  hevi_ctx* ctx = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int64_t launches_per_replay = 0;
+};
+
+namespace {
+
+// Capture nsteps calls of `step(q_in, q_out)` ping-ponging between q_a and
+// q_b on a private stream, then instantiate.  The context's stream is swapped
+// for the capture stream while capturing and restored afterwards.
+template <class Step>
+hevi_status capture_steps(hevi_ctx* c, double* q_a, double* q_b, int32_t nsteps, Step&& step,
+                          hevi_graph** out) {
+  cudaStream_t cap = nullptr;
+  if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    return HEVI_ERR_CUDA;
+  }
+  // the capture must not start before earlier work on the caller's stream
+  cudaStreamSynchronize(c->stream);
+  cudaStream_t user = c->stream;
+  c->stream = cap;
+  const int64_t l0 = c->launches;
+  hevi_status st = HEVI_OK;
+  cudaGraph_t graph = nullptr;
+  if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+    st = HEVI_ERR_CUDA;
+  } else {
+    for (int32_t k = 0; k < nsteps && st == HEVI_OK; ++k)
+      st = (k % 2 == 0) ? step(q_a, q_b) : step(q_b, q_a);
+    if (cudaStreamEndCapture(cap, &graph) != cudaSuccess && st == HEVI_OK) st = HEVI_ERR_CUDA;
+  }
+  c->stream = user;
+  const int64_t per = c->launches - l0;
+  c->launches = l0;
+  cudaGraphExec_t exec = nullptr;
+  if (st == HEVI_OK && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) st = HEVI_ERR_CUDA;
+  cudaStreamDestroy(cap);
+  if (st != HEVI_OK) {
+    cudaGetLastError();
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  hevi_graph* g = new hevi_graph;
+  g->ctx = c;
+  g->graph = graph;
+  g->exec = exec;
+  g->launches_per_replay = per;
+  *out = g;
+  return HEVI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+hevi_status hevi_lhevi_graph_create(hevi_ctx* c, int32_t s, const double* A, const double* At,
+                                    const double* b, double dt, double* q_a, double* q_b,
+                                    const double* H, int32_t nsteps, int32_t lin_about_rest,
+                                    hevi_graph** out) {
+  if (!out) return HEVI_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!c || !q_a || !q_b || !H || q_a == q_b || nsteps < 1 || !(dt > 0.0) ||
+      !tableau_ok(s, A, At, b))
+    return HEVI_ERR_INVALID_ARG;
+  hevi_status st = ensure_work(c, 2 * s + 1);  // no allocation inside the capture
+  if (st != HEVI_OK) return st;
+  std::vector<double> a(A, A + s * s), at(At, At + s * s), w(b, b + s);
+  return capture_steps(c, q_a, q_b, nsteps, [&](const double* qi, double* qo) {
+    return hevi_lhevi_step(c, s, a.data(), at.data(), w.data(), dt, qi, H, qo, lin_about_rest);
+  }, out);
+}
+
+hevi_status hevi_nhevi_graph_create(hevi_ctx* c, int32_t s, const double* A, const double* At,
+                                    const double* b, double dt, double* q_a, double* q_b,
+                                    const double* H, int32_t nsteps, double rtol,
+                                    int32_t max_iter, hevi_graph** out) {
+  if (!out) return HEVI_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!c || !q_a || !q_b || !H || q_a == q_b || nsteps < 1 || !(dt > 0.0) ||
+      !tableau_ok(s, A, At, b) || !(rtol > 0.0) || max_iter < 1)
+    return HEVI_ERR_INVALID_ARG;
+  hevi_status st = ensure_work(c, s + 2);
+  if (st != HEVI_OK) return st;
+  if ((st = ensure_newton(c))) return st;
+  std::vector<double> a(A, A + s * s), at(At, At + s * s), w(b, b + s);
+  return capture_steps(c, q_a, q_b, nsteps, [&](const double* qi, double* qo) {
+    return hevi_nhevi_step(c, s, a.data(), at.data(), w.data(), dt, qi, H, qo, rtol, max_iter);
+  }, out);
+}
+
+hevi_status hevi_graph_launch(hevi_graph* g) {
+  if (!g || !g->exec || !g->ctx) return HEVI_ERR_INVALID_ARG;
+  if (cudaGraphLaunch(g->exec, g->ctx->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return HEVI_ERR_CUDA;
+  }
+  g->ctx->launches += g->launches_per_replay;
+  return HEVI_OK;
+}
+
+void hevi_graph_destroy(hevi_graph* g) {
+  if (!g) return;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  delete g;
+}
+
+}  // extern "C"
