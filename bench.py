@@ -292,13 +292,13 @@ def gpu_arm(args, rank, world, local_rank, pool, cores):
     avg_ms = per[dom][0] / per[dom][1]
     if dom == "stage_solve":
         ach = BYTES_SOLVE_FP32IR * NCOLS / (avg_ms * 1e-3) / 1e9
-        roof = {"kernel": "k_solve<IR> (stage_solve)", "bound": "hbm", "achieved": ach,
+        roof = {"kernel": "k_solve_ir (stage_solve)", "bound": "hbm", "achieved": ach,
                 "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": ach / pk["hbm_gbs"],
                 "traffic": None, "peak_source": pk["source"],
                 "algorithmic_bytes_per_launch": BYTES_SOLVE_FP32IR * NCOLS}
     elif dom == "factor":
         ach = factor_flops() * NCOLS / (avg_ms * 1e-3) / 1e12
-        roof = {"kernel": "k_factor<float> (factor)", "bound": "alu", "achieved": ach,
+        roof = {"kernel": "k_factor_g (factor)", "bound": "alu", "achieved": ach,
                 "peak": pk["fp32_tflops"], "unit": "TFLOP/s", "frac": ach / pk["fp32_tflops"],
                 "traffic": None, "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz",
                 "algorithmic_flops_per_launch": factor_flops() * NCOLS}
