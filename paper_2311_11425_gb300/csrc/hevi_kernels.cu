@@ -447,18 +447,6 @@ __global__ void __launch_bounds__(64) k_factor(DevView v, double lam, const doub
   factor_column<N, T, SCALED>(v, t, lane, lam, q0, win, stride);
 }
 
-// ---------------------------------------------------------------------------
-// Group-cooperative FP32 factorisation: eight threads per column, four
-// columns per warp.  The column's active window, (K+1) rows x (2K+1)
-// columns of A_hat = S^-1 A S (Sec. 4.2.3 band LU, dgbtrf semantics), is a
-// ring in shared memory; thread q owns the window columns c = q (mod 8).  At
-// pivot step j the owner of column j finds the pivot (first maximal |a|),
-// swaps, forms the multipliers and publishes them; after one group barrier
-// every thread swaps and updates its own columns, writes its entries of U's
-// row j into the column-oriented backward records and assembles its entries
-// of the row that enters the window.
-// ---------------------------------------------------------------------------
-constexpr int kFgWarps = 8;
 // shared-memory floats reserved for the row coefficient table
 constexpr int kGSz = (kMaxOrder + 2) * (2 * kMaxOrder + 1) + 3;
 
@@ -509,40 +497,72 @@ __device__ __forceinline__ float ahat_entry(const RowInfo& ri, int col, const fl
   return fmaf(lam_s * g * kvu, sr, a);
 }
 
+// ---------------------------------------------------------------------------
+// Row-per-thread FP32 factorisation (Sec. 4.2.3 band LU, dgbtrf semantics).
+//
+// One thread per row of the column's active window ((K+1) rows, 2K+1
+// columns of A_hat = S^-1 A S): GW threads per column (the power of two >=
+// K+1), 32/GW columns per warp.  A thread keeps its row's 2K+1 entries in
+// registers at positions relative to the pivot column (a[s] = column j+s),
+// so every position is a compile-time register and the window's shift by one
+// column per step is folded into the update (a[s] <- a[s+1] - l u[s]).
+// Interchanges swap row labels between threads instead of moving entries.  At step j: a width-GW shuffle argmax over (|a_ij|, row label)
+// finds the pivot (first maximal |a|); the pivot row publishes its 2K entries
+// of U's row j through shared memory; every other row forms its multiplier
+// and updates its 2K entries from registers; the pivot row's thread retires
+// and takes the row that enters the window, which the group assembled during
+// the step (entries of S^-1 A S from FP64 point coefficients).  Records are
+// written in the layout of the solves: per step an L record {l_1..l_K, pivot
+// offset, 1/u_jj} and column-oriented U records.
+// ---------------------------------------------------------------------------
 template <int N>
-__global__ void __launch_bounds__(kFgWarps * 32) k_factor_g(DevView v, double lam, const double* q0,
-                                                           int wstride) {
-  extern __shared__ float fg_smem[];
-  constexpr int K = Band<N>::K, WR = Band<N>::WR, WC = Band<N>::WC, FR = Band<N>::FR;
+struct FRow {
+  static constexpr int K = Band<N>::K, WR = Band<N>::WR, WC = Band<N>::WC;
+  static constexpr int GW = WR <= 8 ? 8 : (WR <= 16 ? 16 : 32);  // threads per column
+  static constexpr int CPW = 32 / GW;                              // columns per warp
+  static constexpr int CPB = CPW * 4;                              // columns per 4-warp block
+  static constexpr int UB = ((2 * K + 3) / 4) * 4;                 // U row buffer (floats)
+  static constexpr int RB = ((WC + 3) / 4) * 4;                    // entering-row buffer
+};
+constexpr int kGSzA = (kGSz + 3) / 4 * 4;  // coefficient table, 16-byte aligned
+
+template <int N>
+__global__ void __launch_bounds__(128) k_factor_r(DevView v, double lam, const double* q0,
+                                                  int linstride) {
+  using P = FRow<N>;
+  constexpr int K = P::K, WR = P::WR, WC = P::WC, GW = P::GW, FRn = Band<N>::FR;
   constexpr int BR = Band<N>::BR;
   constexpr int NG = (N + 2) * (2 * N + 1);
+  extern __shared__ __align__(16) float fr_smem[];
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int grp = lane / 8, q = lane % 8;
-  const int64_t tile = v.tile_begin + blockIdx.x;
-  if (tile >= (int64_t)v.tile_begin + v.tile_count) return;
+  const int sub = lane / GW, r = lane % GW;
+  constexpr int bpt = kTile / P::CPB;  // blocks per tile
+  const int64_t tile = v.tile_begin + blockIdx.x / bpt;
   const TileDesc t = v.tiles[tile];
-  float* G = fg_smem;  // row coefficient table of order N
+  const int cl0 = (blockIdx.x % bpt) * P::CPB;
+  float* G = fr_smem;
   for (int k = threadIdx.x; k < NG; k += blockDim.x)
     G[k] = c_tab.gcoef[N][k / (2 * N + 1)][k % (2 * N + 1)];
   __syncthreads();
-  if (warp * 4 >= t.count) return;  // warp-uniform: no column for this warp
+  if (cl0 + warp * P::CPW >= t.count) return;  // warp-uniform: no column for this warp
+  const int colw = warp * P::CPW + sub;
+  const bool active = cl0 + colw < t.count;
   // groups past the tile's last column shadow it without writing anything
-  const bool active = warp * 4 + grp < t.count;
-  const int cl = active ? warp * 4 + grp : t.count - 1;
+  const int cl = active ? cl0 + colw : t.count - 1;
   const Col c = make_col(v, t, cl, N);
   const Phys ph = v.ph;
-  float* W = fg_smem + kGSz + (int64_t)(warp * 4 + grp) * wstride;  // WR x WC ring
-  float* bcast = W + WR * WC;                                        // 2 x (K + 2)
-  float* lin32 = bcast + 2 * (K + 2);                                // 3 n_z coefficients
+  float* ubuf = fr_smem + kGSzA + (int64_t)colw * (2 * P::UB + 2 * P::RB + linstride);
+  float* rbuf = ubuf + 2 * P::UB;
+  float* lin32 = rbuf + 2 * P::RB;
   const float* s32 = v.s32 + c.off;
   const float* is32 = v.is32 + c.off;
   float* tb = reinterpret_cast<float*>(v.fac) + t.fac_off;
-  float* bb = tb + (int64_t)c.n * FR * kTile;
+  float* bb = tb + (int64_t)c.n * FRn * kTile;
   const int n = c.n;
 
   // point coefficients of L(q0) (FP64): w, theta, c = gamma P / Theta
   bool ok = true;
-  for (int I = q; I < c.nz; I += 8) {
+  for (int I = r; I < c.nz; I += GW) {
     const int64_t a = c.off + 3 * I;
     double rho, m, Th;
     if (q0) {
@@ -565,154 +585,114 @@ __global__ void __launch_bounds__(kFgWarps * 32) k_factor_g(DevView v, double la
     lin32[3 * I + 1] = (float)th;
     lin32[3 * I + 2] = (float)cc;
   }
-  {  // AND over the group's eight lanes (every lane of the warp takes part)
+  {  // AND over the group's lanes (every lane of the warp takes part)
     int okv = ok ? 1 : 0;
-    okv &= __shfl_xor_sync(0xffffffffu, okv, 1, 8);
-    okv &= __shfl_xor_sync(0xffffffffu, okv, 2, 8);
-    okv &= __shfl_xor_sync(0xffffffffu, okv, 4, 8);
+#pragma unroll
+    for (int off = 1; off < GW; off <<= 1) okv &= __shfl_xor_sync(0xffffffffu, okv, off, GW);
     ok = okv != 0;
   }
   __syncwarp();
   const float lam_s = (float)(lam * c.s), lam_g = (float)(lam * ph.g);
 
-  // initial window: rows 0..K, columns 0..2K (ring positions = indices)
-  for (int r = 0; r < WR; ++r) {
-    const RowInfo ri = row_info<N>(c, is32, r < n ? r : 0);
-    for (int cc = q; cc < WC; cc += 8)
-      W[r * WC + cc] = (r < n && cc < n && cc <= r + K)
-                           ? ahat_entry<N>(ri, cc, lin32, s32, G, lam_s, lam_g)
-                           : 0.0f;
+  // initial window: thread r holds row r; a[s] is the entry of column j + s
+  float a[WC];
+  int label = r < WR ? r : -1;
+  {
+    const bool has = r < WR && r < n;
+    const RowInfo ri = row_info<N>(c, is32, has ? r : 0);
+#pragma unroll
+    for (int cc = 0; cc < WC; ++cc)
+      a[cc] = (has && cc < n && cc <= r + K) ? ahat_entry<N>(ri, cc, lin32, s32, G, lam_s, lam_g)
+                                             : 0.0f;
   }
-  __syncwarp();
 
-  int rowoff[WR];  // ring offsets of window rows j .. j+K
-#pragma unroll
-  for (int r = 0; r < WR; ++r) rowoff[r] = r * WC;
   int info = 0;
-  int cs_j = 0;  // ring column of column j
   for (int j = 0; j < n; ++j) {
-    const int nr = min(K, n - 1 - j), ncol = min(2 * K, n - 1 - j);
-    const int buf = (j & 1) * (K + 2);
+    const int buf = j & 1;
+    float* ub = ubuf + buf * P::UB;
+    float* rb = rbuf + buf * P::RB;
+    // the row that enters after this step, j+K+1: entries of columns j+1+s
     {
-      // pivot: first row of maximal |a| among rows 0..nr of column j, the
-      // rows split over the group's eight threads and combined by shuffles
-      // (larger |a| wins, equal |a| keeps the smaller row)
-      constexpr int MR = (K + 1 + 7) / 8;  // rows per thread
-      float best = -1.0f, bval = 0.0f;
-      int bi = 0;
-      float cv[MR];
-#pragma unroll
-      for (int m = 0; m < MR; ++m) {
-        const int r = q + 8 * m;
-        cv[m] = 0.0f;
-        if (r <= nr) {
-          cv[m] = W[((j + r) % WR) * WC + cs_j];
-          if (fabsf(cv[m]) > best) {
-            best = fabsf(cv[m]);
-            bval = cv[m];
-            bi = r;
-          }
-        }
+      const int inew = j + K + 1;
+      const RowInfo ri = row_info<N>(c, is32, inew < n ? inew : 0);
+      for (int s = r; s < WC; s += GW) {
+        const int col = j + 1 + s;
+        rb[s] = (inew < n && col < n) ? ahat_entry<N>(ri, col, lin32, s32, G, lam_s, lam_g) : 0.0f;
       }
+    }
+    // pivot: first row of maximal |a| among window rows j .. j+nr of column j
+    const int nr = min(K, n - 1 - j);
+    const bool cand = label >= j && label <= j + nr;
+    float key = cand ? fabsf(a[0]) : -1.0f;
+    int kl = cand ? label : 0x7fffffff;
+    float kv = a[0];
 #pragma unroll
-      for (int off = 1; off < 8; off <<= 1) {
-        const float ob = __shfl_xor_sync(0xffffffffu, best, off, 8);
-        const float ov = __shfl_xor_sync(0xffffffffu, bval, off, 8);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, off, 8);
-        if (ob > best || (ob == best && oi < bi)) {
-          best = ob;
-          bval = ov;
-          bi = oi;
-        }
+    for (int off = 1; off < GW; off <<= 1) {
+      const float ok2 = __shfl_xor_sync(0xffffffffu, key, off, GW);
+      const int ol = __shfl_xor_sync(0xffffffffu, kl, off, GW);
+      const float ov = __shfl_xor_sync(0xffffffffu, kv, off, GW);
+      if (ok2 > key || (ok2 == key && ol < kl)) {
+        key = ok2;
+        kl = ol;
+        kv = ov;
       }
-      const int p = bi;
-      const bool sing = !(best > 0.0f);
-      if (sing && info == 0) info = j + 1;
-      const float invd = sing ? 0.0f : 1.0f / bval;
-      // row 0 before the interchange becomes row p (column j retires after
-      // this step, so it is not swapped in place)
-      const float v0 = W[rowoff[0] + cs_j];
+    }
+    const int pl = kl;
+    const bool sing = !(key > 0.0f);
+    if (sing && info == 0) info = j + 1;
+    const float invd = sing ? 0.0f : 1.0f / kv;
+    const int p = pl - j;
+    // interchange rows j and j+p: the labels swap
+    const bool piv = label == pl;
+    if (p != 0) {
+      if (label == j)
+        label = pl;
+      else if (piv)
+        label = j;
+    }
+    // U's row j from the pivot row
+    if (piv) {
 #pragma unroll
-      for (int m = 0; m < MR; ++m) {
-        const int r = q + 8 * m;
-        if (r >= 1 && r <= K) {
-          const float a = (r == p) ? v0 : cv[m];
-          const float l = (r <= nr && !sing) ? a * invd : 0.0f;
-          bcast[buf + r - 1] = l;
-          if (active) tb[((int64_t)(j * (FR / 4) + (r - 1) / 4) * kTile + cl) * 4 + ((r - 1) & 3)] = l;
-        }
-      }
-      if (q == 0) {
-        bcast[buf + K] = (float)p;
-        bcast[buf + K + 1] = invd;
-        if (active) {
-          tb[((int64_t)(j * (FR / 4) + K / 4) * kTile + cl) * 4 + (K & 3)] = (float)p;
-          tb[((int64_t)(j * (FR / 4) + (K + 1) / 4) * kTile + cl) * 4 + ((K + 1) & 3)] = invd;
-#pragma unroll
-          for (int e = K + 2; e < FR; ++e)
-            tb[((int64_t)(j * (FR / 4) + e / 4) * kTile + cl) * 4 + (e & 3)] = 0.0f;
-        }
-      }
+      for (int cc = 1; cc <= 2 * K; ++cc) ub[cc - 1] = a[cc];
     }
     __syncwarp();
-    const int p = (int)bcast[buf + K];
-    float l[K];
+    // multiplier, then update and shift by one column (a[s] <- column j+1+s)
+    const int rr = label - j;  // position of my row after the interchange
+    const bool below = rr >= 1 && rr <= K;
+    const float l = (below && rr <= nr && !sing) ? a[0] * invd : 0.0f;
 #pragma unroll
-    for (int r = 0; r < K; ++r) l[r] = bcast[buf + r];
-    const int rp = ((j + p) % WR) * WC;
-    // my columns j < col <= j + ncol, col = q (mod 8)
-    const int c0 = j + 1 + ((q - (j + 1)) & 7);
-    int cs = cs_j + (c0 - j);
-    if (cs >= WC) cs -= WC;
-    for (int col = c0; col <= j + ncol; col += 8) {
-      if (p) {
-        const float t0 = W[rowoff[0] + cs];
-        W[rowoff[0] + cs] = W[rp + cs];
-        W[rp + cs] = t0;
+    for (int s = 0; s < 2 * K; ++s) a[s] = fmaf(-l, ub[s], a[s + 1]);
+    a[2 * K] = 0.0f;
+    if (active) {
+      const int64_t fj = (int64_t)j * (FRn / 4);
+      if (below) tb[((fj + (rr - 1) / 4) * kTile + cl) * 4 + ((rr - 1) & 3)] = l;
+      if (r == 0) {
+        tb[((fj + K / 4) * kTile + cl) * 4 + (K & 3)] = (float)p;
+        tb[((fj + (K + 1) / 4) * kTile + cl) * 4 + ((K + 1) & 3)] = invd;
+#pragma unroll
+        for (int e = K + 2; e < FRn; ++e) tb[((fj + e / 4) * kTile + cl) * 4 + (e & 3)] = 0.0f;
       }
-      const float u = W[rowoff[0] + cs];
-#pragma unroll
-      for (int r = 1; r <= K; ++r)
-        if (r <= nr) W[rowoff[r] + cs] = fmaf(-l[r - 1], u, W[rowoff[r] + cs]);
-      const int d = col - j - 1;  // U[j][col] is entry d of column col's backward record
-      if (active) bb[((int64_t)(col * (BR / 4) + d / 4) * kTile + cl) * 4 + (d & 3)] = u;
-      cs += 8;
-      if (cs >= WC) cs -= WC;
+      // U[j][j+cc] is entry cc-1 of column j+cc's backward record
+      const int ncol = min(2 * K, n - 1 - j);
+      for (int cc = 1 + r; cc <= ncol; cc += GW)
+        bb[((int64_t)((j + cc) * (BR / 4) + (cc - 1) / 4) * kTile + cl) * 4 + ((cc - 1) & 3)] =
+            ub[cc - 1];
+      // entries of B_j that no row reaches (rows j - 1 - d < 0) and the padding
+      if (j < BR)
+        for (int d = r; d < BR; d += GW)
+          if (d >= j || d >= 2 * K)
+            bb[((int64_t)(j * (BR / 4) + d / 4) * kTile + cl) * 4 + (d & 3)] = 0.0f;
     }
-    // entries of B_j that no row reaches (rows j - 1 - d < 0) and the padding
-    if (j < BR)
-      for (int d = q; d < BR; d += 8)
-        if (active && (d >= j || d >= 2 * K))
-          bb[((int64_t)(j * (BR / 4) + d / 4) * kTile + cl) * 4 + (d & 3)] = 0.0f;
-    // the window advances: row j+K+1 enters ring row rowoff[0], column j+2K+1
-    // enters ring column cs_j
-    const int inew = j + K + 1, cnew = j + 2 * K + 1;
-    const RowInfo ri = row_info<N>(c, is32, inew < n ? inew : 0);
-    const int cb0 = j + 1 + ((q - (j + 1)) & 7);
-    int cs2 = cs_j + (cb0 - j);
-    if (cs2 >= WC) cs2 -= WC;
-    for (int col = cb0; col <= cnew; col += 8) {
-      if (col == cnew) {
+    // the pivot row retires; its thread takes row j+K+1
+    if (label == j) {
 #pragma unroll
-        for (int r = 1; r <= K; ++r) W[rowoff[r] + cs2] = 0.0f;
-      }
-      W[rowoff[0] + cs2] =
-          (inew < n && col < n) ? ahat_entry<N>(ri, col, lin32, s32, G, lam_s, lam_g) : 0.0f;
-      cs2 += 8;
-      if (cs2 >= WC) cs2 -= WC;
+      for (int s = 0; s < WC; ++s) a[s] = rb[s];
+      label = j + K + 1;
     }
-    // rotate: ring row of j+1+r is the old ring row of j+1+r; the freed row
-    // (now holding j+K+1) becomes the last
-    const int r0 = rowoff[0];
-#pragma unroll
-    for (int r = 0; r < K; ++r) rowoff[r] = rowoff[r + 1];
-    rowoff[K] = r0;
-    cs_j = (cs_j + 1 == WC) ? 0 : cs_j + 1;
   }
-  info = max(info, __shfl_xor_sync(0xffffffffu, info, 1, 8));
-  info = max(info, __shfl_xor_sync(0xffffffffu, info, 2, 8));
-  info = max(info, __shfl_xor_sync(0xffffffffu, info, 4, 8));
-  if (q == 0 && active) {
+#pragma unroll
+  for (int off = 1; off < GW; off <<= 1) info = max(info, __shfl_xor_sync(0xffffffffu, info, off, GW));
+  if (r == 0 && active) {
     const int st = !ok ? HEVI_COL_BAD_INPUT : (info ? HEVI_COL_SINGULAR : HEVI_COL_OK);
     v.fac_status[c.col] = st;
     if (st != HEVI_COL_OK)
@@ -741,14 +721,15 @@ static void launch_factor_n(const DevView& v, hevi_precision prec, double lam, c
     cudaFuncSetAttribute(k_factor<N, double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     k_factor<N, double, false><<<grid, blk, smem, st>>>(v, lam, q0);
   } else {
-    // group-cooperative: one CTA of eight warps per tile of 32 columns
+    // row-per-thread: blocks of four warps, 32/GW columns per warp
     constexpr int K = Band<N>::K;
+    using P = FRow<N>;
     const int nmax = ylen - 2 * K;  // longest n of these tiles
-    int wstride = Band<N>::WR * Band<N>::WC + 2 * (K + 2) + nmax;  // ring, bcast, 3 n_z coefs
-    if ((wstride & 1) == 0) wstride += 1;
-    const int gsmem = (kGSz + 32 * wstride) * (int)sizeof(float);
-    cudaFuncSetAttribute(k_factor_g<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, gsmem);
-    k_factor_g<N><<<(unsigned)v.tile_count, kFgWarps * 32, gsmem, st>>>(v, lam, q0, wstride);
+    const int linstride = (3 * (nmax / 3) + 3) / 4 * 4;
+    const int rsmem = (kGSzA + P::CPB * (2 * P::UB + 2 * P::RB + linstride)) * (int)sizeof(float);
+    cudaFuncSetAttribute(k_factor_r<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, rsmem);
+    k_factor_r<N><<<(unsigned)(v.tile_count * (kTile / P::CPB)), 128, rsmem, st>>>(v, lam, q0,
+                                                                                 linstride);
     (void)grid;
     (void)smem;
   }
