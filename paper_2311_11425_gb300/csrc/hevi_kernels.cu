@@ -611,34 +611,71 @@ __global__ void __launch_bounds__(128) k_factor_r(DevView v, double lam, const d
     const int buf = j & 1;
     float* ub = ubuf + buf * P::UB;
     float* rb = rbuf + buf * P::RB;
-    // the row that enters after this step, j+K+1: entries of columns j+1+s
+    // the row that enters after this step, j+K+1, entries of columns j+1+s:
+    // lane r <= 2N takes the three columns of point J = I + r - N (they share
+    // the coefficient G[cls][J-I] and J's linearisation); lane 2N+1 clears the
+    // two slots of the band that no point within N of I reaches
     {
       const int inew = j + K + 1;
-      const RowInfo ri = row_info<N>(c, is32, inew < n ? inew : 0);
-      for (int s = r; s < WC; s += GW) {
-        const int col = j + 1 + s;
-        rb[s] = (inew < n && col < n) ? ahat_entry<N>(ri, col, lin32, s32, G, lam_s, lam_g) : 0.0f;
+      const bool live = inew < n;
+      const RowInfo ri = row_info<N>(c, is32, live ? inew : 0);
+      if (r <= 2 * N) {
+        const int dJ = r - N, J = ri.I + dJ;
+        const int s0 = 3 * dJ - ri.v + K;  // slot of (J, u = 0), in [2 - v, 2K - v - 2]
+        float e[3] = {0.0f, 0.0f, 0.0f};
+        if (live && J >= 0 && J < c.nz) {
+          if (ri.ident) {
+#pragma unroll
+            for (int u = 0; u < 3; ++u) e[u] = (3 * J + u == inew) ? 1.0f : 0.0f;
+          } else {
+            const float g = G[ri.cls * (2 * N + 1) + dJ + N];
+            const float w = lin32[3 * J], th = lin32[3 * J + 1];
+            float kv[3];
+            if (ri.v == 0) {
+              kv[0] = 0.0f; kv[1] = 1.0f; kv[2] = 0.0f;
+            } else if (ri.v == 1) {
+              kv[0] = -w * w; kv[1] = 2.0f * w; kv[2] = lin32[3 * J + 2];
+            } else {
+              kv[0] = -th * w; kv[1] = th; kv[2] = w;
+            }
+#pragma unroll
+            for (int u = 0; u < 3; ++u) {
+              const int col = 3 * J + u;
+              float a0 = (col == inew) ? 1.0f : 0.0f;
+              const float sr = s32[col] * ri.isi;
+              if (ri.v == 1 && u == 0 && dJ == 0) a0 = fmaf(lam_g, sr, a0);
+              e[u] = fmaf(lam_s * g * kv[u], sr, a0);
+            }
+          }
+        }
+        rb[s0] = e[0];
+        rb[s0 + 1] = e[1];
+        rb[s0 + 2] = e[2];
+      } else if (r == 2 * N + 1) {
+        // uncovered slots: s < 2 - v and s > 2K - v
+        const int v0 = live ? ri.v : 0;
+        for (int s = 0; s < 2 - v0; ++s) rb[s] = 0.0f;
+        for (int s = 2 * K - v0 + 1; s < WC; ++s) rb[s] = 0.0f;
       }
     }
     // pivot: first row of maximal |a| among window rows j .. j+nr of column j
     const int nr = min(K, n - 1 - j);
+    // one 64-bit key per lane, larger is better: |a| (the bit pattern of a
+    // non-negative float orders like its value), then the smaller label, then
+    // the lane; rows that are not candidates have key 0 and never win
     const bool cand = label >= j && label <= j + nr;
-    float key = cand ? fabsf(a[0]) : -1.0f;
-    int kl = cand ? label : 0x7fffffff;
-    float kv = a[0];
+    unsigned long long key =
+        cand ? ((unsigned long long)__float_as_uint(fabsf(a[0])) << 32) |
+                   ((unsigned long long)(0xffffu - (unsigned)label) << 8) | (unsigned)lane
+             : 0ull;
 #pragma unroll
     for (int off = 1; off < GW; off <<= 1) {
-      const float ok2 = __shfl_xor_sync(0xffffffffu, key, off, GW);
-      const int ol = __shfl_xor_sync(0xffffffffu, kl, off, GW);
-      const float ov = __shfl_xor_sync(0xffffffffu, kv, off, GW);
-      if (ok2 > key || (ok2 == key && ol < kl)) {
-        key = ok2;
-        kl = ol;
-        kv = ov;
-      }
+      const unsigned long long o = __shfl_xor_sync(0xffffffffu, key, off, GW);
+      key = o > key ? o : key;
     }
-    const int pl = kl;
-    const bool sing = !(key > 0.0f);
+    const int pl = (int)(0xffffu - (unsigned)((key >> 8) & 0xffffu));
+    const float kv = __shfl_sync(0xffffffffu, a[0], (int)(key & 0xffu));
+    const bool sing = !(__uint_as_float((unsigned)(key >> 32)) > 0.0f);
     if (sing && info == 0) info = j + 1;
     const float invd = sing ? 0.0f : 1.0f / kv;
     const int p = pl - j;
@@ -650,10 +687,17 @@ __global__ void __launch_bounds__(128) k_factor_r(DevView v, double lam, const d
       else if (piv)
         label = j;
     }
-    // U's row j from the pivot row
+    // U's row j from the pivot row (float4 stores; entries past 2K are 0)
     if (piv) {
 #pragma unroll
-      for (int cc = 1; cc <= 2 * K; ++cc) ub[cc - 1] = a[cc];
+      for (int q4 = 0; q4 < P::UB / 4; ++q4) {
+        float4 u4;
+        u4.x = (4 * q4 + 1 <= 2 * K) ? a[4 * q4 + 1] : 0.0f;
+        u4.y = (4 * q4 + 2 <= 2 * K) ? a[4 * q4 + 2] : 0.0f;
+        u4.z = (4 * q4 + 3 <= 2 * K) ? a[4 * q4 + 3] : 0.0f;
+        u4.w = (4 * q4 + 4 <= 2 * K) ? a[4 * q4 + 4] : 0.0f;
+        reinterpret_cast<float4*>(ub)[q4] = u4;
+      }
     }
     __syncwarp();
     // multiplier, then update and shift by one column (a[s] <- column j+1+s)
@@ -661,7 +705,15 @@ __global__ void __launch_bounds__(128) k_factor_r(DevView v, double lam, const d
     const bool below = rr >= 1 && rr <= K;
     const float l = (below && rr <= nr && !sing) ? a[0] * invd : 0.0f;
 #pragma unroll
-    for (int s = 0; s < 2 * K; ++s) a[s] = fmaf(-l, ub[s], a[s + 1]);
+    for (int q4 = 0; q4 < P::UB / 4; ++q4) {
+      const float4 u4 = reinterpret_cast<const float4*>(ub)[q4];
+      const float uu[4] = {u4.x, u4.y, u4.z, u4.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int s = 4 * q4 + e;
+        if (s < 2 * K) a[s] = fmaf(-l, uu[e], a[s + 1]);
+      }
+    }
     a[2 * K] = 0.0f;
     if (active) {
       const int64_t fj = (int64_t)j * (FRn / 4);
@@ -686,7 +738,13 @@ __global__ void __launch_bounds__(128) k_factor_r(DevView v, double lam, const d
     // the pivot row retires; its thread takes row j+K+1
     if (label == j) {
 #pragma unroll
-      for (int s = 0; s < WC; ++s) a[s] = rb[s];
+      for (int q4 = 0; q4 < P::RB / 4; ++q4) {
+        const float4 r4 = reinterpret_cast<const float4*>(rb)[q4];
+        if (4 * q4 < WC) a[4 * q4] = r4.x;
+        if (4 * q4 + 1 < WC) a[4 * q4 + 1] = r4.y;
+        if (4 * q4 + 2 < WC) a[4 * q4 + 2] = r4.z;
+        if (4 * q4 + 3 < WC) a[4 * q4 + 3] = r4.w;
+      }
       label = j + K + 1;
     }
   }
