@@ -201,9 +201,12 @@ hevi_status hevi_column_status(hevi_ctx* ctx, int32_t* status, int32_t* iters);
  * s x s, At[0][0] = 0, constant diagonal gamma), b (weights, shared).
  * q_in, H, q_out (dev, state layout); H is the explicit (horizontal) tendency,
  * held constant over the step; q_out may not alias q_in.
- *   hevi_lhevi_step: LHEVI (Sec. 4.3): L linearised about q_in (LHEVI-PS) when
- *     lin_about_rest == 0, about the rest state (LHEVI-RS) otherwise; one
- *     factorisation for the step, one stage solve per implicit stage.
+ *   hevi_lhevi_step: LHEVI (Sec. 4.3), one stage solve per implicit stage;
+ *     lin_about_rest selects the Jacobian: 0 = refactor with L linearised
+ *     about q_in (LHEVI-PS), 1 = refactor about the rest state (LHEVI-RS),
+ *     2 = keep the current factorisation and its L (a Jacobian update interval
+ *     of more than one step, Sec. 4.3 and the update time-step of Sec. 7.1;
+ *     INVALID_ARG unless the context holds factors of the same gamma * dt).
  *   hevi_nhevi_step: NHEVI-LU (Sec. 4.2): one Newton solve per implicit stage
  *     from the previous stage value.
  * Asynchronous; per-column failures are recorded for hevi_column_status. */
@@ -253,7 +256,8 @@ int64_t hevi_estimate_bytes(const hevi_column_grid* grid, hevi_precision precisi
 
 /* Named ESDIRK tableaux of Sec. 6 (the paper names them; the coefficients
  * come from the cited constructions): "ARK2" = ARK(2,3,2)b with a32 = 1/2,
- * "ARK3" = ARK3(2)4L[2]SA and "ARK4" = ARK4(3)6L[2]SA of Kennedy & Carpenter.
+ * "ARK3" = ARK3(2)4L[2]SA and "ARK4" = ARK4(3)6L[2]SA of Kennedy & Carpenter,
+ * "ARS3" = ARK(3,4,3) of Ascher, Ruuth & Spiteri.
  * Writes the stage count to *s and the row-major A, At (s x s) and b (s) to
  * host arrays of at least 64, 64 and 8 doubles.  INVALID_ARG for an unknown
  * name. */

@@ -76,6 +76,8 @@ def _load():
                                       c_int, _I, _I]),
                 "or_lhevi_step": (c_int, [c_int, c_int, c_int, _D, c_int, _D, _D, _D, c_double,
                                           c_int, _D, _D, _D, _I]),
+                "or_lhevi_step_about": (c_int, [c_int, c_int, c_int, _D, c_int, _D, _D, _D,
+                                                c_double, c_int, _D, _D, _D, _D, _I]),
                 "or_nhevi_step": (c_int, [c_int, c_int, c_int, _D, c_int, _D, _D, _D, c_double,
                                           _D, _D, c_double, c_int, _D, _I, _I]),
             }
@@ -257,16 +259,26 @@ def newton(nez: int, N: int, ztop, lam: float, R, q_init, rtol: float = 1e-10,
     return q, it, st
 
 
-def lhevi_step(nez: int, N: int, ztop, tab, dt: float, qn, H, lin: int = 0):
+def lhevi_step(nez: int, N: int, ztop, tab, dt: float, qn, H, lin: int = 0, q_lin=None):
     """One LHEVI ARK step (Sec. 4.3); lin 0 = PS, 1 = RS, 2 = linear test
-    problem V := L_RS (q - q_bar).  Returns (q_next, info)."""
+    problem V := L_RS (q - q_bar).  With q_lin (state layout, per column) the
+    Jacobian is linearised about q_lin instead (a Jacobian kept from an earlier
+    step; lin then only selects V: 0 nonlinear, 2 the linear test problem).
+    Returns (q_next, info)."""
     qn, H = _f64(np.atleast_2d(qn)), _f64(np.atleast_2d(H))
     zt = _ztop(ztop, qn.shape[0])
     A, At, b = (_f64(tab.A), _f64(tab.At), _f64(tab.b))
     out = np.zeros_like(qn)
     info = np.zeros(qn.shape[0], dtype=np.intc)
-    _load().or_lhevi_step(qn.shape[0], nez, N, _dp(zt), tab.s, _dp(A), _dp(At), _dp(b), float(dt),
-                          int(lin), _dp(qn), _dp(H), _dp(out), _ip(info))
+    if q_lin is None:
+        _load().or_lhevi_step(qn.shape[0], nez, N, _dp(zt), tab.s, _dp(A), _dp(At), _dp(b),
+                              float(dt), int(lin), _dp(qn), _dp(H), _dp(out), _ip(info))
+    else:
+        ql = _f64(np.atleast_2d(q_lin))
+        assert ql.shape == qn.shape
+        _load().or_lhevi_step_about(qn.shape[0], nez, N, _dp(zt), tab.s, _dp(A), _dp(At), _dp(b),
+                                    float(dt), int(lin), _dp(ql), _dp(qn), _dp(H), _dp(out),
+                                    _ip(info))
     return out, info
 
 

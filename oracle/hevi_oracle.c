@@ -555,9 +555,14 @@ int or_newton(int ncols, int nez, int N, const double* ztop, double lam, const d
  * the reference state (LHEVI-RS); lin = 2: V itself replaced by the
  * reference-state linear operator V(q) := L_RS (q - q_bar), the linear test
  * problem.  info[c] = band-LU info of the step's factorisation. */
-int or_lhevi_step(int ncols, int nez, int N, const double* ztop, int s, const double* A,
-                  const double* At, const double* b, double dt, int lin, const double* qn,
-                  const double* H, double* qout, int* info) {
+/* One LHEVI step with L linearised about qlin (per column, state layout)
+ * when qlin != NULL: a Jacobian kept from an earlier step (the update
+ * interval of Sec. 4.3 and the timing table of Sec. 7.1, R10); otherwise as
+ * or_lhevi_step. */
+static int lhevi_step_impl(int ncols, int nez, int N, const double* ztop, int s, const double* A,
+                           const double* At, const double* b, double dt, int lin,
+                           const double* qlin, const double* qn, const double* H, double* qout,
+                           int* info) {
   int n = 3 * (nez * N + 1), kl = 3 * (N + 1) - 1, ldab = 3 * kl + 1;
   double gam = At[1 * s + 1], lam = gam * dt;
   double* ab = (double*)malloc(sizeof(double) * (size_t)ldab * n);
@@ -574,7 +579,7 @@ int or_lhevi_step(int ncols, int nez, int N, const double* ztop, int s, const do
       qbar[3 * I + 1] = 0.0;
       qbar[3 * I + 2] = col.Theta_b[I];
     }
-    memcpy(q0, lin == 0 ? qnc : qbar, sizeof(double) * n);
+    memcpy(q0, qlin ? qlin + o : (lin == 0 ? qnc : qbar), sizeof(double) * n);
     assemble_band(&col, lam, q0, ab, ldab);
     info[c] = or_gbtrf(n, kl, kl, ab, ldab, ipiv);
     for (int i = 0; i < s; ++i) {
@@ -620,6 +625,20 @@ int or_lhevi_step(int ncols, int nez, int N, const double* ztop, int s, const do
   free(ipiv);
   free(Q);
   return 0;
+}
+
+int or_lhevi_step(int ncols, int nez, int N, const double* ztop, int s, const double* A,
+                  const double* At, const double* b, double dt, int lin, const double* qn,
+                  const double* H, double* qout, int* info) {
+  return lhevi_step_impl(ncols, nez, N, ztop, s, A, At, b, dt, lin, NULL, qn, H, qout, info);
+}
+
+/* LHEVI step with the Jacobian linearised about a given state qlin; lin = 0
+ * for V itself, 2 for the linear test problem V := L_RS (q - q_bar). */
+int or_lhevi_step_about(int ncols, int nez, int N, const double* ztop, int s, const double* A,
+                        const double* At, const double* b, double dt, int lin, const double* qlin,
+                        const double* qn, const double* H, double* qout, int* info) {
+  return lhevi_step_impl(ncols, nez, N, ztop, s, A, At, b, dt, lin, qlin, qn, H, qout, info);
 }
 
 /* NHEVI-LU (Sec. 4.2): stage i solves F(Q_i) = Q_i - gamma dt V(Q_i) - R_i = 0,

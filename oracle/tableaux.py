@@ -12,6 +12,11 @@ their order conditions and observed convergence order in the tests:
         gamma = 1 - 1/sqrt(2).
   ARK3  ARK3(2)4L[2]SA of Kennedy & Carpenter (2003).
   ARK4  ARK4(3)6L[2]SA of Kennedy & Carpenter (2003).
+  ARS3  ARK(3,4,3) of Ascher, Ruuth & Spiteri (1997) (Sec. 6 names it ARS3):
+        gamma the root in (1/6, 1/2) of 6 g^3 - 18 g^2 + 9 g - 1 = 0, the
+        construction's free explicit coefficients a42 = a43 = 0.5529291480359398,
+        a31 and a32 from its closed forms in gamma, a42 and a43; the implicit
+        part has a zero first column.
 """
 
 from __future__ import annotations
@@ -96,7 +101,24 @@ def _ark4() -> Tableau:
     return Tableau("ARK4", 4, _to_np(A), _to_np(At), np.array([float(x) for x in b]))
 
 
+def _ars3() -> Tableau:
+    g = 0.4358665215  # Newton on the cubic from the published 10-digit value
+    for _ in range(4):
+        g -= (6 * g ** 3 - 18 * g ** 2 + 9 * g - 1) / (18 * g ** 2 - 36 * g + 9)
+    a42 = a43 = 0.5529291480359398
+    b1 = -1.5 * g * g + 4.0 * g - 0.25
+    b2 = 1.5 * g * g - 5.0 * g + 1.25
+    a31 = ((1 - 4.5 * g + 1.5 * g * g) * a42 + (2.75 - 10.5 * g + 3.75 * g * g) * a43
+           - 3.5 + 13 * g - 4.5 * g * g)
+    a32 = ((-1 + 4.5 * g - 1.5 * g * g) * a42 + (-2.75 + 10.5 * g - 3.75 * g * g) * a43
+           + 4 - 12.5 * g + 4.5 * g * g)
+    A = np.array([[0, 0, 0, 0], [g, 0, 0, 0], [a31, a32, 0, 0], [1 - a42 - a43, a42, a43, 0]])
+    At = np.array([[0, 0, 0, 0], [0, g, 0, 0], [0, (1 - g) / 2, g, 0], [0, b1, b2, g]])
+    return Tableau("ARS3", 3, A, At, np.array([0.0, b1, b2, g]))
+
+
 ARK2 = _ark2()
 ARK3 = _ark3()
 ARK4 = _ark4()
-ALL = {t.name: t for t in (ARK2, ARK3, ARK4)}
+ARS3 = _ars3()
+ALL = {t.name: t for t in (ARK2, ARK3, ARK4, ARS3)}

@@ -373,13 +373,17 @@ class Context:
         _check(self._lib.hevi_column_status(self._h, _ptr(st), _ptr(it)), "hevi_column_status")
         return st, it
 
-    def hevi_lhevi_step(self, tab, dt, q_in, H, q_out=None, lin_about_rest=False):
+    def hevi_lhevi_step(self, tab, dt, q_in, H, q_out=None, lin_about_rest=False,
+                        refactor=True):
+        """One LHEVI step; refactor=False keeps the current factorisation (a
+        Jacobian update interval of more than one step)."""
         q_out = self.empty() if q_out is None else q_out
         A, pA = _darr(tab.A)
         At, pAt = _darr(tab.At)
         b, pb = _darr(tab.b)
+        mode = 2 if not refactor else int(bool(lin_about_rest))
         _check(self._lib.hevi_lhevi_step(self._h, len(b), pA, pAt, pb, float(dt), self._v(q_in),
-                                         self._v(H), self._v(q_out), int(bool(lin_about_rest))),
+                                         self._v(H), self._v(q_out), mode),
                "hevi_lhevi_step")
         return q_out
 
@@ -393,7 +397,8 @@ class Context:
                "hevi_nhevi_step")
         return q_out
 
-    def hevi_lhevi_graph(self, tab, dt, q_a, q_b, H, nsteps=1, lin_about_rest=False):
+    def hevi_lhevi_graph(self, tab, dt, q_a, q_b, H, nsteps=1, lin_about_rest=False,
+                         refactor=True):
         """nsteps LHEVI steps captured into one CUDA graph (hevi_lhevi_graph_create);
         replays ping-pong between q_a and q_b (result in q_b for odd nsteps)."""
         A, pA = _darr(tab.A)
@@ -402,7 +407,8 @@ class Context:
         h = _P()
         _check(self._lib.hevi_lhevi_graph_create(
             self._h, len(b), pA, pAt, pb, float(dt), self._v(q_a), self._v(q_b), self._v(H),
-            int(nsteps), int(bool(lin_about_rest)), ctypes.byref(h)), "hevi_lhevi_graph_create")
+            int(nsteps), 2 if not refactor else int(bool(lin_about_rest)), ctypes.byref(h)),
+            "hevi_lhevi_graph_create")
         g = Graph(self, h, (q_a, q_b, H))
         self._graphs.add(g)
         return g

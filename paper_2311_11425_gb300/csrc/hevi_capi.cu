@@ -749,7 +749,8 @@ static bool tableau_ok(int32_t s, const double* A, const double* At, const doubl
 hevi_status hevi_lhevi_step(hevi_ctx* c, int32_t s, const double* A, const double* At,
                             const double* b, double dt, const double* q_in, const double* H,
                             double* q_out, int32_t lin_about_rest) {
-  if (!c || !q_in || !H || !q_out || q_in == q_out || !(dt > 0.0) || !tableau_ok(s, A, At, b))
+  if (!c || !q_in || !H || !q_out || q_in == q_out || !(dt > 0.0) || !tableau_ok(s, A, At, b) ||
+      lin_about_rest < 0 || lin_about_rest > 2)
     return HEVI_ERR_INVALID_ARG;
   // ARK form of LHEVI (Sec. 4.3, Eq. lhevi-ark-final-3), S(Q) = H + V(Q),
   // w_ij = (at_ij - a_ij) / gamma:
@@ -766,7 +767,12 @@ hevi_status hevi_lhevi_step(hevi_ctx* c, int32_t s, const double* A, const doubl
   double* rhs = c->work + 2 * s * n;
   const double gam = At[1 * s + 1], lam = gam * dt;
   auto Qp = [&](int j) -> const double* { return j == 0 ? q_in : Qb + j * n; };
-  if ((st = hevi_factor(c, lam, lin_about_rest ? nullptr : q_in))) return st;
+  if (lin_about_rest == 2) {
+    // Jacobian kept from the last factorisation (update interval > 1 step)
+    if (!c->factored || c->lam != lam) return HEVI_ERR_INVALID_ARG;
+  } else if ((st = hevi_factor(c, lam, lin_about_rest ? nullptr : q_in))) {
+    return st;
+  }
   {
     Scope sc(c, kApply);
     for_orders(c, c->v, [&](const DevView& v, int N, int, cudaStream_t sk) {
@@ -979,6 +985,28 @@ extern "C" hevi_status hevi_tableau(const char* name, int32_t* s_out, double* A,
     a(A, 5, 3) = r({3354512671639.0, 8306763924573.0});
     a(A, 5, 4) = r({4040.0, 17871.0});
     for (int j = 0; j < 6; ++j) b[j] = bb[j];
+  } else if (nm == "ARS3") {
+    // ARK(3,4,3) of Ascher, Ruuth & Spiteri: gamma solves 6g^3 - 18g^2 + 9g - 1
+    // = 0 in (1/6, 1/2); the free explicit coefficients a42 = a43; a31, a32
+    // from the construction's closed forms; implicit first column zero
+    s = 4;
+    double g = 0.4358665215;
+    for (int it = 0; it < 4; ++it)
+      g -= (6.0 * g * g * g - 18.0 * g * g + 9.0 * g - 1.0) / (18.0 * g * g - 36.0 * g + 9.0);
+    const double e42 = 0.5529291480359398, e43 = e42, g2 = g * g;
+    const double b1 = -1.5 * g2 + 4.0 * g - 0.25, b2 = 1.5 * g2 - 5.0 * g + 1.25;
+    a(A, 1, 0) = g;
+    a(A, 2, 0) = (1.0 - 4.5 * g + 1.5 * g2) * e42 + (2.75 - 10.5 * g + 3.75 * g2) * e43 - 3.5 +
+                 13.0 * g - 4.5 * g2;
+    a(A, 2, 1) = (-1.0 + 4.5 * g - 1.5 * g2) * e42 + (-2.75 + 10.5 * g - 3.75 * g2) * e43 + 4.0 -
+                 12.5 * g + 4.5 * g2;
+    a(A, 3, 0) = 1.0 - e42 - e43;
+    a(A, 3, 1) = e42;
+    a(A, 3, 2) = e43;
+    a(At, 1, 1) = g;
+    a(At, 2, 1) = 0.5 * (1.0 - g); a(At, 2, 2) = g;
+    a(At, 3, 1) = b1; a(At, 3, 2) = b2; a(At, 3, 3) = g;
+    b[0] = 0.0; b[1] = b1; b[2] = b2; b[3] = g;
   } else {
     return HEVI_ERR_INVALID_ARG;
   }

@@ -300,7 +300,7 @@ def test_newton_full_size_sampled(hv):
 # whole ARK steps
 # ---------------------------------------------------------------------------
 
-@pytest.mark.parametrize("name", ["ARK2", "ARK3"])
+@pytest.mark.parametrize("name", ["ARK2", "ARK3", "ARS3", "ARK4"])
 @pytest.mark.parametrize("prec", ["FP64", "FP32_IR"])
 def test_lhevi_step_parity(hv, name, prec):
     nez, N, ncols = 10, 4, 45

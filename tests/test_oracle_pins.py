@@ -443,7 +443,7 @@ def _gamma(tree):
     return g
 
 
-@pytest.mark.parametrize("name", ["ARK2", "ARK3", "ARK4"])
+@pytest.mark.parametrize("name", ["ARK2", "ARK3", "ARK4", "ARS3"])
 def test_tableau_structure_and_order_conditions(name):
     t = tableaux.ALL[name]
     A, At, b = t.A, t.At, t.b
@@ -462,6 +462,23 @@ def test_tableau_structure_and_order_conditions(name):
             count += 1
     # number of trees with two-coloured non-root vertices: 3, 10, 36 up to order 2, 3, 4
     assert count == {2: 3, 3: 10, 4: 36}[t.order]
+
+
+def test_ars3_published_values():
+    """ARS(3,4,3) (Ascher, Ruuth & Spiteri 1997) at the digits the construction
+    publishes, and the singly diagonal L-stable gamma: R(inf) = 0 of its
+    implicit part."""
+    t = tableaux.ARS3
+    assert abs(t.gamma - 0.4358665215) < 1e-10
+    np.testing.assert_allclose(t.A[2, :2], [0.3212788860, 0.3966543747], atol=1e-10)
+    np.testing.assert_allclose(t.A[3, :3], [-0.105858296, 0.5529291479, 0.5529291479], atol=1e-9)
+    np.testing.assert_allclose(t.b, [0.0, 1.208496649, -0.644363171, 0.4358665215], atol=1e-9)
+    np.testing.assert_allclose(t.c, [0.0, t.gamma, (1 + t.gamma) / 2, 1.0], atol=1e-15)
+    # stiff decay: the implicit stages 2..4 form an L-stable SDIRK, R(inf) = 0
+    Ai = t.At[1:, 1:]
+    bi = t.b[1:]
+    r_inf = 1.0 - bi @ np.linalg.solve(Ai, np.ones(3))
+    assert abs(r_inf) < 1e-14
 
 
 def test_ark2_gamma_and_a32():
@@ -487,7 +504,7 @@ def _linear_exact(nez, N, q_bar, dq0, H, T):
     return y[:n]
 
 
-@pytest.mark.parametrize("name", ["ARK2", "ARK3", "ARK4"])
+@pytest.mark.parametrize("name", ["ARK2", "ARK3", "ARK4", "ARS3"])
 def test_ark_linear_problem_converges_at_order(name):
     tab = tableaux.ALL[name]
     nez, N = 4, 4
@@ -514,6 +531,54 @@ def test_ark_linear_problem_converges_at_order(name):
         errs.append(np.linalg.norm(q[0] - q_bar[0] - exact) / np.linalg.norm(exact))
     rates = [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
     assert min(rates) > tab.order - 0.35, (errs, rates)
+
+
+def test_lhevi_about_own_state_and_rest_equal_ps_and_rs():
+    """The Jacobian-state entry point reduces to LHEVI-PS for q_lin = q^n and
+    to LHEVI-RS for q_lin = q_bar, bit for bit."""
+    nez, N, dt = 8, 4, 300.0
+    qn = _perturbed_state(nez, N, seed=31, amp_w=1.0, amp_th=0.5)[None]
+    H = np.zeros_like(qn)
+    H[0, 2::3] = 1e-6 * qn[0, 2::3]
+    for lin, ql in ((0, qn), (1, _rest(nez, N))):
+        ref, _ = oracle.lhevi_step(nez, N, ZTOP, tableaux.ARK3, dt, qn, H, lin=lin)
+        got, _ = oracle.lhevi_step(nez, N, ZTOP, tableaux.ARK3, dt, qn, H, lin=0, q_lin=ql)
+        assert np.array_equal(ref, got), lin
+
+
+@pytest.mark.parametrize("name", ["ARK2", "ARK3"])
+def test_lagged_jacobian_keeps_order_on_linear_problem(name):
+    """Jacobian update interval (Sec. 4.3, the update time-step of Sec. 7.1):
+    the implicit operator is L(q_lin) of a state other than the one the ODE is
+    linear about, so L and V - L are a different IMEX splitting of the same
+    linear problem dq'/dt = L_RS q' + H; the ARK pair still converges at its
+    order to the exact (matrix exponential) solution."""
+    tab = tableaux.ALL[name]
+    nez, N = 4, 4
+    q_bar = _rest(nez, N)
+    z, _ = oracle.column_grid(nez, N, ZTOP)
+    rho, _, _, _ = oracle.reference_state(z)
+    dq0 = np.zeros((z.size, 3))
+    dq0[:, 2] = rho * 1.0 * np.sin(np.pi * z / ZTOP)
+    dq0 = dq0.reshape(-1)
+    H = np.zeros_like(dq0)
+    H[2::3] = 1e-4 * rho
+    q_lin = _perturbed_state(nez, N, seed=32, amp_w=3.0, amp_th=2.0)[None]
+    T = 8.0
+    exact = _linear_exact(nez, N, q_bar, dq0, H, T)
+    errs = []
+    for dt in (2.0, 1.0, 0.5):
+        q = q_bar + dq0
+        for _ in range(int(round(T / dt))):
+            q, info = oracle.lhevi_step(nez, N, ZTOP, tab, dt, q, H[None], lin=2, q_lin=q_lin)
+            assert info[0] == 0
+        errs.append(np.linalg.norm(q[0] - q_bar[0] - exact) / np.linalg.norm(exact))
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert min(rates) > tab.order - 0.35, (errs, rates)
+    # and it is a different method: the step differs from the L_RS splitting
+    q1, _ = oracle.lhevi_step(nez, N, ZTOP, tab, 1.0, q_bar + dq0, H[None], lin=2)
+    q2, _ = oracle.lhevi_step(nez, N, ZTOP, tab, 1.0, q_bar + dq0, H[None], lin=2, q_lin=q_lin)
+    assert np.linalg.norm(q1 - q2) > 1e-8 * np.linalg.norm(q1 - q_bar - dq0)
 
 
 @pytest.mark.slow
