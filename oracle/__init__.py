@@ -78,6 +78,8 @@ def _load():
                                           c_int, _D, _D, _D, _I]),
                 "or_lhevi_step_about": (c_int, [c_int, c_int, c_int, _D, c_int, _D, _D, _D,
                                                 c_double, c_int, _D, _D, _D, _D, _I]),
+                "or_newton_gmres": (c_int, [c_int, c_int, c_int, _D, c_double, _D, _D, c_double,
+                                            c_double, c_double, c_int, c_int, _I, _I, _I]),
                 "or_nhevi_step": (c_int, [c_int, c_int, c_int, _D, c_int, _D, _D, _D, c_double,
                                           _D, _D, c_double, c_int, _D, _I, _I]),
             }
@@ -257,6 +259,27 @@ def newton(nez: int, N: int, ztop, lam: float, R, q_init, rtol: float = 1e-10,
     _load().or_newton(q.shape[0], nez, N, _dp(zt), float(lam), _dp(R), _dp(q), float(rtol),
                       int(max_iter), _ip(it), _ip(st))
     return q, it, st
+
+
+def newton_gmres(nez: int, N: int, ztop, lam: float, R, q_init, eps: float = 0.05,
+                 rtol: float = 1e-5, gtol: float = 1e-9, max_newton: int = 30,
+                 kmax: int | None = None):
+    """NHEVI-GMRES (Sec. 4.2.1): Jacobian-free Newton-Krylov solve of
+    F(q) = q - Lambda V(q) - R = 0; Frechet perturbation eps S (reading R14),
+    unrestarted GMRES to gtol, Newton stop as ``newton`` (reading R7).
+    Returns (q, newton_iters, krylov_iters, status)."""
+    R = _f64(np.atleast_2d(R))
+    q = _f64(np.atleast_2d(q_init)).copy()
+    zt = _ztop(ztop, q.shape[0])
+    n = q.shape[1]
+    kmax = n if kmax is None else int(kmax)
+    it = np.zeros(q.shape[0], dtype=np.intc)
+    kit = np.zeros(q.shape[0], dtype=np.intc)
+    st = np.zeros(q.shape[0], dtype=np.intc)
+    _load().or_newton_gmres(q.shape[0], nez, N, _dp(zt), float(lam), _dp(R), _dp(q), float(eps),
+                            float(rtol), float(gtol), int(max_newton), kmax, _ip(it), _ip(kit),
+                            _ip(st))
+    return q, it, kit, st
 
 
 def lhevi_step(nez: int, N: int, ztop, tab, dt: float, qn, H, lin: int = 0, q_lin=None):

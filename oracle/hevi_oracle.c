@@ -39,6 +39,10 @@
  *       the relative test cannot be met when ||F(q_0)|| is itself within
  *       1/rtol of that level (a column already near its stage solution).
  *       Both tests are applied to q_0 as well (m = 0 updates).
+ *   R14 NHEVI-GMRES: the Frechet perturbation E of Eq. Frechet-derivative is
+ *       diagonal, eps S with the reference scales S (per-variable magnitudes),
+ *       applied to the equilibrated system; GMRES starts at zero and is not
+ *       restarted (restarted GMRES(30..60) stagnates on these columns).
  */
 #include <float.h>
 #include <math.h>
@@ -487,6 +491,134 @@ static double scaled_norm(const column_t* c, const double* F) {
     s2 += a * a + b * b + d * d;
   }
   return sqrt(s2);
+}
+
+/* Reference scale of unknown i (rho_bar, rho_bar c_s, Theta_bar at point i/3). */
+static double unknown_scale(const column_t* c, int i) {
+  int I = i / 3, u = i - 3 * I;
+  if (u == 0) return c->rho_b[I];
+  if (u == 1) return c->rho_b[I] * sqrt(or_gamma() * OR_R * OR_T0);
+  return c->Theta_b[I];
+}
+
+/* Sec. 4.2.1 (NHEVI-GMRES): Jacobian-free Newton-Krylov.  Newton on
+ * F(q) = q - Lambda V(q) - R; each Newton system J(q_m) dq = -F(q_m) is
+ * solved by unpreconditioned GMRES (zero start, no restart: modified
+ * Gram-Schmidt Arnoldi, Givens rotations) on the equilibrated system
+ * J^ y = -S^-1 F(q_m), J^ = S^-1 J S, dq = S y, with the Frechet
+ * difference (Eq. Frechet-derivative) J^ v ~ S^-1 [F(q_m + eps S v) - F(q_m)]
+ * / eps, i.e. the diagonal perturbation E = eps S (reading R14: per-variable
+ * magnitudes from the reference scales).  GMRES stops when its residual
+ * estimate is <= gtol |S^-1 F(q_m)| or after kmax iterations; Newton stops
+ * as in or_newton (reading R7).  iters[c] = Newton updates, kits[c] = Krylov
+ * iterations in all, status 0 / 5 (Newton not converged) / 6 (non-physical
+ * state met). */
+int or_newton_gmres(int ncols, int nez, int N, const double* ztop, double lam, const double* R,
+                    double* q, double eps, double rtol, double gtol, int max_newton, int kmax,
+                    int* iters, int* kits, int* status) {
+  int n = 3 * (nez * N + 1);
+  double* F = (double*)malloc(sizeof(double) * n);
+  double* qp = (double*)malloc(sizeof(double) * n);
+  double* w = (double*)malloc(sizeof(double) * n);
+  double* sc = (double*)malloc(sizeof(double) * n);
+  double* Vb = (double*)malloc(sizeof(double) * (size_t)n * (kmax + 1));
+  double* H = (double*)malloc(sizeof(double) * (size_t)(kmax + 1) * kmax);
+  double* cs = (double*)malloc(sizeof(double) * kmax);
+  double* sn = (double*)malloc(sizeof(double) * kmax);
+  double* g = (double*)malloc(sizeof(double) * (kmax + 1));
+  double* y = (double*)malloc(sizeof(double) * kmax);
+  for (int c = 0; c < ncols; ++c) {
+    column_t col;
+    if (column_init(&col, nez, N, ztop[c])) return 1;
+    size_t o = (size_t)c * n;
+    double* qc = q + o;
+    const double* Rc = R + o;
+    for (int i = 0; i < n; ++i) sc[i] = unknown_scale(&col, i);
+    residual_F(&col, lam, qc, Rc, F);
+    double f0 = scaled_norm(&col, F);
+    iters[c] = 0;
+    kits[c] = 0;
+    status[c] = 0;
+    if (!(f0 > OR_NEWTON_FLOOR * scaled_norm(&col, qc))) {
+      column_free(&col);
+      continue;
+    }
+    status[c] = 5;
+    for (int m = 1; m <= max_newton; ++m) {
+      /* b = -S^-1 F, V_0 = b / beta */
+      double beta = 0.0;
+      for (int i = 0; i < n; ++i) {
+        double bi = -F[i] / sc[i];
+        Vb[i] = bi;
+        beta += bi * bi;
+      }
+      beta = sqrt(beta);
+      for (int i = 0; i < n; ++i) Vb[i] /= beta;
+      for (int k = 0; k <= kmax; ++k) g[k] = 0.0;
+      g[0] = beta;
+      int kk = 0;
+      for (int k = 0; k < kmax; ++k) {
+        double* Vk = Vb + (size_t)k * n;
+        /* w = S^-1 [F(q + eps S V_k) - F(q)] / eps */
+        for (int i = 0; i < n; ++i) qp[i] = qc[i] + eps * sc[i] * Vk[i];
+        residual_F(&col, lam, qp, Rc, w);
+        for (int i = 0; i < n; ++i) w[i] = (w[i] - F[i]) / eps / sc[i];
+        /* modified Gram-Schmidt */
+        double* Hk = H + (size_t)k * (kmax + 1);
+        for (int j = 0; j <= k; ++j) {
+          const double* Vj = Vb + (size_t)j * n;
+          double h = 0.0;
+          for (int i = 0; i < n; ++i) h += w[i] * Vj[i];
+          Hk[j] = h;
+          for (int i = 0; i < n; ++i) w[i] -= h * Vj[i];
+        }
+        double hn = 0.0;
+        for (int i = 0; i < n; ++i) hn += w[i] * w[i];
+        hn = sqrt(hn);
+        Hk[k + 1] = hn;
+        double* Vn = Vb + (size_t)(k + 1) * n;
+        for (int i = 0; i < n; ++i) Vn[i] = hn > 0.0 ? w[i] / hn : 0.0;
+        /* previous rotations, then the one that zeroes H[k+1][k] */
+        for (int j = 0; j < k; ++j) {
+          double t = cs[j] * Hk[j] + sn[j] * Hk[j + 1];
+          Hk[j + 1] = -sn[j] * Hk[j] + cs[j] * Hk[j + 1];
+          Hk[j] = t;
+        }
+        double r = hypot(Hk[k], Hk[k + 1]);
+        cs[k] = r > 0.0 ? Hk[k] / r : 1.0;
+        sn[k] = r > 0.0 ? Hk[k + 1] / r : 0.0;
+        Hk[k] = r;
+        Hk[k + 1] = 0.0;
+        g[k + 1] = -sn[k] * g[k];
+        g[k] = cs[k] * g[k];
+        kk = k + 1;
+        if (fabs(g[k + 1]) <= gtol * beta || hn == 0.0) break;
+      }
+      kits[c] += kk;
+      /* R y = g (back substitution), dq = S sum_j y_j V_j */
+      for (int j = kk - 1; j >= 0; --j) {
+        double t = g[j];
+        for (int l = j + 1; l < kk; ++l) t -= H[(size_t)l * (kmax + 1) + j] * y[l];
+        y[j] = t / H[(size_t)j * (kmax + 1) + j];
+      }
+      for (int i = 0; i < n; ++i) {
+        double d = 0.0;
+        for (int j = 0; j < kk; ++j) d += y[j] * Vb[(size_t)j * n + i];
+        qc[i] += sc[i] * d;
+      }
+      iters[c] = m;
+      residual_F(&col, lam, qc, Rc, F);
+      double fn = scaled_norm(&col, F);
+      if (!(fn == fn)) { status[c] = 6; break; }
+      if (fn <= rtol * f0 || fn <= OR_NEWTON_FLOOR * scaled_norm(&col, qc)) {
+        status[c] = 0;
+        break;
+      }
+    }
+    column_free(&col);
+  }
+  free(F); free(qp); free(w); free(sc); free(Vb); free(H); free(cs); free(sn); free(g); free(y);
+  return 0;
 }
 
 /* Sec. 4.2.3 (NHEVI-LU): Newton-Raphson, Eqs. (Newton-system-update) and

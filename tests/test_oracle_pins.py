@@ -370,6 +370,63 @@ def test_newton_restart_from_root_stops_at_rounding_floor():
     assert it3[0] == 0 or np.linalg.norm((moved - root) / s) < 1e-12
 
 
+# --------------------------------------------------------------------------
+# NHEVI-GMRES (Sec. 4.2.1): Jacobian-free Newton-Krylov
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("nez,N", [(16, 3), (10, 4)])
+def test_newton_gmres_reaches_the_lu_root(nez, N):
+    """With a small Frechet perturbation and tight tolerances JFNK-GMRES and
+    Newton-LU find the same root of F; GMRES needs at most n iterations per
+    Newton step (unrestarted GMRES is exact after n)."""
+    lam = tableaux.ARK2.gamma * 300.0
+    q0 = _perturbed_state(nez, N, seed=41, amp_w=1.0, amp_th=0.5)[None]
+    R = q0.copy()
+    n = q0.shape[1]
+    q, it, kit, st = oracle.newton_gmres(nez, N, ZTOP, lam, R, q0, eps=1e-7, rtol=1e-12,
+                                         gtol=1e-12)
+    qr, _, str_ = oracle.newton(nez, N, ZTOP, lam, R, q0, rtol=1e-12)
+    assert st[0] == 0 and str_[0] == 0
+    s = oracle.scales(oracle.column_grid(nez, N, ZTOP)[0])
+    assert np.linalg.norm((q - qr)[0] / s) < 1e-10 * np.linalg.norm((qr - q0)[0] / s)
+    assert 1 <= it[0] <= 6 and it[0] <= kit[0] <= it[0] * n
+
+
+def test_one_gmres_newton_step_is_one_lu_newton_step():
+    """One Newton update with a tiny perturbation and a tight GMRES tolerance
+    solves the same linear system as one Newton-LU update: the two agree to
+    the Frechet difference error (Eq. Frechet-derivative)."""
+    nez, N = 8, 4
+    lam = 87.868
+    q0 = _perturbed_state(nez, N, seed=42, amp_w=2.0, amp_th=1.0)[None]
+    R = q0 + 1e-3 * oracle.scales(oracle.column_grid(nez, N, ZTOP)[0])[None]
+    R[0, 1] = R[0, -2] = 0.0
+    q1, it, kit, st = oracle.newton_gmres(nez, N, ZTOP, lam, R, q0, eps=1e-8, rtol=0.0,
+                                          gtol=1e-13, max_newton=1)
+    ql, itl, _ = oracle.newton(nez, N, ZTOP, lam, R, q0, rtol=0.0, max_iter=1)
+    assert it[0] == 1 and itl[0] == 1
+    d_lu = np.linalg.norm(ql - q0)
+    assert np.linalg.norm(q1 - ql) < 1e-6 * d_lu
+
+
+def test_newton_gmres_paper_settings_converge():
+    """The configuration of the paper's timing table (eps = 0.05, Newton
+    tolerance 1e-5, GMRES tolerance 1e-9): converged, with the residual
+    reduced 1e5-fold and the root within that tolerance of the LU root."""
+    nez, N = 16, 3
+    lam = tableaux.ARK2.gamma * 300.0
+    q0 = _perturbed_state(nez, N, seed=43, amp_w=1.0, amp_th=0.5)[None]
+    R = q0.copy()
+    q, it, kit, st = oracle.newton_gmres(nez, N, ZTOP, lam, R, q0)
+    assert st[0] == 0
+    s = oracle.scales(oracle.column_grid(nez, N, ZTOP)[0])
+    F0 = q0 - lam * oracle.apply_V(nez, N, ZTOP, q0) - R
+    F = q - lam * oracle.apply_V(nez, N, ZTOP, q) - R
+    assert np.linalg.norm(F[0] / s) <= 1e-5 * np.linalg.norm(F0[0] / s)
+    qr, _, _ = oracle.newton(nez, N, ZTOP, lam, R, q0, rtol=1e-12)
+    assert np.linalg.norm((q - qr)[0] / s) < 1e-3 * np.linalg.norm((qr - q0)[0] / s)
+
+
 def test_newton_linear_problem_one_iteration():
     """For V := L_RS (q - q_bar) (linear), Newton converges in one iteration;
     checked through the ARK driver: NHEVI and LHEVI-RS agree on the linear
