@@ -363,6 +363,7 @@ def gpu_arm(args, rank, world, local_rank, pool, cores):
                                           if v[1]}}
     if world == 1 and not args.no_extra:
         line["batched"] = batched_run(args)
+        line["nhevi_gmres_vs_lu"] = gmres_run(args)
         line["serving"] = serving_run(args)
     if world == 1 and not args.no_cpu:
         rate, cb = cpu_oracle_rate(pool, cores)
@@ -436,6 +437,51 @@ def batched_run(args):
             "ms_per_step_graph": ms_graph, "ms_per_step_calls": ms_calls,
             "kernel_launches_per_step": launches, "steps_timed": 2 * reps,
             "status": st, "state_finite": finite}
+
+
+def gmres_run(args):
+    """NHEVI column solves of the NHEVI workload's class ((16, 3), 30 km, the
+    rest state plus the seeded increment, Lambda = gamma dt of ARK2 at 300 s) on
+    8,192 columns: Newton-LU against JFNK-GMRES at the paper's settings
+    (eps 0.05, Newton 1e-5, GMRES 1e-9), same Newton tolerance."""
+    import torch
+    import hevi_inputs
+    import paper_2311_11425_gb300 as hv
+    ncols = 8192
+    inp = hevi_inputs.nhevi_ark2(seed=3, ncols=ncols)
+    ctx = hv.Context([(inp["nez"], inp["N"])], inp["ztop"], precision=hv.FP32_IR)
+    q0 = ctx.hevi_reference_state() + torch.from_numpy(inp["dq"].reshape(-1)).cuda()
+    lam = hv.tableau("ARK2").gamma * inp["dt"]
+    R = q0.clone()
+    kry = torch.zeros(ncols, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {}
+    for name, solve in (("lu", lambda q: ctx.hevi_newton_solve(lam, q, R, rtol=1e-5)),
+                        ("gmres", lambda q: ctx.hevi_newton_gmres_solve(lam, q, R, krylov=kry))):
+        q = q0.clone()
+        solve(q)  # warm-up (allocates the GMRES scratch)
+        reps = 3
+        ms = 0.0
+        for _ in range(reps):
+            q.copy_(q0)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            solve(q)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1) / reps
+        _, it = ctx.hevi_column_status()
+        out[name] = {"ms": ms, "column_solves_per_s": ncols / (ms * 1e-3),
+                     "newton_iters_mean": float(it.float().mean())}
+    out["gmres"]["krylov_iters_mean"] = float(kry.float().mean())
+    ctx.close()
+    torch.cuda.empty_cache()
+    return {"workload": f"NHEVI column solves: {ncols} columns of (16, 3), 30 km, "
+                        "Lambda = gamma dt (ARK2, 300 s), Newton tolerance 1e-5; GMRES with "
+                        "eps 0.05, GMRES tolerance 1e-9, FP64 Krylov",
+            "lu": out["lu"], "gmres": out["gmres"],
+            "gmres_over_lu_time": out["gmres"]["ms"] / out["lu"]["ms"]}
 
 
 def serving_run(args):

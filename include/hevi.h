@@ -185,6 +185,29 @@ hevi_status hevi_newton_solve_noalloc(int32_t nez, int32_t order, double z_top, 
                                       double rtol, int32_t max_iter, int32_t* status,
                                       int32_t* iters, void* stream);
 
+/* NHEVI-GMRES (Sec. 4.2.1): the stage problem F(q) = q - gamma_dt V(q) - R = 0
+ * per column by Jacobian-free Newton-Krylov: Newton updates, each solving
+ * J dq = -F by unpreconditioned GMRES (started at zero, not restarted) on the
+ * equilibrated system S^-1 J S y = -S^-1 F, dq = S y, with the Frechet
+ * difference (Eq. Frechet-derivative) J^ v ~ S^-1 [F(q + eps S v) - F(q)] /
+ * eps, i.e. the diagonal perturbation eps S of the reference scales S =
+ * (rho_bar, rho_bar c_s, Theta_bar) (the paper's configuration: eps = 0.05,
+ * Newton tolerance rtol = 1e-5, GMRES tolerance gtol = 1e-9).  GMRES stops
+ * when its residual estimate is <= gtol |S^-1 F| or after kmax iterations
+ * (kmax = 0: the context's longest column length n, after which GMRES is
+ * exact).  Newton stops as hevi_newton_solve.  state (dev, in/out) holds the
+ * initial guess; R (dev) as hevi_newton_solve; krylov (dev, ncols int32, may
+ * be NULL) receives the Krylov iterations per column, hevi_column_status the
+ * Newton updates.  FP64 throughout; scratch of about 8 (kmax + 1) (n + kmax /
+ * 2) bytes per column is allocated on first use.  Status as
+ * hevi_newton_solve; the _async form only records per-column status. */
+hevi_status hevi_newton_gmres_solve(hevi_ctx* ctx, double gamma_dt, double* state, const double* R,
+                                    double eps, double rtol, double gtol, int32_t max_newton,
+                                    int32_t kmax, int32_t* krylov);
+hevi_status hevi_newton_gmres_solve_async(hevi_ctx* ctx, double gamma_dt, double* state,
+                                          const double* R, double eps, double rtol, double gtol,
+                                          int32_t max_newton, int32_t kmax, int32_t* krylov);
+
 /* Vertical operator apply (App. A.2 / Sec. 4.3.1), x, y (dev, state layout):
  *   nonlinear != 0:  y = V(x);
  *   nonlinear == 0:  y = L(q0) x with q0 of the last hevi_factor. */

@@ -100,6 +100,8 @@ def load(build: bool = False):
                                            ctypes.POINTER(_P)]),
         "hevi_graph_launch": (_I32, [_P]),
         "hevi_estimate_bytes": (_I64, [ctypes.POINTER(_Grid), _I32, _I32, _I32]),
+        "hevi_newton_gmres_solve": (_I32, [_P, _D, _P, _P, _D, _D, _D, _I32, _I32, _P]),
+        "hevi_newton_gmres_solve_async": (_I32, [_P, _D, _P, _P, _D, _D, _D, _I32, _I32, _P]),
         "hevi_graph_destroy": (None, [_P]),
     }
     for name, (res, args) in sigs.items():
@@ -425,6 +427,19 @@ class Context:
         g = Graph(self, h, (q_a, q_b, H))
         self._graphs.add(g)
         return g
+
+    def hevi_newton_gmres_solve(self, gamma_dt, state, R, eps=0.05, rtol=1e-5, gtol=1e-9,
+                                max_newton=30, kmax=0, krylov=None, blocking=True):
+        """NHEVI-GMRES column solve in place on `state` (hevi_newton_gmres_solve);
+        `krylov` (int32 tensor of ncols, optional) receives the Krylov
+        iterations per column."""
+        fn = (self._lib.hevi_newton_gmres_solve if blocking
+              else self._lib.hevi_newton_gmres_solve_async)
+        import torch
+        kp = _ptr(krylov, self.ncols, torch.int32) if krylov is not None else None
+        _check(fn(self._h, float(gamma_dt), self._v(state), self._v(R), float(eps), float(rtol),
+                  float(gtol), int(max_newton), int(kmax), kp), "hevi_newton_gmres_solve")
+        return state
 
     def hevi_profile(self, enable: bool):
         _check(self._lib.hevi_profile(self._h, int(bool(enable))), "hevi_profile")

@@ -165,6 +165,10 @@ struct hevi_ctx {
   // device allocations
   std::vector<void*> allocs;
   double* lin_newton = nullptr;
+  // NHEVI-GMRES scratch: three state vectors and per-tile Krylov storage
+  double* gm_vec = nullptr;
+  double* gm_tile = nullptr;
+  int gm_kmax = 0;
   float* scr = nullptr;
   double* work = nullptr;
   int64_t work_vecs = 0;
@@ -332,6 +336,35 @@ hevi_status ensure_newton(hevi_ctx* c) {
   s = c->alloc(&c->scr, (size_t)c->scr_floats);
   if (s != HEVI_OK) return s;
   c->v.scr = c->scr;
+  return HEVI_OK;
+}
+
+// Longest column of the context (unknowns).
+int64_t max_unknowns(const hevi_ctx* c) {
+  int64_t m = 0;
+  for (const TileDesc& t : c->h_tiles) m = std::max<int64_t>(m, 3 * ((int64_t)t.nez * t.order + 1));
+  return m;
+}
+
+hevi_status ensure_gmres(hevi_ctx* c, int kmax) {
+  if (c->gm_kmax >= kmax && c->gm_vec) return HEVI_OK;
+  cudaStreamSynchronize(c->stream);
+  for (double** p : {&c->gm_vec, &c->gm_tile}) {
+    if (*p) {
+      auto it = std::find(c->allocs.begin(), c->allocs.end(), (void*)*p);
+      if (it != c->allocs.end()) c->allocs.erase(it);
+      cudaFree(*p);
+      *p = nullptr;
+    }
+  }
+  const int64_t nmax = max_unknowns(c);
+  const int64_t per_tile = ((int64_t)(kmax + 1) * nmax + (int64_t)kmax * (kmax + 3) / 2 +
+                            4 * (int64_t)kmax + 1) * kTile;
+  hevi_status s = c->alloc(&c->gm_vec, (size_t)(3 * c->state_size));
+  if (s != HEVI_OK) return s;
+  s = c->alloc(&c->gm_tile, (size_t)(per_tile * c->ntiles));
+  if (s != HEVI_OK) return s;
+  c->gm_kmax = kmax;
   return HEVI_OK;
 }
 
@@ -669,6 +702,56 @@ hevi_status hevi_newton_solve(hevi_ctx* c, double gamma_dt, double* state, const
   if (!c) return HEVI_ERR_INVALID_ARG;
   reset_fail(c);
   hevi_status s = hevi_newton_solve_async(c, gamma_dt, state, R, rtol, max_iter);
+  if (s != HEVI_OK) return s;
+  return wait_status(c);
+}
+
+hevi_status hevi_newton_gmres_solve_async(hevi_ctx* c, double gamma_dt, double* state,
+                                          const double* R, double eps, double rtol, double gtol,
+                                          int32_t max_newton, int32_t kmax, int32_t* krylov) {
+  if (!c || !state || !R || state == R || !(gamma_dt >= 0.0) || !(eps > 0.0) || !(rtol >= 0.0) ||
+      !(gtol > 0.0) || max_newton < 0 || max_newton > 1000 || kmax < 0)
+    return HEVI_ERR_INVALID_ARG;
+  const int64_t nmax = max_unknowns(c);
+  if (kmax == 0 || kmax > nmax) kmax = (int32_t)nmax;  // GMRES is exact after n iterations
+  hevi_status s = ensure_gmres(c, kmax);
+  if (s != HEVI_OK) return s;
+  hevi::GmArgs a;
+  a.lam = gamma_dt;
+  a.eps = eps;
+  a.rtol = rtol;
+  a.gtol = gtol;
+  a.max_newton = max_newton;
+  a.kmax = kmax;
+  a.nmax = (int)nmax;
+  a.kstride = (int64_t)(kmax + 1) * nmax * kTile;
+  a.hstride = (int64_t)kmax * (kmax + 3) / 2 * kTile;
+  a.astride = (4 * (int64_t)kmax + 1) * kTile;
+  a.q = state;
+  a.R = R;
+  a.F = c->gm_vec;
+  a.Qp = c->gm_vec + c->state_size;
+  a.Vp = c->gm_vec + 2 * c->state_size;
+  a.Kb = c->gm_tile;
+  a.Hb = c->gm_tile + a.kstride * c->ntiles;
+  a.Ab = a.Hb + a.hstride * c->ntiles;
+  a.kits = krylov;
+  {
+    Scope sc(c, kNewton);
+    for_orders(c, c->v, [&](const DevView& v, int N, int, cudaStream_t sk) {
+      hevi::launch_newton_gmres(v, N, a, sk);
+    });
+  }
+  return check_launch(c);
+}
+
+hevi_status hevi_newton_gmres_solve(hevi_ctx* c, double gamma_dt, double* state, const double* R,
+                                    double eps, double rtol, double gtol, int32_t max_newton,
+                                    int32_t kmax, int32_t* krylov) {
+  if (!c) return HEVI_ERR_INVALID_ARG;
+  reset_fail(c);
+  hevi_status s = hevi_newton_gmres_solve_async(c, gamma_dt, state, R, eps, rtol, gtol,
+                                                max_newton, kmax, krylov);
   if (s != HEVI_OK) return s;
   return wait_status(c);
 }

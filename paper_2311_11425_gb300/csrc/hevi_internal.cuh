@@ -206,6 +206,24 @@ void launch_apply_rhs(const DevView& v, int order, const double* Q, const double
                       cudaStream_t st);
 void launch_newton(const DevView& v, int order, double lam, double* q, const double* R,
                    double rtol, int max_iter, int ylen, cudaStream_t st);
+// Arguments of the NHEVI-GMRES column solve (Krylov scratch per tile:
+// kstride = (kmax + 1) nmax 32, hstride = kmax (kmax + 3) / 2 32,
+// astride = (4 kmax + 1) 32 doubles).
+struct GmArgs {
+  double lam, eps, rtol, gtol;
+  int max_newton, kmax, nmax;
+  int64_t kstride, hstride, astride;
+  double* q;
+  const double* R;
+  double* F;
+  double* Qp;
+  double* Vp;
+  double* Kb;
+  double* Hb;
+  double* Ab;
+  int32_t* kits;  // per column Krylov iterations, or null
+};
+void launch_newton_gmres(const DevView& v, int order, const GmArgs& a, cudaStream_t st);
 void launch_combine(int64_t count, const double* base, int nterms, const double* const* vec,
                     const double* coef, double* out, cudaStream_t st);
 void launch_reference_state(const DevView& v, double* q, cudaStream_t st);

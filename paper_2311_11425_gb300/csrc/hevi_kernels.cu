@@ -1141,7 +1141,8 @@ void launch_solve(const DevView& v, int order, hevi_precision prec, double lam, 
 // ---------------------------------------------------------------------------
 template <int N>
 __device__ void apply_V_column(const DevView& v, const Col& c, const double* q, double* out,
-                               double scale_lq, const double* add, const double* sub) {
+                               double scale_lq, const double* add, const double* sub,
+                               bool report = true) {
   // out = add + V(q) - sub (add / sub may be null)
   const Phys ph = v.ph;
   const double* ref = v.ref + c.off;
@@ -1171,7 +1172,7 @@ __device__ void apply_V_column(const DevView& v, const Col& c, const double* q, 
     }
   };
   element_pass<N>(c, c_tab.w[N], c_tab.wD[N], flux, o);
-  if (!ok) fail(v, c.col, HEVI_COL_BAD_INPUT);
+  if (!ok && report) fail(v, c.col, HEVI_COL_BAD_INPUT);
   (void)scale_lq;
 }
 
@@ -1472,6 +1473,152 @@ void launch_newton(const DevView& v, int order, double lam, double* q, const dou
 // ---------------------------------------------------------------------------
 // out = base + sum_t coef[t] vec[t]  (ARK stage right-hand sides and update)
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// NHEVI-GMRES (Sec. 4.2.1): Jacobian-free Newton-Krylov, one column per
+// thread.  Newton on F(q) = q - Lambda V(q) - R; each Newton system is solved
+// by unrestarted GMRES (modified Gram-Schmidt Arnoldi, Givens rotations) on
+// the equilibrated system J^ y = -S^-1 F, J^ = S^-1 J S, with the Frechet
+// difference J^ v ~ S^-1 [F(q + eps S v) - F(q)] / eps (diagonal perturbation
+// eps S).  FP64 throughout.  The Krylov basis, the Hessenberg columns (column
+// k keeps its k+2 entries at k (k+3) / 2) and the rotations live in per-tile
+// scratch interleaved over the tile's 32 lanes; F, the perturbed state and
+// its V use three state-size scratch vectors.
+// ---------------------------------------------------------------------------
+template <int N>
+__device__ void gmres_column(const DevView& v, const TileDesc& t, int64_t tile, int lane,
+                             const GmArgs& a) {
+  const Col c = make_col(v, t, lane, N);
+  const int n = c.n, kmax = a.kmax;
+  const double cs0 = v.ph.cs, lam = a.lam, eps = a.eps;
+  const double* ref = v.ref + c.off;
+  auto scl = [&](int i) { return ref_scale(ref, cs0, 3 * (i / 3), i % 3); };
+  double* qc = a.q + c.off;
+  const double* Rc = a.R + c.off;
+  double* F = a.F + c.off;
+  double* Qp = a.Qp + c.off;
+  const double* Vp = a.Vp + c.off;
+  double* K = a.Kb + tile * a.kstride + lane;  // element (k, i) at 32 (k nmax + i)
+  double* H = a.Hb + tile * a.hstride + lane;  // element e at 32 e
+  double* rc = a.Ab + tile * a.astride + lane;
+  double* rs = rc + 32 * (int64_t)kmax;
+  double* g = rs + 32 * (int64_t)kmax;
+  double* y = g + 32 * (int64_t)(kmax + 1);
+  auto Ke = [&](int k, int i) -> double& { return K[32 * ((int64_t)k * a.nmax + i)]; };
+  auto He = [&](int k, int j) -> double& { return H[32 * ((int64_t)k * (k + 3) / 2 + j)]; };
+  // F(q) from V(q); returns |S^-1 F|^2 and |S^-1 q|^2
+  auto residual = [&](double& f2, double& q2) {
+    apply_V_column<N>(v, c, a.q, a.Vp, 0.0, nullptr, nullptr, false);
+    f2 = 0.0;
+    q2 = 0.0;
+    for (int i = 0; i < n; ++i) {
+      const double fi = qc[i] - lam * Vp[i] - Rc[i];
+      F[i] = fi;
+      const double si = scl(i);
+      f2 += (fi / si) * (fi / si);
+      q2 += (qc[i] / si) * (qc[i] / si);
+    }
+  };
+  double f2, q2;
+  residual(f2, q2);
+  const double f0 = sqrt(f2);
+  int it = 0, kit = 0, status = HEVI_COL_OK;
+  if (!(f0 == f0)) status = HEVI_COL_BAD_INPUT;
+  else if (f0 > kNewtonFloor * sqrt(q2)) {
+    status = HEVI_COL_NOT_CONVERGED;
+    for (int m = 1; m <= a.max_newton; ++m) {
+      double beta = 0.0;
+      for (int i = 0; i < n; ++i) {
+        const double bi = -F[i] / scl(i);
+        Ke(0, i) = bi;
+        beta += bi * bi;
+      }
+      beta = sqrt(beta);
+      for (int i = 0; i < n; ++i) Ke(0, i) /= beta;
+      for (int k = 0; k <= kmax; ++k) g[32 * k] = 0.0;
+      g[0] = beta;
+      int kk = 0;
+      for (int k = 0; k < kmax; ++k) {
+        // w = S^-1 [F(q + eps S V_k) - F(q)] / eps into slot k+1
+        for (int i = 0; i < n; ++i) Qp[i] = qc[i] + eps * scl(i) * Ke(k, i);
+        apply_V_column<N>(v, c, a.Qp, a.Vp, 0.0, nullptr, nullptr, false);
+        for (int i = 0; i < n; ++i) {
+          const double fp = Qp[i] - lam * Vp[i] - Rc[i];
+          Ke(k + 1, i) = (fp - F[i]) / eps / scl(i);
+        }
+        for (int j = 0; j <= k; ++j) {  // modified Gram-Schmidt
+          double h = 0.0;
+          for (int i = 0; i < n; ++i) h += Ke(k + 1, i) * Ke(j, i);
+          He(k, j) = h;
+          for (int i = 0; i < n; ++i) Ke(k + 1, i) -= h * Ke(j, i);
+        }
+        double hn = 0.0;
+        for (int i = 0; i < n; ++i) hn += Ke(k + 1, i) * Ke(k + 1, i);
+        hn = sqrt(hn);
+        He(k, k + 1) = hn;
+        for (int i = 0; i < n; ++i) Ke(k + 1, i) = hn > 0.0 ? Ke(k + 1, i) / hn : 0.0;
+        for (int j = 0; j < k; ++j) {
+          const double t0 = rc[32 * j] * He(k, j) + rs[32 * j] * He(k, j + 1);
+          He(k, j + 1) = -rs[32 * j] * He(k, j) + rc[32 * j] * He(k, j + 1);
+          He(k, j) = t0;
+        }
+        const double r = hypot(He(k, k), He(k, k + 1));
+        rc[32 * k] = r > 0.0 ? He(k, k) / r : 1.0;
+        rs[32 * k] = r > 0.0 ? He(k, k + 1) / r : 0.0;
+        He(k, k) = r;
+        He(k, k + 1) = 0.0;
+        g[32 * (k + 1)] = -rs[32 * k] * g[32 * k];
+        g[32 * k] = rc[32 * k] * g[32 * k];
+        kk = k + 1;
+        if (fabs(g[32 * (k + 1)]) <= a.gtol * beta || hn == 0.0) break;
+      }
+      kit += kk;
+      for (int j = kk - 1; j >= 0; --j) {  // R y = g
+        double tj = g[32 * j];
+        for (int l = j + 1; l < kk; ++l) tj -= He(l, j) * y[32 * l];
+        y[32 * j] = tj / He(j, j);
+      }
+      for (int i = 0; i < n; ++i) {
+        double d = 0.0;
+        for (int j = 0; j < kk; ++j) d += y[32 * j] * Ke(j, i);
+        qc[i] += scl(i) * d;
+      }
+      it = m;
+      residual(f2, q2);
+      const double fn = sqrt(f2);
+      if (!(fn == fn)) {
+        status = HEVI_COL_BAD_INPUT;
+        break;
+      }
+      if (fn <= a.rtol * f0 || fn <= kNewtonFloor * sqrt(q2)) {
+        status = HEVI_COL_OK;
+        break;
+      }
+    }
+  }
+  v.col_iters[c.col] = it;
+  if (a.kits) a.kits[c.col] = kit;
+  if (status != HEVI_COL_OK)
+    fail(v, c.col, status);
+  else
+    v.col_status[c.col] = HEVI_COL_OK;
+}
+
+template <int N>
+__global__ void __launch_bounds__(64) k_newton_gmres(DevView v, GmArgs a) {
+  const int warp = threadIdx.x / kTile, lane = threadIdx.x % kTile;
+  const int64_t tile = v.tile_begin + (int64_t)blockIdx.x * (blockDim.x / kTile) + warp;
+  if (tile >= (int64_t)v.tile_begin + v.tile_count) return;
+  const TileDesc t = v.tiles[tile];
+  if (lane >= t.count) return;
+  gmres_column<N>(v, t, tile, lane, a);
+}
+
+void launch_newton_gmres(const DevView& v, int order, const GmArgs& a, cudaStream_t st) {
+#define HEVI_CALL(NN) k_newton_gmres<NN><<<col_grid(v, 64), 64, 0, st>>>(v, a)
+  HEVI_ORDER_SWITCH(order, HEVI_CALL)
+#undef HEVI_CALL
+}
+
 constexpr int kMaxTerms = 16;
 struct CombineArgs {
   const double* vec[kMaxTerms];
