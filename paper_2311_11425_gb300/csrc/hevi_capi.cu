@@ -106,6 +106,7 @@ hevi::LglTables make_tables() {
         t.wDf[N][k * (N + 1) + j] = (float)v;
       }
     for (int k = 0; k <= N; ++k) t.iwf[N][k] = (float)(1.0 / t.w[N][k]);
+    for (int k = 0; k <= N; ++k) t.iw[N][k] = 1.0 / t.w[N][k];
     {
       auto wD = [&](int k, int j) { return t.wD[N][k * (N + 1) + j]; };
       for (int dJ = -N; dJ <= N; ++dJ) {

@@ -32,7 +32,7 @@ struct Band {
 };
 
 // Physical constants of the isothermal reference atmosphere.
-constexpr int kEosTerms = 12;
+constexpr int kEosTerms = 9;
 struct Phys {
   double T0, p0, R, cp, g;
   double cv, gamma, cs;   // cp - R, cp / cv, sqrt(gamma R T0)
@@ -63,6 +63,7 @@ struct LglTables {
   double wD[kMaxOrder + 1][(kMaxOrder + 1) * (kMaxOrder + 1)];
   float wDf[kMaxOrder + 1][(kMaxOrder + 1) * (kMaxOrder + 1)];
   float iwf[kMaxOrder + 1][kMaxOrder + 1];  // 1 / w_k
+  double iw[kMaxOrder + 1][kMaxOrder + 1];  // 1 / w_k (FP64)
   // Row coefficients of the DSS'd derivative: for a point of class cls
   // (0 bottom end, 1 top end, 2 shared element boundary, 2 + k interior
   // local index k) and dJ = J - I in [-N, N], G = sum_e w_k Dhat_kj / W_I.
@@ -127,8 +128,9 @@ template <int N>
 __device__ __forceinline__ void elem_deriv(const double (&f)[N + 1][3], double (&cc)[N + 1][3]);
 
 template <int N, class FluxF, class OutF>
-__device__ __forceinline__ void element_pass(const Col& c, const double* w, const double* wD,
+__device__ __forceinline__ void element_pass(const Col& c, const double* w, const double* iw,
                                              FluxF&& flux, OutF&& out) {
+  (void)w;
   double f[N + 1][3];
   double carry[3] = {0.0, 0.0, 0.0};
   flux(0, f[0]);
@@ -140,7 +142,7 @@ __device__ __forceinline__ void element_pass(const Col& c, const double* w, cons
     elem_deriv<N>(f, cc);
     {
       double D[3];
-      const double sc = c.s / (e == 0 ? w[0] : 2.0 * w[0]);
+      const double sc = c.s * (e == 0 ? iw[0] : 0.5 * iw[0]);
 #pragma unroll
       for (int v = 0; v < 3; ++v) D[v] = (carry[v] + cc[0][v]) * sc;
       out(I0, D);
@@ -148,7 +150,7 @@ __device__ __forceinline__ void element_pass(const Col& c, const double* w, cons
 #pragma unroll
     for (int k = 1; k < N; ++k) {
       double D[3];
-      const double sc = c.s / w[k];
+      const double sc = c.s * iw[k];
 #pragma unroll
       for (int v = 0; v < 3; ++v) D[v] = cc[k][v] * sc;
       out(I0 + k, D);
@@ -160,10 +162,22 @@ __device__ __forceinline__ void element_pass(const Col& c, const double* w, cons
     }
   }
   double D[3];
-  const double sc = c.s / w[0];
+  const double sc = c.s * iw[0];
 #pragma unroll
   for (int v = 0; v < 3; ++v) D[v] = carry[v] * sc;
   out(c.nz - 1, D);
+}
+
+// 1/x in FP64 from an FP32 reciprocal seed and two Newton-Raphson steps
+// r <- r + r (1 - x r) (quadratic: relative error ~1e-7, ~1e-14, then
+// rounding), for positive x within the FP32 range; a few FP64 operations
+// instead of a division.
+__device__ __forceinline__ double rcp64(double x) {
+  double r = (double)(1.0f / (float)x);
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
 }
 
 // Equation of state of set 2C (App. A.1): P = p0 (R Theta / p0)^gamma.
@@ -175,6 +189,7 @@ __device__ __forceinline__ double eos(const Phys& ph, double Theta) {
 // state: P(Theta) - P_bar = P_bar ((1 + x)^gamma - 1), x = (Theta - Theta_bar) /
 // Theta_bar, exactly zero at Theta = Theta_bar and free of the cancellation of
 // two O(1e5 Pa) numbers.  For |x| <= 0.02 the binomial series (kEosTerms terms,
+// truncation below 1e-18 of the perturbation,
 // truncation below 1e-19 relative) replaces the FP64 log1p/expm1 pair, which
 // costs several times more on this part's FP64 pipe.
 __device__ __forceinline__ double eos_perturbation(const Phys& ph, double Theta, double Theta_bar,

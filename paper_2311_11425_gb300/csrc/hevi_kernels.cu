@@ -172,11 +172,11 @@ __device__ __forceinline__ bool lin_coefs(const Phys& ph, double rho, double m, 
                                           double Th_bar, double P_bar, double* w, double* th,
                                           double* c, double* dP, const double* ithb = nullptr) {
   if (!(rho > 0.0) || !(Th > 0.0) || !isfinite(m)) return false;
-  const double ir = 1.0 / rho;
+  const double ir = rcp64(rho);
   *w = m * ir;
   *th = Th * ir;
   *dP = eos_perturbation(ph, Th, Th_bar, P_bar, ithb);
-  *c = ph.gamma * (P_bar + *dP) / Th;
+  *c = ph.gamma * (P_bar + *dP) * rcp64(Th);
   return true;
 }
 
@@ -978,7 +978,6 @@ __device__ void solve_ir_column(const DevView& v, const TileDesc& t, int lane, d
   double* xc = x + c.off;
   const double g = v.ph.g;
   const double* w = c_tab.w[N];
-  const double* wD = c_tab.wD[N];
   if (v.fac_status[c.col] != HEVI_COL_OK) {  // no usable factors for this column
     for (int i = 0; i < c.n; ++i) xc[i] = __longlong_as_double(0x7ff8000000000000LL);
     v.col_iters[c.col] = 0;
@@ -1061,7 +1060,7 @@ __device__ void solve_ir_column(const DevView& v, const TileDesc& t, int lane, d
         y[i * stride] = (float)r * is32[i];
       }
     };
-    element_pass<N>(c, w, wD, flux, out);
+    element_pass<N>(c, w, c_tab.iw[N], flux, out);
     xnorm = sqrt(xs);
     dprev = dn;
     first = false;
@@ -1151,7 +1150,7 @@ __device__ void apply_V_column(const DevView& v, const Col& c, const double* q, 
   auto flux = [&](int I, double* f) {
     const double rho = qc[3 * I], m = qc[3 * I + 1], Th = qc[3 * I + 2];
     if (!(rho > 0.0) || !(Th > 0.0)) ok = false;
-    const double ir = 1.0 / rho;
+    const double ir = rcp64(rho);
     f[0] = m;
     f[1] = fma(m * m, ir, eos_perturbation(ph, Th, ref[3 * I + 2], ref[3 * I + 1],
                                            v.ithb ? v.ithb + c.off / 3 + I : nullptr));
@@ -1171,7 +1170,7 @@ __device__ void apply_V_column(const DevView& v, const Col& c, const double* q, 
       out[i] = val;
     }
   };
-  element_pass<N>(c, c_tab.w[N], c_tab.wD[N], flux, o);
+  element_pass<N>(c, c_tab.w[N], c_tab.iw[N], flux, o);
   if (!ok && report) fail(v, c.col, HEVI_COL_BAD_INPUT);
   (void)scale_lq;
 }
@@ -1194,7 +1193,7 @@ __device__ void apply_L_column(const DevView& v, const Col& c, const double* x, 
     out[a + 1] = (I == 0 || I == c.nz - 1) ? 0.0 : -D[1] - g * xc[3 * I];
     out[a + 2] = -D[2];
   };
-  element_pass<N>(c, c_tab.w[N], c_tab.wD[N], flux, o);
+  element_pass<N>(c, c_tab.w[N], c_tab.iw[N], flux, o);
 }
 
 template <int N>
@@ -1374,7 +1373,7 @@ __device__ void newton_column(const DevView& v, const TileDesc& t, int lane, dou
         y[i * stride] = (float)(-sF);
       }
     };
-    element_pass<N>(c, c_tab.w[N], c_tab.wD[N], flux, out);
+    element_pass<N>(c, c_tab.w[N], c_tab.iw[N], flux, out);
     qnorm = sqrt(qn);
     return sqrt(fn);
   };
