@@ -308,7 +308,7 @@ def gpu_arm(args, rank, world, local_rank, pool, cores):
                 "algorithmic_bytes_per_launch": BYTES_SOLVE_FP32IR * NCOLS}
     elif dom == "factor":
         ach = factor_flops() * NCOLS / (avg_ms * 1e-3) / 1e12
-        roof = {"kernel": "k_factor_g (factor)", "bound": "alu", "achieved": ach,
+        roof = {"kernel": "k_factor_r (factor)", "bound": "alu", "achieved": ach,
                 "peak": pk["fp32_tflops"], "unit": "TFLOP/s", "frac": ach / pk["fp32_tflops"],
                 "traffic": None, "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz",
                 "algorithmic_flops_per_launch": factor_flops() * NCOLS}
