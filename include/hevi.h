@@ -47,7 +47,8 @@ typedef enum {
   HEVI_ERR_OOM = 3,          /* device allocation failed in setup */
   HEVI_ERR_SINGULAR = 4,     /* some column met an exactly zero pivot */
   HEVI_ERR_NOT_CONVERGED = 5, /* some column's refinement or Newton hit its limit */
-  HEVI_ERR_BAD_INPUT = 6      /* some column's state is non-physical (rho or Theta <= 0, NaN) */
+  HEVI_ERR_BAD_INPUT = 6,     /* some column's state is non-physical (rho or Theta <= 0, NaN) */
+  HEVI_ERR_WAIT_TIMEOUT = 7   /* a device-side wait for an asynchronous copy exceeded its limit */
 } hevi_status;
 
 /* One column size class: Nez elements of LGL order N (1 <= N <= 5). */
@@ -89,6 +90,9 @@ typedef struct hevi_ctx hevi_ctx;
 #define HEVI_COL_SINGULAR 4
 #define HEVI_COL_NOT_CONVERGED 5
 #define HEVI_COL_BAD_INPUT 6
+/* A device-side wait for an asynchronous copy of the column's factor records
+ * exceeded its limit (about a second); the column's output is NaN. */
+#define HEVI_COL_WAIT_TIMEOUT 7
 
 /* Create a context: builds the LGL tables of each size class (Sec. 3) and
  * the reference state of every column on the device, and allocates the

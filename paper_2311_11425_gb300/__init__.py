@@ -22,7 +22,8 @@ __all__ = ["load", "Context", "HeviError", "FP64", "FP32_IR", "tableau", "Tablea
 
 FP64, FP32_IR = 0, 1
 STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of device memory",
-          4: "singular column", 5: "not converged", 6: "non-physical input state"}
+          4: "singular column", 5: "not converged", 6: "non-physical input state",
+          7: "device wait past its limit"}
 COL_OK, COL_SINGULAR, COL_NOT_CONVERGED, COL_BAD_INPUT = 0, 4, 5, 6
 
 

@@ -24,7 +24,7 @@ namespace {
 
 // Failure counters on the device: [0] any, [1] singular, [2] not converged,
 // [3] bad input.
-constexpr int kFailSlots = 4;
+constexpr int kFailSlots = 5;
 
 int rl_of(int N) {  // record length per pivot step
   const int K = 3 * (N + 1) - 1;
@@ -309,6 +309,7 @@ hevi_status wait_status(hevi_ctx* c) {
     return HEVI_ERR_CUDA;
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return HEVI_ERR_CUDA;
   if (c->h_fail[0] == 0) return HEVI_OK;
+  if (c->h_fail[4]) return HEVI_ERR_WAIT_TIMEOUT;
   if (c->h_fail[3]) return HEVI_ERR_BAD_INPUT;
   if (c->h_fail[1]) return HEVI_ERR_SINGULAR;
   return HEVI_ERR_NOT_CONVERGED;
@@ -461,7 +462,10 @@ hevi_status hevi_setup(hevi_ctx** out, const hevi_column_grid* grid, const hevi_
     t.scr_off = scr_off;
     t.y_off = y_off;
     const int64_t n = 3 * ((int64_t)t.nez * t.order + 1);
-    y_off += (n + 2 * (3 * (t.order + 1) - 1) + 4) * kTile;
+    // the refinement's interleaved scratch: y (FP32, n + 2K + 4 rows), x, b
+    // and the point coefficients of L(q0) (FP64, n rows each), S and S^-1
+    // (FP32, n rows each)
+    y_off += (9 * n + 2 * (3 * (t.order + 1) - 1) + 4) * kTile;
     fac_off += n * rl_of(t.order) * kTile;
     scr_off += n * ur2_of(t.order) * kTile;
     if (c->order_count[t.order] == 0) c->order_begin[t.order] = (int32_t)c->h_tiles.size();
@@ -604,7 +608,7 @@ int64_t hevi_estimate_bytes(const hevi_column_grid* grid, hevi_precision precisi
     const int64_t tiles = (count[c] + kTile - 1) / kTile;
     state += n * count[c];
     ntiles += tiles;
-    ysc += tiles * (n + 2 * (3 * (N + 1) - 1) + 4) * kTile;
+    ysc += tiles * (9 * n + 2 * (3 * (N + 1) - 1) + 4) * kTile;
     fac += tiles * n * rl_of(N) * kTile;
     scr += tiles * n * ur2_of(N) * kTile;
   }

@@ -83,11 +83,15 @@ __device__ __forceinline__ T* brec_vec(T* tile_base, int n, int j, int e, int la
 }
 
 // Record a per-column failure; counters: [0] any, [1] singular, [2] not
-// converged, [3] bad input.
+// converged, [3] bad input, [4] a device wait past its limit.
 __device__ __forceinline__ void fail(const DevView& v, int64_t col, int code) {
   v.col_status[col] = code;
   atomicAdd(v.fail_count, 1);
-  atomicAdd(v.fail_count + (code == HEVI_COL_SINGULAR ? 1 : code == HEVI_COL_NOT_CONVERGED ? 2 : 3), 1);
+  atomicAdd(v.fail_count + (code == HEVI_COL_SINGULAR        ? 1
+                            : code == HEVI_COL_NOT_CONVERGED ? 2
+                            : code == HEVI_COL_WAIT_TIMEOUT  ? 4
+                                                             : 3),
+            1);
 }
 
 __device__ __forceinline__ Col make_col(const DevView& v, const TileDesc& t, int lane, int N) {
@@ -99,6 +103,28 @@ __device__ __forceinline__ Col make_col(const DevView& v, const TileDesc& t, int
   c.n = 3 * c.nz;
   c.s = 2.0 / v.col_dz[c.col];
   return c;
+}
+
+// A tile's refinement scratch, every array interleaved [row][lane] so that a
+// warp's 32 columns read and write one contiguous line per row: the work
+// vector y (FP32, n + 2K + 4 rows), the iterate x, the right-hand side b and
+// the point coefficients (w, theta, c) of L(q0) (FP64, n rows each), and the
+// scales S, S^-1 (FP32, n rows each).
+struct TileScr {
+  float* y;
+  double *x, *b, *lin;
+  float *s, *is;
+};
+__device__ __forceinline__ TileScr tile_scratch(const DevView& v, const TileDesc& t) {
+  const int64_t n = 3 * ((int64_t)t.nez * t.order + 1), K = 3 * (t.order + 1) - 1;
+  TileScr r;
+  r.y = v.ysc + t.y_off;
+  r.x = reinterpret_cast<double*>(r.y + (n + 2 * K + 4) * kTile);
+  r.b = r.x + n * kTile;
+  r.lin = r.b + n * kTile;
+  r.s = reinterpret_cast<float*>(r.lin + n * kTile);
+  r.is = r.s + n * kTile;
+  return r;
 }
 
 // ---------------------------------------------------------------------------
@@ -138,10 +164,25 @@ __global__ void k_setup_ref(DevView v, const int32_t* col_order, const int32_t* 
   }
 }
 
+// Interleaved copies of S and S^-1 in each tile's refinement scratch.
+__global__ void k_setup_tile_scales(DevView v) {
+  const TileDesc t = v.tiles[blockIdx.x];
+  const int lane = threadIdx.x;
+  if (lane >= t.count) return;
+  const TileScr sc = tile_scratch(v, t);
+  const int64_t off = v.col_off[v.perm[t.first + lane]];
+  const int n = 3 * (t.nez * t.order + 1);
+  for (int i = 0; i < n; ++i) {
+    sc.s[(int64_t)i * kTile + lane] = v.s32[off + i];
+    sc.is[(int64_t)i * kTile + lane] = v.is32[off + i];
+  }
+}
+
 void launch_setup_ref(const DevView& v, const int32_t* col_order, const int32_t* col_nez,
                       cudaStream_t st) {
   int blk = 128;
   k_setup_ref<<<(unsigned)((v.ncols + blk - 1) / blk), blk, 0, st>>>(v, col_order, col_nez);
+  if (v.ysc && v.ntiles > 0) k_setup_tile_scales<<<(unsigned)v.ntiles, kTile, 0, st>>>(v);
 }
 
 __global__ void k_reference_state(DevView v, double* q) {
@@ -559,6 +600,7 @@ __global__ void __launch_bounds__(128) k_factor_r(DevView v, double lam, const d
   float* tb = reinterpret_cast<float*>(v.fac) + t.fac_off;
   float* bb = tb + (int64_t)c.n * FRn * kTile;
   const int n = c.n;
+  double* lin_t = tile_scratch(v, t).lin;
 
   // point coefficients of L(q0) (FP64): w, theta, c = gamma P / Theta
   bool ok = true;
@@ -580,6 +622,10 @@ __global__ void __launch_bounds__(128) k_factor_r(DevView v, double lam, const d
       v.lin[a] = w;
       v.lin[a + 1] = th;
       v.lin[a + 2] = cc;
+      double* lt = lin_t + (int64_t)(3 * I) * kTile + cl;
+      lt[0] = w;
+      lt[kTile] = th;
+      lt[2 * kTile] = cc;
     }
     lin32[3 * I] = (float)w;
     lin32[3 * I + 1] = (float)th;
@@ -861,6 +907,8 @@ __device__ __forceinline__ void forward_sweep(const T* base, int lane, int n, Y*
             for (int vv = 0; vv < NVF; ++vv)
               prefetch_line(frec_vec<N, T>(const_cast<T*>(base), j + PD, vv * Vec<T>::W, lane));
           }
+          // and the work-vector row that enters the window PD steps later
+          if (j + WR + PD < n + 2 * K) prefetch_line(&y[(j + WR + PD) * stride]);
         }
         T f[FR];
         load_vecs<N, T>(frec_vec<N, T>(const_cast<T*>(base), j, 0, lane), f, FR);
@@ -911,6 +959,7 @@ __device__ __forceinline__ Y backward_sweep(const T* base, int lane, int n, Y* y
       if (j >= 0) {
         if constexpr (PD > 0) {
           if (j - PD >= 0) prefetch_step(j - PD);
+          if (j - WB - PD >= 0) prefetch_line(&y[(j - WB - PD) * stride]);
         }
         T u[BR];
         load_vecs<N, T>(brec_vec<N, T>(const_cast<T*>(base), n, j, 0, lane), u, BR);
@@ -932,6 +981,449 @@ __device__ __forceinline__ Y backward_sweep(const T* base, int lane, int n, Y* y
   }
   (void)FR;
   return ss;
+}
+
+// ---------------------------------------------------------------------------
+// Record ring for the FP32 solve: the warp's records stream through a small
+// shared-memory ring filled by bulk asynchronous copies (cp.async.bulk, the
+// TMA engine's linear mode) that complete on one mbarrier per slot.  One lane
+// issues the copies of step j + D while the warp computes step j; the 32
+// lanes' records of a step are one contiguous block of the tile, so a step is
+// one (forward) or two (backward: B record + the 1/u_jj vector) copies.
+// Every wait is bounded: past the limit the ring records the failure, stops
+// issuing, and the caller drains what is still in flight before returning.
+// ---------------------------------------------------------------------------
+constexpr int kRingWaitTries = 1 << 16;
+constexpr int kWarpSweepLanes = 6;  // at most this many refining lanes: warp_sweeps       // x suspend hint below: ~1.3 s bound
+constexpr unsigned kRingSuspendNs = 20000;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+// true once the phase of the given parity has completed, false past the limit
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+  const uint32_t a = smem_u32(bar);
+  for (int it = 0; it < kRingWaitTries; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(a), "r"(parity), "r"(kRingSuspendNs)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ uint64_t evict_first_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar,
+                                         uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+      " [%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
+      : "memory");
+}
+
+template <int N>
+struct RingCfg {
+  static constexpr int FB = Band<N>::FR * kTile * 4;        // forward step: F record
+  static constexpr int BB = (Band<N>::BR + 4) * kTile * 4;  // backward: B record + 1/u_jj vector
+  static constexpr int BYTES = 2 * BB;                      // ring size
+  static constexpr int DF = BYTES / FB;                     // forward slots (>= 3)
+  static constexpr int DB = 2;                              // backward slots
+  static constexpr int NBAR = DF > DB ? DF : DB;
+  static constexpr int TRANSPOSE = kTile * 17 * 8;          // b / x transpose tile
+  static constexpr int YST = 512;                           // warp_sweeps' vector (floats)
+  static constexpr int SMEM = (BYTES > TRANSPOSE ? BYTES : TRANSPOSE) + YST * 4;  // barriers follow
+  static_assert(DF >= 3, "forward ring too shallow");
+};
+
+// Dynamic shared memory of the solve kernel: the ring, then its barriers.
+extern __shared__ __align__(128) unsigned char g_ring[];
+
+// Lane-uniform state of one warp's ring; the buffer and the barriers are the
+// kernel's dynamic shared memory (RingCfg<N>::SMEM bytes of ring, then NBAR
+// barriers).
+template <int N>
+struct Ring {
+  unsigned phase;    // expected parity per barrier (bit s)
+  unsigned pending;  // barriers with a copy in flight (bit s)
+  bool ok;
+  __device__ __forceinline__ static unsigned char* buf() { return g_ring; }
+  __device__ __forceinline__ static uint64_t* bar() {
+    return reinterpret_cast<uint64_t*>(g_ring + RingCfg<N>::SMEM);
+  }
+  __device__ __forceinline__ bool wait(int s) {
+    bool good = ok;
+    if (good) good = mbar_wait(&bar()[s], (phase >> s) & 1u);
+    good = __all_sync(0xffffffffu, good);
+    if (good) {
+      phase ^= 1u << s;
+      pending &= ~(1u << s);
+    }
+    ok = good;
+    return good;
+  }
+  // wait (bounded) for every copy still in flight; the ring is idle after
+  __device__ __forceinline__ void drain() {
+    for (int s = 0; s < RingCfg<N>::NBAR; ++s)
+      if (pending & (1u << s)) {
+        mbar_wait(&bar()[s], (phase >> s) & 1u);
+        phase ^= 1u << s;
+      }
+    pending = 0;
+    __syncwarp();
+  }
+};
+
+template <int N>
+__device__ __forceinline__ void ring_issue_f(Ring<N>& rg, const float* base, int j, int slot,
+                                             int lane) {
+  using C = RingCfg<N>;
+  rg.pending |= 1u << slot;
+  if (lane == 0) {
+    uint64_t* bar = &Ring<N>::bar()[slot];
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(bar, C::FB);
+    bulk_g2s(Ring<N>::buf() + slot * C::FB, frec_vec<N, float>(const_cast<float*>(base), j, 0, 0),
+             C::FB, bar, evict_first_policy());
+  }
+}
+template <int N>
+__device__ __forceinline__ void ring_issue_b(Ring<N>& rg, const float* base, int n, int j,
+                                             int slot, int lane) {
+  using C = RingCfg<N>;
+  constexpr int K = Band<N>::K;
+  rg.pending |= 1u << slot;
+  if (lane == 0) {
+    uint64_t* bar = &Ring<N>::bar()[slot];
+    const uint64_t pol = evict_first_policy();
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(bar, C::BB);
+    unsigned char* dst = Ring<N>::buf() + slot * C::BB;
+    bulk_g2s(dst, brec_vec<N, float>(const_cast<float*>(base), n, j, 0, 0), Band<N>::BR * kTile * 4,
+             bar, pol);
+    bulk_g2s(dst + Band<N>::BR * kTile * 4, frec_vec<N, float>(const_cast<float*>(base), j, K + 1, 0),
+             4 * kTile * 4, bar, pol);
+  }
+}
+
+// Forward sweep of forward_sweep with the F records taken from the ring.
+template <int N>
+__device__ __forceinline__ void forward_sweep_ring(Ring<N>& rg, const float* base, int lane, int n,
+                                                   float* y, int stride) {
+  using C = RingCfg<N>;
+  constexpr int K = Band<N>::K, WR = Band<N>::WR, FR = Band<N>::FR;
+  for (int s = 0; s < C::DF && s < n; ++s) ring_issue_f<N>(rg, base, s, s, lane);
+  float w[WR];
+#pragma unroll
+  for (int r = 0; r < WR; ++r) w[r] = y[r * stride];
+  int slot = 0;
+  for (int j0 = 0; j0 < n; j0 += WR) {
+#pragma unroll
+    for (int t = 0; t < WR; ++t) {
+      const int j = j0 + t;
+      if (j < n) {
+        rg.wait(slot);
+        float f[FR];
+        const float4* src = reinterpret_cast<const float4*>(Ring<N>::buf() + slot * C::FB) + lane;
+#pragma unroll
+        for (int q = 0; q < FR; q += 4) {
+          const float4 x = src[(q / 4) * kTile];
+          f[q] = x.x; f[q + 1] = x.y; f[q + 2] = x.z; f[q + 3] = x.w;
+        }
+        const int p = (int)f[K];
+        float yp = w[t];
+#pragma unroll
+        for (int r = 1; r <= K; ++r)
+          if (p == r) yp = w[(t + r) % WR];
+#pragma unroll
+        for (int r = 1; r <= K; ++r)
+          if (p == r) w[(t + r) % WR] = w[t];
+#pragma unroll
+        for (int r = 1; r <= K; ++r) w[(t + r) % WR] -= f[r - 1] * yp;
+        // refill the slot just read with step j + D
+        __syncwarp();
+        if (j + C::DF < n && rg.ok) ring_issue_f<N>(rg, base, j + C::DF, slot, lane);
+        slot = slot + 1 == C::DF ? 0 : slot + 1;
+        y[j * stride] = yp;
+        w[t] = y[(j + WR) * stride];
+      }
+    }
+  }
+}
+
+// Backward sweep of backward_sweep with the B records and 1/u_jj from the ring.
+template <int N>
+__device__ __forceinline__ float backward_sweep_ring(Ring<N>& rg, const float* base, int lane, int n,
+                                                     float* y, int stride) {
+  using C = RingCfg<N>;
+  constexpr int K = Band<N>::K, WB = Band<N>::WC, BR = Band<N>::BR;
+  for (int s = 0; s < C::DB && s < n; ++s) ring_issue_b<N>(rg, base, n, n - 1 - s, s, lane);
+  float w[WB];
+#pragma unroll
+  for (int cc = 0; cc < WB; ++cc) {
+    const int i = n - 1 - cc;
+    w[cc] = i >= 0 ? y[i * stride] : 0.0f;
+  }
+  float ss = 0.0f;
+  int slot = 0;
+  for (int j0 = n - 1; j0 >= 0; j0 -= WB) {
+#pragma unroll
+    for (int t = 0; t < WB; ++t) {
+      const int j = j0 - t;
+      if (j >= 0) {
+        rg.wait(slot);
+        float u[BR];
+        const float4* src = reinterpret_cast<const float4*>(Ring<N>::buf() + slot * C::BB) + lane;
+#pragma unroll
+        for (int q = 0; q < BR; q += 4) {
+          const float4 x = src[(q / 4) * kTile];
+          u[q] = x.x; u[q + 1] = x.y; u[q + 2] = x.z; u[q + 3] = x.w;
+        }
+        const float4 dv = src[(BR / 4) * kTile];
+        const float invd = ((K + 1) % 4 == 0)   ? dv.x
+                           : ((K + 1) % 4 == 1) ? dv.y
+                           : ((K + 1) % 4 == 2) ? dv.z
+                                                : dv.w;
+        const float x = w[t] * invd;
+        ss += x * x;
+#pragma unroll
+        for (int cc = 1; cc <= 2 * K; ++cc) w[(t + cc) % WB] -= u[cc - 1] * x;
+        // refill the slot just read with step j - D
+        __syncwarp();
+        if (j - C::DB >= 0 && rg.ok) ring_issue_b<N>(rg, base, n, j - C::DB, slot, lane);
+        slot ^= 1;
+        y[j * stride] = x;
+        const int jn = j - WB;
+        w[t] = jn >= 0 ? y[jn * stride] : 0.0f;
+      }
+    }
+  }
+  return ss;
+}
+
+// Copy `count` 16-byte vectors src(q), q = 0..count-1, into dst[q] with the
+// warp, four loads in flight per lane before their stores.
+template <class Src>
+__device__ __forceinline__ void stage_vecs(float* dst, int count, int lane, Src&& src) {
+  float4* d = reinterpret_cast<float4*>(dst);
+  for (int q0 = 0; q0 < count; q0 += 4 * 32) {
+    float4 v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int q = q0 + k * 32 + lane;
+      if (q < count) v[k] = *src(q);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int q = q0 + k * 32 + lane;
+      if (q < count) d[q] = v[k];
+    }
+  }
+}
+
+// Forward and backward substitution of ONE column (tile lane c) by the whole
+// warp.  Lane l carries the window rows i = l (mod 32) and the row 32 below
+// (forward: above) it, so a pivot step is two shuffles and one FMA per lane
+// instead of a per-thread chain of loads; the column's records are staged
+// into the (idle) ring a chunk of steps at a time.  Same arithmetic as
+// forward_sweep / backward_sweep.  Used for the few lanes that still refine
+// after the ring sweeps, which would otherwise set the kernel's tail.
+template <int N>
+__device__ __noinline__ void warp_sweeps(const float* base, int c, int n, float* ytile, int lane) {
+  constexpr int K = Band<N>::K, FR = Band<N>::FR, BR = Band<N>::BR;
+  constexpr int NVF = FR / 4, NVB = BR / 4, RS = BR + 4;
+  constexpr int CAP = RingCfg<N>::SMEM / 4 - RingCfg<N>::YST;  // floats of staging space
+  constexpr unsigned FULL = 0xffffffffu;
+  float* sm = reinterpret_cast<float*>(Ring<N>::buf());
+  float* yc = sm + CAP;  // the column's work vector, rows 0 .. n + 2K - 1
+  const int ylen = n + 2 * K;
+  float* fb = const_cast<float*>(base);
+  for (int i = lane; i < ylen; i += 32) yc[i] = ytile[(int64_t)i * kTile + c];
+  __syncwarp();
+  {  // forward: L y = P b
+    constexpr int CH = CAP / FR;
+    float yw = lane < ylen ? yc[lane] : 0.0f;
+    float yn = lane + 32 < ylen ? yc[lane + 32] : 0.0f;
+    for (int j0 = 0; j0 < n; j0 += CH) {
+      const int cnt = min(CH, n - j0);
+      __syncwarp();
+      stage_vecs(sm, cnt * NVF, lane, [&](int q) {
+        return reinterpret_cast<const float4*>(frec_vec<N, float>(fb, j0 + q / NVF, (q % NVF) * 4, c));
+      });
+      __syncwarp();
+      for (int jj = 0; jj < cnt; ++jj) {
+        const int j = j0 + jj;
+        const float* f = sm + jj * FR;
+        const int p = (int)f[K];
+        const int l0 = j & 31, lp = (j + p) & 31;
+        const int rel = (lane - j) & 31;  // this lane's row is j + rel
+        const float lr = f[rel >= 1 && rel <= K ? rel - 1 : K + 1];
+        const float ynext = j + 64 < ylen ? yc[j + 64] : 0.0f;
+        const float yj = __shfl_sync(FULL, yw, lp);  // row j after the interchange
+        const float yo = __shfl_sync(FULL, yw, l0);
+        yw = lane == lp ? yo : yw;
+        yw = rel >= 1 && rel <= K ? yw - lr * yj : yw;
+        if (lane == l0) yc[j] = yj;
+        yw = lane == l0 ? yn : yw;
+        yn = lane == l0 ? ynext : yn;
+      }
+    }
+  }
+  {  // backward: U x = y
+    constexpr int CH = CAP / RS;
+    __syncwarp();
+    const int il = n - 1 - ((n - 1 - lane) & 31);  // the lane's row nearest below n
+    float yw = il >= 0 ? yc[il] : 0.0f;
+    float yn = il - 32 >= 0 ? yc[il - 32] : 0.0f;
+    for (int j1 = n - 1; j1 >= 0; j1 -= CH) {
+      const int cnt = min(CH, j1 + 1);  // steps j1, j1 - 1, .., j1 - cnt + 1
+      __syncwarp();
+      stage_vecs(sm, cnt * (NVB + 1), lane, [&](int q) {
+        const int jj = q / (NVB + 1), vv = q % (NVB + 1);
+        return reinterpret_cast<const float4*>(vv < NVB ? brec_vec<N, float>(fb, n, j1 - jj, vv * 4, c)
+                                                        : frec_vec<N, float>(fb, j1 - jj, K + 1, c));
+      });
+      __syncwarp();
+      for (int jj = 0; jj < cnt; ++jj) {
+        const int j = j1 - jj;
+        const float* u = sm + jj * RS;
+        const int l0 = j & 31;
+        const int rel = (j - lane) & 31;  // this lane's row is j - rel
+        const float ur = u[rel >= 1 && rel <= 2 * K ? rel - 1 : BR];
+        const float ynext = j - 64 >= 0 ? yc[j - 64] : 0.0f;
+        const float xj = __shfl_sync(FULL, yw, l0) * u[BR + (K + 1) % 4];
+        yw = rel >= 1 && rel <= 2 * K ? yw - ur * xj : yw;
+        if (lane == l0) yc[j] = xj;
+        yw = lane == l0 ? yn : yw;
+        yn = lane == l0 ? ynext : yn;
+      }
+    }
+  }
+  __syncwarp();
+  for (int i = lane; i < n; i += 32) ytile[(int64_t)i * kTile + c] = yc[i];
+  __syncwarp();
+}
+
+// The other refinement passes of ONE column (tile lane c) by the whole warp,
+// lanes over the column's rows / points; same arithmetic as the per-thread
+// passes of solve_ir_column except the order of the sums.
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// |S y|^2 of column c.
+__device__ __noinline__ float warp_d2(const TileScr& sc, int c, int n, int lane) {
+  float d2 = 0.0f;
+  for (int i = lane; i < n; i += 32) {
+    const float d = sc.y[(int64_t)i * kTile + c] * sc.s[(int64_t)i * kTile + c];
+    d2 = fmaf(d, d, d2);
+  }
+  return warp_sum(d2);
+}
+
+// x += S y (x = S y on the first sweep) of column c.
+__device__ __noinline__ void warp_update_x(const TileScr& sc, int c, int n, bool fst, int lane) {
+  for (int i = lane; i < n; i += 32) {
+    const int64_t a = (int64_t)i * kTile + c;
+    const double d = (double)(sc.y[a] * sc.s[a]);
+    sc.x[a] = fst ? d : sc.x[a] + d;
+  }
+  __syncwarp();
+}
+
+// Fused pass of column c: x += S y, r = b - A x, y = S^-1 r; returns |x|^2.
+// The point fluxes K x go through shared memory so that each lane can form
+// the element derivative (and the direct-stiffness sum at element ends) of
+// its own points.
+template <int N>
+__device__ __noinline__ double warp_residual(const TileScr& sc, int c, int nez, double cs,
+                                             double lam, double g, bool fst, int lane) {
+  const int nz = nez * N + 1;
+  double* F = reinterpret_cast<double*>(Ring<N>::buf());  // [nz][3], then the tables
+  double* Dm = F + 3 * nz;                                 // wD (lane-dependent rows)
+  double* iw = Dm + (N + 1) * (N + 1);
+  double xsq = 0.0;
+  __syncwarp();
+  for (int k = lane; k < (N + 1) * (N + 1); k += 32) Dm[k] = c_tab.wD[N][k];
+  if (lane <= N) iw[lane] = c_tab.iw[N][lane];
+  for (int I = lane; I < nz; I += 32) {
+    double xi[3];
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      const int64_t a = (int64_t)(3 * I + u) * kTile + c;
+      const double d = (double)(sc.y[a] * sc.s[a]);
+      xi[u] = fst ? d : sc.x[a] + d;
+      sc.x[a] = xi[u];
+      xsq = fma(xi[u], xi[u], xsq);
+    }
+    const int64_t a0 = (int64_t)(3 * I) * kTile + c;
+    const double wI = sc.lin[a0], thI = sc.lin[a0 + kTile], cI = sc.lin[a0 + 2 * kTile];
+    F[3 * I] = xi[1];
+    F[3 * I + 1] = fma(-wI * wI, xi[0], fma(2.0 * wI, xi[1], cI * xi[2]));
+    F[3 * I + 2] = fma(-thI * wI, xi[0], fma(thI, xi[1], wI * xi[2]));
+  }
+  __syncwarp();
+  auto cc = [&](int e, int k, int v) {  // element e's derivative row k of field v
+    double sum = 0.0;
+#pragma unroll
+    for (int j = 0; j <= N; ++j) sum = fma(Dm[k * (N + 1) + j], F[3 * (e * N + j) + v], sum);
+    return sum;
+  };
+  for (int I = lane; I < nz; I += 32) {
+    const int e = I == nz - 1 ? nez - 1 : I / N, k = I - e * N;
+    double D[3];
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+      if (k != 0 && k != N) {
+        D[v] = cc(e, k, v) * (cs * iw[k]);
+      } else if (I == 0) {
+        D[v] = cc(0, 0, v) * (cs * iw[0]);
+      } else if (I == nz - 1) {
+        D[v] = cc(nez - 1, N, v) * (cs * iw[0]);
+      } else {
+        D[v] = (cc(e - 1, N, v) + cc(e, 0, v)) * (cs * (0.5 * iw[0]));
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      const int64_t a = (int64_t)(3 * I + u) * kTile + c;
+      const double xv = sc.x[a], bv = sc.b[a];
+      double r;
+      if (u == 1 && (I == 0 || I == nz - 1)) {
+        r = bv - xv;
+      } else {
+        double ax = D[u];
+        if (u == 1) ax = fma(g, sc.x[(int64_t)(3 * I) * kTile + c], ax);
+        r = bv - fma(lam, ax, xv);
+      }
+      sc.y[a] = (float)r * sc.is[a];
+    }
+  }
+  __syncwarp();
+  return warp_sum(xsq);
 }
 
 // Plain FP64 solve (K = one column per thread, FP64 factors).
@@ -966,125 +1458,230 @@ __device__ __forceinline__ double ref_scale(const double* ref, double cs, int64_
 //   matrix-free from the point coefficients of L(q0)); y = S^-1 r (FP32);
 //   solve; until the predicted relative error |d_k|^2/|d_{k-1}| / |x| (plain
 //   2-norms) is below tol, or max_sweeps.
+// The loop is warp-uniform: a sweep in which all 32 lanes still refine (the
+// first two always do) streams the tile's records through the ring; a sweep
+// with fewer lanes loads each active lane's records on its own, so lanes that
+// have stopped cost no traffic.
 template <int N>
 __device__ void solve_ir_column(const DevView& v, const TileDesc& t, int lane, double lam,
-                                const double* b, double* x, float* y, int stride, double tol,
-                                int max_sweeps) {
+                                const double* b, double* x, double tol, int max_sweeps,
+                                Ring<N>& rg) {
+  constexpr int stride = kTile;
+  const TileScr sc = tile_scratch(v, t);
+  float* y = sc.y + lane;
+  double* xs_ = sc.x + lane;
+  double* bs_ = sc.b + lane;
+  const double* lin = sc.lin + lane;
+  const float* s32 = sc.s + lane;
+  const float* is32 = sc.is + lane;
   constexpr int K = Band<N>::K;
-  const Col c = make_col(v, t, lane, N);
+  const bool valid = lane < t.count;
+  const int n = 3 * (t.nez * N + 1);
   const float* base = reinterpret_cast<const float*>(v.fac) + t.fac_off;
-  const double* lin = v.lin + c.off;
-  const double* bc = b + c.off;
+  Col c{};
+  bool active = false;
+  if (valid) {
+    c = make_col(v, t, lane, N);
+    if (v.fac_status[c.col] != HEVI_COL_OK) {  // no usable factors for this column
+      for (int i = 0; i < c.n; ++i) x[c.off + i] = __longlong_as_double(0x7ff8000000000000LL);
+      v.col_iters[c.col] = 0;
+      fail(v, c.col, v.fac_status[c.col]);
+    } else {
+      active = true;
+    }
+  }
   double* xc = x + c.off;
   const double g = v.ph.g;
   const double* w = c_tab.w[N];
-  if (v.fac_status[c.col] != HEVI_COL_OK) {  // no usable factors for this column
-    for (int i = 0; i < c.n; ++i) xc[i] = __longlong_as_double(0x7ff8000000000000LL);
-    v.col_iters[c.col] = 0;
-    fail(v, c.col, v.fac_status[c.col]);
-    return;
+  // b enters the tile's interleaved scratch (bs_) through a transpose in the
+  // idle ring, 16 rows x 32 columns a round, so that both the caller's
+  // column-contiguous b and the scratch are accessed in whole lines; x is
+  // refined in xs_ and leaves the same way at the end.
+  const int64_t myoff = valid ? c.off : 0;
+  double* tr = reinterpret_cast<double*>(Ring<N>::buf());  // [32 columns][17]
+  for (int r0 = 0; r0 < n; r0 += 16) {
+#pragma unroll 4
+    for (int cc = 0; cc < kTile; cc += 2) {
+      const int col = cc + (lane >> 4), k = lane & 15;
+      const int64_t o = __shfl_sync(0xffffffffu, myoff, col);
+      if (col < t.count && r0 + k < n) tr[col * 17 + k] = b[o + r0 + k];
+    }
+    __syncwarp();
+    for (int k = 0; k < 16 && r0 + k < n; ++k) {
+      const double bi = tr[lane * 17 + k];
+      bs_[(r0 + k) * stride] = bi;
+      y[(r0 + k) * stride] = (float)bi * is32[(r0 + k) * stride];
+    }
+    __syncwarp();
   }
-  const float* s32 = v.s32 + c.off;
-  const float* is32 = v.is32 + c.off;
-  for (int i = 0; i < c.n; ++i) y[i * stride] = (float)bc[i] * is32[i];
-  for (int i = c.n; i < c.n + 2 * K; ++i) y[i * stride] = 0.0f;
+  for (int i = n; i < n + 2 * K; ++i) y[i * stride] = 0.0f;
+  const bool ran = active;
 
   int sweeps = 0, status = HEVI_COL_NOT_CONVERGED;
   double dprev = 0.0, xnorm = 0.0;
   bool first = true;
+  const bool coop_ok = 2 * K < kTile && n + 2 * K <= RingCfg<N>::YST;
   while (true) {
-    // records of step j+2 are prefetched into L1 while step j computes
-    forward_sweep<N, float, float, 2>(base, lane, c.n, y, stride);
-    backward_sweep<N, float, float, 2>(base, lane, c.n, y, stride);
-    ++sweeps;
+    const unsigned act = __ballot_sync(0xffffffffu, active);
+    if (act == 0) break;
+    // few lanes left: the warp works on their columns together
+    const bool coop = coop_ok && __popc(act) <= kWarpSweepLanes;
+    if (act == 0xffffffffu && rg.ok) {
+      forward_sweep_ring<N>(rg, base, lane, n, y, stride);
+      backward_sweep_ring<N>(rg, base, lane, n, y, stride);
+      if (!rg.ok) {  // a copy did not arrive within the wait limit
+        rg.drain();
+        for (int i = 0; i < n; ++i) xc[i] = __longlong_as_double(0x7ff8000000000000LL);
+        v.col_iters[c.col] = sweeps;
+        fail(v, c.col, HEVI_COL_WAIT_TIMEOUT);
+        return;
+      }
+    } else if (coop) {
+      // a few straggling lanes: the warp solves their columns one at a time
+      // (its 32 lanes hold the 2K + 1 rows of the backward window for N <= 4)
+      if constexpr (2 * K < kTile)
+        for (unsigned m = act; m; m &= m - 1) warp_sweeps<N>(base, __ffs(m) - 1, n, sc.y, lane);
+    } else if (active) {
+      // records of step j+2 are prefetched into L1 while step j computes
+      forward_sweep<N, float, float, 2>(base, lane, n, y, stride);
+      backward_sweep<N, float, float, 2>(base, lane, n, y, stride);
+    }
     // size of the correction d = S y in the caller's (unscaled) norm
     float d2 = 0.0f;
-    for (int i = 0; i < c.n; ++i) {
-      const float d = y[i * stride] * s32[i];
-      d2 = fmaf(d, d, d2);
+    if (coop) {
+      for (unsigned m = act; m; m &= m - 1) {
+        const float t2 = warp_d2(sc, __ffs(m) - 1, n, lane);
+        if (lane == __ffs(m) - 1) d2 = t2;
+      }
+    } else if (active) {
+      for (int i = 0; i < n; ++i) {
+        const float d = y[i * stride] * s32[i * stride];
+        d2 = fmaf(d, d, d2);
+      }
     }
-    const double dn = sqrt((double)d2);
-    const double xref = first ? dn : xnorm;
     bool stop = false;
-    if (dn <= tol * xref) {
-      stop = true;
-      status = HEVI_COL_OK;
-    } else if (!first) {
-      const double pred = dn * (dn / dprev);  // error left after applying d
-      if (pred <= tol * xref) {
+    const double dn = sqrt((double)d2);
+    if (active) {
+      ++sweeps;
+      const double xref = first ? dn : xnorm;
+      if (dn <= tol * xref) {
         stop = true;
         status = HEVI_COL_OK;
-      } else if (dn > 0.5 * dprev) {
-        stop = true;  // refinement is not contracting
-      }
-    }
-    if (sweeps >= max_sweeps) stop = true;
-    if (stop) {
-      for (int i = 0; i < c.n; ++i) {
-        const double d = (double)(y[i * stride] * s32[i]);
-        xc[i] = first ? d : xc[i] + d;
-      }
-      break;
-    }
-    // fused pass: x += S y, r = b - A x, y = S^-1 r, |S^-1 x|
-    double xs = 0.0;
-    const bool fst = first;
-    auto flux = [&](int I, double* f) {
-      double xi[3];
-#pragma unroll
-      for (int u = 0; u < 3; ++u) {
-        const int i = 3 * I + u;
-        const double d = (double)(y[i * stride] * s32[i]);
-        xi[u] = fst ? d : xc[i] + d;
-        xc[i] = xi[u];
-        xs = fma(xi[u], xi[u], xs);
-      }
-      const double wI = lin[3 * I], thI = lin[3 * I + 1], cI = lin[3 * I + 2];
-      f[0] = xi[1];
-      f[1] = fma(-wI * wI, xi[0], fma(2.0 * wI, xi[1], cI * xi[2]));
-      f[2] = fma(-thI * wI, xi[0], fma(thI, xi[1], wI * xi[2]));
-    };
-    auto out = [&](int I, const double* D) {
-      // A x = x + Lambda (Dcal[K x] + G x);  r = b - A x
-#pragma unroll
-      for (int u = 0; u < 3; ++u) {
-        const int i = 3 * I + u;
-        double r;
-        if (u == 1 && (I == 0 || I == c.nz - 1)) {
-          r = bc[i] - xc[i];
-        } else {
-          double ax = D[u];
-          if (u == 1) ax = fma(g, xc[3 * I], ax);
-          r = bc[i] - fma(lam, ax, xc[i]);
+      } else if (!first) {
+        const double pred = dn * (dn / dprev);  // error left after applying d
+        if (pred <= tol * xref) {
+          stop = true;
+          status = HEVI_COL_OK;
+        } else if (dn > 0.5 * dprev) {
+          stop = true;  // refinement is not contracting
         }
-        y[i * stride] = (float)r * is32[i];
       }
-    };
-    element_pass<N>(c, w, c_tab.iw[N], flux, out);
-    xnorm = sqrt(xs);
-    dprev = dn;
-    first = false;
+      if (sweeps >= max_sweeps) stop = true;
+    }
+    const bool stopping = active && stop, more = active && !stop;
+    // stopping lanes: x += S y, and the column is done
+    if (coop) {
+      for (unsigned m = __ballot_sync(0xffffffffu, stopping); m; m &= m - 1)
+        warp_update_x(sc, __ffs(m) - 1, n, __shfl_sync(0xffffffffu, first, __ffs(m) - 1), lane);
+    } else if (stopping) {
+      for (int i = 0; i < n; ++i) {
+        const double d = (double)(y[i * stride] * s32[i * stride]);
+        xs_[i * stride] = first ? d : xs_[i * stride] + d;
+      }
+    }
+    if (stopping) {
+      active = false;
+      v.col_iters[c.col] = sweeps;
+      if (status != HEVI_COL_OK)
+        fail(v, c.col, status);
+      else
+        v.col_status[c.col] = HEVI_COL_OK;
+    }
+    // refining lanes, fused pass: x += S y, r = b - A x, y = S^-1 r, |S^-1 x|
+    const unsigned mm = __ballot_sync(0xffffffffu, more);
+    if (coop_ok && __popc(mm) <= kWarpSweepLanes) {
+      for (unsigned m = mm; m; m &= m - 1) {
+        const int cl = __ffs(m) - 1;
+        const double xsq = warp_residual<N>(sc, cl, t.nez, __shfl_sync(0xffffffffu, c.s, cl), lam, g,
+                                            __shfl_sync(0xffffffffu, first, cl), lane);
+        if (lane == cl) xnorm = sqrt(xsq);
+      }
+    } else if (more) {
+      double xs = 0.0;
+      const bool fst = first;
+      auto flux = [&](int I, double* f) {
+        double xi[3];
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+          const int i = 3 * I + u;
+          const double d = (double)(y[i * stride] * s32[i * stride]);
+          xi[u] = fst ? d : xs_[i * stride] + d;
+          xs_[i * stride] = xi[u];
+          xs = fma(xi[u], xi[u], xs);
+        }
+        const double wI = lin[(3 * I) * stride], thI = lin[(3 * I + 1) * stride],
+                     cI = lin[(3 * I + 2) * stride];
+        f[0] = xi[1];
+        f[1] = fma(-wI * wI, xi[0], fma(2.0 * wI, xi[1], cI * xi[2]));
+        f[2] = fma(-thI * wI, xi[0], fma(thI, xi[1], wI * xi[2]));
+      };
+      auto out = [&](int I, const double* D) {
+        // A x = x + Lambda (Dcal[K x] + G x);  r = b - A x
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+          const int i = 3 * I + u;
+          double r;
+          const double xv = xs_[i * stride], bv = bs_[i * stride];
+          if (u == 1 && (I == 0 || I == c.nz - 1)) {
+            r = bv - xv;
+          } else {
+            double ax = D[u];
+            if (u == 1) ax = fma(g, xs_[(3 * I) * stride], ax);
+            r = bv - fma(lam, ax, xv);
+          }
+          y[i * stride] = (float)r * is32[i * stride];
+        }
+      };
+      element_pass<N>(c, w, c_tab.iw[N], flux, out);
+      xnorm = sqrt(xs);
+    }
+    if (more) {
+      dprev = dn;
+      first = false;
+    }
   }
-  v.col_iters[c.col] = sweeps;
-  if (status != HEVI_COL_OK)
-    fail(v, c.col, status);
-  else
-    v.col_status[c.col] = HEVI_COL_OK;
+  const unsigned ranmask = __ballot_sync(0xffffffffu, ran);
+  for (int r0 = 0; r0 < n; r0 += 16) {
+    for (int k = 0; k < 16 && r0 + k < n; ++k) tr[lane * 17 + k] = xs_[(r0 + k) * stride];
+    __syncwarp();
+#pragma unroll 4
+    for (int cc = 0; cc < kTile; cc += 2) {
+      const int col = cc + (lane >> 4), k = lane & 15;
+      const int64_t o = __shfl_sync(0xffffffffu, myoff, col);
+      if (((ranmask >> col) & 1u) && r0 + k < n) x[o + r0 + k] = tr[col * 17 + k];
+    }
+    __syncwarp();
+  }
 }
 
 // FP32 + refinement solve: one warp per block, one column per thread, the
-// work vector in the tile's interleaved global scratch.  The solve is latency
-// bound per thread (two dependent passes of n pivot steps), so what matters is
-// that every column is resident at once: with 96 registers 20 one-warp blocks
-// fit an SM, i.e. 97k columns in one wave on 152 SMs.
+// work vector in the tile's interleaved global scratch, the factor records
+// streamed through the block's shared-memory ring.  The solve is a dependent
+// chain of 2n pivot steps per sweep, so what matters is that every column is
+// resident at once: with 96 registers and a ring of 2 backward steps, 20
+// one-warp blocks fit an SM, i.e. 97k columns in one wave on 152 SMs.
 template <int N>
 __global__ void __launch_bounds__(32, 20) k_solve_ir(DevView v, double lam, const double* b,
                                                      double* x, double tol, int max_sweeps) {
   const int lane = threadIdx.x;
   const TileDesc t = v.tiles[v.tile_begin + blockIdx.x];
-  if (lane >= t.count) return;
-  float* y = v.ysc + t.y_off + lane;
-  solve_ir_column<N>(v, t, lane, lam, b, x, y, kTile, tol, max_sweeps);
+  if (lane == 0) {
+    for (int s = 0; s < RingCfg<N>::NBAR; ++s) mbar_init(&Ring<N>::bar()[s], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  Ring<N> rg{0u, 0u, true};
+  solve_ir_column<N>(v, t, lane, lam, b, x, tol, max_sweeps, rg);
 }
 
 // Plain FP64 solve; the work vectors live in shared memory.
@@ -1118,7 +1715,16 @@ static void launch_solve_n(const DevView& v, hevi_precision prec, double lam, co
     cudaFuncSetAttribute(k_solve_fp64<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     k_solve_fp64<N><<<grid, blk, smem, st>>>(v, b, x);
   } else {
-    k_solve_ir<N><<<(unsigned)v.tile_count, kTile, 0, st>>>(v, lam, b, x, tol, max_sweeps);
+    constexpr int smem = RingCfg<N>::SMEM + RingCfg<N>::NBAR * 8;
+    static bool configured = false;
+    if (!configured) {
+      cudaFuncSetAttribute(k_solve_ir<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      // carve enough shared memory for 20 resident blocks; the rest stays L1
+      cudaFuncSetAttribute(k_solve_ir<N>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           std::min(100, (20 * (smem + 1024 + 64) * 100 + 232447) / 232448));
+      configured = true;
+    }
+    k_solve_ir<N><<<(unsigned)v.tile_count, kTile, smem, st>>>(v, lam, b, x, tol, max_sweeps);
   }
 }
 
