@@ -93,7 +93,7 @@ void lagrange_derivative(int N, const double* x, double* D) {
 }
 
 hevi::LglTables make_tables() {
-  hevi::LglTables t;
+  hevi::LglTables t{};
   std::memset(&t, 0, sizeof(t));
   for (int N = 1; N <= kMaxOrder; ++N) {
     double D[(kMaxOrder + 1) * (kMaxOrder + 1)];
@@ -132,6 +132,19 @@ hevi::LglTables make_tables() {
     if (N % 2 == 0)
       for (int j = 0; j < P; ++j)
         t.om[N][j] = 0.5 * (t.wD[N][(N / 2) * (N + 1) + j] - t.wD[N][(N / 2) * (N + 1) + N - j]);
+    // double-float pairs: hi = v rounded to FP32, lo = the remainder rounded
+    auto split = [](double v) {
+      const float hi = (float)v;
+      return float2{hi, (float)(v - (double)hi)};
+    };
+    for (int k = 0; k < (N + 1) * (N + 1); ++k) t.wD2[N][k] = split(t.wD[N][k]);
+    for (int k = 0; k <= N; ++k) t.iw2[N][k] = split(t.iw[N][k]);
+    for (int k = 0; k < 3; ++k)
+      for (int j = 0; j < 3; ++j) {
+        t.ep2[N][k][j] = split(t.ep[N][k][j]);
+        t.op2[N][k][j] = split(t.op[N][k][j]);
+      }
+    for (int j = 0; j < 3; ++j) t.om2[N][j] = split(t.om[N][j]);
   }
   return t;
 }

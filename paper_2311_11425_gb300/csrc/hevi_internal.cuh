@@ -71,6 +71,13 @@ struct LglTables {
   double ep[kMaxOrder + 1][3][3];
   double op[kMaxOrder + 1][3][3];
   double om[kMaxOrder + 1][3];
+  // the same FP64 values split into double-float pairs (hi, lo) for the
+  // refinement residual: wD, 1/w and the even-odd halves
+  float2 wD2[kMaxOrder + 1][(kMaxOrder + 1) * (kMaxOrder + 1)];
+  float2 iw2[kMaxOrder + 1][kMaxOrder + 1];
+  float2 ep2[kMaxOrder + 1][3][3];
+  float2 op2[kMaxOrder + 1][3][3];
+  float2 om2[kMaxOrder + 1][3];
 };
 
 // Device view of a context's buffers (passed to kernels by value).
@@ -166,6 +173,70 @@ __device__ __forceinline__ void element_pass(const Col& c, const double* w, cons
 #pragma unroll
   for (int v = 0; v < 3; ++v) D[v] = carry[v] * sc;
   out(c.nz - 1, D);
+}
+
+// ---------------------------------------------------------------------------
+// Double-float arithmetic for the refinement residual.  A value is an
+// unevaluated sum hi + lo of two floats (|lo| < ulp(hi)), about 48
+// significant bits, computed on the FP32 pipes, which on this part issue at
+// many times the FP64 rate.  The building blocks are the error-free
+// transformations of Dekker (1971) and Knuth (TAOCP vol. 2, "TwoSum") and
+// the FMA-based exact product of Ogita, Rump and Oishi (2005); additions use
+// the "sloppy" double-word sum, whose error is bounded relative to |x| + |y|
+// (Joldes, Muller and Popescu, 2017), which is the bound a residual
+// b - A x needs.  Every operation below is written with explicit fmaf so
+// that contraction cannot change it.
+// ---------------------------------------------------------------------------
+struct df {
+  float hi, lo;
+};
+__device__ __forceinline__ df df_fast_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ df df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ df df_add(df x, df y) {
+  const df s = df_two_sum(x.hi, y.hi);
+  return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+}
+__device__ __forceinline__ df df_sub(df x, df y) { return df_add(x, {-y.hi, -y.lo}); }
+__device__ __forceinline__ df df_add_f(df x, float f) {
+  const df s = df_two_sum(x.hi, f);
+  return df_fast_two_sum(s.hi, __fadd_rn(s.lo, x.lo));
+}
+__device__ __forceinline__ df df_mul(df x, df y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  float e = fmaf(x.hi, y.hi, -p);
+  e = fmaf(x.hi, y.lo, e);
+  e = fmaf(x.lo, y.hi, e);
+  return df_fast_two_sum(p, e);
+}
+__device__ __forceinline__ df df_fma(df a, df b, df c) { return df_add(df_mul(a, b), c); }
+__device__ __forceinline__ df df_of(float2 v) { return {v.x, v.y}; }
+__device__ __forceinline__ float2 df_pack(df v) { return make_float2(v.hi, v.lo); }
+__device__ __forceinline__ double df_to_double(df v) { return (double)v.hi + (double)v.lo; }
+
+// Split an FP64 value into a double-float pair with integer operations: hi
+// keeps the top 24 significand bits, lo the next 29 (rounded to 24 by the
+// integer-to-float conversion); values outside 2^-63 .. 2^127 in magnitude
+// (and 0, NaN, Inf) take the FP64 conversions instead.
+__device__ __forceinline__ df df_from_double(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const int E = (int)((b >> 52) & 0x7ffu);
+  if (E < 960 || E > 1150) {
+    const float hi = __double2float_rn(v);
+    return {hi, __double2float_rn(v - (double)hi)};
+  }
+  const unsigned long long M = b & 0xfffffffffffffull;
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const float hi = __uint_as_float(sign | ((unsigned)(E - 1023 + 127) << 23) | (unsigned)(M >> 29));
+  const float lo = __fmul_rn(__uint2float_rn((unsigned)(M & 0x1fffffffu)),
+                             __uint_as_float((unsigned)(E - 1075 + 127) << 23));
+  return {hi, sign ? -lo : lo};
 }
 
 // 1/x in FP64 from an FP32 reciprocal seed and two Newton-Raphson steps

@@ -51,6 +51,88 @@ __device__ __forceinline__ void elem_deriv(const double (&f)[N + 1][3], double (
   }
 }
 
+// One field of elem_deriv_df.
+template <int N>
+__device__ __forceinline__ void elem_deriv_df1(const df (&f)[N + 1], df (&cc)[N + 1]) {
+  constexpr int P = (N + 1) / 2;
+  df e[P], o[P];
+#pragma unroll
+  for (int j = 0; j < P; ++j) {
+    e[j] = df_add(f[j], f[N - j]);
+    o[j] = df_sub(f[j], f[N - j]);
+  }
+#pragma unroll
+  for (int k = 0; k < P; ++k) {
+    df sE = df_mul(df_of(c_tab.ep2[N][k][0]), e[0]);
+    df sO = df_mul(df_of(c_tab.op2[N][k][0]), o[0]);
+#pragma unroll
+    for (int j = 1; j < P; ++j) {
+      sE = df_fma(df_of(c_tab.ep2[N][k][j]), e[j], sE);
+      sO = df_fma(df_of(c_tab.op2[N][k][j]), o[j], sO);
+    }
+    if (N % 2 == 0) sE = df_fma(df_of(c_tab.wD2[N][k * (N + 1) + N / 2]), f[N / 2], sE);
+    cc[k] = df_add(sE, sO);
+    cc[N - k] = df_sub(sO, sE);
+  }
+  if (N % 2 == 0) {
+    df sm = df_mul(df_of(c_tab.om2[N][0]), o[0]);
+#pragma unroll
+    for (int j = 1; j < P; ++j) sm = df_fma(df_of(c_tab.om2[N][j]), o[j], sm);
+    cc[N / 2] = sm;
+  }
+}
+
+// element_pass in double-float arithmetic for one thread's column, with the
+// element's point fluxes and derivatives parked in the thread's own slots of
+// shared memory (sm: (2N + 1) x 3 pairs per lane, lane fastest) so that one
+// field at a time is live in registers.  flux(I, f[3]) gives the point
+// fluxes, out(I, D[3]) receives the DSS'd derivative; cs = 2 / dz.
+template <int N, class FluxF, class OutF>
+__device__ __forceinline__ void element_pass_df(int nez, df cs, float2* sm, int lane, FluxF&& flux,
+                                                OutF&& out) {
+  auto FS = [&](int k, int v) -> float2& { return sm[(k * 3 + v) * kTile + lane]; };
+  auto DS = [&](int k, int v) -> float2& { return sm[((N + 1 + k) * 3 + v) * kTile + lane]; };
+  df carry[3] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
+  {
+    df f[3];
+    flux(0, f);
+#pragma unroll
+    for (int v = 0; v < 3; ++v) FS(0, v) = df_pack(f[v]);
+  }
+  const df iw0 = df_of(c_tab.iw2[N][0]);
+  for (int e = 0; e < nez; ++e) {
+    const int I0 = e * N;
+#pragma unroll
+    for (int k = 1; k <= N; ++k) {
+      df f[3];
+      flux(I0 + k, f);
+#pragma unroll
+      for (int v = 0; v < 3; ++v) FS(k, v) = df_pack(f[v]);
+    }
+    const df sc0 = df_mul(cs, e == 0 ? iw0 : df{0.5f * iw0.hi, 0.5f * iw0.lo});
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+      df fv[N + 1], cc[N + 1];
+#pragma unroll
+      for (int k = 0; k <= N; ++k) fv[k] = df_of(FS(k, v));
+      elem_deriv_df1<N>(fv, cc);
+      DS(0, v) = df_pack(df_mul(df_add(carry[v], cc[0]), sc0));
+#pragma unroll
+      for (int k = 1; k < N; ++k) DS(k, v) = df_pack(df_mul(cc[k], df_mul(cs, df_of(c_tab.iw2[N][k]))));
+      carry[v] = cc[N];
+      FS(0, v) = FS(N, v);
+    }
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      const df D[3] = {df_of(DS(k, 0)), df_of(DS(k, 1)), df_of(DS(k, 2))};
+      out(I0 + k, D);
+    }
+  }
+  const df sc = df_mul(cs, iw0);
+  const df D[3] = {df_mul(carry[0], sc), df_mul(carry[1], sc), df_mul(carry[2], sc)};
+  out(nez * N, D);
+}
+
 // ---------------------------------------------------------------------------
 // Record addressing
 // ---------------------------------------------------------------------------
@@ -1344,82 +1426,89 @@ __device__ __noinline__ float warp_d2(const TileScr& sc, int c, int n, int lane)
   return warp_sum(d2);
 }
 
-// x += S y (x = S y on the first sweep) of column c.
+// x += S y (x = S y on the first sweep) of column c (x as double-float pairs).
 __device__ __noinline__ void warp_update_x(const TileScr& sc, int c, int n, bool fst, int lane) {
+  float2* xd = reinterpret_cast<float2*>(sc.x);
   for (int i = lane; i < n; i += 32) {
     const int64_t a = (int64_t)i * kTile + c;
-    const double d = (double)(sc.y[a] * sc.s[a]);
-    sc.x[a] = fst ? d : sc.x[a] + d;
+    const float d = sc.y[a] * sc.s[a];
+    xd[a] = df_pack(fst ? df{d, 0.0f} : df_add_f(df_of(xd[a]), d));
   }
   __syncwarp();
 }
 
-// Fused pass of column c: x += S y, r = b - A x, y = S^-1 r; returns |x|^2.
-// The point fluxes K x go through shared memory so that each lane can form
-// the element derivative (and the direct-stiffness sum at element ends) of
-// its own points.
+// Fused pass of column c: x += S y, r = b - A x, y = S^-1 r (double-float
+// arithmetic, as the per-thread pass); returns |x|^2 (FP32).  The point
+// fluxes K x go through shared memory so that each lane can form the element
+// derivative (and the direct-stiffness sum at element ends) of its own points.
 template <int N>
-__device__ __noinline__ double warp_residual(const TileScr& sc, int c, int nez, double cs,
-                                             double lam, double g, bool fst, int lane) {
+__device__ __noinline__ float warp_residual(const TileScr& sc, int c, int nez, double cs,
+                                            double lam, double g, bool fst, int lane) {
   const int nz = nez * N + 1;
-  double* F = reinterpret_cast<double*>(Ring<N>::buf());  // [nz][3], then the tables
-  double* Dm = F + 3 * nz;                                 // wD (lane-dependent rows)
-  double* iw = Dm + (N + 1) * (N + 1);
-  double xsq = 0.0;
+  float2* F = reinterpret_cast<float2*>(Ring<N>::buf());  // [nz][3], then the tables
+  float2* Dm = F + 3 * nz;                                 // wD (lane-dependent rows)
+  float2* iw = Dm + (N + 1) * (N + 1);
+  float2* xd = reinterpret_cast<float2*>(sc.x);
+  const float2* bd = reinterpret_cast<const float2*>(sc.b);
+  const df lamd = df_from_double(lam), gd = df_from_double(g), csd = df_from_double(cs);
+  float xsq = 0.0f;
   __syncwarp();
-  for (int k = lane; k < (N + 1) * (N + 1); k += 32) Dm[k] = c_tab.wD[N][k];
-  if (lane <= N) iw[lane] = c_tab.iw[N][lane];
+  for (int k = lane; k < (N + 1) * (N + 1); k += 32) Dm[k] = c_tab.wD2[N][k];
+  if (lane <= N) iw[lane] = c_tab.iw2[N][lane];
   for (int I = lane; I < nz; I += 32) {
-    double xi[3];
+    df xi[3];
 #pragma unroll
     for (int u = 0; u < 3; ++u) {
       const int64_t a = (int64_t)(3 * I + u) * kTile + c;
-      const double d = (double)(sc.y[a] * sc.s[a]);
-      xi[u] = fst ? d : sc.x[a] + d;
-      sc.x[a] = xi[u];
-      xsq = fma(xi[u], xi[u], xsq);
+      const float d = sc.y[a] * sc.s[a];
+      xi[u] = fst ? df{d, 0.0f} : df_add_f(df_of(xd[a]), d);
+      xd[a] = df_pack(xi[u]);
+      xsq = fmaf(xi[u].hi, xi[u].hi, xsq);
     }
     const int64_t a0 = (int64_t)(3 * I) * kTile + c;
-    const double wI = sc.lin[a0], thI = sc.lin[a0 + kTile], cI = sc.lin[a0 + 2 * kTile];
-    F[3 * I] = xi[1];
-    F[3 * I + 1] = fma(-wI * wI, xi[0], fma(2.0 * wI, xi[1], cI * xi[2]));
-    F[3 * I + 2] = fma(-thI * wI, xi[0], fma(thI, xi[1], wI * xi[2]));
+    const df wI = df_from_double(sc.lin[a0]), thI = df_from_double(sc.lin[a0 + kTile]),
+             cI = df_from_double(sc.lin[a0 + 2 * kTile]);
+    F[3 * I] = df_pack(xi[1]);
+    F[3 * I + 1] = df_pack(df_sub(df_fma({2.0f * wI.hi, 2.0f * wI.lo}, xi[1], df_mul(cI, xi[2])),
+                                  df_mul(df_mul(wI, wI), xi[0])));
+    F[3 * I + 2] = df_pack(df_sub(df_fma(thI, xi[1], df_mul(wI, xi[2])), df_mul(df_mul(thI, wI), xi[0])));
   }
   __syncwarp();
   auto cc = [&](int e, int k, int v) {  // element e's derivative row k of field v
-    double sum = 0.0;
+    df sum = df_mul(df_of(Dm[k * (N + 1)]), df_of(F[3 * (e * N) + v]));
 #pragma unroll
-    for (int j = 0; j <= N; ++j) sum = fma(Dm[k * (N + 1) + j], F[3 * (e * N + j) + v], sum);
+    for (int j = 1; j <= N; ++j) sum = df_fma(df_of(Dm[k * (N + 1) + j]), df_of(F[3 * (e * N + j) + v]), sum);
     return sum;
   };
   for (int I = lane; I < nz; I += 32) {
     const int e = I == nz - 1 ? nez - 1 : I / N, k = I - e * N;
-    double D[3];
+    const df iw0 = df_of(iw[0]);
+    df D[3];
 #pragma unroll
     for (int v = 0; v < 3; ++v) {
       if (k != 0 && k != N) {
-        D[v] = cc(e, k, v) * (cs * iw[k]);
+        D[v] = df_mul(cc(e, k, v), df_mul(csd, df_of(iw[k])));
       } else if (I == 0) {
-        D[v] = cc(0, 0, v) * (cs * iw[0]);
+        D[v] = df_mul(cc(0, 0, v), df_mul(csd, iw0));
       } else if (I == nz - 1) {
-        D[v] = cc(nez - 1, N, v) * (cs * iw[0]);
+        D[v] = df_mul(cc(nez - 1, N, v), df_mul(csd, iw0));
       } else {
-        D[v] = (cc(e - 1, N, v) + cc(e, 0, v)) * (cs * (0.5 * iw[0]));
+        D[v] = df_mul(df_add(cc(e - 1, N, v), cc(e, 0, v)), df_mul(csd, {0.5f * iw0.hi, 0.5f * iw0.lo}));
       }
     }
 #pragma unroll
     for (int u = 0; u < 3; ++u) {
       const int64_t a = (int64_t)(3 * I + u) * kTile + c;
-      const double xv = sc.x[a], bv = sc.b[a];
-      double r;
+      const df xv = df_of(xd[a]), bv = df_of(bd[a]);
+      df r;
       if (u == 1 && (I == 0 || I == nz - 1)) {
-        r = bv - xv;
+        r = df_sub(bv, xv);
       } else {
-        double ax = D[u];
-        if (u == 1) ax = fma(g, sc.x[(int64_t)(3 * I) * kTile + c], ax);
-        r = bv - fma(lam, ax, xv);
+        df ax = D[u];
+        if (u == 1) ax = df_fma(gd, df_of(xd[(int64_t)(3 * I) * kTile + c]), ax);
+        r = df_sub(bv, df_fma(lamd, ax, xv));
       }
-      sc.y[a] = (float)r * sc.is[a];
+      sc.y[a] = __fadd_rn(r.hi, r.lo) * sc.is[a];
     }
   }
   __syncwarp();
@@ -1469,8 +1558,8 @@ __device__ void solve_ir_column(const DevView& v, const TileDesc& t, int lane, d
   constexpr int stride = kTile;
   const TileScr sc = tile_scratch(v, t);
   float* y = sc.y + lane;
-  double* xs_ = sc.x + lane;
-  double* bs_ = sc.b + lane;
+  float2* xs_ = reinterpret_cast<float2*>(sc.x) + lane;  // double-float pairs
+  float2* bs_ = reinterpret_cast<float2*>(sc.b) + lane;
   const double* lin = sc.lin + lane;
   const float* s32 = sc.s + lane;
   const float* is32 = sc.is + lane;
@@ -1492,7 +1581,6 @@ __device__ void solve_ir_column(const DevView& v, const TileDesc& t, int lane, d
   }
   double* xc = x + c.off;
   const double g = v.ph.g;
-  const double* w = c_tab.w[N];
   // b enters the tile's interleaved scratch (bs_) through a transpose in the
   // idle ring, 16 rows x 32 columns a round, so that both the caller's
   // column-contiguous b and the scratch are accessed in whole lines; x is
@@ -1508,9 +1596,9 @@ __device__ void solve_ir_column(const DevView& v, const TileDesc& t, int lane, d
     }
     __syncwarp();
     for (int k = 0; k < 16 && r0 + k < n; ++k) {
-      const double bi = tr[lane * 17 + k];
-      bs_[(r0 + k) * stride] = bi;
-      y[(r0 + k) * stride] = (float)bi * is32[(r0 + k) * stride];
+      const df bi = df_from_double(tr[lane * 17 + k]);
+      bs_[(r0 + k) * stride] = df_pack(bi);
+      y[(r0 + k) * stride] = __fadd_rn(bi.hi, bi.lo) * is32[(r0 + k) * stride];
     }
     __syncwarp();
   }
@@ -1585,8 +1673,8 @@ __device__ void solve_ir_column(const DevView& v, const TileDesc& t, int lane, d
         warp_update_x(sc, __ffs(m) - 1, n, __shfl_sync(0xffffffffu, first, __ffs(m) - 1), lane);
     } else if (stopping) {
       for (int i = 0; i < n; ++i) {
-        const double d = (double)(y[i * stride] * s32[i * stride]);
-        xs_[i * stride] = first ? d : xs_[i * stride] + d;
+        const float d = y[i * stride] * s32[i * stride];
+        xs_[i * stride] = df_pack(first ? df{d, 0.0f} : df_add_f(df_of(xs_[i * stride]), d));
       }
     }
     if (stopping) {
@@ -1602,48 +1690,101 @@ __device__ void solve_ir_column(const DevView& v, const TileDesc& t, int lane, d
     if (coop_ok && __popc(mm) <= kWarpSweepLanes) {
       for (unsigned m = mm; m; m &= m - 1) {
         const int cl = __ffs(m) - 1;
-        const double xsq = warp_residual<N>(sc, cl, t.nez, __shfl_sync(0xffffffffu, c.s, cl), lam, g,
-                                            __shfl_sync(0xffffffffu, first, cl), lane);
-        if (lane == cl) xnorm = sqrt(xsq);
+        const float xsq = warp_residual<N>(sc, cl, t.nez, __shfl_sync(0xffffffffu, c.s, cl), lam, g,
+                                           __shfl_sync(0xffffffffu, first, cl), lane);
+        if (lane == cl) xnorm = sqrt((double)xsq);
       }
     } else if (more) {
-      double xs = 0.0;
+      // double-float arithmetic (FP32 pipes); |x| in FP32 is only a scale
+      float xs = 0.0f;
       const bool fst = first;
-      auto flux = [&](int I, double* f) {
-        double xi[3];
+      const df lamd = df_from_double(lam), gd = df_from_double(g), csd = df_from_double(c.s);
+      // Each call loads the next point's values of y and x (flux) or x and b
+      // (out) before it stores its own, so that the loads are not held back
+      // behind the stores; lin and the scales are read-only here (__ldg).
+      const int nzc = 3 * (t.nez * N + 1);
+      float py[3];
+      float2 px[3];
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        py[u] = y[u * stride];
+        px[u] = xs_[u * stride];
+      }
+      auto flux = [&](int I, df* f) {
+        float yc3[3];
+        float2 xc3[3];
 #pragma unroll
         for (int u = 0; u < 3; ++u) {
-          const int i = 3 * I + u;
-          const double d = (double)(y[i * stride] * s32[i * stride]);
-          xi[u] = fst ? d : xs_[i * stride] + d;
-          xs_[i * stride] = xi[u];
-          xs = fma(xi[u], xi[u], xs);
+          yc3[u] = py[u];
+          xc3[u] = px[u];
         }
-        const double wI = lin[(3 * I) * stride], thI = lin[(3 * I + 1) * stride],
-                     cI = lin[(3 * I + 2) * stride];
-        f[0] = xi[1];
-        f[1] = fma(-wI * wI, xi[0], fma(2.0 * wI, xi[1], cI * xi[2]));
-        f[2] = fma(-thI * wI, xi[0], fma(thI, xi[1], wI * xi[2]));
-      };
-      auto out = [&](int I, const double* D) {
-        // A x = x + Lambda (Dcal[K x] + G x);  r = b - A x
+        if (3 * I + 3 < nzc) {
 #pragma unroll
-        for (int u = 0; u < 3; ++u) {
-          const int i = 3 * I + u;
-          double r;
-          const double xv = xs_[i * stride], bv = bs_[i * stride];
-          if (u == 1 && (I == 0 || I == c.nz - 1)) {
-            r = bv - xv;
-          } else {
-            double ax = D[u];
-            if (u == 1) ax = fma(g, xs_[(3 * I) * stride], ax);
-            r = bv - fma(lam, ax, xv);
+          for (int u = 0; u < 3; ++u) {
+            py[u] = y[(3 * I + 3 + u) * stride];
+            px[u] = xs_[(3 * I + 3 + u) * stride];
           }
-          y[i * stride] = (float)r * is32[i * stride];
+        }
+        df xi[3];
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+          const int i = 3 * I + u;
+          const float d = yc3[u] * __ldg(&s32[i * stride]);
+          xi[u] = fst ? df{d, 0.0f} : df_add_f(df_of(xc3[u]), d);
+          xs_[i * stride] = df_pack(xi[u]);
+          xs = fmaf(xi[u].hi, xi[u].hi, xs);
+        }
+        const df wI = df_from_double(__ldg(&lin[(3 * I) * stride]));
+        const df thI = df_from_double(__ldg(&lin[(3 * I + 1) * stride]));
+        const df cI = df_from_double(__ldg(&lin[(3 * I + 2) * stride]));
+        f[0] = xi[1];
+        // f1 = -w^2 rho + 2 w m + c Theta,  f2 = -theta w rho + theta m + w Theta
+        f[1] = df_sub(df_fma({2.0f * wI.hi, 2.0f * wI.lo}, xi[1], df_mul(cI, xi[2])),
+                      df_mul(df_mul(wI, wI), xi[0]));
+        f[2] = df_sub(df_fma(thI, xi[1], df_mul(wI, xi[2])), df_mul(df_mul(thI, wI), xi[0]));
+      };
+      float2 qx[3], qb[3];
+      bool qfirst = true;
+      auto out = [&](int I, const df* D) {
+        // A x = x + Lambda (Dcal[K x] + G x);  r = b - A x
+        if (qfirst) {  // x of point 0 is final once flux(0) has run
+#pragma unroll
+          for (int u = 0; u < 3; ++u) {
+            qx[u] = xs_[u * stride];
+            qb[u] = bs_[u * stride];
+          }
+          qfirst = false;
+        }
+        float2 xc3[3], bc3[3];
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+          xc3[u] = qx[u];
+          bc3[u] = qb[u];
+        }
+        if (3 * I + 3 < nzc) {  // flux has already run for point I + 1
+#pragma unroll
+          for (int u = 0; u < 3; ++u) {
+            qx[u] = xs_[(3 * I + 3 + u) * stride];
+            qb[u] = bs_[(3 * I + 3 + u) * stride];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+          const int i = 3 * I + u;
+          const df xv = df_of(xc3[u]), bv = df_of(bc3[u]);
+          df r;
+          if (u == 1 && (I == 0 || I == c.nz - 1)) {
+            r = df_sub(bv, xv);
+          } else {
+            df ax = D[u];
+            if (u == 1) ax = df_fma(gd, df_of(xc3[0]), ax);
+            r = df_sub(bv, df_fma(lamd, ax, xv));
+          }
+          y[i * stride] = __fadd_rn(r.hi, r.lo) * __ldg(&is32[i * stride]);
         }
       };
-      element_pass<N>(c, w, c_tab.iw[N], flux, out);
-      xnorm = sqrt(xs);
+      element_pass_df<N>(t.nez, csd, reinterpret_cast<float2*>(Ring<N>::buf()), lane, flux, out);
+      xnorm = sqrt((double)xs);
     }
     if (more) {
       dprev = dn;
@@ -1652,7 +1793,7 @@ __device__ void solve_ir_column(const DevView& v, const TileDesc& t, int lane, d
   }
   const unsigned ranmask = __ballot_sync(0xffffffffu, ran);
   for (int r0 = 0; r0 < n; r0 += 16) {
-    for (int k = 0; k < 16 && r0 + k < n; ++k) tr[lane * 17 + k] = xs_[(r0 + k) * stride];
+    for (int k = 0; k < 16 && r0 + k < n; ++k) tr[lane * 17 + k] = df_to_double(df_of(xs_[(r0 + k) * stride]));
     __syncwarp();
 #pragma unroll 4
     for (int cc = 0; cc < kTile; cc += 2) {
