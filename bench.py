@@ -57,6 +57,24 @@ def factor_flops(n=NUNK, k=K_BAND):
     return f
 
 
+# DRAM bytes (read + write) per launch of the dominant kernels from one ncu
+# capture of `python bench.py --ncu-case solve|factor` (the summaries under
+# profiles/ give the commands), valid only for the kernel source they were
+# taken from: the SHA-256 of the kernel file at capture time.
+NCU_TRAFFIC = {}
+KERNEL_SOURCE = os.path.join(ROOT, "paper_2311_11425_gb300", "csrc", "hevi_kernels.cu")
+
+
+def ncu_traffic(kernel):
+    import hashlib
+    rec = NCU_TRAFFIC.get(kernel)
+    if not rec:
+        return None
+    with open(KERNEL_SOURCE, "rb") as fh:
+        digest = hashlib.sha256(fh.read()).hexdigest()
+    return rec["bytes"] if digest == rec["sha256"] else None
+
+
 def peaks():
     p = {"hbm_gbs": 6777.0, "source": "fallback"}
     try:
@@ -304,13 +322,13 @@ def gpu_arm(args, rank, world, local_rank, pool, cores):
         ach = BYTES_SOLVE_FP32IR * NCOLS / (avg_ms * 1e-3) / 1e9
         roof = {"kernel": "k_solve_ir (stage_solve)", "bound": "hbm", "achieved": ach,
                 "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": ach / pk["hbm_gbs"],
-                "traffic": None, "peak_source": pk["source"],
+                "traffic": ncu_traffic("k_solve_ir"), "peak_source": pk["source"],
                 "algorithmic_bytes_per_launch": BYTES_SOLVE_FP32IR * NCOLS}
     elif dom == "factor":
         ach = factor_flops() * NCOLS / (avg_ms * 1e-3) / 1e12
         roof = {"kernel": "k_factor_r (factor)", "bound": "alu", "achieved": ach,
                 "peak": pk["fp32_tflops"], "unit": "TFLOP/s", "frac": ach / pk["fp32_tflops"],
-                "traffic": None, "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz",
+                "traffic": ncu_traffic("k_factor_r"), "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz",
                 "algorithmic_flops_per_launch": factor_flops() * NCOLS}
     else:
         roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": None, "unit": None,

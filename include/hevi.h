@@ -132,9 +132,11 @@ hevi_status hevi_factor(hevi_ctx* ctx, double gamma_dt, const double* lin_state)
 /* Solve (I - Lambda L(q0)) x = rhs for every column with the factors of the
  * last hevi_factor (Sec. 4.3, Eq. lhevi-ark-final-2).  rhs, x (dev, state
  * layout, may not alias).  In HEVI_FP32_IR mode the FP32 solution is refined
- * with FP64 residuals b - A x until the predicted relative error (2-norm,
+ * with residuals b - A x carried to about 48 significant bits (double-float
+ * arithmetic) until the predicted relative error (2-norm,
  * |d_k|^2 / |d_(k-1)| / |x|) is below 1e-11, at most 10 sweeps
- * (hevi_set_refinement).
+ * (hevi_set_refinement).  A device-side wait that exceeds its limit marks
+ * the column WAIT_TIMEOUT (its x is NaN) and returns HEVI_ERR_WAIT_TIMEOUT.
  * Blocking: returns SINGULAR / NOT_CONVERGED if any column failed. */
 hevi_status hevi_stage_solve(hevi_ctx* ctx, const double* rhs, double* x);
 /* As hevi_stage_solve but does not wait: failures are only recorded for

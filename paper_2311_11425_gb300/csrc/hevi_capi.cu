@@ -518,6 +518,9 @@ hevi_status hevi_setup(hevi_ctx** out, const hevi_column_grid* grid, const hevi_
       (s = c->alloc(&c->v.s32, c->state_size)) || (s = c->alloc(&c->v.is32, c->state_size)) ||
       (s = c->alloc(&c->v.ithb, c->state_size / 3)) ||
       (s = precision == HEVI_FP32_IR ? c->alloc(&c->v.ysc, c->ysc_floats) : HEVI_OK) ||
+      (s = precision == HEVI_FP32_IR ? c->alloc(&c->v.tail_list, c->ntiles * kTile) : HEVI_OK) ||
+      (s = precision == HEVI_FP32_IR ? c->alloc(&c->v.tail_count, hevi::kMaxOrder + 1) : HEVI_OK) ||
+      (s = precision == HEVI_FP32_IR ? c->alloc(&c->v.tail_dprev, ncols) : HEVI_OK) ||
       (s = c->alloc(&d_fs, ncols)) || (s = c->alloc(&d_cs, ncols)) || (s = c->alloc(&d_it, ncols)) ||
       (s = c->alloc(&d_fail, kFailSlots)) ||
       (s = precision == HEVI_FP64 ? c->alloc((double**)&d_fac, c->fac_elems)
@@ -628,7 +631,10 @@ int64_t hevi_estimate_bytes(const hevi_column_grid* grid, hevi_precision precisi
   const int64_t esz = precision == HEVI_FP64 ? 8 : 4;
   int64_t b = (ncols + 1) * 8 + 3 * ncols * 4 + ncols * 8 + 2 * state * 8 +
               ntiles * (int64_t)sizeof(TileDesc) + 2 * state * 4 + (state / 3) * 8 +
-              (precision == HEVI_FP32_IR ? ysc * 4 : 0) + 3 * ncols * 4 + kFailSlots * 4 +
+              (precision == HEVI_FP32_IR ? ysc * 4 + ntiles * kTile * 4 + (hevi::kMaxOrder + 1) * 4 +
+                                               ncols * 8
+                                         : 0) +
+              3 * ncols * 4 + kFailSlots * 4 +
               fac * esz;
   if (kind == 1) b += (2 * (int64_t)stages + 1) * state * 8;
   if (kind == 2) b += ((int64_t)stages + 2) * state * 8 + state * 8 + scr * 4;

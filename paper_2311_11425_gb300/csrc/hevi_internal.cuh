@@ -99,6 +99,9 @@ struct DevView {
   void* fac;                // factor records (float or double)
   float* scr;               // Newton scratch (U records)
   float* ysc;               // per tile: the FP32 work vectors of the refinement solve
+  int32_t* tail_list;       // [ntiles * 32] columns left to the tail kernel (tile << 5 | lane)
+  int32_t* tail_count;      // [kMaxOrder + 1] entries per order
+  double* tail_dprev;       // [ncols] |d| of the last sweep of a handed-over column
   int32_t* fac_status;      // [ncols] status of the last factorisation
   int32_t* col_status;      // [ncols] status of the last call
   int32_t* col_iters;       // [ncols]

@@ -1075,9 +1075,14 @@ __device__ __forceinline__ Y backward_sweep(const T* base, int lane, int n, Y* y
 // Every wait is bounded: past the limit the ring records the failure, stops
 // issuing, and the caller drains what is still in flight before returning.
 // ---------------------------------------------------------------------------
-constexpr int kRingWaitTries = 1 << 16;
-constexpr int kWarpSweepLanes = 6;  // at most this many refining lanes: warp_sweeps       // x suspend hint below: ~1.3 s bound
+constexpr int kRingWaitTries = 1 << 16;  // x the suspend hint below: ~1.3 s bound
 constexpr unsigned kRingSuspendNs = 20000;
+// A sweep in which at least kRingLanes lanes still refine streams the whole
+// tile's records through the ring (the stopped lanes compute on their own
+// scratch, which is no longer read); with at most kWarpSweepLanes the warp
+// solves those columns one at a time (warp_sweeps and the warp_* passes).
+constexpr int kRingLanes = 3;
+constexpr int kWarpSweepLanes = 2;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -1542,6 +1547,108 @@ __device__ __forceinline__ double ref_scale(const double* ref, double cs, int64_
   return u == 0 ? ref[a] : (u == 1 ? ref[a] * cs : ref[a + 2]);
 }
 
+// Fused refinement pass of one thread's column (rows kTile apart): x += S y
+// (skipped when !update), r = b - A x, y = S^-1 r, in double-float
+// arithmetic; slots are the thread's shared-memory slots for element_pass_df.
+// Returns |x|^2 (FP32: it only scales the stop test).
+template <int N>
+__device__ __forceinline__ float lane_residual(float* y, const float* s32, float2* xs_,
+                                               const float2* bs_, const double* lin,
+                                               const float* is32, int nez, double lam, double g,
+                                               double cs, bool fst, bool update, float2* slots,
+                                               int slot_lane) {
+  constexpr int stride = kTile;
+  const int nz = nez * N + 1;
+  float xs = 0.0f;
+  const df lamd = df_from_double(lam), gd = df_from_double(g), csd = df_from_double(cs);
+  // Each call loads the next point's values of y and x (flux) or x and b
+  // (out) before it stores its own, so that the loads are not held back
+  // behind the stores; lin and the scales are read-only here (__ldg).
+  const int nzc = 3 * nz;
+  float py[3];
+  float2 px[3];
+#pragma unroll
+  for (int u = 0; u < 3; ++u) {
+    py[u] = y[u * stride];
+    px[u] = xs_[u * stride];
+  }
+  auto flux = [&](int I, df* f) {
+    float yc3[3];
+    float2 xc3[3];
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      yc3[u] = py[u];
+      xc3[u] = px[u];
+    }
+    if (3 * I + 3 < nzc) {
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        py[u] = y[(3 * I + 3 + u) * stride];
+        px[u] = xs_[(3 * I + 3 + u) * stride];
+      }
+    }
+    df xi[3];
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      const int i = 3 * I + u;
+      const float d = update ? yc3[u] * __ldg(&s32[i * stride]) : 0.0f;
+      xi[u] = !update ? df_of(xc3[u]) : fst ? df{d, 0.0f} : df_add_f(df_of(xc3[u]), d);
+      xs_[i * stride] = df_pack(xi[u]);
+      xs = fmaf(xi[u].hi, xi[u].hi, xs);
+    }
+    const df wI = df_from_double(__ldg(&lin[(3 * I) * stride]));
+    const df thI = df_from_double(__ldg(&lin[(3 * I + 1) * stride]));
+    const df cI = df_from_double(__ldg(&lin[(3 * I + 2) * stride]));
+    f[0] = xi[1];
+    // f1 = -w^2 rho + 2 w m + c Theta,  f2 = -theta w rho + theta m + w Theta
+    f[1] = df_sub(df_fma({2.0f * wI.hi, 2.0f * wI.lo}, xi[1], df_mul(cI, xi[2])),
+                  df_mul(df_mul(wI, wI), xi[0]));
+    f[2] = df_sub(df_fma(thI, xi[1], df_mul(wI, xi[2])), df_mul(df_mul(thI, wI), xi[0]));
+  };
+  float2 qx[3], qb[3];
+  bool qfirst = true;
+  auto out = [&](int I, const df* D) {
+    // A x = x + Lambda (Dcal[K x] + G x);  r = b - A x
+    if (qfirst) {  // x of point 0 is final once flux(0) has run
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        qx[u] = xs_[u * stride];
+        qb[u] = bs_[u * stride];
+      }
+      qfirst = false;
+    }
+    float2 xc3[3], bc3[3];
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      xc3[u] = qx[u];
+      bc3[u] = qb[u];
+    }
+    if (3 * I + 3 < nzc) {  // flux has already run for point I + 1
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        qx[u] = xs_[(3 * I + 3 + u) * stride];
+        qb[u] = bs_[(3 * I + 3 + u) * stride];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      const int i = 3 * I + u;
+      const df xv = df_of(xc3[u]), bv = df_of(bc3[u]);
+      df r;
+      if (u == 1 && (I == 0 || I == nz - 1)) {
+        r = df_sub(bv, xv);
+      } else {
+        df ax = D[u];
+        if (u == 1) ax = df_fma(gd, df_of(xc3[0]), ax);
+        r = df_sub(bv, df_fma(lamd, ax, xv));
+      }
+      y[i * stride] = __fadd_rn(r.hi, r.lo) * __ldg(&is32[i * stride]);
+    }
+  };
+  element_pass_df<N>(nez, csd, slots, slot_lane, flux, out);
+  return xs;
+}
+
 // FP32 factors + FP64 iterative refinement.
 //   y0 = S^-1 b (FP32), solve; then repeat: x += S y; r = b - A x (FP64,
 //   matrix-free from the point coefficients of L(q0)); y = S^-1 r (FP32);
@@ -1554,7 +1661,7 @@ __device__ __forceinline__ double ref_scale(const double* ref, double cs, int64_
 template <int N>
 __device__ void solve_ir_column(const DevView& v, const TileDesc& t, int lane, double lam,
                                 const double* b, double* x, double tol, int max_sweeps,
-                                Ring<N>& rg) {
+                                bool tail, Ring<N>& rg) {
   constexpr int stride = kTile;
   const TileScr sc = tile_scratch(v, t);
   float* y = sc.y + lane;
@@ -1603,7 +1710,7 @@ __device__ void solve_ir_column(const DevView& v, const TileDesc& t, int lane, d
     __syncwarp();
   }
   for (int i = n; i < n + 2 * K; ++i) y[i * stride] = 0.0f;
-  const bool ran = active;
+  bool ran = active;  // the lanes whose x leaves through the final transpose
 
   int sweeps = 0, status = HEVI_COL_NOT_CONVERGED;
   double dprev = 0.0, xnorm = 0.0;
@@ -1614,15 +1721,19 @@ __device__ void solve_ir_column(const DevView& v, const TileDesc& t, int lane, d
     if (act == 0) break;
     // few lanes left: the warp works on their columns together
     const bool coop = coop_ok && __popc(act) <= kWarpSweepLanes;
-    if (act == 0xffffffffu && rg.ok) {
+    if (__popc(act) >= kRingLanes && rg.ok) {
       forward_sweep_ring<N>(rg, base, lane, n, y, stride);
       backward_sweep_ring<N>(rg, base, lane, n, y, stride);
       if (!rg.ok) {  // a copy did not arrive within the wait limit
         rg.drain();
-        for (int i = 0; i < n; ++i) xc[i] = __longlong_as_double(0x7ff8000000000000LL);
-        v.col_iters[c.col] = sweeps;
-        fail(v, c.col, HEVI_COL_WAIT_TIMEOUT);
-        return;
+        if (active) {
+          for (int i = 0; i < n; ++i) xc[i] = __longlong_as_double(0x7ff8000000000000LL);
+          v.col_iters[c.col] = sweeps;
+          fail(v, c.col, HEVI_COL_WAIT_TIMEOUT);
+          ran = false;
+          active = false;
+        }
+        break;
       }
     } else if (coop) {
       // a few straggling lanes: the warp solves their columns one at a time
@@ -1666,7 +1777,8 @@ __device__ void solve_ir_column(const DevView& v, const TileDesc& t, int lane, d
       }
       if (sweeps >= max_sweeps) stop = true;
     }
-    const bool stopping = active && stop, more = active && !stop;
+    const bool stopping = active && stop;
+    bool more = active && !stop;
     // stopping lanes: x += S y, and the column is done
     if (coop) {
       for (unsigned m = __ballot_sync(0xffffffffu, stopping); m; m &= m - 1)
@@ -1685,6 +1797,18 @@ __device__ void solve_ir_column(const DevView& v, const TileDesc& t, int lane, d
       else
         v.col_status[c.col] = HEVI_COL_OK;
     }
+    // a third sweep is left to the tail kernel: x += S y now, hand over
+    if (more && !first && tail) {
+      for (int i = 0; i < n; ++i) {
+        const float d = y[i * stride] * s32[i * stride];
+        xs_[i * stride] = df_pack(df_add_f(df_of(xs_[i * stride]), d));
+      }
+      v.tail_dprev[c.col] = dn;
+      v.tail_list[v.tile_begin * kTile + atomicAdd(&v.tail_count[N], 1)] =
+          (int32_t)(((v.tile_begin + blockIdx.x) << 5) | lane);
+      more = false;
+      active = false;
+    }
     // refining lanes, fused pass: x += S y, r = b - A x, y = S^-1 r, |S^-1 x|
     const unsigned mm = __ballot_sync(0xffffffffu, more);
     if (coop_ok && __popc(mm) <= kWarpSweepLanes) {
@@ -1695,95 +1819,8 @@ __device__ void solve_ir_column(const DevView& v, const TileDesc& t, int lane, d
         if (lane == cl) xnorm = sqrt((double)xsq);
       }
     } else if (more) {
-      // double-float arithmetic (FP32 pipes); |x| in FP32 is only a scale
-      float xs = 0.0f;
-      const bool fst = first;
-      const df lamd = df_from_double(lam), gd = df_from_double(g), csd = df_from_double(c.s);
-      // Each call loads the next point's values of y and x (flux) or x and b
-      // (out) before it stores its own, so that the loads are not held back
-      // behind the stores; lin and the scales are read-only here (__ldg).
-      const int nzc = 3 * (t.nez * N + 1);
-      float py[3];
-      float2 px[3];
-#pragma unroll
-      for (int u = 0; u < 3; ++u) {
-        py[u] = y[u * stride];
-        px[u] = xs_[u * stride];
-      }
-      auto flux = [&](int I, df* f) {
-        float yc3[3];
-        float2 xc3[3];
-#pragma unroll
-        for (int u = 0; u < 3; ++u) {
-          yc3[u] = py[u];
-          xc3[u] = px[u];
-        }
-        if (3 * I + 3 < nzc) {
-#pragma unroll
-          for (int u = 0; u < 3; ++u) {
-            py[u] = y[(3 * I + 3 + u) * stride];
-            px[u] = xs_[(3 * I + 3 + u) * stride];
-          }
-        }
-        df xi[3];
-#pragma unroll
-        for (int u = 0; u < 3; ++u) {
-          const int i = 3 * I + u;
-          const float d = yc3[u] * __ldg(&s32[i * stride]);
-          xi[u] = fst ? df{d, 0.0f} : df_add_f(df_of(xc3[u]), d);
-          xs_[i * stride] = df_pack(xi[u]);
-          xs = fmaf(xi[u].hi, xi[u].hi, xs);
-        }
-        const df wI = df_from_double(__ldg(&lin[(3 * I) * stride]));
-        const df thI = df_from_double(__ldg(&lin[(3 * I + 1) * stride]));
-        const df cI = df_from_double(__ldg(&lin[(3 * I + 2) * stride]));
-        f[0] = xi[1];
-        // f1 = -w^2 rho + 2 w m + c Theta,  f2 = -theta w rho + theta m + w Theta
-        f[1] = df_sub(df_fma({2.0f * wI.hi, 2.0f * wI.lo}, xi[1], df_mul(cI, xi[2])),
-                      df_mul(df_mul(wI, wI), xi[0]));
-        f[2] = df_sub(df_fma(thI, xi[1], df_mul(wI, xi[2])), df_mul(df_mul(thI, wI), xi[0]));
-      };
-      float2 qx[3], qb[3];
-      bool qfirst = true;
-      auto out = [&](int I, const df* D) {
-        // A x = x + Lambda (Dcal[K x] + G x);  r = b - A x
-        if (qfirst) {  // x of point 0 is final once flux(0) has run
-#pragma unroll
-          for (int u = 0; u < 3; ++u) {
-            qx[u] = xs_[u * stride];
-            qb[u] = bs_[u * stride];
-          }
-          qfirst = false;
-        }
-        float2 xc3[3], bc3[3];
-#pragma unroll
-        for (int u = 0; u < 3; ++u) {
-          xc3[u] = qx[u];
-          bc3[u] = qb[u];
-        }
-        if (3 * I + 3 < nzc) {  // flux has already run for point I + 1
-#pragma unroll
-          for (int u = 0; u < 3; ++u) {
-            qx[u] = xs_[(3 * I + 3 + u) * stride];
-            qb[u] = bs_[(3 * I + 3 + u) * stride];
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < 3; ++u) {
-          const int i = 3 * I + u;
-          const df xv = df_of(xc3[u]), bv = df_of(bc3[u]);
-          df r;
-          if (u == 1 && (I == 0 || I == c.nz - 1)) {
-            r = df_sub(bv, xv);
-          } else {
-            df ax = D[u];
-            if (u == 1) ax = df_fma(gd, df_of(xc3[0]), ax);
-            r = df_sub(bv, df_fma(lamd, ax, xv));
-          }
-          y[i * stride] = __fadd_rn(r.hi, r.lo) * __ldg(&is32[i * stride]);
-        }
-      };
-      element_pass_df<N>(t.nez, csd, reinterpret_cast<float2*>(Ring<N>::buf()), lane, flux, out);
+      const float xs = lane_residual<N>(y, s32, xs_, bs_, lin, is32, t.nez, lam, g, c.s, first, true,
+                                        reinterpret_cast<float2*>(Ring<N>::buf()), lane);
       xnorm = sqrt((double)xs);
     }
     if (more) {
@@ -1822,7 +1859,75 @@ __global__ void __launch_bounds__(32, 20) k_solve_ir(DevView v, double lam, cons
   }
   __syncwarp();
   Ring<N> rg{0u, 0u, true};
-  solve_ir_column<N>(v, t, lane, lam, b, x, tol, max_sweeps, rg);
+  solve_ir_column<N>(v, t, lane, lam, b, x, tol, max_sweeps, true, rg);
+}
+
+// Tail of the FP32 + refinement solve: one thread per column that needed a
+// third sweep (handed over by k_solve_ir with x updated after its second
+// sweep): residual, sweep, stop test, as in solve_ir_column, then x.  The
+// columns come from many tiles, so each thread reads its own records (one
+// column per thread, the L1-prefetched per-thread sweeps); handing them over
+// keeps k_solve_ir's warps at two uniform sweeps.
+template <int N>
+__global__ void __launch_bounds__(128) k_solve_tail(DevView v, double lam, double* x, double tol,
+                                                    int max_sweeps) {
+  constexpr int stride = kTile;
+  extern __shared__ __align__(16) float2 tail_slots[];  // (2N + 1) x 3 pairs per lane, per warp
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= v.tail_count[N]) return;
+  const int32_t e = v.tail_list[v.tile_begin * kTile + idx];
+  const TileDesc t = v.tiles[e >> 5];
+  const int lane = e & 31;
+  const Col c = make_col(v, t, lane, N);
+  const TileScr sc = tile_scratch(v, t);
+  float* y = sc.y + lane;
+  float2* xs_ = reinterpret_cast<float2*>(sc.x) + lane;
+  const float2* bs_ = reinterpret_cast<const float2*>(sc.b) + lane;
+  const double* lin = sc.lin + lane;
+  const float* s32 = sc.s + lane;
+  const float* is32 = sc.is + lane;
+  const float* base = reinterpret_cast<const float*>(v.fac) + t.fac_off;
+  float2* slots = tail_slots + (threadIdx.x / 32) * (2 * N + 1) * 3 * kTile;
+  const int n = c.n;
+  double dprev = v.tail_dprev[c.col];
+  int sweeps = 2, status = HEVI_COL_NOT_CONVERGED;
+  bool update = false;  // x already holds the second sweep's correction
+  while (true) {
+    const double xnorm =
+        sqrt((double)lane_residual<N>(y, s32, xs_, bs_, lin, is32, t.nez, lam, v.ph.g, c.s, false,
+                                      update, slots, threadIdx.x & 31));
+    update = true;
+    forward_sweep<N, float, float, 2>(base, lane, n, y, stride);
+    backward_sweep<N, float, float, 2>(base, lane, n, y, stride);
+    ++sweeps;
+    float d2 = 0.0f;
+    for (int i = 0; i < n; ++i) {
+      const float d = y[i * stride] * s32[i * stride];
+      d2 = fmaf(d, d, d2);
+    }
+    const double dn = sqrt((double)d2);
+    bool stop = false;
+    if (dn <= tol * xnorm || dn * (dn / dprev) <= tol * xnorm) {
+      stop = true;
+      status = HEVI_COL_OK;
+    } else if (dn > 0.5 * dprev || sweeps >= max_sweeps) {
+      stop = true;
+    }
+    if (stop) {
+      double* xc = x + c.off;
+      for (int i = 0; i < n; ++i) {
+        const float d = y[i * stride] * s32[i * stride];
+        xc[i] = df_to_double(df_add_f(df_of(xs_[i * stride]), d));
+      }
+      break;
+    }
+    dprev = dn;
+  }
+  v.col_iters[c.col] = sweeps;
+  if (status != HEVI_COL_OK)
+    fail(v, c.col, status);
+  else
+    v.col_status[c.col] = HEVI_COL_OK;
 }
 
 // Plain FP64 solve; the work vectors live in shared memory.
@@ -1865,7 +1970,18 @@ static void launch_solve_n(const DevView& v, hevi_precision prec, double lam, co
                            std::min(100, (20 * (smem + 1024 + 64) * 100 + 232447) / 232448));
       configured = true;
     }
+    cudaMemsetAsync(v.tail_count + N, 0, sizeof(int32_t), st);
     k_solve_ir<N><<<(unsigned)v.tile_count, kTile, smem, st>>>(v, lam, b, x, tol, max_sweeps);
+    // the handed-over columns: one thread each (the grid covers every column
+    // of this order; threads past the count return at once)
+    constexpr int tail_smem = 4 * (2 * N + 1) * 3 * kTile * (int)sizeof(float2);
+    static bool tail_configured = false;
+    if (!tail_configured) {
+      cudaFuncSetAttribute(k_solve_tail<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, tail_smem);
+      tail_configured = true;
+    }
+    k_solve_tail<N><<<(unsigned)((v.tile_count * kTile + 127) / 128), 128, tail_smem, st>>>(
+        v, lam, x, tol, max_sweeps);
   }
 }
 

@@ -124,6 +124,42 @@ def test_stage_solve_parity(hv, prec, nez, N, ncols):
         assert its.min() >= 2 and its.max() <= 4
 
 
+@pytest.mark.parametrize("ncols,tol,sweeps", [
+    (5, 1e-11, 10),     # one partial tile: every sweep by the whole warp, one column at a time
+    (40, 1e-11, 10),    # a full tile (shared-memory record ring) and a partial one
+    (40, 1e-15, 6),     # every column refines past the contraction limit: ring for all sweeps
+    (70, 1e-13, 10),    # mixed: ring sweeps, then a few lanes per warp continue
+    (64, 1.0, 10),      # one sweep (the first FP32 solve) is accepted
+])
+def test_stage_solve_refinement_paths(hv, ncols, tol, sweeps):
+    """The FP32 + refinement solve takes three code paths per warp (all 32
+    lanes through the record ring, a few lanes by the whole warp, otherwise
+    one lane per column); each must give the oracle's solution."""
+    nez, N, lam = 10, 4, 87.868
+    ctx = hv.Context([(nez, N)], ZTOP, ncols=ncols, precision=hv.FP32_IR)
+    ctx.hevi_set_refinement(tol, sweeps)
+    q0 = _perturbed(nez, N, ncols, seed=21)
+    b = _rhs(nez, N, ncols, seed=22)
+    ctx.hevi_factor(lam, _t(q0))
+    x = ctx.empty()
+    try:
+        ctx.hevi_stage_solve(_t(b), x)
+    except hv.HeviError as e:
+        assert tol < 1e-14 and e.code == 5, e   # the contraction stop reports NOT_CONVERGED
+    x = _np(x, ncols)
+    x_ref, info = oracle.stage_solve(nez, N, ZTOP, lam, q0, b)
+    assert (info == 0).all()
+    err = _rel_cols(x, x_ref)
+    st, it = ctx.hevi_column_status()
+    its = it.cpu().numpy()
+    if tol >= 1.0:
+        assert (its == 1).all()
+        assert err.max() < 1e-3, err.max()  # FP32 factors alone
+    else:
+        assert err.max() < TOL, err.max()
+        assert its.min() >= 2 and its.max() <= sweeps
+
+
 @pytest.mark.parametrize("prec", ["FP64", "FP32_IR"])
 def test_stage_solve_lhevi_stage_workload(hv, prec):
     """1,538 columns, Nez=8, N=4, 30 km, about the rest state (all columns)."""
