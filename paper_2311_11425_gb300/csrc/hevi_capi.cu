@@ -223,9 +223,9 @@ struct hevi_ctx {
 
 namespace {
 
-enum Kind { kSetup = 0, kFactor, kSolve, kApply, kApplyStage, kNewton, kCombine, kNumKinds };
+enum Kind { kSetup = 0, kFactor, kSolve, kApply, kApplyStage, kNewton, kCombine, kSolveTail, kNumKinds };
 const char* kKindNames[kNumKinds] = {"setup", "factor", "stage_solve", "apply",
-                                     "apply_stage", "newton", "combine"};
+                                     "apply_stage", "newton", "combine", "stage_solve_tail"};
 
 cudaEvent_t get_event(hevi_ctx* c) {
   if (!c->ev_pool.empty()) {
@@ -689,7 +689,13 @@ hevi_status hevi_stage_solve_async(hevi_ctx* c, const double* rhs, double* x) {
   {
     Scope sc(c, kSolve);
     for_orders(c, c->v, [&](const DevView& v, int N, int ylen, cudaStream_t sk) {
-      hevi::launch_solve(v, N, c->prec, c->lam, rhs, x, c->ir_tol, c->ir_max, ylen, sk);
+      hevi::launch_solve(v, N, c->prec, c->lam, rhs, x, c->ir_tol, c->ir_max, ylen, 0, sk);
+    });
+  }
+  if (c->prec == HEVI_FP32_IR) {
+    Scope sc(c, kSolveTail);
+    for_orders(c, c->v, [&](const DevView& v, int N, int ylen, cudaStream_t sk) {
+      hevi::launch_solve(v, N, c->prec, c->lam, rhs, x, c->ir_tol, c->ir_max, ylen, 1, sk);
     });
   }
   return check_launch(c);
@@ -904,7 +910,13 @@ hevi_status hevi_lhevi_step(hevi_ctx* c, int32_t s, const double* A, const doubl
     {
       Scope sc(c, kSolve);
       for_orders(c, c->v, [&](const DevView& v, int N, int ylen, cudaStream_t sk) {
-        hevi::launch_solve(v, N, c->prec, lam, rhs, Qi, c->ir_tol, c->ir_max, ylen, sk);
+        hevi::launch_solve(v, N, c->prec, lam, rhs, Qi, c->ir_tol, c->ir_max, ylen, 0, sk);
+      });
+    }
+    if (c->prec == HEVI_FP32_IR) {
+      Scope sc(c, kSolveTail);
+      for_orders(c, c->v, [&](const DevView& v, int N, int ylen, cudaStream_t sk) {
+        hevi::launch_solve(v, N, c->prec, lam, rhs, Qi, c->ir_tol, c->ir_max, ylen, 1, sk);
       });
     }
     nt = 0;

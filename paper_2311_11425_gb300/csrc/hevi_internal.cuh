@@ -285,8 +285,11 @@ void launch_setup_ref(const DevView& v, const int32_t* col_order, const int32_t*
 // v.tile_count), all of order `order`; ylen is the longest n + 2K among them.
 void launch_factor(const DevView& v, int order, hevi_precision prec, double lam, const double* q0,
                    int ylen, cudaStream_t st);
+// launch_solve: part 0 is the solve proper (FP64, or FP32 + two refinement
+// sweeps for every column); part 1 (FP32 + refinement only) finishes the
+// columns part 0 handed over.  Both, in this order, make one stage solve.
 void launch_solve(const DevView& v, int order, hevi_precision prec, double lam, const double* b,
-                  double* x, double tol, int max_sweeps, int ylen, cudaStream_t st);
+                  double* x, double tol, int max_sweeps, int ylen, int part, cudaStream_t st);
 void launch_apply(const DevView& v, int order, const double* x, double* y, int nonlinear,
                   cudaStream_t st);
 void launch_apply_stage(const DevView& v, int order, const double* Q, const double* H, double* E,

@@ -1952,7 +1952,22 @@ static int pick_block(int bytes, int max_blk) {
 
 template <int N>
 static void launch_solve_n(const DevView& v, hevi_precision prec, double lam, const double* b,
-                           double* x, double tol, int max_sweeps, int ylen, cudaStream_t st) {
+                           double* x, double tol, int max_sweeps, int ylen, int part,
+                           cudaStream_t st) {
+  if (part == 1) {  // the tail of the FP32 + refinement solve
+    if (prec == HEVI_FP64) return;
+    // the handed-over columns: one thread each (the grid covers every column
+    // of this order; threads past the count return at once)
+    constexpr int tail_smem = 4 * (2 * N + 1) * 3 * kTile * (int)sizeof(float2);
+    static bool tail_configured = false;
+    if (!tail_configured) {
+      cudaFuncSetAttribute(k_solve_tail<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, tail_smem);
+      tail_configured = true;
+    }
+    k_solve_tail<N><<<(unsigned)((v.tile_count * kTile + 127) / 128), 128, tail_smem, st>>>(
+        v, lam, x, tol, max_sweeps);
+    return;
+  }
   if (prec == HEVI_FP64) {
     const int esz = (int)sizeof(double);
     const int blk = pick_block(ylen * esz, 128), tiles_per_blk = blk / kTile;
@@ -1972,27 +1987,17 @@ static void launch_solve_n(const DevView& v, hevi_precision prec, double lam, co
     }
     cudaMemsetAsync(v.tail_count + N, 0, sizeof(int32_t), st);
     k_solve_ir<N><<<(unsigned)v.tile_count, kTile, smem, st>>>(v, lam, b, x, tol, max_sweeps);
-    // the handed-over columns: one thread each (the grid covers every column
-    // of this order; threads past the count return at once)
-    constexpr int tail_smem = 4 * (2 * N + 1) * 3 * kTile * (int)sizeof(float2);
-    static bool tail_configured = false;
-    if (!tail_configured) {
-      cudaFuncSetAttribute(k_solve_tail<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, tail_smem);
-      tail_configured = true;
-    }
-    k_solve_tail<N><<<(unsigned)((v.tile_count * kTile + 127) / 128), 128, tail_smem, st>>>(
-        v, lam, x, tol, max_sweeps);
   }
 }
 
 void launch_solve(const DevView& v, int order, hevi_precision prec, double lam, const double* b,
-                  double* x, double tol, int max_sweeps, int ylen, cudaStream_t st) {
+                  double* x, double tol, int max_sweeps, int ylen, int part, cudaStream_t st) {
   switch (order) {
-    case 1: launch_solve_n<1>(v, prec, lam, b, x, tol, max_sweeps, ylen, st); break;
-    case 2: launch_solve_n<2>(v, prec, lam, b, x, tol, max_sweeps, ylen, st); break;
-    case 3: launch_solve_n<3>(v, prec, lam, b, x, tol, max_sweeps, ylen, st); break;
-    case 4: launch_solve_n<4>(v, prec, lam, b, x, tol, max_sweeps, ylen, st); break;
-    case 5: launch_solve_n<5>(v, prec, lam, b, x, tol, max_sweeps, ylen, st); break;
+    case 1: launch_solve_n<1>(v, prec, lam, b, x, tol, max_sweeps, ylen, part, st); break;
+    case 2: launch_solve_n<2>(v, prec, lam, b, x, tol, max_sweeps, ylen, part, st); break;
+    case 3: launch_solve_n<3>(v, prec, lam, b, x, tol, max_sweeps, ylen, part, st); break;
+    case 4: launch_solve_n<4>(v, prec, lam, b, x, tol, max_sweeps, ylen, part, st); break;
+    case 5: launch_solve_n<5>(v, prec, lam, b, x, tol, max_sweeps, ylen, part, st); break;
     default: break;
   }
 }
