@@ -147,6 +147,14 @@ hevi_status hevi_stage_solve_async(hevi_ctx* ctx, const double* rhs, double* x);
  * relative error and the sweep limit (defaults 1e-11 and 10). */
 hevi_status hevi_set_refinement(hevi_ctx* ctx, double tol, int32_t max_sweeps);
 
+/* Test hook for the bounded device waits: with step >= 0 every later
+ * HEVI_FP32_IR stage solve announces, but does not issue, the asynchronous
+ * copy of forward pivot step `step` of each tile's first sweep, so that the
+ * wait for it runs out (about a second) and the tile's columns end
+ * HEVI_COL_WAIT_TIMEOUT; step < 0 turns it off.  No copy is left in flight
+ * and the context stays usable. */
+hevi_status hevi_test_drop_record_copy(hevi_ctx* ctx, int32_t step);
+
 /* NHEVI-LU (Sec. 4.2.3): for every column, Newton-Raphson on
  * F(q) = q - gamma_dt V(q) - R, rebuilding and LU-factoring the Jacobian at
  * every iteration; state (dev) holds the initial guess on entry and the

@@ -79,6 +79,7 @@ def load(build: bool = False):
         "hevi_stage_solve": (_I32, [_P, _P, _P]),
         "hevi_stage_solve_async": (_I32, [_P, _P, _P]),
         "hevi_set_refinement": (_I32, [_P, _D, _I32]),
+        "hevi_test_drop_record_copy": (_I32, [_P, _I32]),
         "hevi_newton_solve": (_I32, [_P, _D, _P, _P, _D, _I32]),
         "hevi_newton_solve_async": (_I32, [_P, _D, _P, _P, _D, _I32]),
         "hevi_apply_Lv": (_I32, [_P, _P, _P, ctypes.c_int]),
@@ -350,6 +351,12 @@ class Context:
     def hevi_set_refinement(self, tol: float, max_sweeps: int):
         _check(self._lib.hevi_set_refinement(self._h, float(tol), int(max_sweeps)),
                "hevi_set_refinement")
+
+    def hevi_test_drop_record_copy(self, step: int):
+        """Test hook: leave out one record copy per tile so that the solve's
+        bounded wait runs out (step < 0 turns it off)."""
+        _check(self._lib.hevi_test_drop_record_copy(self._h, int(step)),
+               "hevi_test_drop_record_copy")
 
     def hevi_stage_solve(self, rhs, x=None, blocking=True):
         x = self.empty() if x is None else x

@@ -671,6 +671,12 @@ hevi_status hevi_set_refinement(hevi_ctx* c, double tol, int32_t max_sweeps) {
   return HEVI_OK;
 }
 
+hevi_status hevi_test_drop_record_copy(hevi_ctx* c, int32_t step) {
+  if (!c) return HEVI_ERR_INVALID_ARG;
+  c->v.drop_copy = step >= 0 ? step + 1 : 0;
+  return HEVI_OK;
+}
+
 hevi_status hevi_factor(hevi_ctx* c, double gamma_dt, const double* lin_state) {
   if (!c || !(gamma_dt >= 0.0) || !std::isfinite(gamma_dt)) return HEVI_ERR_INVALID_ARG;
   {

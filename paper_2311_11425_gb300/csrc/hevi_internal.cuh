@@ -106,6 +106,7 @@ struct DevView {
   int32_t* col_status;      // [ncols] status of the last call
   int32_t* col_iters;       // [ncols]
   int32_t* fail_count;      // [1]
+  int32_t drop_copy;        // test hook: > 0 = the ring leaves out the copy of forward step drop_copy - 1
 };
 
 // Per-column geometry in a kernel.

@@ -1150,6 +1150,7 @@ struct Ring {
   unsigned phase;    // expected parity per barrier (bit s)
   unsigned pending;  // barriers with a copy in flight (bit s)
   bool ok;
+  int drop;          // test hook: forward step + 1 whose copy is announced but not issued
   __device__ __forceinline__ static unsigned char* buf() { return g_ring; }
   __device__ __forceinline__ static uint64_t* bar() {
     return reinterpret_cast<uint64_t*>(g_ring + RingCfg<N>::SMEM);
@@ -1186,8 +1187,9 @@ __device__ __forceinline__ void ring_issue_f(Ring<N>& rg, const float* base, int
     uint64_t* bar = &Ring<N>::bar()[slot];
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     mbar_expect_tx(bar, C::FB);
-    bulk_g2s(Ring<N>::buf() + slot * C::FB, frec_vec<N, float>(const_cast<float*>(base), j, 0, 0),
-             C::FB, bar, evict_first_policy());
+    if (rg.drop != j + 1)
+      bulk_g2s(Ring<N>::buf() + slot * C::FB, frec_vec<N, float>(const_cast<float*>(base), j, 0, 0),
+               C::FB, bar, evict_first_policy());
   }
 }
 template <int N>
@@ -1215,7 +1217,8 @@ __device__ __forceinline__ void forward_sweep_ring(Ring<N>& rg, const float* bas
                                                    float* y, int stride) {
   using C = RingCfg<N>;
   constexpr int K = Band<N>::K, WR = Band<N>::WR, FR = Band<N>::FR;
-  for (int s = 0; s < C::DF && s < n; ++s) ring_issue_f<N>(rg, base, s, s, lane);
+  if (rg.ok)
+    for (int s = 0; s < C::DF && s < n; ++s) ring_issue_f<N>(rg, base, s, s, lane);
   float w[WR];
 #pragma unroll
   for (int r = 0; r < WR; ++r) w[r] = y[r * stride];
@@ -1260,7 +1263,8 @@ __device__ __forceinline__ float backward_sweep_ring(Ring<N>& rg, const float* b
                                                      float* y, int stride) {
   using C = RingCfg<N>;
   constexpr int K = Band<N>::K, WB = Band<N>::WC, BR = Band<N>::BR;
-  for (int s = 0; s < C::DB && s < n; ++s) ring_issue_b<N>(rg, base, n, n - 1 - s, s, lane);
+  if (rg.ok)  // after a wait ran out nothing more is issued
+    for (int s = 0; s < C::DB && s < n; ++s) ring_issue_b<N>(rg, base, n, n - 1 - s, s, lane);
   float w[WB];
 #pragma unroll
   for (int cc = 0; cc < WB; ++cc) {
@@ -1858,7 +1862,7 @@ __global__ void __launch_bounds__(32, 20) k_solve_ir(DevView v, double lam, cons
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncwarp();
-  Ring<N> rg{0u, 0u, true};
+  Ring<N> rg{0u, 0u, true, v.drop_copy};
   solve_ir_column<N>(v, t, lane, lam, b, x, tol, max_sweeps, true, rg);
 }
 

@@ -160,6 +160,29 @@ def test_stage_solve_refinement_paths(hv, ncols, tol, sweeps):
         assert its.min() >= 2 and its.max() <= sweeps
 
 
+def test_record_copy_wait_runs_out(hv):
+    """A record copy that never arrives: the ring's bounded wait runs out, the
+    tiles' columns end WAIT_TIMEOUT with x = NaN, nothing is left in flight,
+    and the same context then solves normally."""
+    nez, N, ncols, lam = 10, 4, 64, 87.868
+    ctx = hv.Context([(nez, N)], ZTOP, ncols=ncols, precision=hv.FP32_IR)
+    q0 = _perturbed(nez, N, ncols, seed=23)
+    b = _rhs(nez, N, ncols, seed=24)
+    ctx.hevi_factor(lam, _t(q0))
+    ctx.hevi_test_drop_record_copy(5)
+    x = ctx.empty()
+    with pytest.raises(hv.HeviError) as e:
+        ctx.hevi_stage_solve(_t(b), x)
+    assert e.value.code == 7
+    st, _ = ctx.hevi_column_status()
+    assert bool((st == 7).all())
+    assert bool(x.isnan().all())
+    ctx.hevi_test_drop_record_copy(-1)
+    x = _np(ctx.hevi_stage_solve(_t(b)), ncols)
+    x_ref, info = oracle.stage_solve(nez, N, ZTOP, lam, q0, b)
+    assert _rel_cols(x, x_ref).max() < TOL
+
+
 @pytest.mark.parametrize("prec", ["FP64", "FP32_IR"])
 def test_stage_solve_lhevi_stage_workload(hv, prec):
     """1,538 columns, Nez=8, N=4, 30 km, about the rest state (all columns)."""
