@@ -396,6 +396,7 @@ const char* hevi_status_string(hevi_status s) {
     case HEVI_ERR_SINGULAR: return "singular column";
     case HEVI_ERR_NOT_CONVERGED: return "not converged";
     case HEVI_ERR_BAD_INPUT: return "non-physical input state";
+    case HEVI_ERR_WAIT_TIMEOUT: return "device wait past its limit";
   }
   return "unknown status";
 }

@@ -32,6 +32,8 @@ def test_library_exports_every_declared_symbol():
     assert not missing, missing
     hv.load()
     assert hv.load().hevi_status_string(5) == b"not converged"
+    assert hv.load().hevi_status_string(7) == b"device wait past its limit"
+    assert hv.STATUS[7] == "device wait past its limit"
 
 
 def test_tableaux_without_gpu():
