@@ -319,10 +319,6 @@ def gpu_arm(args, rank, world, local_rank, pool, cores):
     value = world * STAGES * NCOLS / (r["ms_per_step"] * 1e-3)
     # dominant kernel and its roofline
     per = {k: list(v) for k, v in r["kernels"].items() if v[1] > 0}
-    # the stage solve is k_solve_ir (two sweeps for every column) followed by
-    # k_solve_tail (the columns that need a third); its roofline is over both
-    if "stage_solve_tail" in per and "stage_solve" in per:
-        per["stage_solve"][0] += per.pop("stage_solve_tail")[0]
     dom = max(per, key=lambda k: per[k][0])
     pk = peaks()
     avg_ms = per[dom][0] / per[dom][1]

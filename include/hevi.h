@@ -78,9 +78,14 @@ typedef struct {
 /* Precision of the band factorisation:
  *   HEVI_FP64     plain FP64 band LU with partial pivoting (LAPACK dgbtrf
  *                 semantics, Sec. 4.2.3), one column per thread;
- *   HEVI_FP32_IR  the band is equilibrated with the reference-state scales,
- *                 rounded to FP32 and LU-factored with partial pivoting in
- *                 FP32; solves are refined with FP64 residuals. */
+ *   HEVI_FP32_IR  the band is equilibrated with the reference-state scales
+ *                 (rho_bar, rho_bar c_s, Theta_bar), rounded to FP32 and
+ *                 LU-factored WITHOUT interchanges (L and U each keep the K
+ *                 band diagonals; an exactly zero pivot marks the column
+ *                 SINGULAR); solves are refined with residuals carried to
+ *                 about 48 significant bits (double-float arithmetic), so the
+ *                 result is the solution of the FP64 system to the
+ *                 refinement tolerance. */
 typedef enum { HEVI_FP64 = 0, HEVI_FP32_IR = 1 } hevi_precision;
 
 typedef struct hevi_ctx hevi_ctx;
@@ -147,12 +152,20 @@ hevi_status hevi_stage_solve_async(hevi_ctx* ctx, const double* rhs, double* x);
  * relative error and the sweep limit (defaults 1e-11 and 10). */
 hevi_status hevi_set_refinement(hevi_ctx* ctx, double tol, int32_t max_sweeps);
 
+/* Resident warps per SM of the HEVI_FP32_IR stage solve (1 .. 32; 0 restores
+ * the default of 2).  Each warp solves tiles of 32 columns one after another;
+ * few warps per SM keep the factor records of the tiles in flight in L2
+ * between a tile's refinement sweeps, more warps hide more latency.  The
+ * setting changes the speed, not the result.  Not a paper quantity: a
+ * launch-shape control of this implementation. */
+hevi_status hevi_set_solve_warps(hevi_ctx* ctx, int32_t warps_per_sm);
+
 /* Test hook for the bounded device waits: with step >= 0 every later
  * HEVI_FP32_IR stage solve announces, but does not issue, the asynchronous
- * copy of forward pivot step `step` of each tile's first sweep, so that the
- * wait for it runs out (about a second) and the tile's columns end
- * HEVI_COL_WAIT_TIMEOUT; step < 0 turns it off.  No copy is left in flight
- * and the context stays usable. */
+ * copy of the chunk of factor records that holds forward pivot step `step`
+ * in each tile's first sweep, so that the wait for it runs out (about a
+ * second) and the tile's columns end HEVI_COL_WAIT_TIMEOUT; step < 0 turns it
+ * off.  No copy is left in flight and the context stays usable. */
 hevi_status hevi_test_drop_record_copy(hevi_ctx* ctx, int32_t step);
 
 /* NHEVI-LU (Sec. 4.2.3): for every column, Newton-Raphson on

@@ -80,6 +80,7 @@ def load(build: bool = False):
         "hevi_stage_solve_async": (_I32, [_P, _P, _P]),
         "hevi_set_refinement": (_I32, [_P, _D, _I32]),
         "hevi_test_drop_record_copy": (_I32, [_P, _I32]),
+        "hevi_set_solve_warps": (_I32, [_P, _I32]),
         "hevi_newton_solve": (_I32, [_P, _D, _P, _P, _D, _I32]),
         "hevi_newton_solve_async": (_I32, [_P, _D, _P, _P, _D, _I32]),
         "hevi_apply_Lv": (_I32, [_P, _P, _P, ctypes.c_int]),
@@ -351,6 +352,9 @@ class Context:
     def hevi_set_refinement(self, tol: float, max_sweeps: int):
         _check(self._lib.hevi_set_refinement(self._h, float(tol), int(max_sweeps)),
                "hevi_set_refinement")
+
+    def hevi_set_solve_warps(self, warps_per_sm: int):
+        _check(self._lib.hevi_set_solve_warps(self._h, int(warps_per_sm)), "hevi_set_solve_warps")
 
     def hevi_test_drop_record_copy(self, step: int):
         """Test hook: leave out one record copy per tile so that the solve's

@@ -26,7 +26,11 @@ namespace {
 // [3] bad input.
 constexpr int kFailSlots = 5;
 
-int rl_of(int N) {  // record length per pivot step
+// Factor record length per pivot step and column: FP64 band LU with partial
+// pivoting (L record {l_1..l_K, pivot, 1/u_jj}, U record of 2K entries) or
+// the FP32 no-pivot factors (K multipliers; 1/u_jj and K entries of U).
+int rl_of(int N, hevi_precision prec) {
+  if (prec == HEVI_FP32_IR) return hevi::np_record_floats(N);
   const int K = 3 * (N + 1) - 1;
   return ((K + 2) + 3) / 4 * 4 + ((2 * K) + 3) / 4 * 4;
 }
@@ -107,6 +111,7 @@ hevi::LglTables make_tables() {
       }
     for (int k = 0; k <= N; ++k) t.iwf[N][k] = (float)(1.0 / t.w[N][k]);
     for (int k = 0; k <= N; ++k) t.iw[N][k] = 1.0 / t.w[N][k];
+    for (int k = 0; k <= N; ++k) t.xh[N][k] = (float)(0.5 * (t.xi[N][k] + 1.0));
     {
       auto wD = [&](int k, int j) { return t.wD[N][k * (N + 1) + j]; };
       for (int dJ = -N; dJ <= N; ++dJ) {
@@ -223,9 +228,9 @@ struct hevi_ctx {
 
 namespace {
 
-enum Kind { kSetup = 0, kFactor, kSolve, kApply, kApplyStage, kNewton, kCombine, kSolveTail, kNumKinds };
+enum Kind { kSetup = 0, kFactor, kSolve, kApply, kApplyStage, kNewton, kCombine, kNumKinds };
 const char* kKindNames[kNumKinds] = {"setup", "factor", "stage_solve", "apply",
-                                     "apply_stage", "newton", "combine", "stage_solve_tail"};
+                                     "apply_stage", "newton", "combine"};
 
 cudaEvent_t get_event(hevi_ctx* c) {
   if (!c->ev_pool.empty()) {
@@ -436,16 +441,7 @@ hevi_status hevi_setup(hevi_ctx** out, const hevi_column_grid* grid, const hevi_
   ph.R = ref ? ref->R : 287.17;
   ph.cp = ref ? ref->cp : 1004.67;
   ph.g = ref ? ref->g : 9.80616;
-  ph.cv = ph.cp - ph.R;
-  ph.gamma = ph.cp / ph.cv;
-  ph.cs = std::sqrt(ph.gamma * ph.R * ph.T0);
-  {
-    double coef = 1.0;  // C(gamma, k) = C(gamma, k-1) (gamma - k + 1) / k
-    for (int k = 1; k <= hevi::kEosTerms; ++k) {
-      coef *= (ph.gamma - k + 1.0) / k;
-      ph.bin[k - 1] = coef;
-    }
-  }
+  hevi::phys_derive(ph);
   c->v.ph = ph;
   c->v.ncols = ncols;
 
@@ -476,11 +472,11 @@ hevi_status hevi_setup(hevi_ctx** out, const hevi_column_grid* grid, const hevi_
     t.scr_off = scr_off;
     t.y_off = y_off;
     const int64_t n = 3 * ((int64_t)t.nez * t.order + 1);
-    // the refinement's interleaved scratch: y (FP32, n + 2K + 4 rows), x, b
-    // and the point coefficients of L(q0) (FP64, n rows each), S and S^-1
-    // (FP32, n rows each)
-    y_off += (9 * n + 2 * (3 * (t.order + 1) - 1) + 4) * kTile;
-    fac_off += n * rl_of(t.order) * kTile;
+    // the FP32 solve's scratch, [row][lane]: the point coefficients of L(q0)
+    // (FP64, n rows), the work vector (n + K + 1 rows, rounded to 4) and the
+    // first solution, the correction sum and the residual (n rows each)
+    y_off += (2 * n + (n + 3 * (t.order + 1) + 3) / 4 * 4 + 3 * n) * kTile;
+    fac_off += n * rl_of(t.order, precision) * kTile;
     scr_off += n * ur2_of(t.order) * kTile;
     if (c->order_count[t.order] == 0) c->order_begin[t.order] = (int32_t)c->h_tiles.size();
     c->order_count[t.order] += 1;
@@ -503,7 +499,11 @@ hevi_status hevi_setup(hevi_ctx** out, const hevi_column_grid* grid, const hevi_
     tables = make_tables();
     tables_done = true;
   }
-  hevi::upload_tables(tables);
+  if (hevi::upload_tables(tables) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return HEVI_ERR_CUDA;
+  }
 
   hevi_status s = HEVI_OK;
   int64_t* d_off;
@@ -516,12 +516,8 @@ hevi_status hevi_setup(hevi_ctx** out, const hevi_column_grid* grid, const hevi_
       (s = c->alloc(&d_order, ncols)) || (s = c->alloc(&d_nez, ncols)) ||
       (s = c->alloc(&d_dz, ncols)) || (s = c->alloc(&d_ref, c->state_size)) ||
       (s = c->alloc(&c->v.lin, c->state_size)) || (s = c->alloc(&d_tiles, c->ntiles)) ||
-      (s = c->alloc(&c->v.s32, c->state_size)) || (s = c->alloc(&c->v.is32, c->state_size)) ||
       (s = c->alloc(&c->v.ithb, c->state_size / 3)) ||
       (s = precision == HEVI_FP32_IR ? c->alloc(&c->v.ysc, c->ysc_floats) : HEVI_OK) ||
-      (s = precision == HEVI_FP32_IR ? c->alloc(&c->v.tail_list, c->ntiles * kTile) : HEVI_OK) ||
-      (s = precision == HEVI_FP32_IR ? c->alloc(&c->v.tail_count, hevi::kMaxOrder + 1) : HEVI_OK) ||
-      (s = precision == HEVI_FP32_IR ? c->alloc(&c->v.tail_dprev, ncols) : HEVI_OK) ||
       (s = c->alloc(&d_fs, ncols)) || (s = c->alloc(&d_cs, ncols)) || (s = c->alloc(&d_it, ncols)) ||
       (s = c->alloc(&d_fail, kFailSlots)) ||
       (s = precision == HEVI_FP64 ? c->alloc((double**)&d_fac, c->fac_elems)
@@ -625,16 +621,14 @@ int64_t hevi_estimate_bytes(const hevi_column_grid* grid, hevi_precision precisi
     const int64_t tiles = (count[c] + kTile - 1) / kTile;
     state += n * count[c];
     ntiles += tiles;
-    ysc += tiles * (9 * n + 2 * (3 * (N + 1) - 1) + 4) * kTile;
-    fac += tiles * n * rl_of(N) * kTile;
+    ysc += tiles * (2 * n + (n + 3 * (N + 1) + 3) / 4 * 4 + 3 * n) * kTile;
+    fac += tiles * n * rl_of(N, precision) * kTile;
     scr += tiles * n * ur2_of(N) * kTile;
   }
   const int64_t esz = precision == HEVI_FP64 ? 8 : 4;
   int64_t b = (ncols + 1) * 8 + 3 * ncols * 4 + ncols * 8 + 2 * state * 8 +
-              ntiles * (int64_t)sizeof(TileDesc) + 2 * state * 4 + (state / 3) * 8 +
-              (precision == HEVI_FP32_IR ? ysc * 4 + ntiles * kTile * 4 + (hevi::kMaxOrder + 1) * 4 +
-                                               ncols * 8
-                                         : 0) +
+              ntiles * (int64_t)sizeof(TileDesc) + (state / 3) * 8 +
+              (precision == HEVI_FP32_IR ? ysc * 4 : 0) +
               3 * ncols * 4 + kFailSlots * 4 +
               fac * esz;
   if (kind == 1) b += (2 * (int64_t)stages + 1) * state * 8;
@@ -672,6 +666,12 @@ hevi_status hevi_set_refinement(hevi_ctx* c, double tol, int32_t max_sweeps) {
   return HEVI_OK;
 }
 
+hevi_status hevi_set_solve_warps(hevi_ctx* c, int32_t warps_per_sm) {
+  if (!c || warps_per_sm < 0 || warps_per_sm > 32) return HEVI_ERR_INVALID_ARG;
+  c->v.solve_wps = warps_per_sm;
+  return HEVI_OK;
+}
+
 hevi_status hevi_test_drop_record_copy(hevi_ctx* c, int32_t step) {
   if (!c) return HEVI_ERR_INVALID_ARG;
   c->v.drop_copy = step >= 0 ? step + 1 : 0;
@@ -696,13 +696,7 @@ hevi_status hevi_stage_solve_async(hevi_ctx* c, const double* rhs, double* x) {
   {
     Scope sc(c, kSolve);
     for_orders(c, c->v, [&](const DevView& v, int N, int ylen, cudaStream_t sk) {
-      hevi::launch_solve(v, N, c->prec, c->lam, rhs, x, c->ir_tol, c->ir_max, ylen, 0, sk);
-    });
-  }
-  if (c->prec == HEVI_FP32_IR) {
-    Scope sc(c, kSolveTail);
-    for_orders(c, c->v, [&](const DevView& v, int N, int ylen, cudaStream_t sk) {
-      hevi::launch_solve(v, N, c->prec, c->lam, rhs, x, c->ir_tol, c->ir_max, ylen, 1, sk);
+      hevi::launch_solve(v, N, c->prec, c->lam, rhs, x, c->ir_tol, c->ir_max, ylen, sk);
     });
   }
   return check_launch(c);
@@ -917,13 +911,7 @@ hevi_status hevi_lhevi_step(hevi_ctx* c, int32_t s, const double* A, const doubl
     {
       Scope sc(c, kSolve);
       for_orders(c, c->v, [&](const DevView& v, int N, int ylen, cudaStream_t sk) {
-        hevi::launch_solve(v, N, c->prec, lam, rhs, Qi, c->ir_tol, c->ir_max, ylen, 0, sk);
-      });
-    }
-    if (c->prec == HEVI_FP32_IR) {
-      Scope sc(c, kSolveTail);
-      for_orders(c, c->v, [&](const DevView& v, int N, int ylen, cudaStream_t sk) {
-        hevi::launch_solve(v, N, c->prec, lam, rhs, Qi, c->ir_tol, c->ir_max, ylen, 1, sk);
+        hevi::launch_solve(v, N, c->prec, lam, rhs, Qi, c->ir_tol, c->ir_max, ylen, sk);
       });
     }
     nt = 0;

@@ -5,6 +5,7 @@
 // of App. A.1 restricted to the vertical).  Band half-width K = 3(N+1) - 1
 // (Sec. 4.2.3).
 #pragma once
+#include <cmath>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -31,13 +32,39 @@ struct Band {
   static constexpr int RL = FR + BR;        // record length per pivot step
 };
 
+// Record layout of the FP32 factors (no pivoting, equilibrated band; the L
+// factor has K sub-diagonals and U has K super-diagonals).  Per pivot step j
+// a column stores a forward record F_j = {l_1 .. l_K} (unit-lower multipliers
+// of rows j+1 .. j+K) and a backward record B_j = {1/u_jj, u_(j-1)j, ..,
+// u_(j-K)j} (column j of U above the diagonal), each padded to whole float4
+// vectors.  A tile keeps all F records, then all B records, each interleaved
+// [step][vector][lane][4]: one step of a 32-column tile is one contiguous
+// block of FV (or BV) x 512 bytes.
+template <int N>
+struct NpBand {
+  static constexpr int K = 3 * (N + 1) - 1;
+  static constexpr int FV = (K + 3) / 4;      // float4 vectors of F_j
+  static constexpr int BV = (K + 1 + 3) / 4;  // float4 vectors of B_j
+  static constexpr int RL = 4 * (FV + BV);    // floats per step and column
+  static constexpr int WR = K + 1;            // rows of the active window
+};
+inline int np_record_floats(int N) {  // floats per step and column (host)
+  const int K = 3 * (N + 1) - 1;
+  return 4 * ((K + 3) / 4 + (K + 4) / 4);
+}
+
 // Physical constants of the isothermal reference atmosphere.
 constexpr int kEosTerms = 9;
 struct Phys {
   double T0, p0, R, cp, g;
   double cv, gamma, cs;   // cp - R, cp / cv, sqrt(gamma R T0)
   double bin[kEosTerms];  // C(gamma, k), k = 1 .. kEosTerms
+  // FP32 constants of the equilibration scales of the FP32 path:
+  // rho_bar = rho0f exp(-za z), theta_bar = T0f exp(zb z), c_s = csf
+  float rho0f, za, zb, T0f, csf;
 };
+// Fill the derived fields of a Phys from T0, p0, R, cp, g (host).
+inline void phys_derive(Phys& ph);
 
 // One tile = up to 32 columns of the same size class.
 struct TileDesc {
@@ -78,6 +105,7 @@ struct LglTables {
   float2 ep2[kMaxOrder + 1][3][3];
   float2 op2[kMaxOrder + 1][3][3];
   float2 om2[kMaxOrder + 1][3];
+  float xh[kMaxOrder + 1][kMaxOrder + 1];  // (xi_k + 1) / 2 in FP32
 };
 
 // Device view of a context's buffers (passed to kernels by value).
@@ -89,8 +117,6 @@ struct DevView {
   const double* col_dz;     // [ncols] element height
   const double* ref;        // state layout: (rho_bar, P_bar, Theta_bar) per point
   double* ithb;             // per point (index off/3 + I): 1 / Theta_bar, or null
-  float* s32;               // state layout: equilibration scales (rho_bar, rho_bar c_s, Theta_bar)
-  float* is32;              // state layout: their reciprocals
   double* lin;              // state layout: (w0, theta0, c0 = gamma P0 / Theta0)
   const TileDesc* tiles;
   int32_t ntiles;
@@ -98,15 +124,14 @@ struct DevView {
   int32_t tile_count;
   void* fac;                // factor records (float or double)
   float* scr;               // Newton scratch (U records)
-  float* ysc;               // per tile: the FP32 work vectors of the refinement solve
-  int32_t* tail_list;       // [ntiles * 32] columns left to the tail kernel (tile << 5 | lane)
-  int32_t* tail_count;      // [kMaxOrder + 1] entries per order
-  double* tail_dprev;       // [ncols] |d| of the last sweep of a handed-over column
+  float* ysc;               // per tile: FP64 point coefficients of L(q0), [row][lane] (FP32 path)
   int32_t* fac_status;      // [ncols] status of the last factorisation
   int32_t* col_status;      // [ncols] status of the last call
   int32_t* col_iters;       // [ncols]
   int32_t* fail_count;      // [1]
-  int32_t drop_copy;        // test hook: > 0 = the ring leaves out the copy of forward step drop_copy - 1
+  int32_t solve_wps;        // resident stage-solve warps per SM (0: default)
+  int32_t drop_copy;        // test hook: > 0 = the record ring leaves out the copy of the
+                            // chunk holding forward step drop_copy - 1 of a tile's first sweep
 };
 
 // Per-column geometry in a kernel.
@@ -279,6 +304,22 @@ __device__ __forceinline__ double eos_perturbation(const Phys& ph, double Theta,
   return P_bar * expm1(ph.gamma * log1p(x));
 }
 
+inline void phys_derive(Phys& ph) {
+  ph.cv = ph.cp - ph.R;
+  ph.gamma = ph.cp / ph.cv;
+  ph.cs = std::sqrt(ph.gamma * ph.R * ph.T0);
+  double coef = 1.0;  // C(gamma, k) = C(gamma, k-1) (gamma - k + 1) / k
+  for (int k = 1; k <= kEosTerms; ++k) {
+    coef *= (ph.gamma - k + 1.0) / k;
+    ph.bin[k - 1] = coef;
+  }
+  ph.rho0f = (float)(ph.p0 / (ph.R * ph.T0));
+  ph.za = (float)(ph.g / (ph.R * ph.T0));
+  ph.zb = (float)(ph.g / (ph.cp * ph.T0));
+  ph.T0f = (float)ph.T0;
+  ph.csf = (float)ph.cs;
+}
+
 // Launch helpers (host side, defined in hevi_kernels.cu).
 void launch_setup_ref(const DevView& v, const int32_t* col_order, const int32_t* col_nez,
                       cudaStream_t st);
@@ -286,11 +327,16 @@ void launch_setup_ref(const DevView& v, const int32_t* col_order, const int32_t*
 // v.tile_count), all of order `order`; ylen is the longest n + 2K among them.
 void launch_factor(const DevView& v, int order, hevi_precision prec, double lam, const double* q0,
                    int ylen, cudaStream_t st);
-// launch_solve: part 0 is the solve proper (FP64, or FP32 + two refinement
-// sweeps for every column); part 1 (FP32 + refinement only) finishes the
-// columns part 0 handed over.  Both, in this order, make one stage solve.
+// launch_solve: one stage solve, FP64 factors (plain) or FP32 factors with
+// iterative refinement, for the tiles of one order.
 void launch_solve(const DevView& v, int order, hevi_precision prec, double lam, const double* b,
-                  double* x, double tol, int max_sweeps, int ylen, int part, cudaStream_t st);
+                  double* x, double tol, int max_sweeps, int ylen, cudaStream_t st);
+// The FP32 path (hevi_np.cu): no-pivot factorisation of the equilibrated band
+// and the refined stage solve.
+void launch_factor_np(const DevView& v, int order, double lam, const double* q0, int ylen,
+                      cudaStream_t st);
+void launch_solve_np(const DevView& v, int order, double lam, const double* b, double* x,
+                     double tol, int max_sweeps, int ylen, cudaStream_t st);
 void launch_apply(const DevView& v, int order, const double* x, double* y, int nonlinear,
                   cudaStream_t st);
 void launch_apply_stage(const DevView& v, int order, const double* Q, const double* H, double* E,
@@ -320,7 +366,10 @@ void launch_newton_gmres(const DevView& v, int order, const GmArgs& a, cudaStrea
 void launch_combine(int64_t count, const double* base, int nterms, const double* const* vec,
                     const double* coef, double* out, cudaStream_t st);
 void launch_reference_state(const DevView& v, double* q, cudaStream_t st);
-void upload_tables(const LglTables& t);
+// Copy the LGL tables into the constant memory of every kernel translation
+// unit (the current device); returns the first CUDA error.
+cudaError_t upload_tables(const LglTables& t);
+cudaError_t upload_tables_np(const LglTables& t);
 // The LGL tables of every order (built once on the host, FP64).
 const LglTables& lgl_tables();
 

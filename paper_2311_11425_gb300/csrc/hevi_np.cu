@@ -1,0 +1,738 @@
+// hevi_np.cu -- the FP32 path of the HEVI stage solve (sm_103a): LU
+// factorisation of the equilibrated band without pivoting, and the stage
+// solve with iterative refinement.
+//
+// The band A = I + Lambda Dcal K(q0) + Lambda G (Sec. 4.2.3, App. A.3) is
+// equilibrated with the reference-state scales S = (rho_bar, rho_bar c_s,
+// Theta_bar), A_hat = S^-1 A S, rounded to FP32 and factored A_hat = L U
+// without interchanges: L keeps K = k_l sub-diagonals and U keeps K = k_u
+// super-diagonals, so a pivot step stores 2K + 1 numbers instead of the 3K + 2
+// of partial pivoting, and neither triangular sweep has a data-dependent
+// interchange.  The refinement residual b - A x is evaluated in double-float
+// arithmetic from the FP64 point coefficients of L(q0), so the factors only
+// precondition the iteration: the solution matches the partially pivoted FP64
+// solve of the same system to the refinement tolerance.  A pivot that is
+// exactly zero marks the column SINGULAR.
+//
+// Record layout (NpBand<N>): per tile of 32 columns all forward records
+// F_j = {l_1 .. l_K}, then all backward records B_j = {1/u_jj, u_(j-1)j, ..,
+// u_(j-K)j}, each [step][float4 vector][lane][4], so one step of a tile is one
+// contiguous block and a run of steps is one bulk copy.
+#include <algorithm>
+#include <cstdio>
+
+#include "hevi_dev.cuh"
+
+namespace hevi {
+
+cudaError_t upload_tables_np(const LglTables& t) {
+  return cudaMemcpyToSymbol(c_tab, &t, sizeof(LglTables));
+}
+
+namespace {
+
+int sm_count() {
+  static int cached[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (!cached[dev]) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+      cudaGetLastError();
+      n = 1;
+    }
+    cached[dev] = n;
+  }
+  return cached[dev];
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Factorisation: one thread per row of the column's active window
+// ((K+1) rows x (K+1) columns of A_hat), GW threads per column (the power of
+// two >= K+1), 32/GW columns per warp, blocks of four warps.  Without
+// interchanges thread r always holds the rows r, r + (K+1), r + 2(K+1), ...:
+// at step j the thread holding row j publishes U's row j through shared
+// memory, the other rows form their multiplier and update their K entries in
+// registers (a[s] <- a[s+1] - l u[s+1]: the window moves one column per step),
+// and every thread assembles one entry of the column that enters the window
+// and one of the row that replaces row j.
+// ---------------------------------------------------------------------------
+template <int N>
+struct NpF {
+  using B = NpBand<N>;
+  static constexpr int K = B::K, WR = B::WR;
+  static constexpr int GW = WR <= 8 ? 8 : (WR <= 16 ? 16 : 32);  // threads per column
+  static constexpr int CPW = 32 / GW;                              // columns per warp
+  static constexpr int CPB = CPW * 4;                              // columns per block
+  static constexpr int UBW = (K + 1 + 3) / 4 * 4;                  // U row buffer: 1/u_jj, u_j,j+1..
+  static constexpr int RBW = (K + 1 + 3) / 4 * 4;                  // entering row buffer
+};
+constexpr int kGSzA = (kGSz + 3) / 4 * 4;  // coefficient table, 16-byte aligned
+
+template <int N>
+__global__ void __launch_bounds__(128) k_factor_np(DevView v, double lam, const double* q0,
+                                                   int linstride) {
+  using P = NpF<N>;
+  using B = NpBand<N>;
+  constexpr int K = P::K, WR = P::WR, GW = P::GW, FV = B::FV, BV = B::BV;
+  constexpr int NG = (N + 2) * (2 * N + 1);
+  extern __shared__ __align__(16) float np_smem[];
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int sub = lane / GW, r = lane % GW;
+  constexpr int bpt = kTile / P::CPB;  // blocks per tile
+  const int64_t tile = v.tile_begin + blockIdx.x / bpt;
+  const TileDesc t = v.tiles[tile];
+  const int cl0 = (blockIdx.x % bpt) * P::CPB;
+  float* G = np_smem;
+  for (int k = threadIdx.x; k < NG; k += blockDim.x)
+    G[k] = c_tab.gcoef[N][k / (2 * N + 1)][k % (2 * N + 1)];
+  __syncthreads();
+  if (cl0 + warp * P::CPW >= t.count) return;  // warp-uniform: no column for this warp
+  const int colw = warp * P::CPW + sub;
+  const bool active = cl0 + colw < t.count;
+  // groups past the tile's last column shadow it without writing anything
+  const int cl = active ? cl0 + colw : t.count - 1;
+  const Col c = make_col(v, t, cl, N);
+  const Phys ph = v.ph;
+  float* ubuf = np_smem + kGSzA + (int64_t)colw * (2 * P::UBW + 2 * P::RBW + 3 * linstride);
+  float* rbuf = ubuf + 2 * P::UBW;
+  float* lin32 = rbuf + 2 * P::RBW;
+  float* s32 = lin32 + linstride;   // equilibration scales S of the column's unknowns
+  float* is32 = s32 + linstride;    // and their reciprocals
+  const int n = c.n;
+  float* fb = reinterpret_cast<float*>(v.fac) + t.fac_off;  // F records
+  float* bb = fb + (int64_t)n * FV * 4 * kTile;               // B records
+  auto fidx = [&](int j, int e) { return ((int64_t)(j * FV + e / 4) * kTile + cl) * 4 + (e & 3); };
+  auto bidx = [&](int j, int e) { return ((int64_t)(j * BV + e / 4) * kTile + cl) * 4 + (e & 3); };
+  double* lin_t = tile_lin(v, t);
+  const float dzf = (float)v.col_dz[c.col];
+
+  // point coefficients of L(q0) (FP64): w, theta, c = gamma P / Theta, and the
+  // equilibration scales of the point
+  bool ok = true;
+  for (int I = r; I < c.nz; I += GW) {
+    {
+      float sc[3];
+      np_scales(ph, np_point_z<N>(dzf, I, c.nz), sc);
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        s32[3 * I + u] = sc[u];
+        is32[3 * I + u] = 1.0f / sc[u];
+      }
+    }
+    const int64_t a = c.off + 3 * I;
+    double rho, m, Th;
+    if (q0) {
+      rho = q0[a]; m = q0[a + 1]; Th = q0[a + 2];
+    } else {
+      rho = v.ref[a]; m = 0.0; Th = v.ref[a + 2];
+    }
+    double w, th, cc, dP;
+    if (!lin_coefs(ph, rho, m, Th, v.ref[a + 2], v.ref[a + 1], &w, &th, &cc, &dP,
+                   v.ithb ? v.ithb + c.off / 3 + I : nullptr)) {
+      ok = false;
+      w = th = cc = 0.0;
+    }
+    if (active) {
+      v.lin[a] = w;
+      v.lin[a + 1] = th;
+      v.lin[a + 2] = cc;
+      double* lt = lin_t + (int64_t)(3 * I) * kTile + cl;
+      lt[0] = w;
+      lt[kTile] = th;
+      lt[2 * kTile] = cc;
+    }
+    lin32[3 * I] = (float)w;
+    lin32[3 * I + 1] = (float)th;
+    lin32[3 * I + 2] = (float)cc;
+  }
+  {  // AND over the group's lanes (every lane of the warp takes part)
+    int okv = ok ? 1 : 0;
+#pragma unroll
+    for (int off = 1; off < GW; off <<= 1) okv &= __shfl_xor_sync(0xffffffffu, okv, off, GW);
+    ok = okv != 0;
+  }
+  __syncwarp();
+  const float lam_s = (float)(lam * c.s), lam_g = (float)(lam * ph.g);
+  auto entry = [&](int i, int col) -> float {  // A_hat[i][col]; 0 outside the column
+    if (i >= n || col >= n) return 0.0f;
+    return ahat_entry<N>(row_info<N>(c, is32, i), col, lin32, s32, G, lam_s, lam_g);
+  };
+
+  // initial window: thread r < WR holds row r, a[s] = A_hat[r][s]
+  float a[WR];
+#pragma unroll
+  for (int s = 0; s < WR; ++s) a[s] = (r < WR) ? entry(r, s) : 0.0f;
+
+  int info = 0;
+  int pos = r;  // position of this thread's row in the window: row j + pos
+  for (int j = 0; j < n; ++j) {
+    const int buf = j & 1;
+    float* ub = ubuf + buf * P::UBW;
+    float* rb = rbuf + buf * P::RBW;
+    const bool mine = r < WR;
+    // the row that replaces row j: A_hat[j+K+1][j+1+r], thread r = 0..K
+    if (mine) rb[r] = entry(j + K + 1, j + 1 + r);
+    // this row's entry in the column that enters the window (column j+K+1)
+    const float ecol = (mine && pos >= 1) ? entry(j + pos, j + K + 1) : 0.0f;
+    if (mine && pos == 0) {
+      const float u = a[0];
+      const bool sing = !(fabsf(u) > 0.0f) || !isfinite(u);
+      if (sing && info == 0) info = j + 1;
+      const float invd = sing ? 0.0f : 1.0f / u;
+      ub[0] = invd;
+#pragma unroll
+      for (int s = 1; s <= K; ++s) ub[s] = a[s];
+      if (active) {
+        bb[bidx(j, 0)] = invd;
+#pragma unroll
+        for (int e = K + 1; e < 4 * BV; ++e) bb[bidx(j, e)] = 0.0f;  // padding
+        for (int e = j + 1; e <= K; ++e) bb[bidx(j, e)] = 0.0f;      // rows j - e < 0
+#pragma unroll
+        for (int e = K; e < 4 * FV; ++e) fb[fidx(j, e)] = 0.0f;      // padding
+      }
+    }
+    __syncwarp();
+    if (mine && pos >= 1) {
+      const float invd = ub[0];
+      const bool live = j + pos < n;
+      const float l = live ? a[0] * invd : 0.0f;
+#pragma unroll
+      for (int s = 0; s < K; ++s) a[s] = fmaf(-l, ub[s + 1], a[s + 1]);
+      a[K] = ecol;
+      if (active) {
+        fb[fidx(j, pos - 1)] = l;
+        if (live) bb[bidx(j + pos, pos)] = ub[pos];  // u_j,j+pos: entry pos of B_(j+pos)
+      }
+    }
+    __syncwarp();
+    if (mine && pos == 0) {  // row j retires; this thread takes row j+K+1
+#pragma unroll
+      for (int s = 0; s < WR; ++s) a[s] = rb[s];
+    }
+    pos = (pos == 0) ? K : pos - 1;
+  }
+#pragma unroll
+  for (int off = 1; off < GW; off <<= 1) info = max(info, __shfl_xor_sync(0xffffffffu, info, off, GW));
+  if (r == 0 && active) {
+    const int st = !ok ? HEVI_COL_BAD_INPUT : (info ? HEVI_COL_SINGULAR : HEVI_COL_OK);
+    v.fac_status[c.col] = st;
+    if (st != HEVI_COL_OK)
+      fail(v, c.col, st);
+    else
+      v.col_status[c.col] = HEVI_COL_OK;
+    v.col_iters[c.col] = 0;
+  }
+}
+
+template <int N>
+static void launch_factor_np_n(const DevView& v, double lam, const double* q0, int ylen,
+                               cudaStream_t st) {
+  using P = NpF<N>;
+  constexpr int K = NpBand<N>::K;
+  const int nmax = ylen - 2 * K;  // longest n of these tiles
+  const int linstride = (3 * (nmax / 3) + 3) / 4 * 4;
+  const int smem = (kGSzA + P::CPB * (2 * P::UBW + 2 * P::RBW + 3 * linstride)) * (int)sizeof(float);
+  cudaFuncSetAttribute(k_factor_np<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  k_factor_np<N><<<(unsigned)(v.tile_count * (kTile / P::CPB)), 128, smem, st>>>(v, lam, q0,
+                                                                                linstride);
+}
+
+void launch_factor_np(const DevView& v, int order, double lam, const double* q0, int ylen,
+                      cudaStream_t st) {
+  switch (order) {
+    case 1: launch_factor_np_n<1>(v, lam, q0, ylen, st); break;
+    case 2: launch_factor_np_n<2>(v, lam, q0, ylen, st); break;
+    case 3: launch_factor_np_n<3>(v, lam, q0, ylen, st); break;
+    case 4: launch_factor_np_n<4>(v, lam, q0, ylen, st); break;
+    case 5: launch_factor_np_n<5>(v, lam, q0, ylen, st); break;
+    default: break;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Stage solve with FP32 factors and iterative refinement.
+//
+// A persistent kernel of one-warp blocks; each warp takes tiles of 32 columns
+// (one column per lane) in turn.  Per tile: b is read through a shared-memory
+// transpose; then sweeps (forward with L, backward with U, in FP32, the work
+// vector y in shared memory) alternate with the fused refinement pass
+// x += S y, r = b - A x, y = S^-1 r (double-float, from the FP64 point
+// coefficients of L(q0)) until every column's predicted error |d_k|^2 /
+// |d_(k-1)| is below tol |x| (or the iteration stops contracting, or
+// max_sweeps); x leaves through the transpose.  The factor records stream
+// through a shared-memory ring filled by bulk copies (one lane issues the
+// copy of a chunk of kChunk steps; completion on the slot's mbarrier).  The
+// grid keeps a few warps per SM, so the records of the tiles in flight (their
+// first sweep reads them from HBM) are still in L2 when the next sweeps read
+// them again.
+// ---------------------------------------------------------------------------
+template <int N>
+struct NpS {
+  using B = NpBand<N>;
+  static constexpr int K = B::K, WR = B::WR, FV = B::FV, BV = B::BV;
+  static constexpr int VMAX = FV > BV ? FV : BV;
+  static constexpr int C = 2;                 // steps per chunk (a power of two)
+  static constexpr int SLOT = C * VMAX * 512; // bytes per ring slot
+  static constexpr int D = 2;                 // ring slots
+  static constexpr int SLOTS_DF = (2 * N + 1) * 3 * kTile * 8;  // element_pass_df slots
+  static constexpr int RING = D * SLOT > SLOTS_DF ? D * SLOT : SLOTS_DF;
+};
+
+// Warp-uniform state of the record ring.  Chunks are numbered continuously
+// over the warp's life: chunk k sits in slot k % D and completes the phase of
+// parity (k / D) & 1 of that slot's barrier.
+struct NpRing {
+  unsigned char* buf;
+  uint64_t* bar;
+  uint32_t issued, consumed;  // chunks issued / consumed so far
+  bool ok;
+};
+
+// keep: the records will be read again (L2 evict-last), else evict-first.
+template <int N>
+__device__ __forceinline__ void np_issue(NpRing& rg, const float* src, unsigned bytes, bool drop,
+                                         bool keep, int lane) {
+  using S = NpS<N>;
+  const uint32_t k = rg.issued++;
+  if (lane == 0) {
+    uint64_t* bar = &rg.bar[k % S::D];
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(bar, bytes);
+    if (!drop)
+      bulk_g2s(rg.buf + (k % S::D) * S::SLOT, src, bytes, bar,
+               keep ? evict_last_policy() : evict_first_policy());
+  }
+}
+
+// Wait (bounded) for the next chunk; false once a wait has run out.
+template <int N>
+__device__ __forceinline__ bool np_wait(NpRing& rg) {
+  using S = NpS<N>;
+  const uint32_t k = rg.consumed;
+  bool good = rg.ok && mbar_wait(&rg.bar[k % S::D], (k / S::D) & 1u);
+  good = __all_sync(0xffffffffu, good);
+  rg.ok = good;
+  return good;
+}
+
+// After a wait ran out: wait (bounded) for the copies still in flight, then
+// re-arm every barrier so that the ring can serve the next tile.
+template <int N>
+__device__ void np_reset(NpRing& rg, int lane) {
+  using S = NpS<N>;
+  for (uint32_t k = rg.consumed; k < rg.issued; ++k) mbar_wait(&rg.bar[k % S::D], (k / S::D) & 1u);
+  __syncwarp();
+  if (lane == 0) {
+    for (int s = 0; s < S::D; ++s) {
+      asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&rg.bar[s])) : "memory");
+      mbar_init(&rg.bar[s], 1);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  rg.issued = rg.consumed = 0;
+  rg.ok = true;
+}
+
+// Forward sweep L y = y (unit lower, K sub-diagonals), the window of K+1 rows
+// in registers; ys is this lane's column of the work vector (rows kTile
+// apart), rows n .. n+K zero.  drop_step >= 0 leaves out the
+// copy of the chunk holding that step (test hook).
+template <int N>
+__device__ __forceinline__ void np_forward(NpRing& rg, const float* fb, int n, float* ys, int lane,
+                                           int drop_step, bool keep) {
+  using S = NpS<N>;
+  constexpr int K = S::K, WR = S::WR, FV = S::FV, C = S::C, D = S::D;
+  const int nch = (n + C - 1) / C;
+  auto issue = [&](int ci) {
+    const int cnt = min(C, n - ci * C);
+    np_issue<N>(rg, fb + (int64_t)ci * C * FV * 4 * kTile, (unsigned)(cnt * FV * 512),
+                drop_step >= ci * C && drop_step < ci * C + cnt, keep, lane);
+  };
+  for (int ci = 0; ci < D && ci < nch; ++ci) issue(ci);
+  float w[WR];
+#pragma unroll
+  for (int r = 0; r < WR; ++r) w[r] = ys[r * kTile];
+  for (int j0 = 0; j0 < n; j0 += WR) {
+#pragma unroll
+    for (int t = 0; t < WR; ++t) {
+      const int j = j0 + t;
+      if (j < n && rg.ok) {
+        const int k = j & (C - 1), ci = j / C;
+        if (k == 0 && !np_wait<N>(rg)) break;
+        const float4* rec =
+            reinterpret_cast<const float4*>(rg.buf + (rg.consumed % D) * S::SLOT) + k * FV * kTile +
+            lane;
+        float l[4 * FV];
+#pragma unroll
+        for (int q = 0; q < FV; ++q) {
+          const float4 x4 = rec[q * kTile];
+          l[4 * q] = x4.x; l[4 * q + 1] = x4.y; l[4 * q + 2] = x4.z; l[4 * q + 3] = x4.w;
+        }
+        const float yj = w[t];
+        ys[j * kTile] = yj;
+#pragma unroll
+        for (int r = 1; r <= K; ++r) w[(t + r) % WR] = fmaf(-l[r - 1], yj, w[(t + r) % WR]);
+        w[t] = ys[(j + WR) * kTile];
+        if (k == C - 1 || j == n - 1) {  // chunk consumed: refill its slot
+          __syncwarp();
+          rg.consumed++;
+          if (ci + D < nch) issue(ci + D);
+        }
+      }
+    }
+  }
+}
+
+// Backward sweep U x = y (K super-diagonals, column-oriented records), the
+// window of K+1 rows in registers; x overwrites y; returns |x|^2.
+template <int N>
+__device__ __forceinline__ float np_backward(NpRing& rg, const float* bb, int n, float* ys,
+                                            int lane, bool keep) {
+  using S = NpS<N>;
+  constexpr int K = S::K, WR = S::WR, BV = S::BV, C = S::C, D = S::D;
+  const int nch = (n + C - 1) / C;
+  auto issue = [&](int ci) {  // steps hi = n-1-ci C down to lo
+    const int hi = n - 1 - ci * C, lo = max(0, hi - C + 1);
+    np_issue<N>(rg, bb + (int64_t)lo * BV * 4 * kTile, (unsigned)((hi - lo + 1) * BV * 512), false,
+                keep, lane);
+  };
+  for (int ci = 0; ci < D && ci < nch; ++ci) issue(ci);
+  float w[WR];
+#pragma unroll
+  for (int cc = 0; cc < WR; ++cc) {
+    const int i = n - 1 - cc;
+    w[cc] = i >= 0 ? ys[i * kTile] : 0.0f;
+  }
+  float ss = 0.0f;
+  for (int j0 = n - 1; j0 >= 0; j0 -= WR) {
+#pragma unroll
+    for (int t = 0; t < WR; ++t) {
+      const int j = j0 - t;
+      if (j >= 0 && rg.ok) {
+        const int i = n - 1 - j, k = i & (C - 1), ci = i / C;
+        if (k == 0 && !np_wait<N>(rg)) break;
+        const int lo = max(0, n - 1 - ci * C - C + 1);
+        const float4* rec = reinterpret_cast<const float4*>(rg.buf + (rg.consumed % D) * S::SLOT) +
+                            (j - lo) * BV * kTile + lane;
+        float u[4 * BV];
+#pragma unroll
+        for (int q = 0; q < BV; ++q) {
+          const float4 x4 = rec[q * kTile];
+          u[4 * q] = x4.x; u[4 * q + 1] = x4.y; u[4 * q + 2] = x4.z; u[4 * q + 3] = x4.w;
+        }
+        const float xj = w[t] * u[0];
+        ss = fmaf(xj, xj, ss);
+        ys[j * kTile] = xj;
+#pragma unroll
+        for (int cc = 1; cc <= K; ++cc) w[(t + cc) % WR] = fmaf(-u[cc], xj, w[(t + cc) % WR]);
+        const int jn = j - WR;
+        w[t] = jn >= 0 ? ys[jn * kTile] : 0.0f;
+        if (k == C - 1 || j == 0) {
+          __syncwarp();
+          rg.consumed++;
+          if (ci + D < nch) issue(ci + D);
+        }
+      }
+    }
+  }
+  return ss;
+}
+
+// Refinement residual of the tile's columns (one per lane), point by point
+// through the element pass in double-float arithmetic:
+//   v' = S v (v = y, the last sweep's solution in the scaled variables;
+//   the product of two floats is exact as a double-float pair),
+//   r = base - A v',  A v' = v' + Lambda (Dcal[K(q0) v'] + G v'),
+// with base = b (the pair rr + zz) on the first call and the stored residual
+// rr afterwards (r_k+1 = r_k - A d_k).  Then rr = fl(r) and y = S^-1 rr, the
+// next right-hand side.  The first call keeps v in y1 (the first solution),
+// later calls add it to zz (zz = v on the call after the second sweep).  The
+// point coefficients of L(q0) are read from the tile's scratch (one contiguous
+// line per row for the warp).  Writes are predicated on w (the lanes whose
+// column goes on).
+template <int N>
+__device__ void np_residual(const double* lint, int nez, const Phys& ph, float dzf, double cs,
+                            double lam, int sweep, float* y, float* y1, float* zz, float* rr,
+                            float2* slots, int lane, bool w) {
+  const int nz = nez * N + 1;
+  const bool first = sweep == 1;
+  const double* lc0 = lint + lane;
+  const df lamd = df_from_double(lam), gd = df_from_double(ph.g), csd = df_from_double(cs);
+  auto scaled = [&](int I, float (&v)[3], df (&xp)[3], float (&sc)[3]) {
+    np_scales(ph, np_point_z<N>(dzf, I, nz), sc);
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      v[u] = y[(3 * I + u) * kTile];
+      const float p = sc[u] * v[u];
+      xp[u] = {p, fmaf(sc[u], v[u], -p)};
+    }
+  };
+  auto flux = [&](int I, df* f) {
+    const double* lc = lc0 + (int64_t)(3 * I) * kTile;
+    float v[3], sc[3];
+    df xp[3];
+    scaled(I, v, xp, sc);
+    if (w) {
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        const int i = (3 * I + u) * kTile;
+        if (first)
+          y1[i] = v[u];
+        else
+          zz[i] = sweep == 2 ? v[u] : zz[i] + v[u];
+      }
+    }
+    const df wI = df_from_double(lc[0]), thI = df_from_double(lc[kTile]),
+             cI = df_from_double(lc[2 * kTile]);
+    f[0] = xp[1];
+    // f1 = -w^2 rho + 2 w m + c Theta,  f2 = -theta w rho + theta m + w Theta
+    f[1] = df_sub(df_fma({2.0f * wI.hi, 2.0f * wI.lo}, xp[1], df_mul(cI, xp[2])),
+                  df_mul(df_mul(wI, wI), xp[0]));
+    f[2] = df_sub(df_fma(thI, xp[1], df_mul(wI, xp[2])), df_mul(df_mul(thI, wI), xp[0]));
+  };
+  auto out = [&](int I, const df* Dv) {
+    float v[3], sc[3];
+    df xp[3];
+    scaled(I, v, xp, sc);
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      const int i = (3 * I + u) * kTile;
+      const df base = first ? df{rr[i], zz[i]} : df{rr[i], 0.0f};
+      df r;
+      if (u == 1 && (I == 0 || I == nz - 1)) {
+        r = df_sub(base, xp[1]);  // identity rows: w = 0 at the ends
+      } else {
+        df ax = Dv[u];
+        if (u == 1) ax = df_fma(gd, xp[0], ax);
+        r = df_sub(base, df_fma(lamd, ax, xp[u]));
+      }
+      if (w) {
+        const float rf = __fadd_rn(r.hi, r.lo);
+        rr[i] = rf;
+        y[i] = rf * (1.0f / sc[u]);
+      }
+    }
+  };
+  element_pass_df<N>(nez, csd, slots, lane, flux, out);
+  __syncwarp();
+}
+
+// Shared memory of one solve warp: the record ring and its barriers; the
+// element pass of the residual parks its slots in the ring's memory (the ring
+// is idle between sweeps).  The tile's vectors live in its global scratch,
+// [row][lane]: the work vector y (n + K + 1 rows, the rows past n zero), the
+// first sweep's solution y1, the sum zz of the later corrections and the
+// stored residual rr; x = S (y1 + zz).
+struct NpWarpMem {
+  float2* slots;
+};
+
+// The tile's FP32 vectors after its point coefficients in the scratch.
+__device__ __forceinline__ float* np_tile_vectors(const DevView& v, const TileDesc& t) {
+  const int64_t n = 3 * ((int64_t)t.nez * t.order + 1);
+  return v.ysc + t.y_off + 2 * n * kTile;
+}
+
+// One tile: 32 columns, one per lane.
+template <int N>
+__device__ void np_solve_tile(const DevView& v, const TileDesc& t, int lane, double lam,
+                              const double* b, double* x, double tol, int max_sweeps, NpRing& rg,
+                              const NpWarpMem& wm) {
+  using S = NpS<N>;
+  constexpr int K = S::K;
+  constexpr unsigned FULL = 0xffffffffu;
+  const bool valid = lane < t.count;
+  const int nz = t.nez * N + 1, n = 3 * nz;
+  const float* fb = reinterpret_cast<const float*>(v.fac) + t.fac_off;
+  const float* bb = fb + (int64_t)n * S::FV * 4 * kTile;
+  const double* lint = tile_lin(v, t);
+  const int yr = (n + K + 1 + 3) / 4 * 4;
+  float* y = np_tile_vectors(v, t) + lane;
+  float* y1 = y + (int64_t)yr * kTile;
+  float* zz = y1 + (int64_t)n * kTile;
+  float* rr = zz + (int64_t)n * kTile;
+  Col c{};
+  bool active = false;
+  if (valid) {
+    c = make_col(v, t, lane, N);
+    if (v.fac_status[c.col] != HEVI_COL_OK) {  // no usable factors for this column
+      for (int i = 0; i < c.n; ++i) x[c.off + i] = __longlong_as_double(0x7ff8000000000000LL);
+      v.col_iters[c.col] = 0;
+      fail(v, c.col, v.fac_status[c.col]);
+    } else {
+      active = true;
+    }
+  }
+  const float dzf = valid ? (float)v.col_dz[c.col] : 1.0f;
+  const double cs = valid ? c.s : 1.0;
+  // b, read by each lane from its own column: rr + zz = b as a double-float
+  // pair, y = S^-1 b
+  const double* bc = b + (valid ? c.off : 0);
+  for (int I = 0; I < nz; ++I) {
+    float sc[3];
+    np_scales(v.ph, np_point_z<N>(dzf, I, nz), sc);
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      const int i = 3 * I + u;
+      const df bi = valid ? df_from_double(__ldg(bc + i)) : df{0.0f, 0.0f};
+      rr[i * kTile] = bi.hi;
+      zz[i * kTile] = bi.lo;
+      y[i * kTile] = __fadd_rn(bi.hi, bi.lo) * (1.0f / sc[u]);
+    }
+  }
+  for (int i = n; i <= n + K; ++i) y[i * kTile] = 0.0f;
+  __syncwarp();
+  bool ran = active;  // the lanes whose x leaves through the final transpose
+  int status = HEVI_COL_NOT_CONVERGED;
+  double dprev = 0.0, xnorm = 0.0;
+  const int drop = v.drop_copy - 1;
+  // sweeps: every lane takes part (the waits are warp-wide); the stop test,
+  // the folding of the correction and the residual act on the active lanes.
+  // Norms are 2-norms of the scaled variables (the correction |y_k| against
+  // the solution |y_1|).
+  for (int k = 1; __any_sync(FULL, active); ++k) {
+    // the first sweep's records are read again by the next sweep (keep them in L2)
+    np_forward<N>(rg, fb, n, y, lane, k == 1 ? drop : -1, k == 1);
+    float d2 = 0.0f;
+    if (rg.ok) d2 = np_backward<N>(rg, bb, n, y, lane, k == 1);
+    bool more = false;
+    if (rg.ok && active) {
+      const double dn = sqrt((double)d2);
+      bool stop = false;
+      if (k == 1) {
+        xnorm = dn;
+        if (dn <= tol * xnorm) {  // zero right-hand side, or tol >= 1: one sweep
+          stop = true;
+          status = HEVI_COL_OK;
+        }
+      } else {
+        const double pred = dn * (dn / dprev);  // error left after applying d
+        if (dn <= tol * xnorm || pred <= tol * xnorm) {
+          stop = true;
+          status = HEVI_COL_OK;
+        } else if (dn > 0.5 * dprev) {
+          stop = true;  // refinement is not contracting
+        }
+      }
+      if (k >= max_sweeps) stop = true;
+      if (stop) {  // fold this sweep's correction: x = S (y1 + zz)
+        for (int i = 0; i < n; ++i) {
+          const float yi = y[i * kTile];
+          if (k == 1) {
+            y1[i * kTile] = yi;
+            zz[i * kTile] = 0.0f;
+          } else {
+            zz[i * kTile] = k == 2 ? yi : zz[i * kTile] + yi;
+          }
+        }
+        active = false;
+        v.col_iters[c.col] = k;
+        if (status != HEVI_COL_OK)
+          fail(v, c.col, status);
+        else
+          v.col_status[c.col] = HEVI_COL_OK;
+      } else {
+        more = true;
+        dprev = dn;
+      }
+    }
+    // the columns that go on: r = base - A S y, y = S^-1 r
+    if (rg.ok && __any_sync(FULL, more))
+      np_residual<N>(lint, t.nez, v.ph, dzf, cs, lam, k, y, y1, zz, rr, wm.slots, lane, more);
+    if (!rg.ok) {  // a copy did not arrive within the wait limit
+      np_reset<N>(rg, lane);
+      if (active) {
+        for (int i = 0; i < n; ++i) x[c.off + i] = __longlong_as_double(0x7ff8000000000000LL);
+        v.col_iters[c.col] = k;
+        fail(v, c.col, HEVI_COL_WAIT_TIMEOUT);
+      }
+      ran = false;
+      active = false;
+    }
+    __syncwarp();
+  }
+  // x = S (y1 + zz), written by each lane into its own column
+  if (ran) {
+    double* xc = x + c.off;
+    for (int I = 0; I < nz; ++I) {
+      float sc[3];
+      np_scales(v.ph, np_point_z<N>(dzf, I, nz), sc);
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        const int i = 3 * I + u;
+        // S (y1 + zz) as a double-float pair on the FP32 pipes, one FP64 add
+        const df xi = df_mul(df_two_sum(y1[i * kTile], zz[i * kTile]), df{sc[u], 0.0f});
+        xc[i] = (double)xi.hi + (double)xi.lo;
+      }
+    }
+  }
+  __syncwarp();
+}
+
+template <int N>
+__global__ void __launch_bounds__(32, 16) k_solve_np(DevView v, double lam, const double* b, double* x,
+                                                 double tol, int max_sweeps) {
+  using S = NpS<N>;
+  extern __shared__ __align__(128) unsigned char np_dyn[];
+  const int lane = threadIdx.x;
+  NpRing rg;
+  rg.buf = np_dyn;
+  rg.bar = reinterpret_cast<uint64_t*>(np_dyn + S::RING);
+  rg.issued = rg.consumed = 0;
+  rg.ok = true;
+  NpWarpMem wm;
+  wm.slots = reinterpret_cast<float2*>(np_dyn);
+  if (lane == 0) {
+    for (int s = 0; s < S::D; ++s) mbar_init(&rg.bar[s], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  for (int tt = blockIdx.x; tt < v.tile_count; tt += gridDim.x) {
+    const TileDesc t = v.tiles[v.tile_begin + tt];
+    np_solve_tile<N>(v, t, lane, lam, b, x, tol, max_sweeps, rg, wm);
+  }
+}
+
+// Default resident solve warps per SM (the most that fit): the sweeps and the
+// double-float residual are chains of dependent instructions, and only many
+// warps per SM hide their latency.
+constexpr int kNpWarpsPerSm = 16;
+
+template <int N>
+static void launch_solve_np_n(const DevView& v, double lam, const double* b, double* x, double tol,
+                              int max_sweeps, int ylen, cudaStream_t st) {
+  using S = NpS<N>;
+  constexpr int K = S::K;
+  const int nmax = ylen - 2 * K;
+  (void)nmax;
+  const int smem = S::RING + S::D * 8;
+  cudaFuncSetAttribute(k_solve_np<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  int per_sm = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_np<N>, kTile, smem) !=
+          cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  per_sm = std::min(per_sm, v.solve_wps > 0 ? v.solve_wps : kNpWarpsPerSm);
+  const int grid = std::max(1, std::min(v.tile_count, per_sm * sm_count()));
+  k_solve_np<N><<<(unsigned)grid, kTile, smem, st>>>(v, lam, b, x, tol, max_sweeps);
+}
+
+void launch_solve_np(const DevView& v, int order, double lam, const double* b, double* x,
+                     double tol, int max_sweeps, int ylen, cudaStream_t st) {
+  switch (order) {
+    case 1: launch_solve_np_n<1>(v, lam, b, x, tol, max_sweeps, ylen, st); break;
+    case 2: launch_solve_np_n<2>(v, lam, b, x, tol, max_sweeps, ylen, st); break;
+    case 3: launch_solve_np_n<3>(v, lam, b, x, tol, max_sweeps, ylen, st); break;
+    case 4: launch_solve_np_n<4>(v, lam, b, x, tol, max_sweeps, ylen, st); break;
+    case 5: launch_solve_np_n<5>(v, lam, b, x, tol, max_sweeps, ylen, st); break;
+    default: break;
+  }
+}
+
+}  // namespace hevi
