@@ -153,11 +153,12 @@ hevi_status hevi_stage_solve_async(hevi_ctx* ctx, const double* rhs, double* x);
 hevi_status hevi_set_refinement(hevi_ctx* ctx, double tol, int32_t max_sweeps);
 
 /* Resident warps per SM of the HEVI_FP32_IR stage solve (1 .. 32; 0 restores
- * the default of 2).  Each warp solves tiles of 32 columns one after another;
- * few warps per SM keep the factor records of the tiles in flight in L2
- * between a tile's refinement sweeps, more warps hide more latency.  The
- * setting changes the speed, not the result.  Not a paper quantity: a
- * launch-shape control of this implementation. */
+ * the default).  Each warp solves tiles of 32 columns one after another, so a
+ * launch takes ceil(tiles / warps) rounds; by default the library takes the
+ * fewest rounds its occupancy (18 warps per SM) allows and then the fewest
+ * warps per SM that keep that many.  The setting changes the speed, not the
+ * result.  Not a paper quantity: a launch-shape control of this
+ * implementation. */
 hevi_status hevi_set_solve_warps(hevi_ctx* ctx, int32_t warps_per_sm);
 
 /* Test hook for the bounded device waits: with step >= 0 every later

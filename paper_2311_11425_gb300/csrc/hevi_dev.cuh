@@ -181,6 +181,11 @@ __device__ __forceinline__ void np_scales(const Phys& ph, float z, float (&s)[3]
   s[2] = rho * th;
 }
 
+// Prefetch the line holding p into L1 (no registers held).
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
 // cp.async (8-byte, L1-allocating) from global to shared memory, and its
 // group completion.
 __device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc) {

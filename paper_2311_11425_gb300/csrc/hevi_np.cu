@@ -282,6 +282,10 @@ struct NpS {
   static constexpr int RING = D * SLOT > SLOTS_DF ? D * SLOT : SLOTS_DF;
 };
 
+// Points per round of the loops that move a tile's vectors: their loads are
+// issued together (the warps of an SM hide the latency of one round each).
+constexpr int kPts = 4;
+
 // Warp-uniform state of the record ring.  Chunks are numbered continuously
 // over the warp's life: chunk k sits in slot k % D and completes the phase of
 // parity (k / D) & 1 of that slot's barrier.
@@ -354,9 +358,14 @@ __device__ __forceinline__ void np_forward(NpRing& rg, const float* fb, int n, f
                 drop_step >= ci * C && drop_step < ci * C + cnt, keep, lane);
   };
   for (int ci = 0; ci < D && ci < nch; ++ci) issue(ci);
-  float w[WR];
+  // w: the window (rows j .. j+K); nb: the rows that enter it next (rows
+  // j+K+1 .. j+2K+1), loaded a window ahead of use
+  float w[WR], nb[WR];
 #pragma unroll
-  for (int r = 0; r < WR; ++r) w[r] = ys[r * kTile];
+  for (int r = 0; r < WR; ++r) {
+    w[r] = ys[r * kTile];
+    nb[r] = ys[(WR + r) * kTile];
+  }
   for (int j0 = 0; j0 < n; j0 += WR) {
 #pragma unroll
     for (int t = 0; t < WR; ++t) {
@@ -377,7 +386,8 @@ __device__ __forceinline__ void np_forward(NpRing& rg, const float* fb, int n, f
         ys[j * kTile] = yj;
 #pragma unroll
         for (int r = 1; r <= K; ++r) w[(t + r) % WR] = fmaf(-l[r - 1], yj, w[(t + r) % WR]);
-        w[t] = ys[(j + WR) * kTile];
+        w[t] = nb[t];
+        nb[t] = (j + 2 * WR <= n + K) ? ys[(j + 2 * WR) * kTile] : 0.0f;
         if (k == C - 1 || j == n - 1) {  // chunk consumed: refill its slot
           __syncwarp();
           rg.consumed++;
@@ -402,11 +412,12 @@ __device__ __forceinline__ float np_backward(NpRing& rg, const float* bb, int n,
                 keep, lane);
   };
   for (int ci = 0; ci < D && ci < nch; ++ci) issue(ci);
-  float w[WR];
+  float w[WR], nb[WR];  // the window (rows j .. j-K) and the rows that enter it next
 #pragma unroll
   for (int cc = 0; cc < WR; ++cc) {
-    const int i = n - 1 - cc;
+    const int i = n - 1 - cc, i2 = i - WR;
     w[cc] = i >= 0 ? ys[i * kTile] : 0.0f;
+    nb[cc] = i2 >= 0 ? ys[i2 * kTile] : 0.0f;
   }
   float ss = 0.0f;
   for (int j0 = n - 1; j0 >= 0; j0 -= WR) {
@@ -430,8 +441,9 @@ __device__ __forceinline__ float np_backward(NpRing& rg, const float* bb, int n,
         ys[j * kTile] = xj;
 #pragma unroll
         for (int cc = 1; cc <= K; ++cc) w[(t + cc) % WR] = fmaf(-u[cc], xj, w[(t + cc) % WR]);
-        const int jn = j - WR;
-        w[t] = jn >= 0 ? ys[jn * kTile] : 0.0f;
+        w[t] = nb[t];
+        const int jn = j - 2 * WR;
+        nb[t] = jn >= 0 ? ys[jn * kTile] : 0.0f;
         if (k == C - 1 || j == 0) {
           __syncwarp();
           rg.consumed++;
@@ -474,6 +486,18 @@ __device__ void np_residual(const double* lint, int nez, const Phys& ph, float d
   };
   auto flux = [&](int I, df* f) {
     const double* lc = lc0 + (int64_t)(3 * I) * kTile;
+    {  // the rows of the point one element ahead: one line per lane
+      const int Ip = I + N;
+      if (Ip < nz) {
+        const int q = lane % 3, h = lane / 3;  // row 3 Ip + q; lanes 0-8
+        const int64_t row = 3 * Ip + q;
+        if (h == 0) prefetch_l1(y - lane + row * kTile);
+        if (h == 1) prefetch_l1(lc0 - lane + row * kTile);
+        if (h == 2) prefetch_l1(lc0 - lane + row * kTile + 16);
+        if (h == 3) prefetch_l1(rr - lane + row * kTile);
+        if (h == 4 && first) prefetch_l1(zz - lane + row * kTile);
+      }
+    }
     float v[3], sc[3];
     df xp[3];
     scaled(I, v, xp, sc);
@@ -572,17 +596,28 @@ __device__ void np_solve_tile(const DevView& v, const TileDesc& t, int lane, dou
   const double cs = valid ? c.s : 1.0;
   // b, read by each lane from its own column: rr + zz = b as a double-float
   // pair, y = S^-1 b
+  // (kPts points a round, their loads issued together)
   const double* bc = b + (valid ? c.off : 0);
-  for (int I = 0; I < nz; ++I) {
-    float sc[3];
-    np_scales(v.ph, np_point_z<N>(dzf, I, nz), sc);
+  for (int I0 = 0; I0 < nz; I0 += kPts) {
+    double bv[3 * kPts];
 #pragma unroll
-    for (int u = 0; u < 3; ++u) {
-      const int i = 3 * I + u;
-      const df bi = valid ? df_from_double(__ldg(bc + i)) : df{0.0f, 0.0f};
-      rr[i * kTile] = bi.hi;
-      zz[i * kTile] = bi.lo;
-      y[i * kTile] = __fadd_rn(bi.hi, bi.lo) * (1.0f / sc[u]);
+    for (int q = 0; q < 3 * kPts; ++q)
+      bv[q] = (valid && 3 * I0 + q < n) ? __ldg(bc + 3 * I0 + q) : 0.0;
+#pragma unroll
+    for (int p = 0; p < kPts; ++p) {
+      const int I = I0 + p;
+      if (I < nz) {
+        float sc[3];
+        np_scales(v.ph, np_point_z<N>(dzf, I, nz), sc);
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+          const int i = 3 * I + u;
+          const df bi = df_from_double(bv[3 * p + u]);
+          rr[i * kTile] = bi.hi;
+          zz[i * kTile] = bi.lo;
+          y[i * kTile] = __fadd_rn(bi.hi, bi.lo) * (1.0f / sc[u]);
+        }
+      }
     }
   }
   for (int i = n; i <= n + K; ++i) y[i * kTile] = 0.0f;
@@ -621,13 +656,25 @@ __device__ void np_solve_tile(const DevView& v, const TileDesc& t, int lane, dou
       }
       if (k >= max_sweeps) stop = true;
       if (stop) {  // fold this sweep's correction: x = S (y1 + zz)
-        for (int i = 0; i < n; ++i) {
-          const float yi = y[i * kTile];
-          if (k == 1) {
-            y1[i * kTile] = yi;
-            zz[i * kTile] = 0.0f;
-          } else {
-            zz[i * kTile] = k == 2 ? yi : zz[i * kTile] + yi;
+        for (int i0 = 0; i0 < n; i0 += 16) {
+          float yv[16], zv[16];
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            const int i = min(i0 + q, n - 1);
+            yv[q] = y[i * kTile];
+            zv[q] = k > 2 ? zz[i * kTile] : 0.0f;
+          }
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            const int i = i0 + q;
+            if (i < n) {
+              if (k == 1) {
+                y1[i * kTile] = yv[q];
+                zz[i * kTile] = 0.0f;
+              } else {
+                zz[i * kTile] = zv[q] + yv[q];
+              }
+            }
           }
         }
         active = false;
@@ -659,15 +706,27 @@ __device__ void np_solve_tile(const DevView& v, const TileDesc& t, int lane, dou
   // x = S (y1 + zz), written by each lane into its own column
   if (ran) {
     double* xc = x + c.off;
-    for (int I = 0; I < nz; ++I) {
-      float sc[3];
-      np_scales(v.ph, np_point_z<N>(dzf, I, nz), sc);
+    for (int I0 = 0; I0 < nz; I0 += kPts) {
+      float a1[3 * kPts], a2[3 * kPts];
 #pragma unroll
-      for (int u = 0; u < 3; ++u) {
-        const int i = 3 * I + u;
-        // S (y1 + zz) as a double-float pair on the FP32 pipes, one FP64 add
-        const df xi = df_mul(df_two_sum(y1[i * kTile], zz[i * kTile]), df{sc[u], 0.0f});
-        xc[i] = (double)xi.hi + (double)xi.lo;
+      for (int q = 0; q < 3 * kPts; ++q) {
+        const int i = min(3 * I0 + q, n - 1);
+        a1[q] = y1[i * kTile];
+        a2[q] = zz[i * kTile];
+      }
+#pragma unroll
+      for (int p = 0; p < kPts; ++p) {
+        const int I = I0 + p;
+        if (I < nz) {
+          float sc[3];
+          np_scales(v.ph, np_point_z<N>(dzf, I, nz), sc);
+#pragma unroll
+          for (int u = 0; u < 3; ++u) {
+            // S (y1 + zz) as a double-float pair on the FP32 pipes, one FP64 add
+            const df xi = df_mul(df_two_sum(a1[3 * p + u], a2[3 * p + u]), df{sc[u], 0.0f});
+            xc[3 * I + u] = (double)xi.hi + (double)xi.lo;
+          }
+        }
       }
     }
   }
@@ -675,7 +734,7 @@ __device__ void np_solve_tile(const DevView& v, const TileDesc& t, int lane, dou
 }
 
 template <int N>
-__global__ void __launch_bounds__(32, 16) k_solve_np(DevView v, double lam, const double* b, double* x,
+__global__ void __launch_bounds__(32, 18) k_solve_np(DevView v, double lam, const double* b, double* x,
                                                  double tol, int max_sweeps) {
   using S = NpS<N>;
   extern __shared__ __align__(128) unsigned char np_dyn[];
@@ -698,10 +757,10 @@ __global__ void __launch_bounds__(32, 16) k_solve_np(DevView v, double lam, cons
   }
 }
 
-// Default resident solve warps per SM (the most that fit): the sweeps and the
-// double-float residual are chains of dependent instructions, and only many
-// warps per SM hide their latency.
-constexpr int kNpWarpsPerSm = 16;
+// Most resident solve warps per SM (the register budget of the launch
+// bounds): the sweeps and the double-float residual are chains of dependent
+// instructions, and only many warps per SM hide their latency.
+constexpr int kNpWarpsPerSm = 18;
 
 template <int N>
 static void launch_solve_np_n(const DevView& v, double lam, const double* b, double* x, double tol,
@@ -718,8 +777,19 @@ static void launch_solve_np_n(const DevView& v, double lam, const double* b, dou
     cudaGetLastError();
     per_sm = 1;
   }
-  per_sm = std::min(per_sm, v.solve_wps > 0 ? v.solve_wps : kNpWarpsPerSm);
-  const int grid = std::max(1, std::min(v.tile_count, per_sm * sm_count()));
+  const int sms = sm_count();
+  if (v.solve_wps > 0) {
+    per_sm = std::min(per_sm, v.solve_wps);
+  } else {
+    // each warp solves whole tiles, so the launch takes ceil(tiles / warps)
+    // rounds of one tile's latency: take the fewest rounds the occupancy
+    // allows, then the fewest warps per SM that keep that many (no round
+    // partly empty)
+    per_sm = std::min(per_sm, kNpWarpsPerSm);
+    const int rounds = (v.tile_count + per_sm * sms - 1) / (per_sm * sms);
+    per_sm = std::min(per_sm, (v.tile_count + rounds * sms - 1) / (rounds * sms));
+  }
+  const int grid = std::max(1, std::min(v.tile_count, per_sm * sms));
   k_solve_np<N><<<(unsigned)grid, kTile, smem, st>>>(v, lam, b, x, tol, max_sweeps);
 }
 
