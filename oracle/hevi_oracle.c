@@ -626,18 +626,27 @@ int or_newton_gmres(int ncols, int nez, int N, const double* ztop, double lam, c
  * rebuilt in band storage and LU-factored at every iteration.
  * q holds the initial guess on entry and the root on exit.  iters[c] is the
  * number of Newton updates taken; status[c] = 0 converged, 4 singular
- * Jacobian, 5 not converged within max_iter (reading R7). */
+ * Jacobian, 5 not converged within max_iter.  Stop (reading R7; the paper
+ * gives the tolerance, not the test): after update m,
+ *   |S^-1 F(q_m)| <= rtol |S^-1 F(q_0)|  and  |S^-1 dq_m| <= rtol |S^-1 (q_m - q_0)|
+ * (the residual small against the first, and the last update small against
+ * the whole update, so that the iterate agrees with the root to about rtol in
+ * the update's norm), or |S^-1 F(q_m)| at the rounding floor of its FP64
+ * evaluation; S = (rho_bar, rho_bar c_s, Theta_bar). */
 int or_newton(int ncols, int nez, int N, const double* ztop, double lam, const double* R,
               double* q, double rtol, int max_iter, int* iters, int* status) {
   int n = 3 * (nez * N + 1), kl = 3 * (N + 1) - 1, ldab = 3 * kl + 1;
   double* ab = (double*)malloc(sizeof(double) * (size_t)ldab * n);
   double* F = (double*)malloc(sizeof(double) * n);
+  double* qi = (double*)malloc(sizeof(double) * n);
+  double* t = (double*)malloc(sizeof(double) * n);
   int* ipiv = (int*)malloc(sizeof(int) * n);
   for (int c = 0; c < ncols; ++c) {
     column_t col;
     if (column_init(&col, nez, N, ztop[c])) return 1;
     size_t o = (size_t)c * n;
     double* qc = q + o;
+    for (int i = 0; i < n; ++i) qi[i] = qc[i];
     residual_F(&col, lam, qc, R + o, F);
     double f0 = scaled_norm(&col, F);
     iters[c] = 0;
@@ -650,10 +659,13 @@ int or_newton(int ncols, int nez, int N, const double* ztop, double lam, const d
         for (int i = 0; i < n; ++i) F[i] = -F[i];
         or_gbtrs(n, kl, kl, ab, ldab, ipiv, F);
         for (int i = 0; i < n; ++i) qc[i] += F[i];
+        const double dn = scaled_norm(&col, F);
+        for (int i = 0; i < n; ++i) t[i] = qc[i] - qi[i];
+        const double un = scaled_norm(&col, t);
         iters[c] = m;
         residual_F(&col, lam, qc, R + o, F);
         double fn = scaled_norm(&col, F);
-        if (fn <= rtol * f0 || fn <= OR_NEWTON_FLOOR * scaled_norm(&col, qc)) {
+        if ((fn <= rtol * f0 && dn <= rtol * un) || fn <= OR_NEWTON_FLOOR * scaled_norm(&col, qc)) {
           status[c] = 0;
           break;
         }
@@ -663,6 +675,8 @@ int or_newton(int ncols, int nez, int N, const double* ztop, double lam, const d
   }
   free(ab);
   free(F);
+  free(qi);
+  free(t);
   free(ipiv);
   return 0;
 }
