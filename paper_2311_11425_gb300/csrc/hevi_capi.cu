@@ -183,7 +183,15 @@ struct hevi_ctx {
   int64_t ysc_floats = 0;
   // device allocations
   std::vector<void*> allocs;
-  double* lin_newton = nullptr;
+  // NHEVI-LU sequence: q0, -F and the update (state vectors); per column
+  // |S^-1 F(q0)|, convergence, iterations, status, and the status and
+  // iterations the inner factor / solve calls write; per iteration the count
+  // of columns still iterating; failure counters of the inner calls
+  double* nw_vec = nullptr;
+  double* nw_f0 = nullptr;
+  int32_t* nw_int = nullptr;
+  int32_t* nw_active = nullptr;
+  int32_t* nw_fail = nullptr;
   // NHEVI-GMRES scratch: three state vectors and per-tile Krylov storage
   double* gm_vec = nullptr;
   double* gm_tile = nullptr;
@@ -349,14 +357,92 @@ hevi_status ensure_work(hevi_ctx* c, int64_t vecs) {
   return s;
 }
 
+constexpr int kNewtonMaxIter = 1000;
+
 hevi_status ensure_newton(hevi_ctx* c) {
-  if (c->scr) return HEVI_OK;
-  hevi_status s = c->alloc(&c->lin_newton, (size_t)c->state_size);
-  if (s != HEVI_OK) return s;
-  s = c->alloc(&c->scr, (size_t)c->scr_floats);
-  if (s != HEVI_OK) return s;
-  c->v.scr = c->scr;
+  if (c->nw_vec) return HEVI_OK;
+  hevi_status s;
+  if ((s = c->alloc(&c->nw_vec, (size_t)(3 * c->state_size))) ||
+      (s = c->alloc(&c->nw_f0, (size_t)c->ncols)) ||
+      (s = c->alloc(&c->nw_int, (size_t)(5 * c->ncols))) ||
+      (s = c->alloc(&c->nw_active, (size_t)(kNewtonMaxIter + 1))) ||
+      (s = c->alloc(&c->nw_fail, (size_t)kFailSlots)))
+    return s;
   return HEVI_OK;
+}
+
+// NHEVI-LU (Sec. 4.2.3) as a sequence of launches: an F pass at the initial
+// guess, then per iteration the factorisation of J(q_m) (hevi_factor's
+// kernels with q_m as the linearisation state), the refined solve
+// J delta = -F(q_m) (hevi_stage_solve's kernels) and the F pass that applies
+// the update and takes the stop test.  The launches of an iteration do
+// nothing once no column is left iterating (a device-side count gates them),
+// so the sequence needs no host synchronisation and can be captured into a
+// graph; `sync` lets the host stop launching as soon as every column is done.
+hevi_status newton_sequence(hevi_ctx* c, double lam, double* q, const double* R, double rtol,
+                            int32_t max_iter, bool sync) {
+  hevi_status s = ensure_newton(c);
+  if (s != HEVI_OK) return s;
+  const int64_t n = c->state_size, nc = c->ncols;
+  hevi::NewtonArgs a;
+  a.lam = lam;
+  a.rtol = rtol;
+  a.max_iter = max_iter;
+  a.q = q;
+  a.R = R;
+  a.q0 = c->nw_vec;
+  a.rhs = c->nw_vec + n;
+  a.delta = c->nw_vec + 2 * n;
+  a.f0 = c->nw_f0;
+  a.conv = c->nw_int;
+  a.iters = c->nw_int + nc;
+  a.status = c->nw_int + 2 * nc;
+  // the inner factor / solve calls report into scratch, not the context
+  DevView in = c->v;
+  in.col_status = c->nw_int + 3 * nc;
+  in.col_iters = c->nw_int + 4 * nc;
+  in.fail_count = c->nw_fail;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(c->stream, &cap);
+  if (cap != cudaStreamCaptureStatusNone) sync = false;
+  cudaMemcpyAsync(c->nw_vec, q, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+  cudaMemsetAsync(c->nw_active, 0, (max_iter + 1) * sizeof(int32_t), c->stream);
+  Scope sc(c, kNewton);
+  a.iter = 0;
+  a.active_in = nullptr;
+  a.active_out = c->nw_active;
+  for_orders(c, c->v, [&](const DevView& v, int N, int, cudaStream_t sk) {
+    hevi::launch_newton_fpass(v, N, a, sk);
+  });
+  for (int m = 1; m <= max_iter; ++m) {
+    const int32_t* gate = c->nw_active + (m - 1);
+    if (sync) {
+      int32_t h = 0;
+      if (cudaMemcpyAsync(c->h_fail + kFailSlots, gate, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                          c->stream) != cudaSuccess ||
+          cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return HEVI_ERR_CUDA;
+      h = c->h_fail[kFailSlots];
+      if (h == 0) break;
+    }
+    DevView g = in;
+    g.gate = gate;
+    for_orders(c, g, [&](const DevView& v, int N, int ylen, cudaStream_t sk) {
+      hevi::launch_factor(v, N, c->prec, lam, q, ylen, sk);
+      hevi::launch_solve(v, N, c->prec, lam, a.rhs, const_cast<double*>(a.delta), c->ir_tol,
+                         c->ir_max, ylen, sk);
+    });
+    a.iter = m;
+    a.active_in = gate;
+    a.active_out = c->nw_active + m;
+    for_orders(c, c->v, [&](const DevView& v, int N, int, cudaStream_t sk) {
+      hevi::launch_newton_fpass(v, N, a, sk);
+    });
+  }
+  hevi::launch_newton_finish(c->v, a, c->stream);
+  c->launches += 1;
+  c->factored = false;  // the factors now belong to J(q), not to the last hevi_factor
+  return check_launch(c);
 }
 
 // Longest column of the context (unknowns).
@@ -525,7 +611,7 @@ hevi_status hevi_setup(hevi_ctx** out, const hevi_column_grid* grid, const hevi_
     hevi_destroy(c);
     return s;
   }
-  if (cudaMallocHost(&c->h_fail, kFailSlots * sizeof(int32_t)) != cudaSuccess) {
+  if (cudaMallocHost(&c->h_fail, (kFailSlots + 1) * sizeof(int32_t)) != cudaSuccess) {
     cudaGetLastError();
     hevi_destroy(c);
     return HEVI_ERR_OOM;
@@ -632,7 +718,11 @@ int64_t hevi_estimate_bytes(const hevi_column_grid* grid, hevi_precision precisi
               3 * ncols * 4 + kFailSlots * 4 +
               fac * esz;
   if (kind == 1) b += (2 * (int64_t)stages + 1) * state * 8;
-  if (kind == 2) b += ((int64_t)stages + 2) * state * 8 + state * 8 + scr * 4;
+  // NHEVI step: stage work vectors, then the Newton sequence's workspace
+  if (kind == 2)
+    b += ((int64_t)stages + 2) * state * 8 + 3 * state * 8 + ncols * 8 + 5 * ncols * 4 +
+         (kNewtonMaxIter + 1) * 4 + kFailSlots * 4;
+  (void)scr;
   return b;
 }
 
@@ -715,24 +805,16 @@ hevi_status hevi_newton_solve_async(hevi_ctx* c, double gamma_dt, double* state,
   if (!c || !state || !R || state == R || !(gamma_dt >= 0.0) || !(rtol >= 0.0) || max_iter < 0 ||
       max_iter > 1000)
     return HEVI_ERR_INVALID_ARG;
-  hevi_status s = ensure_newton(c);
-  if (s != HEVI_OK) return s;
-  DevView nv = c->v;
-  nv.lin = c->lin_newton;
-  {
-    Scope sc(c, kNewton);
-    for_orders(c, nv, [&](const DevView& v, int N, int ylen, cudaStream_t sk) {
-      hevi::launch_newton(v, N, gamma_dt, state, R, rtol, max_iter, ylen, sk);
-    });
-  }
-  return check_launch(c);
+  return newton_sequence(c, gamma_dt, state, R, rtol, max_iter, false);
 }
 
 hevi_status hevi_newton_solve(hevi_ctx* c, double gamma_dt, double* state, const double* R,
                               double rtol, int32_t max_iter) {
-  if (!c) return HEVI_ERR_INVALID_ARG;
+  if (!c || !state || !R || state == R || !(gamma_dt >= 0.0) || !(rtol >= 0.0) || max_iter < 0 ||
+      max_iter > 1000)
+    return HEVI_ERR_INVALID_ARG;
   reset_fail(c);
-  hevi_status s = hevi_newton_solve_async(c, gamma_dt, state, R, rtol, max_iter);
+  hevi_status s = newton_sequence(c, gamma_dt, state, R, rtol, max_iter, true);
   if (s != HEVI_OK) return s;
   return wait_status(c);
 }
@@ -968,8 +1050,6 @@ hevi_status hevi_nhevi_step(hevi_ctx* c, int32_t s, const double* A, const doubl
     });
   }
   cudaMemcpyAsync(Q, q_in, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
-  DevView nv = c->v;
-  nv.lin = c->lin_newton;
   for (int i = 1; i < s; ++i) {
     const double* vec[16];
     double coef[16];
@@ -986,12 +1066,7 @@ hevi_status hevi_nhevi_step(hevi_ctx* c, int32_t s, const double* A, const doubl
       Scope sc(c, kCombine);
       hevi::launch_combine(n, q_in, nt, vec, coef, R, c->stream);
     }
-    {
-      Scope sc(c, kNewton);
-      for_orders(c, nv, [&](const DevView& v, int N, int ylen, cudaStream_t sk) {
-        hevi::launch_newton(v, N, lam, Q, R, rtol, max_iter, ylen, sk);
-      });
-    }
+    if ((st = newton_sequence(c, lam, Q, R, rtol, max_iter, true))) return st;
     {
       Scope sc(c, kApply);
       for_orders(c, c->v, [&](const DevView& v, int N, int, cudaStream_t sk) {

@@ -130,6 +130,7 @@ struct DevView {
   int32_t* col_iters;       // [ncols]
   int32_t* fail_count;      // [1]
   int32_t solve_wps;        // resident stage-solve warps per SM (0: default)
+  const int32_t* gate;      // if set and *gate == 0, the factor and solve kernels do nothing
   int32_t drop_copy;        // test hook: > 0 = the record ring leaves out the copy of the
                             // chunk holding forward step drop_copy - 1 of a tile's first sweep
 };
@@ -363,6 +364,26 @@ struct GmArgs {
   int32_t* kits;  // per column Krylov iterations, or null
 };
 void launch_newton_gmres(const DevView& v, int order, const GmArgs& a, cudaStream_t st);
+// NHEVI-LU as a sequence of kernels (Sec. 4.2.3): an F pass (FP64) before the
+// first iteration and after each Newton update, with the band factorisation
+// of J(q_m) and the refined solve J delta = -F in between.
+struct NewtonArgs {
+  double lam, rtol;
+  int max_iter, iter;        // iter 0: the pass at the initial guess; m >= 1: after update m
+  double* q;                 // state (updated in place)
+  const double* R;
+  const double* q0;          // initial guess
+  double* rhs;               // -F(q), the next right-hand side
+  const double* delta;       // the update of iteration iter (iter >= 1)
+  double* f0;                // [ncols] |S^-1 F(q_0)|
+  int32_t* conv;             // [ncols] 0 iterating, 1 converged, 2 stopped (status says why)
+  int32_t* iters;            // [ncols]
+  int32_t* status;           // [ncols]
+  const int32_t* active_in;  // columns still iterating before this pass (null: all)
+  int32_t* active_out;       // the pass counts the columns still iterating after it
+};
+void launch_newton_fpass(const DevView& v, int order, const NewtonArgs& a, cudaStream_t st);
+void launch_newton_finish(const DevView& v, const NewtonArgs& a, cudaStream_t st);
 void launch_combine(int64_t count, const double* base, int nterms, const double* const* vec,
                     const double* coef, double* out, cudaStream_t st);
 void launch_reference_state(const DevView& v, double* q, cudaStream_t st);

@@ -360,6 +360,7 @@ __device__ void factor_column(const DevView& v, const TileDesc& t, int lane, dou
 template <int N, typename T, bool SCALED>
 __global__ void __launch_bounds__(64) k_factor(DevView v, double lam, const double* q0) {
   extern __shared__ unsigned char smem_raw[];
+  if (v.gate && *v.gate == 0) return;  // nothing left to do (Newton sequence)
   T* smem = reinterpret_cast<T*>(smem_raw);
   const int warp = threadIdx.x / kTile, lane = threadIdx.x % kTile;
   const int64_t tile = v.tile_begin + (int64_t)blockIdx.x * (blockDim.x / kTile) + warp;
@@ -562,6 +563,7 @@ __device__ void solve_fp64_column(const DevView& v, const TileDesc& t, int lane,
 template <int N>
 __global__ void __launch_bounds__(128) k_solve_fp64(DevView v, const double* b, double* x) {
   extern __shared__ unsigned char smem_raw[];
+  if (v.gate && *v.gate == 0) return;  // nothing left to do (Newton sequence)
   const int warp = threadIdx.x / kTile, lane = threadIdx.x % kTile;
   const int64_t tile = v.tile_begin + (int64_t)blockIdx.x * (blockDim.x / kTile) + warp;
   if (tile >= (int64_t)v.tile_begin + v.tile_count) return;
@@ -930,6 +932,143 @@ static void launch_newton_n(const DevView& v, double lam, double* q, const doubl
   const int smem = (slots + ylen) * blk * (int)sizeof(float);
   cudaFuncSetAttribute(k_newton<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   k_newton<N><<<col_grid(v, blk), blk, smem, st>>>(v, lam, q, R, rtol, max_iter, slots);
+}
+
+// ---------------------------------------------------------------------------
+// NHEVI-LU F pass (Sec. 4.2.3), one column per thread, FP64: for a column
+// still iterating, apply the update q += delta of iteration m (m >= 1), then
+// evaluate F(q) = q - Lambda V(q) - R, write rhs = -F (the right-hand side of
+// the next Newton system) and take the stop test
+//   |S^-1 F(q_m)| <= rtol |S^-1 F(q_0)|  and  |S^-1 delta_m| <= rtol |S^-1 (q_m - q_0)|,
+// or |S^-1 F(q_m)| at the rounding floor of its FP64 evaluation (512 eps
+// |S^-1 q_m|); S = (rho_bar, rho_bar c_s, Theta_bar).  The second half of the
+// first test (the last update small against the whole update) makes the
+// solution agree with the root to about rtol in the update's norm whatever
+// the rate of the iteration.
+// ---------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(128) k_newton_fpass(DevView v, NewtonArgs a) {
+  if (a.active_in && *a.active_in == 0) return;
+  const int warp = threadIdx.x / kTile, lane = threadIdx.x % kTile;
+  const int64_t tile = v.tile_begin + (int64_t)blockIdx.x * (blockDim.x / kTile) + warp;
+  if (tile >= (int64_t)v.tile_begin + v.tile_count) return;
+  const TileDesc t = v.tiles[tile];
+  if (lane >= t.count) return;
+  const Col c = make_col(v, t, lane, N);
+  const Phys ph = v.ph;
+  const int64_t col = c.col;
+  if (a.iter > 0) {
+    if (a.conv[col] != 0) return;
+    const int fs = v.fac_status[col];
+    if (fs != HEVI_COL_OK) {  // J(q_m) could not be factored
+      a.conv[col] = 2;
+      a.status[col] = fs;
+      return;
+    }
+  }
+  const double* ref = v.ref + c.off;
+  double* qc = a.q + c.off;
+  const double* Rc = a.R + c.off;
+  const double* q0c = a.q0 + c.off;
+  double* rc = a.rhs + c.off;
+  const double cs = ph.cs;
+  double dn = 0.0;
+  if (a.iter > 0) {
+    const double* dc = a.delta + c.off;
+    for (int i = 0; i < c.n; ++i) {
+      const double d = dc[i];
+      qc[i] += d;
+      const double sd = d / ref_scale(ref, cs, 3 * (i / 3), i % 3);
+      dn = fma(sd, sd, dn);
+    }
+    dn = sqrt(dn);
+  }
+  bool ok = true;
+  double fn = 0.0, qn = 0.0, un = 0.0;
+  auto flux = [&](int I, double* f) {
+    const double rho = qc[3 * I], m = qc[3 * I + 1], Th = qc[3 * I + 2];
+    double w, th, cc, dP;
+    if (!lin_coefs(ph, rho, m, Th, ref[3 * I + 2], ref[3 * I + 1], &w, &th, &cc, &dP,
+                   v.ithb ? v.ithb + c.off / 3 + I : nullptr)) {
+      ok = false;
+      w = dP = 0.0;
+    }
+    f[0] = m;
+    f[1] = fma(m, w, dP);
+    f[2] = Th * w;
+  };
+  auto out = [&](int I, const double* D) {
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      const int i = 3 * I + u;
+      double F;
+      if (u == 1 && (I == 0 || I == c.nz - 1)) {
+        F = qc[i] - Rc[i];
+      } else {
+        // F = q - Lambda V - R,  V = -D - g (rho - rho_bar) e_m
+        double vterm = D[u];
+        if (u == 1) vterm = fma(ph.g, qc[3 * I] - ref[3 * I], vterm);
+        F = fma(a.lam, vterm, qc[i]) - Rc[i];
+      }
+      rc[i] = -F;
+      const double isc = 1.0 / ref_scale(ref, cs, 3 * I, u);
+      const double sF = F * isc, sq = qc[i] * isc, su = (qc[i] - q0c[i]) * isc;
+      fn = fma(sF, sF, fn);
+      qn = fma(sq, sq, qn);
+      un = fma(su, su, un);
+    }
+  };
+  element_pass<N>(c, c_tab.w[N], c_tab.iw[N], flux, out);
+  fn = sqrt(fn);
+  qn = sqrt(qn);
+  un = sqrt(un);
+  const double floor_ok = kNewtonFloor * qn;
+  int cv = 0, st = HEVI_COL_OK;
+  if (!ok || !(fn == fn)) {
+    cv = 2;
+    st = HEVI_COL_BAD_INPUT;
+  } else if (a.iter == 0) {
+    a.f0[col] = fn;
+    a.iters[col] = 0;
+    if (fn == 0.0 || fn <= floor_ok) cv = 1;
+  } else {
+    a.iters[col] = a.iter;
+    if ((fn <= a.rtol * a.f0[col] && dn <= a.rtol * un) || fn <= floor_ok)
+      cv = 1;
+    else if (a.iter >= a.max_iter) {
+      cv = 2;
+      st = HEVI_COL_NOT_CONVERGED;
+    }
+  }
+  if (a.iter == 0 && a.max_iter == 0 && cv == 0) {
+    cv = 2;
+    st = HEVI_COL_NOT_CONVERGED;
+  }
+  a.conv[col] = cv;
+  a.status[col] = st;
+  if (cv == 0) atomicAdd(a.active_out, 1);
+}
+
+void launch_newton_fpass(const DevView& v, int order, const NewtonArgs& a, cudaStream_t st) {
+#define HEVI_CALL(NN) k_newton_fpass<NN><<<col_grid(v, 128), 128, 0, st>>>(v, a)
+  HEVI_ORDER_SWITCH(order, HEVI_CALL)
+#undef HEVI_CALL
+}
+
+// The per-column result of the Newton sequence into the context's status.
+__global__ void k_newton_finish(DevView v, NewtonArgs a) {
+  const int64_t col = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (col >= v.ncols) return;
+  const int st = a.status[col];
+  v.col_iters[col] = a.iters[col];
+  if (st != HEVI_COL_OK)
+    fail(v, col, st);
+  else
+    v.col_status[col] = HEVI_COL_OK;
+}
+
+void launch_newton_finish(const DevView& v, const NewtonArgs& a, cudaStream_t st) {
+  k_newton_finish<<<(unsigned)((v.ncols + 127) / 128), 128, 0, st>>>(v, a);
 }
 
 void launch_newton(const DevView& v, int order, double lam, double* q, const double* R,

@@ -80,6 +80,7 @@ __global__ void __launch_bounds__(128) k_factor_np(DevView v, double lam, const 
   constexpr int K = P::K, WR = P::WR, GW = P::GW, FV = B::FV, BV = B::BV;
   constexpr int NG = (N + 2) * (2 * N + 1);
   extern __shared__ __align__(16) float np_smem[];
+  if (v.gate && *v.gate == 0) return;  // nothing left to do (Newton sequence)
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int sub = lane / GW, r = lane % GW;
   constexpr int bpt = kTile / P::CPB;  // blocks per tile
@@ -738,6 +739,7 @@ __global__ void __launch_bounds__(32, 18) k_solve_np(DevView v, double lam, cons
                                                  double tol, int max_sweeps) {
   using S = NpS<N>;
   extern __shared__ __align__(128) unsigned char np_dyn[];
+  if (v.gate && *v.gate == 0) return;  // nothing left to do (Newton sequence)
   const int lane = threadIdx.x;
   NpRing rg;
   rg.buf = np_dyn;
