@@ -238,7 +238,7 @@ namespace {
 
 enum Kind { kSetup = 0, kFactor, kSolve, kApply, kApplyStage, kNewton, kCombine, kNumKinds };
 const char* kKindNames[kNumKinds] = {"setup", "factor", "stage_solve", "apply",
-                                     "apply_stage", "newton", "combine"};
+                                     "apply_stage", "newton_fpass", "combine"};
 
 cudaEvent_t get_event(hevi_ctx* c) {
   if (!c->ev_pool.empty()) {
@@ -407,13 +407,15 @@ hevi_status newton_sequence(hevi_ctx* c, double lam, double* q, const double* R,
   if (cap != cudaStreamCaptureStatusNone) sync = false;
   cudaMemcpyAsync(c->nw_vec, q, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
   cudaMemsetAsync(c->nw_active, 0, (max_iter + 1) * sizeof(int32_t), c->stream);
-  Scope sc(c, kNewton);
   a.iter = 0;
   a.active_in = nullptr;
   a.active_out = c->nw_active;
-  for_orders(c, c->v, [&](const DevView& v, int N, int, cudaStream_t sk) {
-    hevi::launch_newton_fpass(v, N, a, sk);
-  });
+  {
+    Scope sc(c, kNewton);
+    for_orders(c, c->v, [&](const DevView& v, int N, int, cudaStream_t sk) {
+      hevi::launch_newton_fpass(v, N, a, sk);
+    });
+  }
   for (int m = 1; m <= max_iter; ++m) {
     const int32_t* gate = c->nw_active + (m - 1);
     if (sync) {
@@ -427,17 +429,28 @@ hevi_status newton_sequence(hevi_ctx* c, double lam, double* q, const double* R,
     }
     DevView g = in;
     g.gate = gate;
-    for_orders(c, g, [&](const DevView& v, int N, int ylen, cudaStream_t sk) {
-      hevi::launch_factor(v, N, c->prec, lam, q, ylen, sk);
-      hevi::launch_solve(v, N, c->prec, lam, a.rhs, const_cast<double*>(a.delta), c->ir_tol,
-                         c->ir_max, ylen, sk);
-    });
+    {
+      Scope sc(c, kFactor);
+      for_orders(c, g, [&](const DevView& v, int N, int ylen, cudaStream_t sk) {
+        hevi::launch_factor(v, N, c->prec, lam, q, ylen, sk);
+      });
+    }
+    {
+      Scope sc(c, kSolve);
+      for_orders(c, g, [&](const DevView& v, int N, int ylen, cudaStream_t sk) {
+        hevi::launch_solve(v, N, c->prec, lam, a.rhs, const_cast<double*>(a.delta), c->ir_tol,
+                           c->ir_max, ylen, sk);
+      });
+    }
     a.iter = m;
     a.active_in = gate;
     a.active_out = c->nw_active + m;
-    for_orders(c, c->v, [&](const DevView& v, int N, int, cudaStream_t sk) {
-      hevi::launch_newton_fpass(v, N, a, sk);
-    });
+    {
+      Scope sc(c, kNewton);
+      for_orders(c, c->v, [&](const DevView& v, int N, int, cudaStream_t sk) {
+        hevi::launch_newton_fpass(v, N, a, sk);
+      });
+    }
   }
   hevi::launch_newton_finish(c->v, a, c->stream);
   c->launches += 1;
