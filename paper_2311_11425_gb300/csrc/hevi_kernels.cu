@@ -971,15 +971,29 @@ __global__ void __launch_bounds__(128) k_newton_fpass(DevView v, NewtonArgs a) {
   const double* Rc = a.R + c.off;
   const double* q0c = a.q0 + c.off;
   double* rc = a.rhs + c.off;
-  const double cs = ph.cs;
+  const double ics = rcp64(ph.cs);
+  // S^-1 of point I: 1/rho_bar, 1/(rho_bar c_s), 1/Theta_bar (one reciprocal
+  // per point, no divisions)
+  auto inv_scales = [&](int I, double (&is)[3]) {
+    const double ir = rcp64(ref[3 * I]);
+    is[0] = ir;
+    is[1] = ir * ics;
+    is[2] = v.ithb ? v.ithb[c.off / 3 + I] : rcp64(ref[3 * I + 2]);
+  };
   double dn = 0.0;
   if (a.iter > 0) {
     const double* dc = a.delta + c.off;
-    for (int i = 0; i < c.n; ++i) {
-      const double d = dc[i];
-      qc[i] += d;
-      const double sd = d / ref_scale(ref, cs, 3 * (i / 3), i % 3);
-      dn = fma(sd, sd, dn);
+    for (int I = 0; I < c.nz; ++I) {
+      double is[3];
+      inv_scales(I, is);
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        const int i = 3 * I + u;
+        const double d = dc[i];
+        qc[i] += d;
+        const double sd = d * is[u];
+        dn = fma(sd, sd, dn);
+      }
     }
     dn = sqrt(dn);
   }
@@ -998,6 +1012,8 @@ __global__ void __launch_bounds__(128) k_newton_fpass(DevView v, NewtonArgs a) {
     f[2] = Th * w;
   };
   auto out = [&](int I, const double* D) {
+    double is[3];
+    inv_scales(I, is);
 #pragma unroll
     for (int u = 0; u < 3; ++u) {
       const int i = 3 * I + u;
@@ -1011,7 +1027,7 @@ __global__ void __launch_bounds__(128) k_newton_fpass(DevView v, NewtonArgs a) {
         F = fma(a.lam, vterm, qc[i]) - Rc[i];
       }
       rc[i] = -F;
-      const double isc = 1.0 / ref_scale(ref, cs, 3 * I, u);
+      const double isc = is[u];
       const double sF = F * isc, sq = qc[i] * isc, su = (qc[i] - q0c[i]) * isc;
       fn = fma(sF, sF, fn);
       qn = fma(sq, sq, qn);

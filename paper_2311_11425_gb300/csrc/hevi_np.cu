@@ -72,6 +72,48 @@ struct NpF {
 };
 constexpr int kGSzA = (kGSz + 3) / 4 * 4;  // coefficient table, 16-byte aligned
 
+// Row data of A_hat for row i, kept in registers while a thread holds the row:
+// point I, variable v (0 rho, 1 m, 2 Theta), point class (0 bottom end, 1 top
+// end, 2 shared element boundary, 2 + k interior local index k), 1 / s_i, and
+// whether it is an identity row (m at an end: w = 0).
+struct NpRow {
+  int i, I, v, cls;
+  float isi;
+  bool ident;
+};
+template <int N>
+__device__ __forceinline__ NpRow np_row(int i, int nz, int n, const float* is32) {
+  NpRow r;
+  r.i = i;
+  r.I = i / 3;
+  r.v = i - 3 * r.I;
+  const int k = r.I % N;
+  r.cls = (r.I == 0) ? 0 : (r.I == nz - 1 ? 1 : (k == 0 ? 2 : 2 + k));
+  r.ident = (r.v == 1) && (r.I == 0 || r.I == nz - 1);
+  r.isi = i < n ? is32[i] : 0.0f;
+  return r;
+}
+
+// Entry (i, col) of A_hat = S^-1 (I + Lambda Dcal K(q0) + Lambda G) S (Sec. 4.2.3,
+// App. A.3) from the point table KS[9 J + 3 v + u] = K_vu(q0_J) s_(3J+u):
+//   delta + Lambda (2/dz) G[cls][J - I] KS / s_i + Lambda g s_(3J) / s_i [v = m, u = rho, J = I],
+// identity rows at the ends' m unknowns, 0 outside the band or the column.
+// Branch-free: the rows of a warp's threads have different v.
+template <int N>
+__device__ __forceinline__ float np_entry(const NpRow& R, int col, int n, const float* KS,
+                                          const float* s32, const float* G, float lam_s,
+                                          float lam_g) {
+  const int J = col / 3, u = col - 3 * J, dJ = J - R.I;
+  const bool live = col < n && R.i < n;
+  const bool inb = live && (unsigned)(dJ + N) <= 2u * N;
+  const float g = G[inb ? R.cls * (2 * N + 1) + dJ + N : 0];
+  const float ks = KS[inb ? 9 * J + 3 * R.v + u : 0];
+  const float one = (col == R.i && live) ? 1.0f : 0.0f;
+  float a = fmaf(inb ? lam_s * g * ks : 0.0f, R.isi, one);
+  if (R.v == 1 && u == 0 && dJ == 0 && live) a = fmaf(lam_g * s32[col], R.isi, a);
+  return R.ident ? one : a;
+}
+
 template <int N>
 __global__ void __launch_bounds__(128) k_factor_np(DevView v, double lam, const double* q0,
                                                    int linstride) {
@@ -98,10 +140,10 @@ __global__ void __launch_bounds__(128) k_factor_np(DevView v, double lam, const 
   const int cl = active ? cl0 + colw : t.count - 1;
   const Col c = make_col(v, t, cl, N);
   const Phys ph = v.ph;
-  float* ubuf = np_smem + kGSzA + (int64_t)colw * (2 * P::UBW + 2 * P::RBW + 3 * linstride);
+  float* ubuf = np_smem + kGSzA + (int64_t)colw * (2 * P::UBW + 2 * P::RBW + 5 * linstride);
   float* rbuf = ubuf + 2 * P::UBW;
-  float* lin32 = rbuf + 2 * P::RBW;
-  float* s32 = lin32 + linstride;   // equilibration scales S of the column's unknowns
+  float* KS = rbuf + 2 * P::RBW;    // per point: K_vu(q0) s_(3J+u), 9 floats
+  float* s32 = KS + 3 * linstride;  // equilibration scales S of the column's unknowns
   float* is32 = s32 + linstride;    // and their reciprocals
   const int n = c.n;
   float* fb = reinterpret_cast<float*>(v.fac) + t.fac_off;  // F records
@@ -115,14 +157,12 @@ __global__ void __launch_bounds__(128) k_factor_np(DevView v, double lam, const 
   // equilibration scales of the point
   bool ok = true;
   for (int I = r; I < c.nz; I += GW) {
-    {
-      float sc[3];
-      np_scales(ph, np_point_z<N>(dzf, I, c.nz), sc);
+    float sc[3];
+    np_scales(ph, np_point_z<N>(dzf, I, c.nz), sc);
 #pragma unroll
-      for (int u = 0; u < 3; ++u) {
-        s32[3 * I + u] = sc[u];
-        is32[3 * I + u] = 1.0f / sc[u];
-      }
+    for (int u = 0; u < 3; ++u) {
+      s32[3 * I + u] = sc[u];
+      is32[3 * I + u] = 1.0f / sc[u];
     }
     const int64_t a = c.off + 3 * I;
     double rho, m, Th;
@@ -146,9 +186,20 @@ __global__ void __launch_bounds__(128) k_factor_np(DevView v, double lam, const 
       lt[kTile] = th;
       lt[2 * kTile] = cc;
     }
-    lin32[3 * I] = (float)w;
-    lin32[3 * I + 1] = (float)th;
-    lin32[3 * I + 2] = (float)cc;
+    // K(q0) at point I (App. A.3 restricted to the vertical), scaled by the
+    // column scales: rho-flux (0, 1, 0), m-flux (-w^2, 2w, c), Theta-flux
+    // (-theta w, theta, w)
+    const float wf = (float)w, tf = (float)th, cf = (float)cc;
+    float* ks = KS + 9 * I;
+    ks[0] = 0.0f;
+    ks[1] = sc[1];
+    ks[2] = 0.0f;
+    ks[3] = -wf * wf * sc[0];
+    ks[4] = 2.0f * wf * sc[1];
+    ks[5] = cf * sc[2];
+    ks[6] = -tf * wf * sc[0];
+    ks[7] = tf * sc[1];
+    ks[8] = wf * sc[2];
   }
   {  // AND over the group's lanes (every lane of the warp takes part)
     int okv = ok ? 1 : 0;
@@ -158,15 +209,15 @@ __global__ void __launch_bounds__(128) k_factor_np(DevView v, double lam, const 
   }
   __syncwarp();
   const float lam_s = (float)(lam * c.s), lam_g = (float)(lam * ph.g);
-  auto entry = [&](int i, int col) -> float {  // A_hat[i][col]; 0 outside the column
-    if (i >= n || col >= n) return 0.0f;
-    return ahat_entry<N>(row_info<N>(c, is32, i), col, lin32, s32, G, lam_s, lam_g);
+  auto entry = [&](const NpRow& R, int col) -> float {
+    return np_entry<N>(R, col, n, KS, s32, G, lam_s, lam_g);
   };
 
   // initial window: thread r < WR holds row r, a[s] = A_hat[r][s]
+  NpRow my = np_row<N>(r < WR ? r : n, c.nz, n, is32);
   float a[WR];
 #pragma unroll
-  for (int s = 0; s < WR; ++s) a[s] = (r < WR) ? entry(r, s) : 0.0f;
+  for (int s = 0; s < WR; ++s) a[s] = (r < WR) ? entry(my, s) : 0.0f;
 
   int info = 0;
   int pos = r;  // position of this thread's row in the window: row j + pos
@@ -176,9 +227,10 @@ __global__ void __launch_bounds__(128) k_factor_np(DevView v, double lam, const 
     float* rb = rbuf + buf * P::RBW;
     const bool mine = r < WR;
     // the row that replaces row j: A_hat[j+K+1][j+1+r], thread r = 0..K
-    if (mine) rb[r] = entry(j + K + 1, j + 1 + r);
+    const NpRow nr = np_row<N>(j + K + 1, c.nz, n, is32);
+    if (mine) rb[r] = entry(nr, j + 1 + r);
     // this row's entry in the column that enters the window (column j+K+1)
-    const float ecol = (mine && pos >= 1) ? entry(j + pos, j + K + 1) : 0.0f;
+    const float ecol = (mine && pos >= 1) ? entry(my, j + K + 1) : 0.0f;
     if (mine && pos == 0) {
       const float u = a[0];
       const bool sing = !(fabsf(u) > 0.0f) || !isfinite(u);
@@ -213,6 +265,7 @@ __global__ void __launch_bounds__(128) k_factor_np(DevView v, double lam, const 
     if (mine && pos == 0) {  // row j retires; this thread takes row j+K+1
 #pragma unroll
       for (int s = 0; s < WR; ++s) a[s] = rb[s];
+      my = nr;
     }
     pos = (pos == 0) ? K : pos - 1;
   }
@@ -236,7 +289,7 @@ static void launch_factor_np_n(const DevView& v, double lam, const double* q0, i
   constexpr int K = NpBand<N>::K;
   const int nmax = ylen - 2 * K;  // longest n of these tiles
   const int linstride = (3 * (nmax / 3) + 3) / 4 * 4;
-  const int smem = (kGSzA + P::CPB * (2 * P::UBW + 2 * P::RBW + 3 * linstride)) * (int)sizeof(float);
+  const int smem = (kGSzA + P::CPB * (2 * P::UBW + 2 * P::RBW + 5 * linstride)) * (int)sizeof(float);
   cudaFuncSetAttribute(k_factor_np<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   k_factor_np<N><<<(unsigned)(v.tile_count * (kTile / P::CPB)), 128, smem, st>>>(v, lam, q0,
                                                                                 linstride);
