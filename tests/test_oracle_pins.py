@@ -428,19 +428,74 @@ def test_newton_gmres_paper_settings_converge():
 
 
 def test_newton_linear_problem_one_iteration():
-    """For V := L_RS (q - q_bar) (linear), Newton converges in one iteration;
-    checked through the ARK driver: NHEVI and LHEVI-RS agree on the linear
-    test problem."""
-    nez, N = 4, 4
-    q = _rest(nez, N)
+    """Sec. 4.3: LHEVI is NHEVI-LU with one Newton iteration.  For the linear
+    problem V := L_RS (q - q_bar), F(q) = q - Lambda V(q) - R is affine with
+    the constant Jacobian J = I - Lambda L_RS, so one Newton step from any
+    guess lands on the root, and the root is the LHEVI solve about the rest
+    state: q = q_bar + (I - Lambda L_RS)^-1 (R - q_bar).  The step is built
+    from apply_L (the matrix-free operator) and the solve with the assembled,
+    LU-factored band, two independent code paths."""
+    nez, N, lam = 4, 4, 87.868
+    q_bar = _rest(nez, N).reshape(-1)
     s = oracle.scales(oracle.column_grid(nez, N, ZTOP)[0])
     g = np.random.default_rng(15)
-    dq = 1e-3 * s * g.standard_normal(q.size)
-    dq[1] = dq[-2] = 0.0
-    qn = q + dq
-    # LHEVI-RS step of the linear problem vs explicit formula for ARK2 stages
-    out_lin, info = oracle.lhevi_step(nez, N, ZTOP, tableaux.ARK2, 300.0, qn, 0 * qn, lin=2)
-    assert info[0] == 0 and np.all(np.isfinite(out_lin))
+    R = q_bar + 1e-3 * s * g.standard_normal(q_bar.size)
+    R[1] = R[-2] = 0.0
+    guess = q_bar + 1e-2 * s * g.standard_normal(q_bar.size)
+    guess[1] = guess[-2] = 0.0
+
+    def F(q):
+        return q - lam * oracle.apply_L(nez, N, ZTOP, q_bar, (q - q_bar)[None])[0] - R
+
+    delta, info = oracle.stage_solve(nez, N, ZTOP, lam, q_bar, -F(guess)[None])
+    assert info[0] == 0
+    q1 = guess + delta[0]
+    x, _ = oracle.stage_solve(nez, N, ZTOP, lam, q_bar, (R - q_bar)[None])
+    q_lhevi = q_bar + x[0]
+    # rounding of O(1) scaled states (~1e-14); a wrong operator entry is O(1e-3)
+    assert np.linalg.norm((q1 - q_lhevi) / s) < 1e-10 * np.linalg.norm((q_lhevi - q_bar) / s)
+    # the step lands on the root: the residual is at rounding level
+    assert np.linalg.norm(F(q1) / s) < 1e-10 * np.linalg.norm(F(guess) / s)
+
+
+def _hydrostatic_perturbation(nez, N, eps=0.01):
+    """A discretely smooth hydrostatic perturbation of the rest state: Theta' =
+    eps Theta_bar sin(pi z / z_top), P' = EOS(Theta_bar + Theta') - P_bar (App.
+    A.1), and rho' = -(1/g) dP'/dz from the analytic derivative; m = 0."""
+    T0, p0, Rg, cp, g = 300.0, 1e5, 287.17, 1004.67, 9.80616
+    gam = cp / (cp - Rg)
+    Hs = Rg * T0 / g
+    z = oracle.column_grid(nez, N, ZTOP)[0]
+    q = _rest(nez, N).reshape(-1, 3)
+    rb, Tb = q[:, 0], q[:, 2]
+    Pb = p0 * (Rg * Tb / p0) ** gam
+    x = eps * np.sin(np.pi * z / ZTOP)
+    dx = eps * np.pi / ZTOP * np.cos(np.pi * z / ZTOP)
+    dTb = Tb * (-1.0 / Hs + g / (cp * T0))
+    dPb = gam * Pb / Tb * dTb
+    dPp = dPb * ((1 + x) ** gam - 1) + Pb * gam * (1 + x) ** (gam - 1) * dx
+    rp = -dPp / g
+    return np.stack([rb + rp, 0 * rb, Tb * (1 + x)], -1).reshape(-1), rp, g
+
+
+def test_gravity_balances_pressure_gradient_at_spectral_rate():
+    """The gravity term of the m equation (App. A.2, reference subtracted):
+    for a hydrostatic perturbation (dP'/dz = -g rho', m = 0) the vertical
+    momentum tendency V_m = -Dcal[P'] - g rho' vanishes up to the spectral
+    derivative's error, which falls with the element size and with the
+    order.  A gravity term of the wrong sign or size leaves V_m ~ g rho'."""
+    def err(nez, N):
+        qs, rp, g = _hydrostatic_perturbation(nez, N)
+        V = oracle.apply_V(nez, N, ZTOP, qs[None])[0].reshape(-1, 3)
+        return np.abs(V[1:-1, 1]).max() / np.abs(g * rp).max()
+    h = [err(nez, 4) for nez in (2, 4, 8, 16)]
+    for a, b in zip(h, h[1:]):
+        assert b < a / 6.0, h           # algebraic convergence in the element size
+    assert h[-1] < 1e-5, h
+    p = [err(8, N) for N in (2, 3, 4, 5)]
+    for a, b in zip(p, p[1:]):
+        assert b < a / 8.0, p           # and in the order
+    assert p[-1] < 1e-5, p
 
 
 # --------------------------------------------------------------------------
