@@ -185,13 +185,17 @@ hevi_status hevi_newton_solve_async(hevi_ctx* ctx, double gamma_dt, double* stat
  * Code that runs inside another framework's memory pool, holds an allocator
  * lock, or lives in a plugin that must not touch the device heap cannot call
  * cudaMalloc, and hevi_setup allocates.  This entry point needs no context
- * and allocates nothing: it runs the Newton kernel of hevi_newton_solve on
- * ncols uniform columns (nez elements of order `order`, model top z_top in
- * metres, default reference constants) with every piece of scratch -- column
- * table, reference state, linearisation coefficients and factor rows -- in
- * one file-scope device array of 64 MiB that every GPU which loads this
- * library holds until the process exits.  The paper has no counterpart; it
- * is a deployment variant of NHEVI-LU (hevi_newton_solve).
+ * and allocates nothing: it runs a fused NHEVI-LU Newton kernel (one column
+ * per thread; the Jacobian assembled from FP64 point coefficients, factored
+ * in FP32 with partial pivoting, stop test |S^-1 F(q_m)| <= rtol
+ * |S^-1 F(q_0)| or the FP64 rounding floor) on ncols uniform columns (nez
+ * elements of order `order`, model top z_top in metres, default reference
+ * constants) with every piece of scratch -- column table, reference state,
+ * linearisation coefficients and factor rows -- in one file-scope device
+ * array of 64 MiB that every GPU which loads this library holds until the
+ * process exits.  Its result agrees with hevi_newton_solve's to the Newton
+ * tolerance.  The paper has no counterpart; it is a deployment variant of
+ * NHEVI-LU.
  *
  * state (dev, in/out) and R (dev) use the state layout with columns packed
  * back to back (column c at offset 3 (nez order + 1) c); status and iters
@@ -201,13 +205,16 @@ hevi_status hevi_newton_solve_async(hevi_ctx* ctx, double gamma_dt, double* stat
  *
  * Limit: the scratch per column is about 3 n doubles plus n (2K+1) floats
  * (n = 3 (nez order + 1), K = 3 (order + 1) - 1), e.g. about 4,000 columns
- * of (16, 3) or (10, 4); larger ncols returns HEVI_ERR_INVALID_ARG.
+ * of (16, 3) or (10, 4); larger ncols returns HEVI_ERR_INVALID_ARG before
+ * any device work, and so does a column so long that the kernel's shared
+ * memory (per one-warp block) exceeds the device's per-block limit.
  *
  * The first call on a device looks up the array's device address and copies
- * the LGL tables to the device; make that first call before any stream
- * capture.  All calls share the array and it keeps the last call's contents:
- * calls that overlap on the GPU (other streams, other threads) race.  The
- * failure counters in it are cleared by every call. */
+ * the LGL tables to the device (under a process-wide lock); make that first
+ * call before any stream capture.  All calls share the array and it keeps
+ * the last call's contents: calls that overlap on the GPU (other streams,
+ * other threads) race.  The failure counters in it are cleared by every
+ * call. */
 hevi_status hevi_newton_solve_noalloc(int32_t nez, int32_t order, double z_top, int64_t ncols,
                                       double gamma_dt, double* state, const double* R,
                                       double rtol, int32_t max_iter, int32_t* status,

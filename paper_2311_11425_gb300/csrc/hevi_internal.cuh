@@ -344,8 +344,10 @@ void launch_apply_stage(const DevView& v, int order, const double* Q, const doub
                         double* LQ, cudaStream_t st);
 void launch_apply_rhs(const DevView& v, int order, const double* Q, const double* H, double* S,
                       cudaStream_t st);
-void launch_newton(const DevView& v, int order, double lam, double* q, const double* R,
-                   double rtol, int max_iter, int ylen, cudaStream_t st);
+// The fused one-column-per-thread Newton kernel (the allocation-free entry
+// point); returns the launch's error.
+cudaError_t launch_newton(const DevView& v, int order, double lam, double* q, const double* R,
+                          double rtol, int max_iter, int ylen, cudaStream_t st);
 // Arguments of the NHEVI-GMRES column solve (Krylov scratch per tile:
 // kstride = (kmax + 1) nmax 32, hstride = kmax (kmax + 3) / 2 32,
 // astride = (4 kmax + 1) 32 doubles).

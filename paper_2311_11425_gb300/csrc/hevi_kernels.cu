@@ -12,6 +12,7 @@
 // (double2) per record vector.
 #include <algorithm>
 #include <cstdio>
+#include <mutex>
 
 #include "hevi_dev.cuh"
 
@@ -925,13 +926,22 @@ __global__ void __launch_bounds__(64) k_newton(DevView v, double lam, double* q,
 }
 
 template <int N>
-static void launch_newton_n(const DevView& v, double lam, double* q, const double* R, double rtol,
-                            int max_iter, int ylen, cudaStream_t st) {
+static cudaError_t launch_newton_n(const DevView& v, double lam, double* q, const double* R,
+                                   double rtol, int max_iter, int ylen, cudaStream_t st) {
   const int slots = window_slots(N);
   const int blk = pick_block((slots + ylen) * (int)sizeof(float), 64);
   const int smem = (slots + ylen) * blk * (int)sizeof(float);
-  cudaFuncSetAttribute(k_newton<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = cudaFuncSetAttribute(k_newton<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
   k_newton<N><<<col_grid(v, blk), blk, smem, st>>>(v, lam, q, R, rtol, max_iter, slots);
+  return cudaGetLastError();
+}
+
+// Dynamic shared memory the fused Newton kernel needs per block at its
+// smallest block (one warp), for columns of n unknowns and order N.
+size_t newton_smem_min(int order, int64_t n) {
+  const int K = 3 * (order + 1) - 1;
+  return (size_t)((K + 1) * (2 * K + 1) + n + 2 * K) * kTile * sizeof(float);
 }
 
 // ---------------------------------------------------------------------------
@@ -1087,11 +1097,16 @@ void launch_newton_finish(const DevView& v, const NewtonArgs& a, cudaStream_t st
   k_newton_finish<<<(unsigned)((v.ncols + 127) / 128), 128, 0, st>>>(v, a);
 }
 
-void launch_newton(const DevView& v, int order, double lam, double* q, const double* R,
-                   double rtol, int max_iter, int ylen, cudaStream_t st) {
-#define HEVI_CALL(NN) launch_newton_n<NN>(v, lam, q, R, rtol, max_iter, ylen, st)
-  HEVI_ORDER_SWITCH(order, HEVI_CALL)
-#undef HEVI_CALL
+cudaError_t launch_newton(const DevView& v, int order, double lam, double* q, const double* R,
+                          double rtol, int max_iter, int ylen, cudaStream_t st) {
+  switch (order) {
+    case 1: return launch_newton_n<1>(v, lam, q, R, rtol, max_iter, ylen, st);
+    case 2: return launch_newton_n<2>(v, lam, q, R, rtol, max_iter, ylen, st);
+    case 3: return launch_newton_n<3>(v, lam, q, R, rtol, max_iter, ylen, st);
+    case 4: return launch_newton_n<4>(v, lam, q, R, rtol, max_iter, ylen, st);
+    case 5: return launch_newton_n<5>(v, lam, q, R, rtol, max_iter, ylen, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1293,11 +1308,13 @@ namespace hevi {
 namespace {
 
 constexpr size_t kNoAllocBytes = 64ull << 20;  // 64 MiB
+constexpr int kNoAllocFailSlots = 5;            // the failure counters fail() writes
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 constexpr int kMaxDevices = 64;
 void* g_noalloc_ptr[kMaxDevices] = {nullptr};
 bool g_noalloc_tables[kMaxDevices] = {false};
+std::mutex g_noalloc_init;  // the per-device lookups above, made once per device
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -1308,7 +1325,7 @@ __global__ void k_noalloc_init(DevView v, int order, int nez, double dz, int64_t
                                int32_t* col_order, int32_t* col_nez) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i == 0) {
-    for (int k = 0; k < 4; ++k) v.fail_count[k] = 0;
+    for (int k = 0; k < kNoAllocFailSlots; ++k) v.fail_count[k] = 0;
   }
   if (i <= v.ncols) col_off[i] = i * n;
   if (i < v.ncols) {
@@ -1345,12 +1362,15 @@ extern "C" hevi_status hevi_newton_solve_noalloc(int32_t nez, int32_t order, dou
     return HEVI_ERR_INVALID_ARG;
   const int64_t nz = (int64_t)nez * order + 1, n = 3 * nz;
   const int K = 3 * (order + 1) - 1, ur2 = ((2 * K + 1) + 3) / 4 * 4;
+  // every column needs at least its reference state and coefficients (2 n
+  // doubles): bound ncols before any offset arithmetic
+  if (ncols > (int64_t)(kNoAllocBytes / (2 * (size_t)n * sizeof(double)))) return HEVI_ERR_INVALID_ARG;
   const int64_t ntiles = (ncols + kTile - 1) / kTile;
   // scratch layout: fail counters | tiles | col_off | perm | col_dz | order | nez | ref | lin |
   // U records
   size_t off = 0;
   const size_t o_fail = off;
-  off = align256(off + 4 * sizeof(int32_t));
+  off = align256(off + kNoAllocFailSlots * sizeof(int32_t));
   const size_t o_tiles = off;
   off = align256(off + ntiles * sizeof(TileDesc));
   const size_t o_off = off;
@@ -1372,23 +1392,39 @@ extern "C" hevi_status hevi_newton_solve_noalloc(int32_t nez, int32_t order, dou
   if (off > kNoAllocBytes) return HEVI_ERR_INVALID_ARG;  // columns do not fit the scratch array
 
   // once per device, with that device current: the device address of the
-  // scratch array and the LGL tables in constant memory
+  // scratch array and the LGL tables in constant memory (serialised, so that
+  // first calls from several host threads do not race)
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return HEVI_ERR_CUDA;
-  if (!g_noalloc_ptr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+  unsigned char* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_init);
+    if (!g_noalloc_ptr[dev]) {
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return HEVI_ERR_CUDA;
+      }
+      g_noalloc_ptr[dev] = p;
+    }
+    if (!g_noalloc_tables[dev]) {
+      if (upload_tables(lgl_tables()) != cudaSuccess) {
+        cudaGetLastError();
+        return HEVI_ERR_CUDA;
+      }
+      g_noalloc_tables[dev] = true;
+    }
+    base = static_cast<unsigned char*>(g_noalloc_ptr[dev]);
+  }
+  // the Newton kernel's shared memory at its smallest block must fit the device
+  {
+    int smax = 0;
+    if (cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
       cudaGetLastError();
       return HEVI_ERR_CUDA;
     }
-    g_noalloc_ptr[dev] = p;
+    if (newton_smem_min(order, n) > (size_t)smax) return HEVI_ERR_INVALID_ARG;
   }
-  if (!g_noalloc_tables[dev]) {
-    upload_tables(lgl_tables());
-    if (cudaGetLastError() != cudaSuccess) return HEVI_ERR_CUDA;
-    g_noalloc_tables[dev] = true;
-  }
-  unsigned char* base = static_cast<unsigned char*>(g_noalloc_ptr[dev]);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
 
   DevView v{};
@@ -1428,8 +1464,12 @@ extern "C" hevi_status hevi_newton_solve_noalloc(int32_t nez, int32_t order, dou
                                                                    col_off, perm, col_dz,
                                                                    col_order, col_nez);
   launch_setup_ref(v, col_order, col_nez, st);
-  launch_newton(v, order, gamma_dt, state, R, rtol, max_iter, (int)(n + 2 * K), st);
-  int32_t h_fail[4] = {0, 0, 0, 0};
+  if (launch_newton(v, order, gamma_dt, state, R, rtol, max_iter, (int)(n + 2 * K), st) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return HEVI_ERR_CUDA;
+  }
+  int32_t h_fail[kNoAllocFailSlots] = {0, 0, 0, 0, 0};
   if (cudaMemcpyAsync(h_fail, v.fail_count, sizeof(h_fail), cudaMemcpyDeviceToHost, st) !=
       cudaSuccess)
     return HEVI_ERR_CUDA;
