@@ -153,13 +153,30 @@ hevi_status hevi_stage_solve_async(hevi_ctx* ctx, const double* rhs, double* x);
 hevi_status hevi_set_refinement(hevi_ctx* ctx, double tol, int32_t max_sweeps);
 
 /* Resident warps per SM of the HEVI_FP32_IR stage solve (1 .. 32; 0 restores
- * the default).  Each warp solves tiles of 32 columns one after another, so a
- * launch takes ceil(tiles / warps) rounds; by default the library takes the
- * fewest rounds its occupancy (18 warps per SM) allows and then the fewest
- * warps per SM that keep that many.  The setting changes the speed, not the
- * result.  Not a paper quantity: a launch-shape control of this
- * implementation. */
+ * the default).  The solve is ONE persistent launch over the tiles of every
+ * polynomial order of the context: each warp takes the next tile of 32
+ * columns from a device counter, the costliest tiles (longest records) first,
+ * so that short tiles fill the end of the launch.  A launch takes about
+ * ceil(tiles / warps) rounds; by default the library takes the fewest rounds
+ * its occupancy (18 warps per SM) allows and then the fewest warps per SM
+ * that keep that many.  The setting changes the speed, not the result.  Not a
+ * paper quantity: a launch-shape control of this implementation. */
 hevi_status hevi_set_solve_warps(hevi_ctx* ctx, int32_t warps_per_sm);
+
+/* Launch-shape autotuner of the HEVI_FP32_IR stage solve (not a paper
+ * quantity).  After hevi_factor, solves A x = rhs (rhs, x: device, state
+ * layout, distinct) `reps` times (1 .. 1000) at the default launch shape and at
+ * every count of resident warps per SM from 1 to the kernel's occupancy
+ * limit, each after one untimed solve, timed with CUDA events on the
+ * context's stream; keeps the fastest count (a larger count must win by more
+ * than 1%) as if set by hevi_set_solve_warps.  Writes the choice to
+ * *warps_per_sm, the mean time of one solve at it to *ms and at the default
+ * shape to *ms_default (ms; any of the three may be null).  x holds the
+ * solution afterwards.  HEVI_ERR_INVALID_ARG for an FP64 context (its launch
+ * shape is fixed), without factors, with bad arguments or while the stream is
+ * being captured; HEVI_ERR_CUDA on a CUDA error.  Synchronises the stream. */
+hevi_status hevi_autotune_solve(hevi_ctx* ctx, const double* rhs, double* x, int32_t reps,
+                                int32_t* warps_per_sm, double* ms, double* ms_default);
 
 /* Test hook for the bounded device waits: with step >= 0 every later
  * HEVI_FP32_IR stage solve announces, but does not issue, the asynchronous

@@ -81,6 +81,7 @@ def load(build: bool = False):
         "hevi_set_refinement": (_I32, [_P, _D, _I32]),
         "hevi_test_drop_record_copy": (_I32, [_P, _I32]),
         "hevi_set_solve_warps": (_I32, [_P, _I32]),
+        "hevi_autotune_solve": (_I32, [_P, _P, _P, _I32, ctypes.POINTER(_I32), DP, DP]),
         "hevi_newton_solve": (_I32, [_P, _D, _P, _P, _D, _I32]),
         "hevi_newton_solve_async": (_I32, [_P, _D, _P, _P, _D, _I32]),
         "hevi_apply_Lv": (_I32, [_P, _P, _P, ctypes.c_int]),
@@ -355,6 +356,16 @@ class Context:
 
     def hevi_set_solve_warps(self, warps_per_sm: int):
         _check(self._lib.hevi_set_solve_warps(self._h, int(warps_per_sm)), "hevi_set_solve_warps")
+
+    def hevi_autotune_solve(self, rhs, x=None, reps: int = 3):
+        """Times the FP32 stage solve at each launch shape and keeps the
+        fastest; returns (warps_per_sm, ms, ms_default)."""
+        x = self.empty() if x is None else x
+        w, ms, md = _I32(0), ctypes.c_double(0.0), ctypes.c_double(0.0)
+        _check(self._lib.hevi_autotune_solve(self._h, self._v(rhs), self._v(x), int(reps),
+                                             ctypes.byref(w), ctypes.byref(ms), ctypes.byref(md)),
+               "hevi_autotune_solve")
+        return int(w.value), float(ms.value), float(md.value)
 
     def hevi_test_drop_record_copy(self, step: int):
         """Test hook: leave out one record copy per tile so that the solve's

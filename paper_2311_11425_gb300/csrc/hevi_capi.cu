@@ -174,6 +174,11 @@ struct hevi_ctx {
   // tiles of each order N occupy [order_begin[N], order_begin[N] + order_count[N])
   int32_t order_begin[kMaxOrder + 1] = {0}, order_count[kMaxOrder + 1] = {0};
   int order_ylen[kMaxOrder + 1] = {0};
+  // FP32 stage solve: the tiles in decreasing cost (records per tile) for the
+  // single launch over all orders (null with one order: tiles in place), and
+  // the launch's tile counter
+  int32_t* d_tile_list = nullptr;
+  int32_t* d_tile_next = nullptr;
   double lam = 0.0;
   bool factored = false;
   double ir_tol = 1e-11;
@@ -310,6 +315,7 @@ void for_orders(hevi_ctx* c, const DevView& base, F&& f) {
     DevView v = base;
     v.tile_begin = c->order_begin[N];
     v.tile_count = c->order_count[N];
+    v.tile_list = nullptr;
     cudaStream_t sk = c->stream;
     if (fork) {
       sk = c->aux[N];
@@ -322,6 +328,26 @@ void for_orders(hevi_ctx* c, const DevView& base, F&& f) {
     }
     c->launches += 1;
   }
+}
+
+// One stage solve x = A^-1 b over every tile.  The FP32 path is a single
+// persistent launch whose warps take the tiles of all orders, longest first,
+// from a shared counter; the FP64 path launches per order.
+void stage_solve_all(hevi_ctx* c, const DevView& base, double lam, const double* b, double* x) {
+  if (c->prec == HEVI_FP32_IR) {
+    DevView v = base;
+    v.tile_begin = 0;
+    v.tile_count = (int32_t)c->ntiles;
+    v.tile_list = c->d_tile_list;
+    v.tile_next = c->d_tile_next;
+    hevi::launch_solve_np(v, c->norders > 1 ? 0 : c->max_order, c->max_order, lam, b, x,
+                          c->ir_tol, c->ir_max, c->stream);
+    c->launches += 1;
+    return;
+  }
+  for_orders(c, base, [&](const DevView& v, int N, int ylen, cudaStream_t sk) {
+    hevi::launch_solve(v, N, c->prec, lam, b, x, c->ir_tol, c->ir_max, ylen, sk);
+  });
 }
 
 void reset_fail(hevi_ctx* c) {
@@ -437,10 +463,7 @@ hevi_status newton_sequence(hevi_ctx* c, double lam, double* q, const double* R,
     }
     {
       Scope sc(c, kSolve);
-      for_orders(c, g, [&](const DevView& v, int N, int ylen, cudaStream_t sk) {
-        hevi::launch_solve(v, N, c->prec, lam, a.rhs, const_cast<double*>(a.delta), c->ir_tol,
-                           c->ir_max, ylen, sk);
-      });
+      stage_solve_all(c, g, lam, a.rhs, const_cast<double*>(a.delta));
     }
     a.iter = m;
     a.active_in = gate;
@@ -618,7 +641,7 @@ hevi_status hevi_setup(hevi_ctx** out, const hevi_column_grid* grid, const hevi_
       (s = c->alloc(&c->v.ithb, c->state_size / 3)) ||
       (s = precision == HEVI_FP32_IR ? c->alloc(&c->v.ysc, c->ysc_floats) : HEVI_OK) ||
       (s = c->alloc(&d_fs, ncols)) || (s = c->alloc(&d_cs, ncols)) || (s = c->alloc(&d_it, ncols)) ||
-      (s = c->alloc(&d_fail, kFailSlots)) ||
+      (s = c->alloc(&d_fail, kFailSlots)) || (s = c->alloc(&c->d_tile_next, 1)) ||
       (s = precision == HEVI_FP64 ? c->alloc((double**)&d_fac, c->fac_elems)
                                   : c->alloc((float**)&d_fac, c->fac_elems))) {
     hevi_destroy(c);
@@ -631,6 +654,21 @@ hevi_status hevi_setup(hevi_ctx** out, const hevi_column_grid* grid, const hevi_
   }
   for (int N = 1; N <= kMaxOrder; ++N) c->norders += c->order_count[N] ? 1 : 0;
   if (c->norders > 1) {
+    // the single-launch solve takes the costliest tiles first, so that the
+    // short ones fill the end of the launch
+    std::vector<int32_t> list(c->ntiles);
+    for (int64_t i = 0; i < c->ntiles; ++i) list[i] = (int32_t)i;
+    auto cost = [&](int32_t i) {
+      const TileDesc& t = c->h_tiles[i];
+      return 3 * ((int64_t)t.nez * t.order + 1) * (int64_t)hevi::np_record_floats(t.order);
+    };
+    std::stable_sort(list.begin(), list.end(),
+                     [&](int32_t a, int32_t b) { return cost(a) > cost(b); });
+    if ((s = c->alloc(&c->d_tile_list, c->ntiles))) {
+      hevi_destroy(c);
+      return s;
+    }
+    cudaMemcpy(c->d_tile_list, list.data(), c->ntiles * sizeof(int32_t), cudaMemcpyHostToDevice);
     bool ok = cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming) == cudaSuccess;
     for (int N = 1; N <= kMaxOrder && ok; ++N) {
       if (!c->order_count[N]) continue;
@@ -665,6 +703,7 @@ hevi_status hevi_setup(hevi_ctx** out, const hevi_column_grid* grid, const hevi_
   c->v.col_status = d_cs;
   c->v.col_iters = d_it;
   c->v.fail_count = d_fail;
+  c->v.tile_next = c->d_tile_next;
   hevi::launch_setup_ref(c->v, d_order, d_nez, c->stream);
   c->launches += 1;
   if (cudaStreamSynchronize(c->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
@@ -713,9 +752,11 @@ int64_t hevi_estimate_bytes(const hevi_column_grid* grid, hevi_precision precisi
   // the same sizes as hevi_setup: tiles of up to 32 columns of one class
   const int64_t ncols = grid->ncols;
   int64_t state = 0, ntiles = 0, fac = 0, scr = 0, ysc = 0;
+  bool has_order[kMaxOrder + 1] = {false};
   for (int c = 0; c < grid->nclasses; ++c) {
     if (!count[c]) continue;
     const int N = grid->classes[c].order;
+    has_order[N] = true;
     const int64_t n = 3 * ((int64_t)grid->classes[c].nez * N + 1);
     const int64_t tiles = (count[c] + kTile - 1) / kTile;
     state += n * count[c];
@@ -728,8 +769,12 @@ int64_t hevi_estimate_bytes(const hevi_column_grid* grid, hevi_precision precisi
   int64_t b = (ncols + 1) * 8 + 3 * ncols * 4 + ncols * 8 + 2 * state * 8 +
               ntiles * (int64_t)sizeof(TileDesc) + (state / 3) * 8 +
               (precision == HEVI_FP32_IR ? ysc * 4 : 0) +
-              3 * ncols * 4 + kFailSlots * 4 +
+              3 * ncols * 4 + kFailSlots * 4 + 4 +
               fac * esz;
+  // the single-launch solve's tile list when several orders are present
+  int norders = 0;
+  for (int N = 1; N <= kMaxOrder; ++N) norders += has_order[N] ? 1 : 0;
+  if (norders > 1) b += ntiles * 4;
   if (kind == 1) b += (2 * (int64_t)stages + 1) * state * 8;
   // NHEVI step: stage work vectors, then the Newton sequence's workspace
   if (kind == 2)
@@ -798,11 +843,58 @@ hevi_status hevi_stage_solve_async(hevi_ctx* c, const double* rhs, double* x) {
   if (!c || !rhs || !x || rhs == x || !c->factored) return HEVI_ERR_INVALID_ARG;
   {
     Scope sc(c, kSolve);
-    for_orders(c, c->v, [&](const DevView& v, int N, int ylen, cudaStream_t sk) {
-      hevi::launch_solve(v, N, c->prec, c->lam, rhs, x, c->ir_tol, c->ir_max, ylen, sk);
-    });
+    stage_solve_all(c, c->v, c->lam, rhs, x);
   }
   return check_launch(c);
+}
+
+hevi_status hevi_autotune_solve(hevi_ctx* c, const double* rhs, double* x, int32_t reps,
+                                int32_t* warps_per_sm, double* ms, double* ms_default) {
+  if (!c || !rhs || !x || rhs == x || !c->factored || c->prec != HEVI_FP32_IR || reps < 1 ||
+      reps > 1000)
+    return HEVI_ERR_INVALID_ARG;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(c->stream, &cap);
+  if (cap != cudaStreamCaptureStatusNone) return HEVI_ERR_INVALID_ARG;
+  cudaEvent_t e0 = get_event(c), e1 = get_event(c);
+  const int32_t saved = c->v.solve_wps;
+  // mean time of one solve with the given warps per SM (0: default shape)
+  auto time_at = [&](int32_t w, float* t) {
+    c->v.solve_wps = w;
+    stage_solve_all(c, c->v, c->lam, rhs, x);
+    cudaEventRecord(e0, c->stream);
+    for (int r = 0; r < reps; ++r) stage_solve_all(c, c->v, c->lam, rhs, x);
+    cudaEventRecord(e1, c->stream);
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(t, e0, e1) != cudaSuccess)
+      return false;
+    *t /= (float)reps;
+    return true;
+  };
+  reset_fail(c);
+  bool ok = true;
+  float t_default = 0.f, best = 0.f;
+  int32_t best_w = 0;
+  ok = time_at(0, &t_default);
+  const int maxw = hevi::solve_np_max_warps_per_sm(c->norders > 1 ? 0 : c->max_order, c->max_order);
+  for (int32_t w = 1; ok && w <= maxw; ++w) {
+    float t = 0.f;
+    ok = time_at(w, &t);
+    if (ok && (best_w == 0 || t < 0.99f * best)) {
+      best = t;
+      best_w = w;
+    }
+  }
+  c->ev_pool.push_back(e0);
+  c->ev_pool.push_back(e1);
+  if (!ok || cudaGetLastError() != cudaSuccess) {
+    c->v.solve_wps = saved;
+    return HEVI_ERR_CUDA;
+  }
+  c->v.solve_wps = best_w;
+  if (warps_per_sm) *warps_per_sm = best_w;
+  if (ms) *ms = best;
+  if (ms_default) *ms_default = t_default;
+  return HEVI_OK;
 }
 
 hevi_status hevi_stage_solve(hevi_ctx* c, const double* rhs, double* x) {
@@ -1005,9 +1097,7 @@ hevi_status hevi_lhevi_step(hevi_ctx* c, int32_t s, const double* A, const doubl
     }
     {
       Scope sc(c, kSolve);
-      for_orders(c, c->v, [&](const DevView& v, int N, int ylen, cudaStream_t sk) {
-        hevi::launch_solve(v, N, c->prec, lam, rhs, Qi, c->ir_tol, c->ir_max, ylen, sk);
-      });
+      stage_solve_all(c, c->v, lam, rhs, Qi);
     }
     nt = 0;
     for (int j = 0; j < i; ++j) {

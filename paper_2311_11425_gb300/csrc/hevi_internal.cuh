@@ -120,8 +120,10 @@ struct DevView {
   double* lin;              // state layout: (w0, theta0, c0 = gamma P0 / Theta0)
   const TileDesc* tiles;
   int32_t ntiles;
-  int32_t tile_begin;       // tiles [tile_begin, tile_begin + tile_count) of one order
-  int32_t tile_count;
+  int32_t tile_begin;       // tiles [tile_begin, tile_begin + tile_count) of one order, or
+  int32_t tile_count;       // entries of tile_list (the single-launch FP32 stage solve)
+  const int32_t* tile_list; // if set: tile indices in decreasing column length (FP32 solve)
+  int32_t* tile_next;       // [1] next tile to take (FP32 solve; zeroed before each launch)
   void* fac;                // factor records (float or double)
   float* scr;               // Newton scratch (U records)
   float* ysc;               // per tile: FP64 point coefficients of L(q0), [row][lane] (FP32 path)
@@ -336,8 +338,14 @@ void launch_solve(const DevView& v, int order, hevi_precision prec, double lam, 
 // and the refined stage solve.
 void launch_factor_np(const DevView& v, int order, double lam, const double* q0, int ylen,
                       cudaStream_t st);
-void launch_solve_np(const DevView& v, int order, double lam, const double* b, double* x,
-                     double tol, int max_sweeps, int ylen, cudaStream_t st);
+// launch_solve_np: one persistent launch over the tiles [tile_begin,
+// tile_begin + tile_count) (or, with tile_list set, over the tiles
+// tile_list[tile_begin ..]); order = N when every tile has order N, else 0
+// with nmax the largest order among them.  v.tile_next must be device memory.
+void launch_solve_np(const DevView& v, int order, int nmax, double lam, const double* b,
+                     double* x, double tol, int max_sweeps, cudaStream_t st);
+// Most stage-solve warps per SM the FP32 kernel's resources allow.
+int solve_np_max_warps_per_sm(int order, int nmax);
 void launch_apply(const DevView& v, int order, const double* x, double* y, int nonlinear,
                   cudaStream_t st);
 void launch_apply_stage(const DevView& v, int order, const double* Q, const double* H, double* E,

@@ -594,7 +594,7 @@ static void launch_solve_n(const DevView& v, const double* b, double* x, int yle
 void launch_solve(const DevView& v, int order, hevi_precision prec, double lam, const double* b,
                   double* x, double tol, int max_sweeps, int ylen, cudaStream_t st) {
   if (prec == HEVI_FP32_IR) {  // FP32 factors + refinement (hevi_np.cu)
-    launch_solve_np(v, order, lam, b, x, tol, max_sweeps, ylen, st);
+    launch_solve_np(v, order, order, lam, b, x, tol, max_sweeps, st);
     return;
   }
   switch (order) {

@@ -324,16 +324,26 @@ void launch_factor_np(const DevView& v, int order, double lam, const double* q0,
 // first sweep reads them from HBM) are still in L2 when the next sweeps read
 // them again.
 // ---------------------------------------------------------------------------
+// Record ring: D slots of C steps' records each.  A launch lays the ring out
+// for the largest order among its tiles (the slot holds the larger of F_j
+// and B_j, BV >= FV), so that one ring serves tiles of every smaller order;
+// the same bytes hold element_pass_df's slots before the sweeps.
+constexpr int kNpC = 2;  // steps per chunk (a power of two)
+constexpr int kNpD = 2;  // ring slots
+__host__ __device__ constexpr int np_slot_bytes(int n) {
+  return kNpC * ((3 * (n + 1) - 1 + 1 + 3) / 4) * 512;
+}
+__host__ __device__ constexpr int np_ring_bytes(int n) {
+  return kNpD * np_slot_bytes(n) > (2 * n + 1) * 3 * kTile * 8 ? kNpD * np_slot_bytes(n)
+                                                                : (2 * n + 1) * 3 * kTile * 8;
+}
 template <int N>
 struct NpS {
   using B = NpBand<N>;
   static constexpr int K = B::K, WR = B::WR, FV = B::FV, BV = B::BV;
-  static constexpr int VMAX = FV > BV ? FV : BV;
-  static constexpr int C = 2;                 // steps per chunk (a power of two)
-  static constexpr int SLOT = C * VMAX * 512; // bytes per ring slot
-  static constexpr int D = 2;                 // ring slots
-  static constexpr int SLOTS_DF = (2 * N + 1) * 3 * kTile * 8;  // element_pass_df slots
-  static constexpr int RING = D * SLOT > SLOTS_DF ? D * SLOT : SLOTS_DF;
+  static constexpr int C = kNpC, D = kNpD;
+  static_assert(C * (FV > BV ? FV : BV) * 512 <= np_slot_bytes(N), "ring slot too small");
+  static_assert((2 * N + 1) * 3 * kTile * 8 <= np_ring_bytes(N), "element slots do not fit");
 };
 
 // Points per round of the loops that move a tile's vectors: their loads are
@@ -346,6 +356,7 @@ constexpr int kPts = 4;
 struct NpRing {
   unsigned char* buf;
   uint64_t* bar;
+  uint32_t slot;              // bytes per slot
   uint32_t issued, consumed;  // chunks issued / consumed so far
   bool ok;
 };
@@ -361,7 +372,7 @@ __device__ __forceinline__ void np_issue(NpRing& rg, const float* src, unsigned 
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     mbar_expect_tx(bar, bytes);
     if (!drop)
-      bulk_g2s(rg.buf + (k % S::D) * S::SLOT, src, bytes, bar,
+      bulk_g2s(rg.buf + (k % S::D) * rg.slot, src, bytes, bar,
                keep ? evict_last_policy() : evict_first_policy());
   }
 }
@@ -428,7 +439,7 @@ __device__ __forceinline__ void np_forward(NpRing& rg, const float* fb, int n, f
         const int k = j & (C - 1), ci = j / C;
         if (k == 0 && !np_wait<N>(rg)) break;
         const float4* rec =
-            reinterpret_cast<const float4*>(rg.buf + (rg.consumed % D) * S::SLOT) + k * FV * kTile +
+            reinterpret_cast<const float4*>(rg.buf + (rg.consumed % D) * rg.slot) + k * FV * kTile +
             lane;
         float l[4 * FV];
 #pragma unroll
@@ -482,7 +493,7 @@ __device__ __forceinline__ float np_backward(NpRing& rg, const float* bb, int n,
         const int i = n - 1 - j, k = i & (C - 1), ci = i / C;
         if (k == 0 && !np_wait<N>(rg)) break;
         const int lo = max(0, n - 1 - ci * C - C + 1);
-        const float4* rec = reinterpret_cast<const float4*>(rg.buf + (rg.consumed % D) * S::SLOT) +
+        const float4* rec = reinterpret_cast<const float4*>(rg.buf + (rg.consumed % D) * rg.slot) +
                             (j - lo) * BV * kTile + lane;
         float u[4 * BV];
 #pragma unroll
@@ -787,28 +798,53 @@ __device__ void np_solve_tile(const DevView& v, const TileDesc& t, int lane, dou
   __syncwarp();
 }
 
-template <int N>
-__global__ void __launch_bounds__(32, 18) k_solve_np(DevView v, double lam, const double* b, double* x,
-                                                 double tol, int max_sweeps) {
-  using S = NpS<N>;
+// One persistent launch solves every tile of the launch's range: each warp
+// takes the next tile from a device counter (with a tile list, in the list's
+// order: the costliest tiles first, so that short ones fill the end of the
+// launch) and solves it with the routine of its order.  NO = 1..5: every tile
+// has order NO (ring and code for that order alone); NO = 0: tiles of any
+// order up to nmax, the ring laid out for nmax.
+template <int NO>
+__global__ void __launch_bounds__(32, 18) k_solve_np(DevView v, double lam, const double* b,
+                                                     double* x, double tol, int max_sweeps,
+                                                     int nmax) {
   extern __shared__ __align__(128) unsigned char np_dyn[];
   if (v.gate && *v.gate == 0) return;  // nothing left to do (Newton sequence)
   const int lane = threadIdx.x;
+  const int nr = NO ? NO : nmax;
   NpRing rg;
   rg.buf = np_dyn;
-  rg.bar = reinterpret_cast<uint64_t*>(np_dyn + S::RING);
+  rg.bar = reinterpret_cast<uint64_t*>(np_dyn + np_ring_bytes(nr));
+  rg.slot = (uint32_t)np_slot_bytes(nr);
   rg.issued = rg.consumed = 0;
   rg.ok = true;
   NpWarpMem wm;
   wm.slots = reinterpret_cast<float2*>(np_dyn);
   if (lane == 0) {
-    for (int s = 0; s < S::D; ++s) mbar_init(&rg.bar[s], 1);
+    for (int s = 0; s < kNpD; ++s) mbar_init(&rg.bar[s], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncwarp();
-  for (int tt = blockIdx.x; tt < v.tile_count; tt += gridDim.x) {
-    const TileDesc t = v.tiles[v.tile_begin + tt];
-    np_solve_tile<N>(v, t, lane, lam, b, x, tol, max_sweeps, rg, wm);
+  while (true) {
+    int tt = 0;
+    if (lane == 0) tt = atomicAdd(v.tile_next, 1);
+    tt = __shfl_sync(0xffffffffu, tt, 0);
+    if (tt >= v.tile_count) break;
+    const int tile = v.tile_list ? v.tile_list[v.tile_begin + tt] : v.tile_begin + tt;
+    const TileDesc t = v.tiles[tile];
+    if constexpr (NO > 0) {
+      if (t.order == NO) np_solve_tile<NO>(v, t, lane, lam, b, x, tol, max_sweeps, rg, wm);
+    } else {
+      if (t.order > nr) continue;  // outside the ring's layout (not in a valid launch)
+      switch (t.order) {
+        case 1: np_solve_tile<1>(v, t, lane, lam, b, x, tol, max_sweeps, rg, wm); break;
+        case 2: np_solve_tile<2>(v, t, lane, lam, b, x, tol, max_sweeps, rg, wm); break;
+        case 3: np_solve_tile<3>(v, t, lane, lam, b, x, tol, max_sweeps, rg, wm); break;
+        case 4: np_solve_tile<4>(v, t, lane, lam, b, x, tol, max_sweeps, rg, wm); break;
+        case 5: np_solve_tile<5>(v, t, lane, lam, b, x, tol, max_sweeps, rg, wm); break;
+        default: break;
+      }
+    }
   }
 }
 
@@ -817,47 +853,52 @@ __global__ void __launch_bounds__(32, 18) k_solve_np(DevView v, double lam, cons
 // instructions, and only many warps per SM hide their latency.
 constexpr int kNpWarpsPerSm = 18;
 
-template <int N>
-static void launch_solve_np_n(const DevView& v, double lam, const double* b, double* x, double tol,
-                              int max_sweeps, int ylen, cudaStream_t st) {
-  using S = NpS<N>;
-  constexpr int K = S::K;
-  const int nmax = ylen - 2 * K;
-  (void)nmax;
-  const int smem = S::RING + S::D * 8;
-  cudaFuncSetAttribute(k_solve_np<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+using SolveNpKernel = void (*)(DevView, double, const double*, double*, double, int, int);
+
+static SolveNpKernel solve_np_kernel(int order) {
+  switch (order) {
+    case 1: return k_solve_np<1>;
+    case 2: return k_solve_np<2>;
+    case 3: return k_solve_np<3>;
+    case 4: return k_solve_np<4>;
+    case 5: return k_solve_np<5>;
+    default: return k_solve_np<0>;
+  }
+}
+
+int solve_np_max_warps_per_sm(int order, int nmax) {
+  const int nr = order ? order : nmax;
+  const int smem = np_ring_bytes(nr) + kNpD * 8;
+  SolveNpKernel k = solve_np_kernel(order);
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   int per_sm = 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_np<N>, kTile, smem) !=
-          cudaSuccess || per_sm < 1) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kTile, smem) != cudaSuccess ||
+      per_sm < 1) {
     cudaGetLastError();
     per_sm = 1;
   }
+  return std::min(per_sm, kNpWarpsPerSm);
+}
+
+void launch_solve_np(const DevView& v, int order, int nmax, double lam, const double* b,
+                     double* x, double tol, int max_sweeps, cudaStream_t st) {
+  if (order < 0 || order > kMaxOrder || nmax < 1 || nmax > kMaxOrder) return;
+  const int nr = order ? order : nmax;
+  const int smem = np_ring_bytes(nr) + kNpD * 8;
+  int per_sm = solve_np_max_warps_per_sm(order, nmax);
   const int sms = sm_count();
   if (v.solve_wps > 0) {
     per_sm = std::min(per_sm, v.solve_wps);
   } else {
-    // each warp solves whole tiles, so the launch takes ceil(tiles / warps)
-    // rounds of one tile's latency: take the fewest rounds the occupancy
-    // allows, then the fewest warps per SM that keep that many (no round
-    // partly empty)
-    per_sm = std::min(per_sm, kNpWarpsPerSm);
+    // each warp solves whole tiles, so the launch takes about ceil(tiles /
+    // warps) rounds of one tile's latency: take the fewest rounds the
+    // occupancy allows, then the fewest warps per SM that keep that many
     const int rounds = (v.tile_count + per_sm * sms - 1) / (per_sm * sms);
     per_sm = std::min(per_sm, (v.tile_count + rounds * sms - 1) / (rounds * sms));
   }
   const int grid = std::max(1, std::min(v.tile_count, per_sm * sms));
-  k_solve_np<N><<<(unsigned)grid, kTile, smem, st>>>(v, lam, b, x, tol, max_sweeps);
-}
-
-void launch_solve_np(const DevView& v, int order, double lam, const double* b, double* x,
-                     double tol, int max_sweeps, int ylen, cudaStream_t st) {
-  switch (order) {
-    case 1: launch_solve_np_n<1>(v, lam, b, x, tol, max_sweeps, ylen, st); break;
-    case 2: launch_solve_np_n<2>(v, lam, b, x, tol, max_sweeps, ylen, st); break;
-    case 3: launch_solve_np_n<3>(v, lam, b, x, tol, max_sweeps, ylen, st); break;
-    case 4: launch_solve_np_n<4>(v, lam, b, x, tol, max_sweeps, ylen, st); break;
-    case 5: launch_solve_np_n<5>(v, lam, b, x, tol, max_sweeps, ylen, st); break;
-    default: break;
-  }
+  cudaMemsetAsync(v.tile_next, 0, sizeof(int32_t), st);
+  solve_np_kernel(order)<<<(unsigned)grid, kTile, smem, st>>>(v, lam, b, x, tol, max_sweeps, nmax);
 }
 
 }  // namespace hevi

@@ -220,3 +220,76 @@ def test_batched_uneven_full_size_graph_parity(hv):
                     assert e_inc < 1e-6, e_inc
         g1.close()
     ctx.close()
+
+
+def _five_orders_ctx(hv, ncols=200, seed=41):
+    """Columns of all five orders, uneven in length, in one FP32 context: the
+    stage solve is one launch over tiles of every order."""
+    classes = [(30, 1), (4, 2), (12, 3), (3, 4), (9, 5)]
+    g = np.random.default_rng(seed)
+    cls = g.integers(0, len(classes), ncols).astype(np.int32)
+    zt = g.uniform(30e3, 80e3, ncols)
+    ctx = hv.Context(classes, zt, class_of_col=cls, precision=hv.FP32_IR)
+    off = ctx.offsets()
+    q0 = np.zeros(ctx.n)
+    b = np.zeros(ctx.n)
+    for c in range(ncols):
+        nez, N = classes[cls[c]]
+        qq = oracle.reference_q(nez, N, zt[c])[0]
+        qq = qq * (1 + 0.001 * np.random.default_rng(c).standard_normal(qq.size))
+        qq[1::3] = 0.0
+        q0[off[c]:off[c + 1]] = qq
+        b[off[c]:off[c + 1]] = np.random.default_rng(500 + c).standard_normal(qq.size)
+    return ctx, classes, cls, zt, q0, b
+
+
+def test_single_launch_all_orders_matches_oracle(hv):
+    ctx, classes, cls, zt, q0, b = _five_orders_ctx(hv)
+    lam = 45.0
+    ctx.hevi_factor(lam, _t(q0))
+    l0 = ctx.launch_count
+    x = ctx.hevi_stage_solve(_t(b)).cpu().numpy()
+    assert ctx.launch_count - l0 == 1  # one launch for the five orders
+    off = ctx.offsets()
+    worst = 0.0
+    for c in range(ctx.ncols):
+        nez, N = classes[cls[c]]
+        xr, info = oracle.stage_solve(nez, N, zt[c], lam, q0[None, off[c]:off[c + 1]],
+                                      b[None, off[c]:off[c + 1]])
+        assert int(info[0]) == 0
+        worst = max(worst, _rel(x[off[c]:off[c + 1]], xr[0]))
+    assert worst < TOL, worst
+    st, it = ctx.hevi_column_status()
+    assert bool((st == 0).all()) and int(it.max()) <= 10
+    ctx.close()
+
+
+def test_autotune_keeps_the_result_and_sets_the_shape(hv):
+    ctx, classes, cls, zt, q0, b = _five_orders_ctx(hv, ncols=300, seed=42)
+    ctx.hevi_factor(45.0, _t(q0))
+    bt = _t(b)
+    ref = ctx.hevi_stage_solve(bt).clone()
+    x = ctx.empty()
+    w, ms, md = ctx.hevi_autotune_solve(bt, x, reps=2)
+    assert 1 <= w <= 32 and ms > 0.0 and md > 0.0
+    # every launch shape gives the same bits (each column is solved by one warp)
+    assert bool((x == ref).all())
+    y = ctx.hevi_stage_solve(bt)
+    assert bool((y == ref).all())
+    for w in (1, 3, 7):
+        ctx.hevi_set_solve_warps(w)
+        assert bool((ctx.hevi_stage_solve(bt) == ref).all())
+    ctx.close()
+
+
+def test_autotune_refuses_fp64_and_unfactored(hv):
+    ctx64 = hv.Context([(4, 3)], 30e3, ncols=40, precision=hv.FP64)
+    q = ctx64.hevi_reference_state()
+    ctx64.hevi_factor(30.0, q)
+    with pytest.raises(hv.HeviError):
+        ctx64.hevi_autotune_solve(q * 0.5)
+    ctx32 = hv.Context([(4, 3)], 30e3, ncols=40, precision=hv.FP32_IR)
+    with pytest.raises(hv.HeviError):
+        ctx32.hevi_autotune_solve(ctx32.hevi_reference_state())
+    ctx32.close()
+    ctx64.close()
