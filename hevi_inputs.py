@@ -232,3 +232,55 @@ def serve_requests(seed: int = 5, count: int = 2000, rate: float = 50.0,
         out.append(dict(rid=i, arrival=t, classes=list(classes), class_of_col=cls, ztop=zt,
                         steps=steps, variant=variant, H=H, dq=dq))
     return out
+
+
+def serve_bank(seed: int = 6, cols_per_class: int = 32768, classes=SIZE_CLASSES,
+               ztop_range=(30e3, 100e3), nhevi_amp: float = 0.1) -> list:
+    """Column banks for a long serving stream: per size class cols_per_class
+    columns drawn as in ``batched`` (model top uniform, tendency H from
+    uniform sphere positions) with the NHEVI start increment dq of
+    ``state_increment`` at amplitude nhevi_amp (see ``serve_requests``).
+    Requests of ``serve_stream`` take windows of these banks, so a stream of
+    thousands of large requests needs no per-request field evaluation.
+    Returns [dict(cls, ztop [cols], H [cols, n], dq [cols, n])] per class."""
+    g = rng(seed)
+    bank = []
+    for nez, N in classes:
+        zt = g.uniform(*ztop_range, cols_per_class)
+        pts = sphere_points_uniform(g, cols_per_class)
+        H = horizontal_tendency(g, pts, nez, N, zt)
+        dq = state_increment(g, nez, N, zt, amp=nhevi_amp)
+        bank.append(dict(cls=(nez, N), ztop=zt, H=H, dq=dq))
+    return bank
+
+
+def serve_stream(seed: int = 5, count: int = 2000, rate: float = 50.0,
+                 cols_range=(2000, 86402), steps_range=(1, 20), nclasses: int = 4,
+                 bank_cols: int = 32768) -> list:
+    """A Poisson stream of serving requests over banks of ``serve_bank``:
+    arrivals at `rate` per second from the stream's seed; per request, from
+    its own seed (the stream seed and its index), a column count and a step
+    count uniform in their ranges, the variant LHEVI or NHEVI with probability
+    1/2, the columns' classes uniform (a multinomial split of the count) and,
+    per class, a window of that class's bank at a uniform start.  Returns a
+    list of dicts (rid, arrival, steps, variant, parts=[(class, start, count)])."""
+    g = rng(seed)
+    t = 0.0
+    out = []
+    for i in range(count):
+        t += float(g.exponential(1.0 / rate))
+        gr = np.random.Generator(np.random.PCG64(np.random.SeedSequence([seed, i])))
+        ncols = int(gr.integers(cols_range[0], cols_range[1] + 1))
+        steps = int(gr.integers(steps_range[0], steps_range[1] + 1))
+        variant = "LHEVI" if gr.random() < 0.5 else "NHEVI"
+        split = gr.multinomial(ncols, [1.0 / nclasses] * nclasses)
+        parts = []
+        for c, m in enumerate(split):
+            m = int(m)
+            if m == 0:
+                continue
+            if m > bank_cols:
+                raise ValueError("a class block is larger than its bank")
+            parts.append((c, int(gr.integers(0, bank_cols - m + 1)), m))
+        out.append(dict(rid=i, arrival=t, steps=steps, variant=variant, parts=parts))
+    return out

@@ -125,6 +125,23 @@ int64_t hevi_device_bytes(const hevi_ctx* ctx);
  * (dev, state layout).  Reference state: isothermal, hydrostatic. */
 hevi_status hevi_reference_state(hevi_ctx* ctx, double* q_bar);
 
+/* As hevi_reference_state for the columns [first, first + count) only; the
+ * rest of q_bar is not touched.  INVALID_ARG if the range leaves the
+ * context. */
+hevi_status hevi_reference_columns(hevi_ctx* ctx, int64_t first, int64_t count, double* q_bar);
+
+/* New model tops for the columns [first, first + count): z_top (host, count
+ * values, each > 0 and finite; it may be released when the call returns).
+ * Recomputes those columns' element height and reference state on the
+ * context's stream, in order with the calls around it; other columns and the
+ * size classes are unchanged.  The factors of the last hevi_factor become
+ * stale (the next stage solve needs a new hevi_factor; the step calls factor
+ * anyway).  With it a long-lived context serves as a pool of column slots
+ * that are reused for new columns of the same size class, with no device
+ * allocation.  INVALID_ARG on a bad range or top. */
+hevi_status hevi_set_column_tops(hevi_ctx* ctx, int64_t first, int64_t count,
+                                 const double* z_top);
+
 /* Assemble A = I - Lambda L(q0) = I + Lambda Dcal K(q0) + Lambda G in band
  * form (Sec. 4.2.3; App. A.3 with the gravity entry coupling the m-row to
  * the rho-column) and LU-factor it with partial pivoting, for every column.
@@ -151,6 +168,15 @@ hevi_status hevi_stage_solve_async(hevi_ctx* ctx, const double* rhs, double* x);
 /* Refinement controls for HEVI_FP32_IR solves: tolerance on the predicted
  * relative error and the sweep limit (defaults 1e-11 and 10). */
 hevi_status hevi_set_refinement(hevi_ctx* ctx, double tol, int32_t max_sweeps);
+
+/* How hevi_nhevi_step ends its Newton sequences.  on = 1 (default): after
+ * each iteration the host reads the device's count of still-iterating
+ * columns (a stream synchronisation) and enqueues no more iterations once it
+ * is zero.  on = 0: every sequence enqueues max_iter iterations without
+ * waiting, each gated on the device by that count (the kernels of an
+ * iteration after convergence return at once), so that a step call never
+ * blocks the calling thread.  Results are the same either way. */
+hevi_status hevi_set_newton_host_check(hevi_ctx* ctx, int32_t on);
 
 /* Resident warps per SM of the HEVI_FP32_IR stage solve (1 .. 32; 0 restores
  * the default).  The solve is ONE persistent launch over the tiles of every

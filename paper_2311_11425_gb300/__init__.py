@@ -81,6 +81,9 @@ def load(build: bool = False):
         "hevi_set_refinement": (_I32, [_P, _D, _I32]),
         "hevi_test_drop_record_copy": (_I32, [_P, _I32]),
         "hevi_set_solve_warps": (_I32, [_P, _I32]),
+        "hevi_reference_columns": (_I32, [_P, _I64, _I64, _P]),
+        "hevi_set_column_tops": (_I32, [_P, _I64, _I64, DP]),
+        "hevi_set_newton_host_check": (_I32, [_P, _I32]),
         "hevi_autotune_solve": (_I32, [_P, _P, _P, _I32, ctypes.POINTER(_I32), DP, DP]),
         "hevi_newton_solve": (_I32, [_P, _D, _P, _P, _D, _I32]),
         "hevi_newton_solve_async": (_I32, [_P, _D, _P, _P, _D, _I32]),
@@ -345,6 +348,24 @@ class Context:
         out = self.empty() if out is None else out
         _check(self._lib.hevi_reference_state(self._h, self._v(out)), "hevi_reference_state")
         return out
+
+    def hevi_reference_columns(self, first: int, count: int, out):
+        """Writes the rest state of the columns [first, first + count) into out."""
+        _check(self._lib.hevi_reference_columns(self._h, int(first), int(count), self._v(out)),
+               "hevi_reference_columns")
+        return out
+
+    def hevi_set_column_tops(self, first: int, z_top):
+        """New model tops (m) for the columns [first, first + len(z_top))."""
+        import numpy as np
+        zt = np.ascontiguousarray(z_top, dtype=np.float64).reshape(-1)
+        _check(self._lib.hevi_set_column_tops(self._h, int(first), int(zt.size),
+                                              zt.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+               "hevi_set_column_tops")
+
+    def hevi_set_newton_host_check(self, on: bool):
+        _check(self._lib.hevi_set_newton_host_check(self._h, 1 if on else 0),
+               "hevi_set_newton_host_check")
 
     def hevi_factor(self, gamma_dt: float, lin_state=None):
         p = None if lin_state is None else self._v(lin_state)

@@ -179,6 +179,13 @@ struct hevi_ctx {
   // the launch's tile counter
   int32_t* d_tile_list = nullptr;
   int32_t* d_tile_next = nullptr;
+  // per column: order and element count (device), for re-topping columns
+  int32_t* d_col_order = nullptr;
+  int32_t* d_col_nez = nullptr;
+  std::vector<int32_t> h_col_nez;
+  // NHEVI-LU: read the count of iterating columns on the host after each
+  // Newton iteration (and stop enqueuing at zero), else gate on the device only
+  bool newton_host_check = true;
   double lam = 0.0;
   bool factored = false;
   double ir_tol = 1e-11;
@@ -684,6 +691,9 @@ hevi_status hevi_setup(hevi_ctx** out, const hevi_column_grid* grid, const hevi_
   cudaMemcpy(d_off, c->h_off.data(), (ncols + 1) * sizeof(int64_t), cudaMemcpyHostToDevice);
   cudaMemcpy(d_perm, perm.data(), ncols * sizeof(int32_t), cudaMemcpyHostToDevice);
   cudaMemcpy(d_order, order.data(), ncols * sizeof(int32_t), cudaMemcpyHostToDevice);
+  c->d_col_order = d_order;
+  c->d_col_nez = d_nez;
+  c->h_col_nez = nez;
   cudaMemcpy(d_nez, nez.data(), ncols * sizeof(int32_t), cudaMemcpyHostToDevice);
   cudaMemcpy(d_dz, dz.data(), ncols * sizeof(double), cudaMemcpyHostToDevice);
   cudaMemcpy(d_tiles, c->h_tiles.data(), c->ntiles * sizeof(TileDesc), cudaMemcpyHostToDevice);
@@ -805,6 +815,40 @@ hevi_status hevi_reference_state(hevi_ctx* c, double* q) {
   if (!c || !q) return HEVI_ERR_INVALID_ARG;
   hevi::launch_reference_state(c->v, q, c->stream);
   return check_launch(c, 1);
+}
+
+hevi_status hevi_reference_columns(hevi_ctx* c, int64_t first, int64_t count, double* q) {
+  if (!c || !q || first < 0 || count < 0 || first + count > c->ncols) return HEVI_ERR_INVALID_ARG;
+  if (count == 0) return HEVI_OK;
+  hevi::launch_reference_state(c->v, q, c->stream, first, count);
+  return check_launch(c, 1);
+}
+
+hevi_status hevi_set_column_tops(hevi_ctx* c, int64_t first, int64_t count, const double* z_top) {
+  if (!c || first < 0 || count < 0 || first + count > c->ncols || (count > 0 && !z_top))
+    return HEVI_ERR_INVALID_ARG;
+  if (count == 0) return HEVI_OK;
+  std::vector<double> dz(count);
+  for (int64_t i = 0; i < count; ++i) {
+    const double zt = z_top[i];
+    if (!(zt > 0.0) || !std::isfinite(zt)) return HEVI_ERR_INVALID_ARG;
+    dz[i] = zt / c->h_col_nez[first + i];
+  }
+  // from pageable memory: the copy is staged before the call returns
+  if (cudaMemcpyAsync(const_cast<double*>(c->v.col_dz) + first, dz.data(), count * sizeof(double),
+                      cudaMemcpyHostToDevice, c->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return HEVI_ERR_CUDA;
+  }
+  hevi::launch_setup_ref(c->v, c->d_col_order, c->d_col_nez, c->stream, first, count);
+  c->factored = false;
+  return check_launch(c, 1);
+}
+
+hevi_status hevi_set_newton_host_check(hevi_ctx* c, int32_t on) {
+  if (!c || (on != 0 && on != 1)) return HEVI_ERR_INVALID_ARG;
+  c->newton_host_check = on != 0;
+  return HEVI_OK;
 }
 
 hevi_status hevi_set_refinement(hevi_ctx* c, double tol, int32_t max_sweeps) {
@@ -1169,7 +1213,7 @@ hevi_status hevi_nhevi_step(hevi_ctx* c, int32_t s, const double* A, const doubl
       Scope sc(c, kCombine);
       hevi::launch_combine(n, q_in, nt, vec, coef, R, c->stream);
     }
-    if ((st = newton_sequence(c, lam, Q, R, rtol, max_iter, true))) return st;
+    if ((st = newton_sequence(c, lam, Q, R, rtol, max_iter, c->newton_host_check))) return st;
     {
       Scope sc(c, kApply);
       for_orders(c, c->v, [&](const DevView& v, int N, int, cudaStream_t sk) {

@@ -324,8 +324,10 @@ inline void phys_derive(Phys& ph) {
 }
 
 // Launch helpers (host side, defined in hevi_kernels.cu).
+// Reference state (and element heights' consequences) of the columns
+// [first, first + count) (count < 0: to the last column).
 void launch_setup_ref(const DevView& v, const int32_t* col_order, const int32_t* col_nez,
-                      cudaStream_t st);
+                      cudaStream_t st, int64_t first = 0, int64_t count = -1);
 // The column launchers below process the tiles [v.tile_begin, v.tile_begin +
 // v.tile_count), all of order `order`; ylen is the longest n + 2K among them.
 void launch_factor(const DevView& v, int order, hevi_precision prec, double lam, const double* q0,
@@ -396,7 +398,10 @@ void launch_newton_fpass(const DevView& v, int order, const NewtonArgs& a, cudaS
 void launch_newton_finish(const DevView& v, const NewtonArgs& a, cudaStream_t st);
 void launch_combine(int64_t count, const double* base, int nterms, const double* const* vec,
                     const double* coef, double* out, cudaStream_t st);
-void launch_reference_state(const DevView& v, double* q, cudaStream_t st);
+// Reference state of the columns [first, first + count) (count < 0: to the
+// last column) into q (state layout).
+void launch_reference_state(const DevView& v, double* q, cudaStream_t st, int64_t first = 0,
+                            int64_t count = -1);
 // Copy the LGL tables into the constant memory of every kernel translation
 // unit (the current device); returns the first CUDA error.
 cudaError_t upload_tables(const LglTables& t);

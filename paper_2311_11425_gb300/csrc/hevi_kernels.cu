@@ -58,9 +58,10 @@ __device__ __forceinline__ T* brec_vec(T* tile_base, int n, int j, int e, int la
 // ---------------------------------------------------------------------------
 // Setup: reference state per point (isothermal, hydrostatic) and rest state
 // ---------------------------------------------------------------------------
-__global__ void k_setup_ref(DevView v, const int32_t* col_order, const int32_t* col_nez) {
-  int64_t col = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (col >= v.ncols) return;
+__global__ void k_setup_ref(DevView v, const int32_t* col_order, const int32_t* col_nez,
+                            int64_t first, int64_t last) {
+  const int64_t col = first + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (col >= last) return;
   const int N = col_order[col], nez = col_nez[col], nz = nez * N + 1;
   const double dz = v.col_dz[col];
   const Phys ph = v.ph;
@@ -84,14 +85,17 @@ __global__ void k_setup_ref(DevView v, const int32_t* col_order, const int32_t* 
 }
 
 void launch_setup_ref(const DevView& v, const int32_t* col_order, const int32_t* col_nez,
-                      cudaStream_t st) {
+                      cudaStream_t st, int64_t first, int64_t count) {
+  if (count < 0) count = v.ncols - first;
+  if (count <= 0) return;
   int blk = 128;
-  k_setup_ref<<<(unsigned)((v.ncols + blk - 1) / blk), blk, 0, st>>>(v, col_order, col_nez);
+  k_setup_ref<<<(unsigned)((count + blk - 1) / blk), blk, 0, st>>>(v, col_order, col_nez, first,
+                                                                   first + count);
 }
 
-__global__ void k_reference_state(DevView v, double* q) {
-  int64_t col = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (col >= v.ncols) return;
+__global__ void k_reference_state(DevView v, double* q, int64_t first, int64_t last) {
+  const int64_t col = first + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (col >= last) return;
   const int64_t a = v.col_off[col], b = v.col_off[col + 1];
   for (int64_t i = a; i < b; i += 3) {
     q[i] = v.ref[i];
@@ -100,9 +104,13 @@ __global__ void k_reference_state(DevView v, double* q) {
   }
 }
 
-void launch_reference_state(const DevView& v, double* q, cudaStream_t st) {
+void launch_reference_state(const DevView& v, double* q, cudaStream_t st, int64_t first,
+                            int64_t count) {
+  if (count < 0) count = v.ncols - first;
+  if (count <= 0) return;
   int blk = 128;
-  k_reference_state<<<(unsigned)((v.ncols + blk - 1) / blk), blk, 0, st>>>(v, q);
+  k_reference_state<<<(unsigned)((count + blk - 1) / blk), blk, 0, st>>>(v, q, first,
+                                                                         first + count);
 }
 
 // ---------------------------------------------------------------------------
