@@ -697,6 +697,8 @@ hevi_status hevi_setup(hevi_ctx** out, const hevi_column_grid* grid, const hevi_
   cudaMemcpy(d_nez, nez.data(), ncols * sizeof(int32_t), cudaMemcpyHostToDevice);
   cudaMemcpy(d_dz, dz.data(), ncols * sizeof(double), cudaMemcpyHostToDevice);
   cudaMemcpy(d_tiles, c->h_tiles.data(), c->ntiles * sizeof(TileDesc), cudaMemcpyHostToDevice);
+  // the records' padding is never written by the factor kernels: zero it once
+  cudaMemset(d_fac, 0, c->fac_elems * (precision == HEVI_FP64 ? 8 : 4));
   cudaMemset(d_fs, 0xff, ncols * sizeof(int32_t));  // no factorisation yet
   cudaMemset(d_cs, 0, ncols * sizeof(int32_t));
   cudaMemset(d_it, 0, ncols * sizeof(int32_t));

@@ -35,9 +35,8 @@ struct Band {
 // Record layout of the FP32 factors (no pivoting, equilibrated band; the L
 // factor has K sub-diagonals and U has K super-diagonals).  Per pivot step j
 // a column stores a forward record F_j = {l_1 .. l_K} (unit-lower multipliers
-// of rows j+1 .. j+K) and a backward record B_j = {1/u_jj, u_(j-1)j, ..,
-// u_(j-K)j} (column j of U above the diagonal), each padded to whole float4
-// vectors.  A tile keeps all F records, then all B records, each interleaved
+// of rows j+1 .. j+K) and a backward record B_j = {1/u_jj, u_j,j+1, ..,
+// u_j,j+K} (row j of U), each padded to whole float4 vectors.  A tile keeps all F records, then all B records, each interleaved
 // [step][vector][lane][4]: one step of a 32-column tile is one contiguous
 // block of FV (or BV) x 512 bytes.
 template <int N>

@@ -15,9 +15,10 @@
 // exactly zero marks the column SINGULAR.
 //
 // Record layout (NpBand<N>): per tile of 32 columns all forward records
-// F_j = {l_1 .. l_K}, then all backward records B_j = {1/u_jj, u_(j-1)j, ..,
-// u_(j-K)j}, each [step][float4 vector][lane][4], so one step of a tile is one
-// contiguous block and a run of steps is one bulk copy.
+// F_j = {l_(j+1)j .. l_(j+K)j} (column j of L), then all backward records
+// B_j = {1/u_jj, u_j,j+1 .. u_j,j+K} (row j of U), each [step][float4
+// vector][lane][4], so one step of a tile is one contiguous block and a run
+// of steps is one bulk copy.
 #include <algorithm>
 #include <cstdio>
 
@@ -53,12 +54,19 @@ int sm_count() {
 // Factorisation: one thread per row of the column's active window
 // ((K+1) rows x (K+1) columns of A_hat), GW threads per column (the power of
 // two >= K+1), 32/GW columns per warp, blocks of four warps.  Without
-// interchanges thread r always holds the rows r, r + (K+1), r + 2(K+1), ...:
-// at step j the thread holding row j publishes U's row j through shared
-// memory, the other rows form their multiplier and update their K entries in
-// registers (a[s] <- a[s+1] - l u[s+1]: the window moves one column per step),
-// and every thread assembles one entry of the column that enters the window
-// and one of the row that replaces row j.
+// interchanges thread r always holds the rows r, r + (K+1), r + 2(K+1), ...
+// At step j:
+//  - every thread forms one entry of the row that replaces row j (row
+//    j+K+1, columns j+1 .. j+K+1) and, for its own row, the entry of the
+//    column that enters the window (column j+K+1);
+//  - the thread holding row j (the pivot) publishes {1/u_jj, u_j,j+1 ..
+//    u_j,j+K} as whole float4 vectors to shared memory, writes the same
+//    vectors as the backward record B_j, and loads the replacement row;
+//  - the other threads form their multiplier, write it to the forward record
+//    F_j and update their K entries in registers (a[s] <- a[s+1] - l u[s+1]:
+//    the window moves one column per step).
+// Row and column indices advance by one per step, so their point, variable
+// and point class are carried along instead of divided out.
 // ---------------------------------------------------------------------------
 template <int N>
 struct NpF {
@@ -67,50 +75,72 @@ struct NpF {
   static constexpr int GW = WR <= 8 ? 8 : (WR <= 16 ? 16 : 32);  // threads per column
   static constexpr int CPW = 32 / GW;                              // columns per warp
   static constexpr int CPB = CPW * 4;                              // columns per block
-  static constexpr int UBW = (K + 1 + 3) / 4 * 4;                  // U row buffer: 1/u_jj, u_j,j+1..
-  static constexpr int RBW = (K + 1 + 3) / 4 * 4;                  // entering row buffer
+  static constexpr int UBW = 4 * B::BV;                            // published pivot row
+  static constexpr int RBW = (K + 1 + 3) / 4 * 4;                  // replacement row
+  // per column in shared memory: UBW + RBW, then per point the scaled K(q0)
+  // table (9 floats), the gravity entries (1) and per unknown 1/s (1)
+  static constexpr int fixed = UBW + RBW;
 };
 constexpr int kGSzA = (kGSz + 3) / 4 * 4;  // coefficient table, 16-byte aligned
 
-// Row data of A_hat for row i, kept in registers while a thread holds the row:
-// point I, variable v (0 rho, 1 m, 2 Theta), point class (0 bottom end, 1 top
-// end, 2 shared element boundary, 2 + k interior local index k), 1 / s_i, and
-// whether it is an identity row (m at an end: w = 0).
-struct NpRow {
-  int i, I, v, cls;
+// A row of A_hat while a thread holds it: index i, point I, variable v (0 rho,
+// 1 m, 2 Theta), I mod N, gi = cls (2N+1) + N - I (the coefficient row of its
+// point class cls, offset so that gi + J indexes point J), 1/s_i, identity
+// row (m at an end: w = 0), and i < n.
+struct NpRowF {
+  int i, I, v, k, gi;
   float isi;
-  bool ident;
+  bool ident, live;
 };
+
 template <int N>
-__device__ __forceinline__ NpRow np_row(int i, int nz, int n, const float* is32) {
-  NpRow r;
-  r.i = i;
-  r.I = i / 3;
-  r.v = i - 3 * r.I;
-  const int k = r.I % N;
-  r.cls = (r.I == 0) ? 0 : (r.I == nz - 1 ? 1 : (k == 0 ? 2 : 2 + k));
-  r.ident = (r.v == 1) && (r.I == 0 || r.I == nz - 1);
-  r.isi = i < n ? is32[i] : 0.0f;
-  return r;
+__device__ __forceinline__ void np_row_derive(NpRowF& R, int nz, int n, const float* is32) {
+  const int cls = (R.I == 0) ? 0 : (R.I == nz - 1 ? 1 : (R.k == 0 ? 2 : 2 + R.k));
+  R.gi = cls * (2 * N + 1) + N - R.I;
+  R.live = R.i < n;
+  R.isi = R.live ? is32[R.i] : 0.0f;
+  R.ident = (R.v == 1) && (R.I == 0 || R.I == nz - 1);
 }
 
-// Entry (i, col) of A_hat = S^-1 (I + Lambda Dcal K(q0) + Lambda G) S (Sec. 4.2.3,
-// App. A.3) from the point table KS[9 J + 3 v + u] = K_vu(q0_J) s_(3J+u):
-//   delta + Lambda (2/dz) G[cls][J - I] KS / s_i + Lambda g s_(3J) / s_i [v = m, u = rho, J = I],
-// identity rows at the ends' m unknowns, 0 outside the band or the column.
-// Branch-free: the rows of a warp's threads have different v.
 template <int N>
-__device__ __forceinline__ float np_entry(const NpRow& R, int col, int n, const float* KS,
-                                          const float* s32, const float* G, float lam_s,
-                                          float lam_g) {
-  const int J = col / 3, u = col - 3 * J, dJ = J - R.I;
-  const bool live = col < n && R.i < n;
+__device__ __forceinline__ NpRowF np_row_at(int i, int nz, int n, const float* is32) {
+  NpRowF R;
+  R.i = i;
+  R.I = i / 3;
+  R.v = i - 3 * R.I;
+  R.k = R.I % N;
+  np_row_derive<N>(R, nz, n, is32);
+  return R;
+}
+
+template <int N>
+__device__ __forceinline__ void np_row_next(NpRowF& R, int nz, int n, const float* is32) {
+  ++R.i;
+  if (++R.v == 3) {
+    R.v = 0;
+    ++R.I;
+    R.k = (R.k + 1 == N) ? 0 : R.k + 1;
+  }
+  np_row_derive<N>(R, nz, n, is32);
+}
+
+// Entry (i, col) of A_hat = S^-1 (I + Lambda Dcal K(q0) + Lambda G) S (Sec.
+// 4.2.3, App. A.3), col = 3J + u, from the column's tables
+//   KSp[9 J + 3 v + u] = Lambda (2/dz) K_vu(q0_J) s_(3J+u),  KG[J] = Lambda g s_(3J):
+//   delta + G[cls][J - I] KSp / s_i + KG / s_i [v = m, u = rho, J = I],
+// identity rows at the ends' m unknowns, 0 outside the band or past the last
+// unknown (colok: col < n).
+template <int N>
+__device__ __forceinline__ float np_ent(const NpRowF& R, int col, int J, int u, bool colok,
+                                        const float* G, const float* KSp, const float* KG) {
+  const int dJ = J - R.I;
+  const bool live = R.live && colok;
   const bool inb = live && (unsigned)(dJ + N) <= 2u * N;
-  const float g = G[inb ? R.cls * (2 * N + 1) + dJ + N : 0];
-  const float ks = KS[inb ? 9 * J + 3 * R.v + u : 0];
+  const float g = G[inb ? R.gi + J : 0];
+  const float ks = KSp[inb ? 9 * J + 3 * R.v + u : 0];
   const float one = (col == R.i && live) ? 1.0f : 0.0f;
-  float a = fmaf(inb ? lam_s * g * ks : 0.0f, R.isi, one);
-  if (R.v == 1 && u == 0 && dJ == 0 && live) a = fmaf(lam_g * s32[col], R.isi, a);
+  float a = fmaf(inb ? g * ks : 0.0f, R.isi, one);
+  if (R.v == 1 && u == 0 && dJ == 0 && live) a = fmaf(KG[J], R.isi, a);
   return R.ident ? one : a;
 }
 
@@ -140,30 +170,27 @@ __global__ void __launch_bounds__(128) k_factor_np(DevView v, double lam, const 
   const int cl = active ? cl0 + colw : t.count - 1;
   const Col c = make_col(v, t, cl, N);
   const Phys ph = v.ph;
-  float* ubuf = np_smem + kGSzA + (int64_t)colw * (2 * P::UBW + 2 * P::RBW + 5 * linstride);
-  float* rbuf = ubuf + 2 * P::UBW;
-  float* KS = rbuf + 2 * P::RBW;    // per point: K_vu(q0) s_(3J+u), 9 floats
-  float* s32 = KS + 3 * linstride;  // equilibration scales S of the column's unknowns
-  float* is32 = s32 + linstride;    // and their reciprocals
-  const int n = c.n;
-  float* fb = reinterpret_cast<float*>(v.fac) + t.fac_off;  // F records
-  float* bb = fb + (int64_t)n * FV * 4 * kTile;               // B records
-  auto fidx = [&](int j, int e) { return ((int64_t)(j * FV + e / 4) * kTile + cl) * 4 + (e & 3); };
-  auto bidx = [&](int j, int e) { return ((int64_t)(j * BV + e / 4) * kTile + cl) * 4 + (e & 3); };
+  float* ub = np_smem + kGSzA + (int64_t)colw * (P::fixed + 5 * linstride);
+  float* rb = ub + P::UBW;
+  float* KSp = rb + P::RBW;          // per point: 9 floats
+  float* KG = KSp + 3 * linstride;   // per point: gravity entry
+  float* is32 = KG + linstride;      // per unknown: 1 / s
+  const int n = c.n, nz = c.nz;
+  float* fb = reinterpret_cast<float*>(v.fac) + t.fac_off;                   // F records
+  float4* bb4 = reinterpret_cast<float4*>(fb + (int64_t)n * FV * 4 * kTile);  // B records
   double* lin_t = tile_lin(v, t);
   const float dzf = (float)v.col_dz[c.col];
+  const float lam_s = (float)(lam * c.s), lam_g = (float)(lam * ph.g);
 
   // point coefficients of L(q0) (FP64): w, theta, c = gamma P / Theta, and the
   // equilibration scales of the point
   bool ok = true;
-  for (int I = r; I < c.nz; I += GW) {
+  for (int I = r; I < nz; I += GW) {
     float sc[3];
-    np_scales(ph, np_point_z<N>(dzf, I, c.nz), sc);
+    np_scales(ph, np_point_z<N>(dzf, I, nz), sc);
 #pragma unroll
-    for (int u = 0; u < 3; ++u) {
-      s32[3 * I + u] = sc[u];
-      is32[3 * I + u] = 1.0f / sc[u];
-    }
+    for (int u = 0; u < 3; ++u) is32[3 * I + u] = 1.0f / sc[u];
+    KG[I] = lam_g * sc[0];
     const int64_t a = c.off + 3 * I;
     double rho, m, Th;
     if (q0) {
@@ -187,19 +214,19 @@ __global__ void __launch_bounds__(128) k_factor_np(DevView v, double lam, const 
       lt[2 * kTile] = cc;
     }
     // K(q0) at point I (App. A.3 restricted to the vertical), scaled by the
-    // column scales: rho-flux (0, 1, 0), m-flux (-w^2, 2w, c), Theta-flux
-    // (-theta w, theta, w)
+    // column scales and Lambda (2/dz): rho-flux (0, 1, 0), m-flux
+    // (-w^2, 2w, c), Theta-flux (-theta w, theta, w)
     const float wf = (float)w, tf = (float)th, cf = (float)cc;
-    float* ks = KS + 9 * I;
+    float* ks = KSp + 9 * I;
     ks[0] = 0.0f;
-    ks[1] = sc[1];
+    ks[1] = lam_s * sc[1];
     ks[2] = 0.0f;
-    ks[3] = -wf * wf * sc[0];
-    ks[4] = 2.0f * wf * sc[1];
-    ks[5] = cf * sc[2];
-    ks[6] = -tf * wf * sc[0];
-    ks[7] = tf * sc[1];
-    ks[8] = wf * sc[2];
+    ks[3] = lam_s * (-wf * wf * sc[0]);
+    ks[4] = lam_s * (2.0f * wf * sc[1]);
+    ks[5] = lam_s * (cf * sc[2]);
+    ks[6] = lam_s * (-tf * wf * sc[0]);
+    ks[7] = lam_s * (tf * sc[1]);
+    ks[8] = lam_s * (wf * sc[2]);
   }
   {  // AND over the group's lanes (every lane of the warp takes part)
     int okv = ok ? 1 : 0;
@@ -208,66 +235,110 @@ __global__ void __launch_bounds__(128) k_factor_np(DevView v, double lam, const 
     ok = okv != 0;
   }
   __syncwarp();
-  const float lam_s = (float)(lam * c.s), lam_g = (float)(lam * ph.g);
-  auto entry = [&](const NpRow& R, int col) -> float {
-    return np_entry<N>(R, col, n, KS, s32, G, lam_s, lam_g);
-  };
 
   // initial window: thread r < WR holds row r, a[s] = A_hat[r][s]
-  NpRow my = np_row<N>(r < WR ? r : n, c.nz, n, is32);
+  const bool mine = r < WR;
+  NpRowF my = np_row_at<N>(mine ? r : n, nz, n, is32);
   float a[WR];
 #pragma unroll
-  for (int s = 0; s < WR; ++s) a[s] = (r < WR) ? entry(my, s) : 0.0f;
+  for (int s = 0; s < WR; ++s)
+    a[s] = mine ? np_ent<N>(my, s, s / 3, s % 3, s < n, G, KSp, KG) : 0.0f;
 
+  // The main loop keeps, for a row, pointers to its coefficient row in G and
+  // its variable's slice of KSp and its effective 1/s (0 for identity rows
+  // and rows past the last unknown): entry (i, 3J + u) = gp[J] kp[9J + u] isx.
+  // Row j+K+1 (the same for every thread) replaces row j; thread r
+  // assembles its column j+1+r (point Jr, variable ur, kr = 9 Jr + ur); the
+  // column entering the window is col = j+K+1 (Jc, kc = 9 Jc + uc).
+  struct Lean {
+    const float* gp;
+    const float* kp;
+    float isx;
+    int I;
+  };
+  auto lean = [&](const NpRowF& R) {
+    Lean L;
+    L.gp = G + R.gi;
+    L.kp = KSp + 3 * R.v;
+    L.isx = (R.live && !R.ident) ? R.isi : 0.0f;
+    L.I = R.I;
+    return L;
+  };
+  Lean me = lean(my);
+  NpRowF nr = np_row_at<N>(K + 1, nz, n, is32);
+  int Jr = (1 + r) / 3, ur = (1 + r) % 3;
+  int kr = 9 * Jr + ur;
+  int Jc = (K + 1) / 3, uc = (K + 1) % 3;
+  int kc = 9 * Jc + uc;
+  const bool diag = r == K;  // thread K assembles the diagonal entry of the new row
+  const float4* ub4 = reinterpret_cast<const float4*>(ub);
+  float* fcol = fb + (int64_t)cl * 4;  // F records of this column, step 0
   int info = 0;
   int pos = r;  // position of this thread's row in the window: row j + pos
   for (int j = 0; j < n; ++j) {
-    const int buf = j & 1;
-    float* ub = ubuf + buf * P::UBW;
-    float* rb = rbuf + buf * P::RBW;
-    const bool mine = r < WR;
-    // the row that replaces row j: A_hat[j+K+1][j+1+r], thread r = 0..K
-    const NpRow nr = np_row<N>(j + K + 1, c.nz, n, is32);
-    if (mine) rb[r] = entry(nr, j + 1 + r);
-    // this row's entry in the column that enters the window (column j+K+1)
-    const float ecol = (mine && pos >= 1) ? entry(my, j + K + 1) : 0.0f;
+    const int col = j + K + 1;
+    if (mine) {
+      // entry (j+K+1, j+1+r) (Jr <= I): in the band unless Jr < I - N; the diagonal;
+      // gravity at the m row's own rho unknown (Sec. 4.2.3, App. A.3)
+      const Lean ln = lean(nr);
+      float e = 0.0f;
+      if (nr.live && Jr >= ln.I - N) e = ln.gp[Jr] * ln.kp[kr] * ln.isx;
+      if (diag && nr.live) e += 1.0f;
+      if (nr.v == 1 && ur == 0 && Jr == ln.I && ln.isx != 0.0f) e = fmaf(KG[Jr], ln.isx, e);
+      rb[r] = e;
+    }
+    // this row's entry in the entering column (above the diagonal: neither
+    // the identity nor the gravity entry)
+    float ecol = 0.0f;
+    if (mine && pos >= 1 && col < n && Jc <= me.I + N) ecol = me.gp[Jc] * me.kp[kc] * me.isx;
+    __syncwarp();
     if (mine && pos == 0) {
       const float u = a[0];
       const bool sing = !(fabsf(u) > 0.0f) || !isfinite(u);
       if (sing && info == 0) info = j + 1;
-      const float invd = sing ? 0.0f : 1.0f / u;
-      ub[0] = invd;
+      float row[4 * BV];
+      row[0] = sing ? 0.0f : __frcp_rn(u);
 #pragma unroll
-      for (int s = 1; s <= K; ++s) ub[s] = a[s];
-      if (active) {
-        bb[bidx(j, 0)] = invd;
+      for (int s = 1; s < 4 * BV; ++s) row[s] = s <= K ? a[s] : 0.0f;
 #pragma unroll
-        for (int e = K + 1; e < 4 * BV; ++e) bb[bidx(j, e)] = 0.0f;  // padding
-        for (int e = j + 1; e <= K; ++e) bb[bidx(j, e)] = 0.0f;      // rows j - e < 0
+      for (int q = 0; q < BV; ++q)
+        reinterpret_cast<float4*>(ub)[q] =
+            make_float4(row[4 * q], row[4 * q + 1], row[4 * q + 2], row[4 * q + 3]);
+      // row j retires; this thread takes row j+K+1
 #pragma unroll
-        for (int e = K; e < 4 * FV; ++e) fb[fidx(j, e)] = 0.0f;      // padding
+      for (int q = 0; q < P::RBW / 4; ++q) {
+        const float4 x4 = reinterpret_cast<const float4*>(rb)[q];
+        if (4 * q < WR) a[4 * q] = x4.x;
+        if (4 * q + 1 < WR) a[4 * q + 1] = x4.y;
+        if (4 * q + 2 < WR) a[4 * q + 2] = x4.z;
+        if (4 * q + 3 < WR) a[4 * q + 3] = x4.w;
       }
+      me = lean(nr);
     }
     __syncwarp();
     if (mine && pos >= 1) {
-      const float invd = ub[0];
-      const bool live = j + pos < n;
-      const float l = live ? a[0] * invd : 0.0f;
+      float uj[4 * BV];
 #pragma unroll
-      for (int s = 0; s < K; ++s) a[s] = fmaf(-l, ub[s + 1], a[s + 1]);
+      for (int q = 0; q < BV; ++q) {
+        const float4 x4 = ub4[q];
+        uj[4 * q] = x4.x; uj[4 * q + 1] = x4.y; uj[4 * q + 2] = x4.z; uj[4 * q + 3] = x4.w;
+      }
+      const float l = (j + pos < n) ? a[0] * uj[0] : 0.0f;
+#pragma unroll
+      for (int s = 0; s < K; ++s) a[s] = fmaf(-l, uj[s + 1], a[s + 1]);
       a[K] = ecol;
       if (active) {
-        fb[fidx(j, pos - 1)] = l;
-        if (live) bb[bidx(j + pos, pos)] = ub[pos];  // u_j,j+pos: entry pos of B_(j+pos)
+        const int e = pos - 1;  // 0 .. K-1: vector e / 4, element e % 4
+        fcol[(e >> 2) * (kTile * 4) + (e & 3)] = l;
       }
     }
-    __syncwarp();
-    if (mine && pos == 0) {  // row j retires; this thread takes row j+K+1
-#pragma unroll
-      for (int s = 0; s < WR; ++s) a[s] = rb[s];
-      my = nr;
-    }
+    // B_j = the published row j of U, one float4 vector per thread q < BV
+    if (active && r < BV) bb4[((int64_t)j * BV + r) * kTile + cl] = ub4[r];
     pos = (pos == 0) ? K : pos - 1;
+    fcol += FV * kTile * 4;
+    np_row_next<N>(nr, nz, n, is32);
+    if (++ur == 3) { ur = 0; ++Jr; kr += 7; } else { ++kr; }
+    if (++uc == 3) { uc = 0; ++Jc; kc += 7; } else { ++kc; }
   }
 #pragma unroll
   for (int off = 1; off < GW; off <<= 1) info = max(info, __shfl_xor_sync(0xffffffffu, info, off, GW));
@@ -289,7 +360,7 @@ static void launch_factor_np_n(const DevView& v, double lam, const double* q0, i
   constexpr int K = NpBand<N>::K;
   const int nmax = ylen - 2 * K;  // longest n of these tiles
   const int linstride = (3 * (nmax / 3) + 3) / 4 * 4;
-  const int smem = (kGSzA + P::CPB * (2 * P::UBW + 2 * P::RBW + 5 * linstride)) * (int)sizeof(float);
+  const int smem = (kGSzA + P::CPB * (P::fixed + 5 * linstride)) * (int)sizeof(float);
   cudaFuncSetAttribute(k_factor_np<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   k_factor_np<N><<<(unsigned)(v.tile_count * (kTile / P::CPB)), 128, smem, st>>>(v, lam, q0,
                                                                                 linstride);
@@ -463,8 +534,9 @@ __device__ __forceinline__ void np_forward(NpRing& rg, const float* fb, int n, f
   }
 }
 
-// Backward sweep U x = y (K super-diagonals, column-oriented records), the
-// window of K+1 rows in registers; x overwrites y; returns |x|^2.
+// Backward sweep U x = y (K super-diagonals, row-oriented records B_j =
+// {1/u_jj, u_j,j+1 .. u_j,j+K}): x_j = (y_j - sum_s u_j,j+s x_(j+s)) / u_jj
+// with the K latest x in registers; x overwrites y; returns |x|^2.
 template <int N>
 __device__ __forceinline__ float np_backward(NpRing& rg, const float* bb, int n, float* ys,
                                             int lane, bool keep) {
@@ -477,12 +549,14 @@ __device__ __forceinline__ float np_backward(NpRing& rg, const float* bb, int n,
                 keep, lane);
   };
   for (int ci = 0; ci < D && ci < nch; ++ci) issue(ci);
-  float w[WR], nb[WR];  // the window (rows j .. j-K) and the rows that enter it next
+  // xw: x_(j+1) .. x_(j+K) at rotating positions (x_(j+s) at (t - s) mod WR);
+  // yv: y_j .. y_(j-K), loaded a window ahead of use
+  float xw[WR], yv[WR];
 #pragma unroll
   for (int cc = 0; cc < WR; ++cc) {
-    const int i = n - 1 - cc, i2 = i - WR;
-    w[cc] = i >= 0 ? ys[i * kTile] : 0.0f;
-    nb[cc] = i2 >= 0 ? ys[i2 * kTile] : 0.0f;
+    const int i = n - 1 - cc;
+    xw[cc] = 0.0f;
+    yv[cc] = i >= 0 ? ys[i * kTile] : 0.0f;
   }
   float ss = 0.0f;
   for (int j0 = n - 1; j0 >= 0; j0 -= WR) {
@@ -501,14 +575,20 @@ __device__ __forceinline__ float np_backward(NpRing& rg, const float* bb, int n,
           const float4 x4 = rec[q * kTile];
           u[4 * q] = x4.x; u[4 * q + 1] = x4.y; u[4 * q + 2] = x4.z; u[4 * q + 3] = x4.w;
         }
-        const float xj = w[t] * u[0];
+        float acc0 = yv[t], acc1 = 0.0f;
+#pragma unroll
+        for (int s = 1; s <= K; ++s) {
+          if (s & 1)
+            acc0 = fmaf(-u[s], xw[(t - s + WR) % WR], acc0);
+          else
+            acc1 = fmaf(-u[s], xw[(t - s + WR) % WR], acc1);
+        }
+        const float xj = (acc0 + acc1) * u[0];
         ss = fmaf(xj, xj, ss);
         ys[j * kTile] = xj;
-#pragma unroll
-        for (int cc = 1; cc <= K; ++cc) w[(t + cc) % WR] = fmaf(-u[cc], xj, w[(t + cc) % WR]);
-        w[t] = nb[t];
-        const int jn = j - 2 * WR;
-        nb[t] = jn >= 0 ? ys[jn * kTile] : 0.0f;
+        xw[t] = xj;
+        const int jn = j - WR;
+        yv[t] = jn >= 0 ? ys[jn * kTile] : 0.0f;
         if (k == C - 1 || j == 0) {
           __syncwarp();
           rg.consumed++;
