@@ -357,6 +357,16 @@ void stage_solve_all(hevi_ctx* c, const DevView& base, double lam, const double*
   });
 }
 
+// S = H + V(Q): in double-float arithmetic on an FP32 context (its solves
+// are refined to about the same accuracy), in FP64 on an FP64 context.
+void apply_rhs(hevi_ctx* c, const DevView& v, int N, const double* Q, const double* H, double* S,
+               cudaStream_t sk) {
+  if (c->prec == HEVI_FP32_IR)
+    hevi::launch_apply_rhs_df(v, N, Q, H, S, sk);
+  else
+    hevi::launch_apply_rhs(v, N, Q, H, S, sk);
+}
+
 void reset_fail(hevi_ctx* c) {
   cudaMemsetAsync(c->v.fail_count, 0, kFailSlots * sizeof(int32_t), c->stream);
 }
@@ -1123,7 +1133,7 @@ hevi_status hevi_lhevi_step(hevi_ctx* c, int32_t s, const double* A, const doubl
   {
     Scope sc(c, kApply);
     for_orders(c, c->v, [&](const DevView& v, int N, int, cudaStream_t sk) {
-      hevi::launch_apply_rhs(v, N, q_in, H, S, sk);
+      apply_rhs(c, v, N, q_in, H, S, sk);
     });
   }
   for (int i = 1; i < s; ++i) {
@@ -1157,7 +1167,7 @@ hevi_status hevi_lhevi_step(hevi_ctx* c, int32_t s, const double* A, const doubl
     {
       Scope sc(c, kApply);
       for_orders(c, c->v, [&](const DevView& v, int N, int, cudaStream_t sk) {
-        hevi::launch_apply_rhs(v, N, Qi, H, S + i * n, sk);
+        apply_rhs(c, v, N, Qi, H, S + i * n, sk);
       });
     }
     c->launches += 2;  // the two combines

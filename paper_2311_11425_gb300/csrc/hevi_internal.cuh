@@ -58,6 +58,7 @@ struct Phys {
   double T0, p0, R, cp, g;
   double cv, gamma, cs;   // cp - R, cp / cv, sqrt(gamma R T0)
   double bin[kEosTerms];  // C(gamma, k), k = 1 .. kEosTerms
+  float binhi[kEosTerms], binlo[kEosTerms];  // the same as double-float pairs
   // FP32 constants of the equilibration scales of the FP32 path:
   // rho_bar = rho0f exp(-za z), theta_bar = T0f exp(zb z), c_s = csf
   float rho0f, za, zb, T0f, csf;
@@ -249,22 +250,37 @@ __device__ __forceinline__ df df_mul(df x, df y) {
 __device__ __forceinline__ df df_fma(df a, df b, df c) { return df_add(df_mul(a, b), c); }
 __device__ __forceinline__ df df_of(float2 v) { return {v.x, v.y}; }
 __device__ __forceinline__ float2 df_pack(df v) { return make_float2(v.hi, v.lo); }
-__device__ __forceinline__ double df_to_double(df v) { return (double)v.hi + (double)v.lo; }
+// float -> double with integer operations only (no FP64 conversion):
+// exact for zero, normal, infinite and NaN values; FP32 subnormals (below
+// 1.2e-38, only ever a low part here) go to zero.  hi + lo then takes one
+// FP64 add.
+__device__ __forceinline__ double f2d(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  const unsigned e = (u >> 23) & 0xffu;
+  const unsigned long long mant = (unsigned long long)(u & 0x7fffffu) << 29;
+  if (e == 0u) return __longlong_as_double((long long)sign);
+  const unsigned long long ed = e == 0xffu ? 0x7ffull : (unsigned long long)(e + 896u);
+  return __longlong_as_double((long long)(sign | (ed << 52) | mant));
+}
+__device__ __forceinline__ double df_to_double(df v) { return f2d(v.hi) + f2d(v.lo); }
 
-// Split an FP64 value into a double-float pair with integer operations: hi
-// keeps the top 24 significand bits, lo the next 29 (rounded to 24 by the
-// integer-to-float conversion); values outside 2^-63 .. 2^127 in magnitude
-// (and 0, NaN, Inf) take the FP64 conversions instead.
+// Split an FP64 value into a double-float pair with integer operations only
+// (no FP64 conversion): hi keeps the top 24 significand bits, lo the next 29
+// (rounded to 24 by the integer-to-float conversion).  Outside 2^-63 .. 2^127
+// in magnitude: below it lo is dropped (24 bits kept, an error under 1e-26)
+// and below FP32's normal range (2^-126) the value goes to zero; above it
+// the pair is +-Inf, and NaN stays NaN.
 __device__ __forceinline__ df df_from_double(double v) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(v);
   const int E = (int)((b >> 52) & 0x7ffu);
-  if (E < 960 || E > 1150) {
-    const float hi = __double2float_rn(v);
-    return {hi, __double2float_rn(v - (double)hi)};
-  }
   const unsigned long long M = b & 0xfffffffffffffull;
   const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  if (E < 897) return {__uint_as_float(sign), 0.0f};
+  if (E > 1150)
+    return {__uint_as_float(sign | 0x7f800000u | (E == 2047 && M ? 0x400000u : 0u)), 0.0f};
   const float hi = __uint_as_float(sign | ((unsigned)(E - 1023 + 127) << 23) | (unsigned)(M >> 29));
+  if (E < 960) return {hi, 0.0f};
   const float lo = __fmul_rn(__uint2float_rn((unsigned)(M & 0x1fffffffu)),
                              __uint_as_float((unsigned)(E - 1075 + 127) << 23));
   return {hi, sign ? -lo : lo};
@@ -314,6 +330,8 @@ inline void phys_derive(Phys& ph) {
   for (int k = 1; k <= kEosTerms; ++k) {
     coef *= (ph.gamma - k + 1.0) / k;
     ph.bin[k - 1] = coef;
+    ph.binhi[k - 1] = (float)coef;
+    ph.binlo[k - 1] = (float)(coef - (double)ph.binhi[k - 1]);
   }
   ph.rho0f = (float)(ph.p0 / (ph.R * ph.T0));
   ph.za = (float)(ph.g / (ph.R * ph.T0));
@@ -351,6 +369,10 @@ void launch_apply(const DevView& v, int order, const double* x, double* y, int n
                   cudaStream_t st);
 void launch_apply_stage(const DevView& v, int order, const double* Q, const double* H, double* E,
                         double* LQ, cudaStream_t st);
+// S = H + V(Q) in double-float arithmetic (hevi_np.cu): the FP32 path's
+// explicit tendency.
+void launch_apply_rhs_df(const DevView& v, int order, const double* Q, const double* H, double* S,
+                         cudaStream_t st);
 void launch_apply_rhs(const DevView& v, int order, const double* Q, const double* H, double* S,
                       cudaStream_t st);
 // The fused one-column-per-thread Newton kernel (the allocation-free entry

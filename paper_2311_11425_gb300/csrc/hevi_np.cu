@@ -981,4 +981,169 @@ void launch_solve_np(const DevView& v, int order, int nmax, double lam, const do
   solve_np_kernel(order)<<<(unsigned)grid, kTile, smem, st>>>(v, lam, b, x, tol, max_sweeps, nmax);
 }
 
+// ---------------------------------------------------------------------------
+// Explicit tendency of the FP32 path: S = H + V(Q) (Sec. 4.1, 4.3; the
+// vertical operator of App. A.2 with the reference state subtracted) in
+// double-float arithmetic on the FP32 pipes.  Point fluxes
+//   f = (m, m^2 / rho + (P - P_bar), Theta m / rho),
+// 1 / rho from an FP32 reciprocal and one double-float Newton step, the
+// pressure perturbation P_bar ((1 + x)^gamma - 1), x = (Theta - Theta_bar) /
+// Theta_bar, from its binomial series (the first three terms in double-float,
+// the rest, below |x|^3 of the leading term, in FP32); the differences
+// Theta - Theta_bar and rho - rho_bar are taken in FP64 first, where they are
+// exact, so that perturbations keep their relative accuracy.  The element
+// derivative, the DSS and the output S = H - Dcal f - g (rho - rho_bar) e_m
+// (w = 0 rows: H) run in double-float and round once to FP64.  About 48
+// significant bits where the FP64 kernel has 53, and a few FP64 operations
+// per point instead of a few dozen.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ df eos_perturbation_df(const Phys& ph, double dTh, double ithb,
+                                                  double P_bar) {
+  const df x = df_mul(df_from_double(dTh), df_from_double(ithb));
+  if (!(fabsf(x.hi) <= 0.02f))  // far from the reference: the FP64 form
+    return df_from_double(P_bar * expm1(ph.gamma * log1p(dTh * ithb)));
+  float t = ph.binhi[kEosTerms - 1];
+#pragma unroll
+  for (int k = kEosTerms - 2; k >= 3; --k) t = fmaf(t, x.hi, ph.binhi[k]);
+  df s = df_fma(x, df{t, 0.0f}, df{ph.binhi[2], ph.binlo[2]});
+  s = df_fma(x, s, df{ph.binhi[1], ph.binlo[1]});
+  s = df_fma(x, s, df{ph.binhi[0], ph.binlo[0]});
+  return df_mul(df_mul(df_from_double(P_bar), x), s);
+}
+
+// One warp per column, N + 1 lanes per element: lane (el, k) of a round
+// holds local point k of element e = e0 + el (the points shared by two
+// elements are held twice), evaluates its point flux, gathers its element's
+// N + 1 fluxes by shuffles and forms its row of the weighted element
+// derivative, cc_k = sum_j w_k Dhat_kj f_j.  Shared points add their two
+// rows (the lane of row 0 takes the row N of the lane before it, or, at the
+// first element of a round, the last row carried from the previous round)
+// and scale by (2/dz) / W_I; every point's output is written by one lane.
+// Loads and stores of a round touch consecutive points of the column.
+template <int N>
+__global__ void __launch_bounds__(128) k_apply_rhs_df(DevView v, const double* Q, const double* H,
+                                                      double* S) {
+  constexpr int P = N + 1;      // lanes per element
+  constexpr int EPR = 32 / P;   // elements per round
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int64_t gw = (int64_t)blockIdx.x * 4 + warp;
+  const int64_t tile = v.tile_begin + gw / kTile;
+  if (tile >= (int64_t)v.tile_begin + v.tile_count) return;  // warp-uniform
+  const TileDesc t = v.tiles[tile];
+  const int cl = (int)(gw % kTile);
+  if (cl >= t.count) return;  // warp-uniform
+  const Col c = make_col(v, t, cl, N);
+  const Phys ph = v.ph;
+  const int el = lane / P, k = lane % P;
+  const bool lane_ok = el < EPR;
+  // this lane's row of w_k Dhat_kj and its scale factors
+  df wd[P];
+#pragma unroll
+  for (int jj = 0; jj < P; ++jj) wd[jj] = df_of(c_tab.wD2[N][(lane_ok ? k : 0) * P + jj]);
+  const df cs = df_from_double(c.s);
+  const df iw0 = df_of(c_tab.iw2[N][0]);
+  const df sc_k = df_mul(cs, df_of(c_tab.iw2[N][lane_ok ? k : 0]));   // interior
+  const df sc_sh = df_mul(cs, df{0.5f * iw0.hi, 0.5f * iw0.lo});      // shared point
+  const df sc_end = df_mul(cs, iw0);                                  // bottom, top
+  const df gd = df_from_double(ph.g);
+  const double* qc = Q + c.off;
+  const double* ref = v.ref + c.off;
+  const double* ith = v.ithb + c.off / 3;
+  const double* hc = H + c.off;
+  double* sc = S + c.off;
+  bool ok = true;
+  df carry[3] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
+  for (int e0 = 0; e0 < c.nez; e0 += EPR) {
+    const int e = e0 + el;
+    const bool act = lane_ok && e < c.nez;
+    const int I = e * N + k;
+    df f[3] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
+    double rho = 0.0, dTh = 0.0, ithb = 0.0, Pb = 0.0, rb = 0.0;
+    if (act) {
+      rho = qc[3 * I];
+      const double m = qc[3 * I + 1], Th = qc[3 * I + 2];
+      rb = ref[3 * I];
+      Pb = ref[3 * I + 1];
+      dTh = Th - ref[3 * I + 2];
+      ithb = ith[I];
+      const df r = df_from_double(rho), md = df_from_double(m), T = df_from_double(Th);
+      if (!(r.hi > 0.0f) || !(T.hi > 0.0f)) ok = false;
+      const float r0 = __frcp_rn(r.hi);
+      const df ee = df_sub(df{1.0f, 0.0f}, df_mul(r, df{r0, 0.0f}));
+      const df ir = df_add_f(df_mul(df{r0, 0.0f}, ee), r0);
+      const df w = df_mul(md, ir);
+      f[0] = md;
+      f[1] = df_add(df_mul(md, w), eos_perturbation_df(ph, dTh, ithb, Pb));
+      f[2] = df_mul(T, w);
+    }
+    // this lane's row of the element derivative from its element's fluxes
+    const int base = (lane_ok ? el : 0) * P;
+    df R[3] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
+#pragma unroll
+    for (int jj = 0; jj < P; ++jj) {
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        const df fj = {__shfl_sync(0xffffffffu, f[u].hi, base + jj),
+                       __shfl_sync(0xffffffffu, f[u].lo, base + jj)};
+        R[u] = jj == 0 ? df_mul(wd[0], fj) : df_fma(wd[jj], fj, R[u]);
+      }
+    }
+    // row N of the element before: from the lane before, or carried
+    df left[3];
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      left[u] = {__shfl_up_sync(0xffffffffu, R[u].hi, 1), __shfl_up_sync(0xffffffffu, R[u].lo, 1)};
+      if (el == 0) left[u] = carry[u];
+    }
+    {  // the last row of this round goes to the next round's first point
+      const int src = (EPR - 1) * P + N;
+#pragma unroll
+      for (int u = 0; u < 3; ++u)
+        carry[u] = {__shfl_sync(0xffffffffu, R[u].hi, src), __shfl_sync(0xffffffffu, R[u].lo, src)};
+    }
+    const bool top = k == N && e == c.nez - 1;
+    if (act && (k < N || top)) {
+      df D[3];
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        if (k == 0 && e == 0)
+          D[u] = df_mul(R[u], sc_end);  // bottom
+        else if (k == 0)
+          D[u] = df_mul(df_add(R[u], left[u]), sc_sh);  // shared point
+        else if (top)
+          D[u] = df_mul(R[u], sc_end);
+        else
+          D[u] = df_mul(R[u], sc_k);
+      }
+      const int nzl = c.nz - 1;
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        const int i = 3 * I + u;
+        df val;
+        if (u == 1 && (I == 0 || I == nzl)) {
+          val = df_from_double(hc[i]);
+        } else {
+          val = df_sub(df_from_double(hc[i]), D[u]);
+          if (u == 1) val = df_sub(val, df_mul(gd, df_from_double(rho - rb)));
+        }
+        sc[i] = df_to_double(val);
+      }
+    }
+  }
+  if (__any_sync(0xffffffffu, !ok) && lane == 0) fail(v, c.col, HEVI_COL_BAD_INPUT);
+}
+
+void launch_apply_rhs_df(const DevView& v, int order, const double* Q, const double* H, double* S,
+                         cudaStream_t st) {
+  const unsigned grid = (unsigned)(v.tile_count * (kTile / 4));  // a warp per column slot
+  switch (order) {
+    case 1: k_apply_rhs_df<1><<<grid, 128, 0, st>>>(v, Q, H, S); break;
+    case 2: k_apply_rhs_df<2><<<grid, 128, 0, st>>>(v, Q, H, S); break;
+    case 3: k_apply_rhs_df<3><<<grid, 128, 0, st>>>(v, Q, H, S); break;
+    case 4: k_apply_rhs_df<4><<<grid, 128, 0, st>>>(v, Q, H, S); break;
+    case 5: k_apply_rhs_df<5><<<grid, 128, 0, st>>>(v, Q, H, S); break;
+    default: break;
+  }
+}
+
 }  // namespace hevi
