@@ -395,7 +395,8 @@ def gpu_arm(args, rank, world, local_rank, pool, cores):
             # Theta_bar) and 1/Theta_bar, writes S
             b = (4 * NUNK + NZ) * 8
             ach = b * NCOLS / (avg * 1e-3) / 1e9
-            return {"kernel": "k_apply_rhs<4> (apply)", "bound": "hbm", "achieved": ach,
+            return {"kernel": "k_apply_rhs_df<4> (apply, double-float)", "bound": "hbm",
+                    "achieved": ach,
                     "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": ach / pk["hbm_gbs"],
                     "traffic": None, "peak_source": pk["source"],
                     "algorithmic_bytes_per_launch": b * NCOLS, "avg_launch_ms": avg}
@@ -423,8 +424,9 @@ def gpu_arm(args, rank, world, local_rank, pool, cores):
                    "unknowns_per_column": NUNK, "implicit_stages": STAGES,
                    "precision": "FP32 LU without interchanges of S^-1 A S (S: reference scales); "
                                 "refinement residual b - A x in double-float arithmetic (~48 bits) "
-                                "on the FP32 pipes; FP64 reference state, operator applies, "
-                                "combinations and output",
+                                "on the FP32 pipes; explicit tendency S = H + V(Q) in double-float "
+                                "arithmetic rounded to FP64; FP64 reference state, state vectors, "
+                                "stage combinations and output",
                    "l2": "working set > L2 (factors 1.36 GB per step); no flush",
                    "parallelism": f"{world} independent column shards, no collective"},
         "e2e": None,
