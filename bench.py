@@ -72,7 +72,12 @@ def factor_flops(n=NUNK, k=K_BAND):
 # capture of `python bench.py --ncu-case solve|factor` (the summaries under
 # profiles/ give the commands), valid only for the kernel source they were
 # taken from: the SHA-256 of the kernel file at capture time.
-NCU_TRAFFIC = {}
+_NP_SHA = "238f0bda8d6ced685e2c0ff01a10034565d17766602259bd0eba80655b9af959"
+NCU_TRAFFIC = {
+    "k_solve_np": {"bytes": 3.742e9, "sha256": _NP_SHA},      # 4.681 TB/s x 0.799 ms
+    "k_factor_np": {"bytes": 1.833e9, "sha256": _NP_SHA},     # 1.729 TB/s x 1.060 ms
+    "k_apply_rhs_df": {"bytes": 0.352e9, "sha256": _NP_SHA},  # 1.382 TB/s x 0.255 ms
+}
 KERNEL_SOURCE = os.path.join(ROOT, "paper_2311_11425_gb300", "csrc", "hevi_np.cu")
 
 
@@ -396,7 +401,7 @@ def gpu_arm(args, rank, world, local_rank, pool, cores):
             b = (4 * NUNK + NZ) * 8
             ach = b * NCOLS / (avg * 1e-3) / 1e9
             return {"kernel": "k_apply_rhs_df<4> (apply, double-float)", "bound": "hbm",
-                    "achieved": ach,
+                    "achieved": ach, "traffic_ncu": ncu_traffic("k_apply_rhs_df"),
                     "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": ach / pk["hbm_gbs"],
                     "traffic": None, "peak_source": pk["source"],
                     "algorithmic_bytes_per_launch": b * NCOLS, "avg_launch_ms": avg}
