@@ -401,9 +401,9 @@ def gpu_arm(args, rank, world, local_rank, pool, cores):
             b = (4 * NUNK + NZ) * 8
             ach = b * NCOLS / (avg * 1e-3) / 1e9
             return {"kernel": "k_apply_rhs_df<4> (apply, double-float)", "bound": "hbm",
-                    "achieved": ach, "traffic_ncu": ncu_traffic("k_apply_rhs_df"),
+                    "achieved": ach,
                     "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": ach / pk["hbm_gbs"],
-                    "traffic": None, "peak_source": pk["source"],
+                    "traffic": ncu_traffic("k_apply_rhs_df"), "peak_source": pk["source"],
                     "algorithmic_bytes_per_launch": b * NCOLS, "avg_launch_ms": avg}
         return {"kernel": kind, "bound": None, "achieved": None, "peak": None, "unit": None,
                 "frac": None, "traffic": None, "avg_launch_ms": avg}
