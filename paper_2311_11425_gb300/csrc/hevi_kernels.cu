@@ -989,34 +989,37 @@ __global__ void __launch_bounds__(128) k_newton_fpass(DevView v, NewtonArgs a) {
   const double* Rc = a.R + c.off;
   const double* q0c = a.q0 + c.off;
   double* rc = a.rhs + c.off;
-  const double ics = rcp64(ph.cs);
-  // S^-1 of point I: 1/rho_bar, 1/(rho_bar c_s), 1/Theta_bar (one reciprocal
-  // per point, no divisions)
-  auto inv_scales = [&](int I, double (&is)[3]) {
-    const double ir = rcp64(ref[3 * I]);
+  // The norms of the stop test only compare magnitudes (relative accuracy
+  // 1e-7 is ample), so they run in FP32 on values rounded toward zero by
+  // integer operations, with S^-1 of point I = 1/rho_bar, 1/(rho_bar c_s),
+  // 1/Theta_bar in FP32; F itself is FP64.
+  const float ics = 1.0f / ph.csf;
+  auto f32 = [](double x) { return df_from_double(x).hi; };
+  auto inv_scales = [&](int I, float (&is)[3]) {
+    const float ir = __frcp_rn(f32(ref[3 * I]));
     is[0] = ir;
     is[1] = ir * ics;
-    is[2] = v.ithb ? v.ithb[c.off / 3 + I] : rcp64(ref[3 * I + 2]);
+    is[2] = v.ithb ? f32(v.ithb[c.off / 3 + I]) : __frcp_rn(f32(ref[3 * I + 2]));
   };
-  double dn = 0.0;
+  float dn2 = 0.0f;
   if (a.iter > 0) {
     const double* dc = a.delta + c.off;
     for (int I = 0; I < c.nz; ++I) {
-      double is[3];
+      float is[3];
       inv_scales(I, is);
 #pragma unroll
       for (int u = 0; u < 3; ++u) {
         const int i = 3 * I + u;
         const double d = dc[i];
         qc[i] += d;
-        const double sd = d * is[u];
-        dn = fma(sd, sd, dn);
+        const float sd = f32(d) * is[u];
+        dn2 = fmaf(sd, sd, dn2);
       }
     }
-    dn = sqrt(dn);
   }
+  const double dn = sqrt((double)dn2);
   bool ok = true;
-  double fn = 0.0, qn = 0.0, un = 0.0;
+  float fn2 = 0.0f, qn2 = 0.0f, un2 = 0.0f;
   auto flux = [&](int I, double* f) {
     const double rho = qc[3 * I], m = qc[3 * I + 1], Th = qc[3 * I + 2];
     double w, th, cc, dP;
@@ -1030,7 +1033,7 @@ __global__ void __launch_bounds__(128) k_newton_fpass(DevView v, NewtonArgs a) {
     f[2] = Th * w;
   };
   auto out = [&](int I, const double* D) {
-    double is[3];
+    float is[3];
     inv_scales(I, is);
 #pragma unroll
     for (int u = 0; u < 3; ++u) {
@@ -1045,17 +1048,15 @@ __global__ void __launch_bounds__(128) k_newton_fpass(DevView v, NewtonArgs a) {
         F = fma(a.lam, vterm, qc[i]) - Rc[i];
       }
       rc[i] = -F;
-      const double isc = is[u];
-      const double sF = F * isc, sq = qc[i] * isc, su = (qc[i] - q0c[i]) * isc;
-      fn = fma(sF, sF, fn);
-      qn = fma(sq, sq, qn);
-      un = fma(su, su, un);
+      const float isc = is[u];
+      const float sF = f32(F) * isc, sq = f32(qc[i]) * isc, su = f32(qc[i] - q0c[i]) * isc;
+      fn2 = fmaf(sF, sF, fn2);
+      qn2 = fmaf(sq, sq, qn2);
+      un2 = fmaf(su, su, un2);
     }
   };
   element_pass<N>(c, c_tab.w[N], c_tab.iw[N], flux, out);
-  fn = sqrt(fn);
-  qn = sqrt(qn);
-  un = sqrt(un);
+  const double fn = sqrt((double)fn2), qn = sqrt((double)qn2), un = sqrt((double)un2);
   const double floor_ok = kNewtonFloor * qn;
   int cv = 0, st = HEVI_COL_OK;
   if (!ok || !(fn == fn)) {
