@@ -81,15 +81,20 @@ __device__ __forceinline__ void elem_deriv_df1(const df (&f)[N + 1], df (&cc)[N 
 
 // element_pass in double-float arithmetic for one thread's column, with the
 // element's point fluxes and derivatives parked in the thread's own slots of
-// shared memory (sm: (2N + 1) x 3 pairs per lane, lane fastest) so that one
-// field at a time is live in registers.  flux(I, f[3]) gives the point
-// fluxes, out(I, D[3]) receives the DSS'd derivative; cs = 2 / dz.
+// shared memory (sm: (2N + 2) x 3 pairs per lane, lane fastest: N + 1 fluxes,
+// N derivatives and the carried boundary row) so that one field at a time is
+// live in registers.  flux(I, f[3]) gives the point fluxes, out(I, D[3])
+// receives the DSS'd derivative; cs = 2 / dz.  The loops over points and
+// fields are kept rolled (their data live in the slots): the code stays small
+// enough for the instruction cache beside the sweeps it runs with.
 template <int N, class FluxF, class OutF>
 __device__ __forceinline__ void element_pass_df(int nez, df cs, float2* sm, int lane, FluxF&& flux,
                                                 OutF&& out) {
   auto FS = [&](int k, int v) -> float2& { return sm[(k * 3 + v) * kTile + lane]; };
   auto DS = [&](int k, int v) -> float2& { return sm[((N + 1 + k) * 3 + v) * kTile + lane]; };
-  df carry[3] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
+  auto CS = [&](int v) -> float2& { return sm[((2 * N + 1) * 3 + v) * kTile + lane]; };
+#pragma unroll
+  for (int v = 0; v < 3; ++v) CS(v) = make_float2(0.0f, 0.0f);
   {
     df f[3];
     flux(0, f);
@@ -99,7 +104,7 @@ __device__ __forceinline__ void element_pass_df(int nez, df cs, float2* sm, int 
   const df iw0 = df_of(c_tab.iw2[N][0]);
   for (int e = 0; e < nez; ++e) {
     const int I0 = e * N;
-#pragma unroll
+#pragma unroll 1
     for (int k = 1; k <= N; ++k) {
       df f[3];
       flux(I0 + k, f);
@@ -107,26 +112,26 @@ __device__ __forceinline__ void element_pass_df(int nez, df cs, float2* sm, int 
       for (int v = 0; v < 3; ++v) FS(k, v) = df_pack(f[v]);
     }
     const df sc0 = df_mul(cs, e == 0 ? iw0 : df{0.5f * iw0.hi, 0.5f * iw0.lo});
-#pragma unroll
+#pragma unroll 1
     for (int v = 0; v < 3; ++v) {
       df fv[N + 1], cc[N + 1];
 #pragma unroll
       for (int k = 0; k <= N; ++k) fv[k] = df_of(FS(k, v));
       elem_deriv_df1<N>(fv, cc);
-      DS(0, v) = df_pack(df_mul(df_add(carry[v], cc[0]), sc0));
+      DS(0, v) = df_pack(df_mul(df_add(df_of(CS(v)), cc[0]), sc0));
 #pragma unroll
       for (int k = 1; k < N; ++k) DS(k, v) = df_pack(df_mul(cc[k], df_mul(cs, df_of(c_tab.iw2[N][k]))));
-      carry[v] = cc[N];
+      CS(v) = df_pack(cc[N]);
       FS(0, v) = FS(N, v);
     }
-#pragma unroll
+#pragma unroll 1
     for (int k = 0; k < N; ++k) {
       const df D[3] = {df_of(DS(k, 0)), df_of(DS(k, 1)), df_of(DS(k, 2))};
       out(I0 + k, D);
     }
   }
   const df sc = df_mul(cs, iw0);
-  const df D[3] = {df_mul(carry[0], sc), df_mul(carry[1], sc), df_mul(carry[2], sc)};
+  const df D[3] = {df_mul(df_of(CS(0)), sc), df_mul(df_of(CS(1)), sc), df_mul(df_of(CS(2)), sc)};
   out(nez * N, D);
 }
 

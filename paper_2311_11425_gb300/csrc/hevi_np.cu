@@ -404,9 +404,12 @@ constexpr int kNpD = 2;  // ring slots
 __host__ __device__ constexpr int np_slot_bytes(int n) {
   return kNpC * ((3 * (n + 1) - 1 + 1 + 3) / 4) * 512;
 }
+__host__ __device__ constexpr int np_elem_slot_bytes(int n) {  // element_pass_df's slots
+  return ((2 * n + 2) * 3) * kTile * 8;
+}
 __host__ __device__ constexpr int np_ring_bytes(int n) {
-  return kNpD * np_slot_bytes(n) > (2 * n + 1) * 3 * kTile * 8 ? kNpD * np_slot_bytes(n)
-                                                                : (2 * n + 1) * 3 * kTile * 8;
+  return kNpD * np_slot_bytes(n) > np_elem_slot_bytes(n) ? kNpD * np_slot_bytes(n)
+                                                         : np_elem_slot_bytes(n);
 }
 template <int N>
 struct NpS {
@@ -414,7 +417,7 @@ struct NpS {
   static constexpr int K = B::K, WR = B::WR, FV = B::FV, BV = B::BV;
   static constexpr int C = kNpC, D = kNpD;
   static_assert(C * (FV > BV ? FV : BV) * 512 <= np_slot_bytes(N), "ring slot too small");
-  static_assert((2 * N + 1) * 3 * kTile * 8 <= np_ring_bytes(N), "element slots do not fit");
+  static_assert(np_elem_slot_bytes(N) <= np_ring_bytes(N), "element slots do not fit");
 };
 
 // Points per round of the loops that move a tile's vectors: their loads are
