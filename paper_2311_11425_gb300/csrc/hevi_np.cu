@@ -482,9 +482,13 @@ __device__ void np_reset(NpRing& rg, int lane) {
 }
 
 // Forward sweep L y = y (unit lower, K sub-diagonals), the window of K+1 rows
-// in registers; ys is this lane's column of the work vector (rows kTile
-// apart), rows n .. n+K zero.  drop_step >= 0 leaves out the
-// copy of the chunk holding that step (test hook).
+// in registers, shifted by one row per step (the shift rides on the update:
+// w[r-1] = w[r] - l_r y_j), so the loop body is one step of code; ys is this
+// lane's column of the work vector (rows kTile apart), rows n .. n+K zero.
+// Rows enter the window two steps ahead of use; lane 0 prefetches the row
+// line (one 128-byte line holds the row for the warp) two windows ahead.
+// drop_step >= 0 leaves out the copy of the chunk holding that step (test
+// hook).
 template <int N>
 __device__ __forceinline__ void np_forward(NpRing& rg, const float* fb, int n, float* ys, int lane,
                                            int drop_step, bool keep) {
@@ -497,49 +501,44 @@ __device__ __forceinline__ void np_forward(NpRing& rg, const float* fb, int n, f
                 drop_step >= ci * C && drop_step < ci * C + cnt, keep, lane);
   };
   for (int ci = 0; ci < D && ci < nch; ++ci) issue(ci);
-  // w: the window (rows j .. j+K); nb: the rows that enter it next (rows
-  // j+K+1 .. j+2K+1), loaded a window ahead of use
-  float w[WR], nb[WR];
+  float w[WR];
 #pragma unroll
-  for (int r = 0; r < WR; ++r) {
-    w[r] = ys[r * kTile];
-    nb[r] = ys[(WR + r) * kTile];
-  }
-  for (int j0 = 0; j0 < n; j0 += WR) {
+  for (int r = 0; r < WR; ++r) w[r] = ys[r * kTile];
+  float q0 = ys[WR * kTile], q1 = ys[(WR + 1) * kTile];  // rows j+K+1, j+K+2
+  const float* yrow = ys - lane;
+#pragma unroll 1
+  for (int j = 0; j < n && rg.ok; ++j) {
+    const int k = j & (C - 1), ci = j / C;
+    if (k == 0 && !np_wait<N>(rg)) break;
+    if (lane == 0 && j + 2 * WR <= n + K) prefetch_l1(yrow + (j + 2 * WR) * kTile);
+    const float4* rec =
+        reinterpret_cast<const float4*>(rg.buf + (rg.consumed % D) * rg.slot) + k * FV * kTile +
+        lane;
+    float l[4 * FV];
 #pragma unroll
-    for (int t = 0; t < WR; ++t) {
-      const int j = j0 + t;
-      if (j < n && rg.ok) {
-        const int k = j & (C - 1), ci = j / C;
-        if (k == 0 && !np_wait<N>(rg)) break;
-        const float4* rec =
-            reinterpret_cast<const float4*>(rg.buf + (rg.consumed % D) * rg.slot) + k * FV * kTile +
-            lane;
-        float l[4 * FV];
+    for (int q = 0; q < FV; ++q) {
+      const float4 x4 = rec[q * kTile];
+      l[4 * q] = x4.x; l[4 * q + 1] = x4.y; l[4 * q + 2] = x4.z; l[4 * q + 3] = x4.w;
+    }
+    const float yj = w[0];
+    ys[j * kTile] = yj;
 #pragma unroll
-        for (int q = 0; q < FV; ++q) {
-          const float4 x4 = rec[q * kTile];
-          l[4 * q] = x4.x; l[4 * q + 1] = x4.y; l[4 * q + 2] = x4.z; l[4 * q + 3] = x4.w;
-        }
-        const float yj = w[t];
-        ys[j * kTile] = yj;
-#pragma unroll
-        for (int r = 1; r <= K; ++r) w[(t + r) % WR] = fmaf(-l[r - 1], yj, w[(t + r) % WR]);
-        w[t] = nb[t];
-        nb[t] = (j + 2 * WR <= n + K) ? ys[(j + 2 * WR) * kTile] : 0.0f;
-        if (k == C - 1 || j == n - 1) {  // chunk consumed: refill its slot
-          __syncwarp();
-          rg.consumed++;
-          if (ci + D < nch) issue(ci + D);
-        }
-      }
+    for (int r = 1; r <= K; ++r) w[r - 1] = fmaf(-l[r - 1], yj, w[r]);
+    w[K] = q0;
+    q0 = q1;
+    q1 = (j + WR + 2 <= n + K) ? ys[(j + WR + 2) * kTile] : 0.0f;
+    if (k == C - 1 || j == n - 1) {  // chunk consumed: refill its slot
+      __syncwarp();
+      rg.consumed++;
+      if (ci + D < nch) issue(ci + D);
     }
   }
 }
 
 // Backward sweep U x = y (K super-diagonals, row-oriented records B_j =
 // {1/u_jj, u_j,j+1 .. u_j,j+K}): x_j = (y_j - sum_s u_j,j+s x_(j+s)) / u_jj
-// with the K latest x in registers; x overwrites y; returns |x|^2.
+// with the K latest x in registers (shifted by one per step); x overwrites y;
+// returns |x|^2.
 template <int N>
 __device__ __forceinline__ float np_backward(NpRing& rg, const float* bb, int n, float* ys,
                                             int lane, bool keep) {
@@ -552,52 +551,46 @@ __device__ __forceinline__ float np_backward(NpRing& rg, const float* bb, int n,
                 keep, lane);
   };
   for (int ci = 0; ci < D && ci < nch; ++ci) issue(ci);
-  // xw: x_(j+1) .. x_(j+K) at rotating positions (x_(j+s) at (t - s) mod WR);
-  // yv: y_j .. y_(j-K), loaded a window ahead of use
-  float xw[WR], yv[WR];
+  float xw[K];  // xw[s - 1] = x_(j+s)
 #pragma unroll
-  for (int cc = 0; cc < WR; ++cc) {
-    const int i = n - 1 - cc;
-    xw[cc] = 0.0f;
-    yv[cc] = i >= 0 ? ys[i * kTile] : 0.0f;
-  }
+  for (int s = 0; s < K; ++s) xw[s] = 0.0f;
+  float q0 = ys[(n - 1) * kTile], q1 = n >= 2 ? ys[(n - 2) * kTile] : 0.0f;  // y_j, y_(j-1)
+  const float* yrow = ys - lane;
   float ss = 0.0f;
-  for (int j0 = n - 1; j0 >= 0; j0 -= WR) {
+#pragma unroll 1
+  for (int j = n - 1; j >= 0 && rg.ok; --j) {
+    const int i = n - 1 - j, k = i & (C - 1), ci = i / C;
+    if (k == 0 && !np_wait<N>(rg)) break;
+    if (lane == 0 && j - 2 * WR >= 0) prefetch_l1(yrow + (j - 2 * WR) * kTile);
+    const int lo = max(0, n - 1 - ci * C - C + 1);
+    const float4* rec = reinterpret_cast<const float4*>(rg.buf + (rg.consumed % D) * rg.slot) +
+                        (j - lo) * BV * kTile + lane;
+    float u[4 * BV];
 #pragma unroll
-    for (int t = 0; t < WR; ++t) {
-      const int j = j0 - t;
-      if (j >= 0 && rg.ok) {
-        const int i = n - 1 - j, k = i & (C - 1), ci = i / C;
-        if (k == 0 && !np_wait<N>(rg)) break;
-        const int lo = max(0, n - 1 - ci * C - C + 1);
-        const float4* rec = reinterpret_cast<const float4*>(rg.buf + (rg.consumed % D) * rg.slot) +
-                            (j - lo) * BV * kTile + lane;
-        float u[4 * BV];
+    for (int q = 0; q < BV; ++q) {
+      const float4 x4 = rec[q * kTile];
+      u[4 * q] = x4.x; u[4 * q + 1] = x4.y; u[4 * q + 2] = x4.z; u[4 * q + 3] = x4.w;
+    }
+    float acc0 = q0, acc1 = 0.0f;
 #pragma unroll
-        for (int q = 0; q < BV; ++q) {
-          const float4 x4 = rec[q * kTile];
-          u[4 * q] = x4.x; u[4 * q + 1] = x4.y; u[4 * q + 2] = x4.z; u[4 * q + 3] = x4.w;
-        }
-        float acc0 = yv[t], acc1 = 0.0f;
+    for (int s = 1; s <= K; ++s) {
+      if (s & 1)
+        acc0 = fmaf(-u[s], xw[s - 1], acc0);
+      else
+        acc1 = fmaf(-u[s], xw[s - 1], acc1);
+    }
+    const float xj = (acc0 + acc1) * u[0];
+    ss = fmaf(xj, xj, ss);
+    ys[j * kTile] = xj;
 #pragma unroll
-        for (int s = 1; s <= K; ++s) {
-          if (s & 1)
-            acc0 = fmaf(-u[s], xw[(t - s + WR) % WR], acc0);
-          else
-            acc1 = fmaf(-u[s], xw[(t - s + WR) % WR], acc1);
-        }
-        const float xj = (acc0 + acc1) * u[0];
-        ss = fmaf(xj, xj, ss);
-        ys[j * kTile] = xj;
-        xw[t] = xj;
-        const int jn = j - WR;
-        yv[t] = jn >= 0 ? ys[jn * kTile] : 0.0f;
-        if (k == C - 1 || j == 0) {
-          __syncwarp();
-          rg.consumed++;
-          if (ci + D < nch) issue(ci + D);
-        }
-      }
+    for (int s = K - 1; s >= 1; --s) xw[s] = xw[s - 1];
+    xw[0] = xj;
+    q0 = q1;
+    q1 = j >= 2 ? ys[(j - 2) * kTile] : 0.0f;
+    if (k == C - 1 || j == 0) {
+      __syncwarp();
+      rg.consumed++;
+      if (ci + D < nch) issue(ci + D);
     }
   }
   return ss;
