@@ -72,11 +72,11 @@ def factor_flops(n=NUNK, k=K_BAND):
 # capture of `python bench.py --ncu-case solve|factor` (the summaries under
 # profiles/ give the commands), valid only for the kernel source they were
 # taken from: the SHA-256 of the kernel file at capture time.
-_NP_SHA = "238f0bda8d6ced685e2c0ff01a10034565d17766602259bd0eba80655b9af959"
+_NP_SHA = "26810b64c1f04e93d98c705d07b063c8370a21882001b0dcce725dee59c87b64"
 NCU_TRAFFIC = {
-    "k_solve_np": {"bytes": 3.742e9, "sha256": _NP_SHA},      # 4.681 TB/s x 0.799 ms
-    "k_factor_np": {"bytes": 1.833e9, "sha256": _NP_SHA},     # 1.729 TB/s x 1.060 ms
-    "k_apply_rhs_df": {"bytes": 0.352e9, "sha256": _NP_SHA},  # 1.382 TB/s x 0.255 ms
+    "k_solve_np": {"bytes": 3.791e9, "sha256": _NP_SHA},      # 5.334 TB/s x 0.711 ms
+    "k_factor_np": {"bytes": 1.833e9, "sha256": _NP_SHA},     # 1.728 TB/s x 1.060 ms
+    "k_apply_rhs_df": {"bytes": 0.352e9, "sha256": _NP_SHA},  # 1.396 TB/s x 0.252 ms
 }
 KERNEL_SOURCE = os.path.join(ROOT, "paper_2311_11425_gb300", "csrc", "hevi_np.cu")
 
