@@ -270,3 +270,26 @@ def test_realtime_latency_stats(hv):
     assert sum(v["request_column_steps"] for v in s["variants"].values()) == \
         sum(r.ncols * r.steps for r in reqs)
     server.close()
+
+
+def test_serve_stream_per_request_seeds_and_bank_windows():
+    """The long stream draws each request from its own seed: a request does not
+    depend on how many requests the stream has, and its class windows stay
+    inside the banks; the arrivals are a Poisson process of the given rate."""
+    s1 = hevi_inputs.serve_stream(seed=5, count=40, rate=50.0, bank_cols=32768)
+    s2 = hevi_inputs.serve_stream(seed=5, count=400, rate=50.0, bank_cols=32768)
+    for a, b in zip(s1, s2):
+        assert a == b
+    gaps = np.diff([0.0] + [r["arrival"] for r in s2])
+    assert abs(gaps.mean() - 1 / 50.0) < 0.2 / 50.0  # mean inter-arrival 1 / rate
+    for r in s2:
+        total = sum(m for _, _, m in r["parts"])
+        assert 2000 <= total <= 86402 and 1 <= r["steps"] <= 20
+        assert r["variant"] in ("LHEVI", "NHEVI")
+        for c, start, m in r["parts"]:
+            assert 0 <= c < 4 and 0 <= start and start + m <= 32768
+    bank = hevi_inputs.serve_bank(seed=6, cols_per_class=64)
+    for b, (nez, N) in zip(bank, hevi_inputs.SIZE_CLASSES):
+        n = 3 * (nez * N + 1)
+        assert b["H"].shape == (64, n) and b["dq"].shape == (64, n) and b["ztop"].shape == (64,)
+        assert (b["ztop"] >= 30e3).all() and (b["ztop"] <= 100e3).all()
