@@ -714,7 +714,7 @@ static unsigned col_grid(const DevView& v, int blk) {
 
 void launch_apply(const DevView& v, int order, const double* x, double* y, int nonlinear,
                   cudaStream_t st) {
-#define HEVI_CALL(NN) k_apply<NN><<<col_grid(v, 128), 128, 0, st>>>(v, x, y, nonlinear)
+#define HEVI_CALL(NN) k_apply<NN><<<col_grid(v, kTile), kTile, 0, st>>>(v, x, y, nonlinear)
   HEVI_ORDER_SWITCH(order, HEVI_CALL)
 #undef HEVI_CALL
 }
@@ -740,7 +740,7 @@ __global__ void __launch_bounds__(128) k_apply_rhs(DevView v, const double* Q, c
 
 void launch_apply_rhs(const DevView& v, int order, const double* Q, const double* H, double* S,
                       cudaStream_t st) {
-#define HEVI_CALL(NN) k_apply_rhs<NN><<<col_grid(v, 128), 128, 0, st>>>(v, Q, H, S)
+#define HEVI_CALL(NN) k_apply_rhs<NN><<<col_grid(v, kTile), kTile, 0, st>>>(v, Q, H, S)
   HEVI_ORDER_SWITCH(order, HEVI_CALL)
 #undef HEVI_CALL
 }
@@ -768,7 +768,7 @@ __global__ void __launch_bounds__(128) k_apply_stage(DevView v, const double* Q,
 
 void launch_apply_stage(const DevView& v, int order, const double* Q, const double* H, double* E,
                         double* LQ, cudaStream_t st) {
-#define HEVI_CALL(NN) k_apply_stage<NN><<<col_grid(v, 128), 128, 0, st>>>(v, Q, H, E, LQ)
+#define HEVI_CALL(NN) k_apply_stage<NN><<<col_grid(v, kTile), kTile, 0, st>>>(v, Q, H, E, LQ)
   HEVI_ORDER_SWITCH(order, HEVI_CALL)
 #undef HEVI_CALL
 }
@@ -1084,8 +1084,10 @@ __global__ void __launch_bounds__(128) k_newton_fpass(DevView v, NewtonArgs a) {
   if (cv == 0) atomicAdd(a.active_out, 1);
 }
 
+// One warp per block: at 106 registers a thread, blocks of four warps fit four
+// to an SM and the launch would spill into a second, nearly empty wave.
 void launch_newton_fpass(const DevView& v, int order, const NewtonArgs& a, cudaStream_t st) {
-#define HEVI_CALL(NN) k_newton_fpass<NN><<<col_grid(v, 128), 128, 0, st>>>(v, a)
+#define HEVI_CALL(NN) k_newton_fpass<NN><<<col_grid(v, kTile), kTile, 0, st>>>(v, a)
   HEVI_ORDER_SWITCH(order, HEVI_CALL)
 #undef HEVI_CALL
 }
