@@ -306,17 +306,22 @@ __device__ __forceinline__ double eos(const Phys& ph, double Theta) {
 // Pressure perturbation about the reference state, from the same equation of
 // state: P(Theta) - P_bar = P_bar ((1 + x)^gamma - 1), x = (Theta - Theta_bar) /
 // Theta_bar, exactly zero at Theta = Theta_bar and free of the cancellation of
-// two O(1e5 Pa) numbers.  For |x| <= 0.02 the binomial series (kEosTerms terms,
-// truncation below 1e-18 of the perturbation,
-// truncation below 1e-19 relative) replaces the FP64 log1p/expm1 pair, which
-// costs several times more on this part's FP64 pipe.
+// two O(1e5 Pa) numbers.  For |x| <= 0.02 the binomial series replaces the
+// FP64 log1p/expm1 pair, which costs several times more on this part's FP64
+// pipe: its first three terms in FP64, the rest (kEosTerms in all; below |x|^3
+// of the leading term, truncation below 1e-19 relative) in FP32, whose
+// rounding then stays below 2e-14 of the perturbation.
 __device__ __forceinline__ double eos_perturbation(const Phys& ph, double Theta, double Theta_bar,
                                                    double P_bar, const double* inv_theta_bar = nullptr) {
   const double x = inv_theta_bar ? (Theta - Theta_bar) * *inv_theta_bar : (Theta - Theta_bar) / Theta_bar;
-  if (fabs(x) <= 0.02) {
-    double s = ph.bin[kEosTerms - 1];
+  const float xf = df_from_double(x).hi;
+  if (fabsf(xf) <= 0.02f) {
+    float t = ph.binhi[kEosTerms - 1];
 #pragma unroll
-    for (int k = kEosTerms - 2; k >= 0; --k) s = fma(s, x, ph.bin[k]);
+    for (int k = kEosTerms - 2; k >= 3; --k) t = fmaf(t, xf, ph.binhi[k]);
+    double s = fma(f2d(t), x, ph.bin[2]);
+    s = fma(s, x, ph.bin[1]);
+    s = fma(s, x, ph.bin[0]);
     return P_bar * (s * x);
   }
   return P_bar * expm1(ph.gamma * log1p(x));
