@@ -347,24 +347,58 @@ def gpu_arm(args, rank, world, local_rank, pool, cores):
             e1.record(stream)
             barrier()
             results["update5"] = dict(ms_per_step=max_over_ranks(e0.elapsed_time(e1)) / steps)
-            # end to end through the C ABI with host buffers: H2D of q^n and H
-            # from pinned memory, the step, D2H of q^{n+1}, every step
+            # end to end through the C ABI with host buffers: every step copies
+            # its q^n and H from pinned memory and reads q^{n+1} back.  The
+            # copies run on their own streams, double-buffered, so that step
+            # k+1's inputs arrive and step k-1's result leaves while step k
+            # computes (the copy engines work beside the kernels)
             hq = qa.cpu().pin_memory()
             hH = H.cpu().pin_memory()
-            hout = torch.empty_like(hq).pin_memory()
-            dq, dH = torch.empty_like(qa), torch.empty_like(H)
+            hout = [torch.empty_like(hq).pin_memory() for _ in range(2)]
+            dq = [torch.empty_like(qa) for _ in range(2)]
+            dH = [torch.empty_like(H) for _ in range(2)]
+            dout = [torch.empty_like(qa) for _ in range(2)]
+            s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+            ev_in = [torch.cuda.Event() for _ in range(2)]
+            ev_used = [torch.cuda.Event() for _ in range(2)]
+            ev_done = [torch.cuda.Event() for _ in range(2)]
+            ev_out = [torch.cuda.Event() for _ in range(2)]
             barrier()
             e0.record(stream)
-            for _ in range(steps):
-                dq.copy_(hq, non_blocking=True)
-                dH.copy_(hH, non_blocking=True)
-                ctx.hevi_lhevi_step(tab, DT, dq, dH, qb)
-                hout.copy_(qb, non_blocking=True)
+            s_in.wait_stream(stream)
+            s_out.wait_stream(stream)
+
+            def upload(k):
+                b = k % 2
+                with torch.cuda.stream(s_in):
+                    if k >= 2:
+                        s_in.wait_event(ev_used[b])  # step k-2 has read these buffers
+                    dq[b].copy_(hq, non_blocking=True)
+                    dH[b].copy_(hH, non_blocking=True)
+                    ev_in[b].record(s_in)
+
+            upload(0)
+            for k in range(steps):
+                b = k % 2
+                if k + 1 < steps:
+                    upload(k + 1)
+                stream.wait_event(ev_in[b])
+                if k >= 2:
+                    stream.wait_event(ev_out[b])  # step k-2's result has left dout[b]
+                ctx.hevi_lhevi_step(tab, DT, dq[b], dH[b], dout[b])
+                ev_used[b].record(stream)
+                ev_done[b].record(stream)
+                with torch.cuda.stream(s_out):
+                    s_out.wait_event(ev_done[b])
+                    hout[b].copy_(dout[b], non_blocking=True)
+                    ev_out[b].record(s_out)
+            stream.wait_stream(s_in)
+            stream.wait_stream(s_out)
             e1.record(stream)
             barrier()
             e2e_ms = max_over_ranks(e0.elapsed_time(e1))
             results["e2e"] = dict(ms_per_step=e2e_ms / steps,
-                                  h2d=(hq.numel() + hH.numel()) * 8, d2h=hout.numel() * 8)
+                                  h2d=(hq.numel() + hH.numel()) * 8, d2h=hout[0].numel() * 8)
         ctx.close()
         del ctx
         torch.cuda.empty_cache()
