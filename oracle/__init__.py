@@ -16,6 +16,7 @@ model-top array ``ztop`` (metres).
 
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 import subprocess
@@ -59,6 +60,7 @@ def _load():
             lib = ctypes.CDLL(build())
             c_int, c_double = ctypes.c_int, ctypes.c_double
             sig = {
+                "or_set_equation_set": (c_int, [c_int]),
                 "or_lgl": (c_int, [c_int, _D, _D]),
                 "or_dmatrix": (c_int, [c_int, _D, _D]),
                 "or_column_grid": (c_int, [c_int, c_int, c_double, _D, _D]),
@@ -89,6 +91,23 @@ def _load():
                 f.argtypes = args
             _lib = lib
     return _lib
+
+
+SET_2C, SET_3C = 0, 1
+
+
+@contextlib.contextmanager
+def equation_set(s: int):
+    """Run the oracle calls inside the block with equation set s (SET_2C:
+    unknowns rho, m, Theta; SET_3C: rho, m, E, total energy, App. A.1 and
+    reading R16 of the C source); set 2C again afterwards."""
+    lib = _load()
+    if lib.or_set_equation_set(int(s)):
+        raise ValueError(f"unknown equation set {s}")
+    try:
+        yield
+    finally:
+        lib.or_set_equation_set(SET_2C)
 
 
 def _dp(a: np.ndarray):

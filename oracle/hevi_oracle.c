@@ -43,6 +43,17 @@
  *       diagonal, eps S with the reference scales S (per-variable magnitudes),
  *       applied to the equilibrated system; GMRES starts at zero and is not
  *       restarted (restarted GMRES(30..60) stagnates on these columns).
+ *   R16 set 3C (App. A.1, Eq. set3c; Jacobian Eq. set3c_jacobian) in a flat
+ *       column without horizontal momentum, unknowns (rho, m = rho w, E): the
+ *       horizontal momenta are only advected by the vertical operator, so zero
+ *       horizontal momentum is an invariant subspace and the coupled system
+ *       keeps three unknowns per point.  Phi = g z; the reference energy is
+ *       E_bar = P_bar / (gamma - 1) + rho_bar g z (P_bar as in R2), the
+ *       pressure flux carries P - P_bar with P = (gamma - 1)(E - m^2/(2 rho) -
+ *       rho g z); the flux Jacobian is that of the fluxes (m, m^2/rho + P,
+ *       (E + P) m / rho), whose printed momentum-row energy entry carries a
+ *       stray 1/rho.  Scales for the Newton norm: (rho_bar, rho_bar c_s,
+ *       E_bar).  Selected by or_set_equation_set(1); 0 (default) is set 2C.
  */
 #include <float.h>
 #include <math.h>
@@ -149,6 +160,15 @@ int or_column_grid(int nez, int N, double ztop, double* z, double* M) {
   return 0;
 }
 
+/* The equation set of every call: 0 = set 2C (unknowns rho, m, Theta),
+ * 1 = set 3C (rho, m, E; reading R16). */
+static int or_set = 0;
+int or_set_equation_set(int s) {
+  if (s != 0 && s != 1) return 1;
+  or_set = s;
+  return 0;
+}
+
 /* App. A.1, Eq. (set2c_pressure): P = P_A (R Theta / P_A)^gamma. */
 static double eos(double Theta) { return OR_P0 * pow(OR_R * Theta / OR_P0, or_gamma()); }
 
@@ -176,7 +196,7 @@ void or_scales(int nz, const double* z, double* s) {
   for (int I = 0; I < nz; ++I) {
     s[3 * I + 0] = rho[I];
     s[3 * I + 1] = rho[I] * cs;
-    s[3 * I + 2] = Th[I];
+    s[3 * I + 2] = or_set ? P[I] / (or_gamma() - 1.0) + rho[I] * OR_G * z[I] : Th[I];
   }
   free(rho);
 }
@@ -192,12 +212,14 @@ typedef struct {
   double* z;   /* nz */
   double* M;   /* nz */
   double *rho_b, *theta_b, *Theta_b, *P_b;
+  double* E_b;  /* set 3C reference energy P_bar / (gamma - 1) + rho_bar g z */
+  double* X_b;  /* reference value of the third unknown: Theta_b (2C) or E_b (3C) */
 } column_t;
 
 static int column_init(column_t* c, int nez, int N, double ztop) {
   c->nez = nez; c->N = N; c->nz = nez * N + 1; c->n = 3 * c->nz;
   if (or_lgl(N, c->xi, c->w)) return 1;
-  c->D = (double*)malloc(sizeof(double) * ((N + 1) * (N + 1) + 6 * c->nz));
+  c->D = (double*)malloc(sizeof(double) * ((N + 1) * (N + 1) + 7 * c->nz));
   c->z = c->D + (N + 1) * (N + 1);
   c->M = c->z + c->nz;
   c->rho_b = c->M + c->nz;
@@ -207,6 +229,10 @@ static int column_init(column_t* c, int nez, int N, double ztop) {
   or_dmatrix(N, c->xi, c->D);
   or_column_grid(nez, N, ztop, c->z, c->M);
   or_reference_state(c->nz, c->z, c->rho_b, c->theta_b, c->Theta_b, c->P_b);
+  c->E_b = c->P_b + c->nz;
+  for (int I = 0; I < c->nz; ++I)
+    c->E_b[I] = c->P_b[I] / (or_gamma() - 1.0) + c->rho_b[I] * OR_G * c->z[I];
+  c->X_b = or_set ? c->E_b : c->Theta_b;
   return 0;
 }
 static void column_free(column_t* c) { free(c->D); }
@@ -241,8 +267,17 @@ static void apply_V(const column_t* c, const double* q, double* v) {
   for (int I = 0; I < nz; ++I) {
     double rho = q[3 * I], m = q[3 * I + 1], Th = q[3 * I + 2];
     fr[I] = m;
-    fm[I] = m * m / rho + (eos(Th) - c->P_b[I]);
-    ft[I] = Th * m / rho;
+    if (or_set) {
+      /* set 3C (R16): Th holds E; P - P_bar from the differences to the reference */
+      double E = Th;
+      double dP = (or_gamma() - 1.0) *
+                  ((E - c->E_b[I]) - m * m / (2.0 * rho) - (rho - c->rho_b[I]) * OR_G * c->z[I]);
+      fm[I] = m * m / rho + dP;
+      ft[I] = (E + c->P_b[I] + dP) * m / rho;
+    } else {
+      fm[I] = m * m / rho + (eos(Th) - c->P_b[I]);
+      ft[I] = Th * m / rho;
+    }
   }
   dss_derivative(c, fr, dr);
   dss_derivative(c, fm, dm);
@@ -264,8 +299,20 @@ static void apply_V(const column_t* c, const double* q, double* v) {
  *   rho-flux   : ( 0,        1,      0  )
  *   m-flux     : ( -w^2,     2w,     P' )
  *   Theta-flux : ( -theta w, theta,  w  )       (reading R5) */
-static void flux_jacobian(const double* q, double K[3][3]) {
+static void flux_jacobian(const double* q, double z, double K[3][3]) {
   double rho = q[0], m = q[1], Th = q[2];
+  if (or_set) {
+    /* set 3C (R16): fluxes (m, m^2/rho + P, (E + P) m / rho), P = (gamma - 1)
+     * (E - m^2/(2 rho) - rho g z): with w = m/rho, h = (E + P)/rho,
+     *   dP/drho = (gamma - 1)(w^2/2 - g z), dP/dm = -(gamma - 1) w, dP/dE = gamma - 1 */
+    double gm = or_gamma() - 1.0, E = Th, w = m / rho;
+    double P = gm * (E - m * w / 2.0 - rho * OR_G * z), h = (E + P) / rho;
+    double Pr = gm * (w * w / 2.0 - OR_G * z), Pm = -gm * w, PE = gm;
+    K[0][0] = 0.0;               K[0][1] = 1.0;         K[0][2] = 0.0;
+    K[1][0] = -w * w + Pr;       K[1][1] = 2 * w + Pm;  K[1][2] = PE;
+    K[2][0] = w * Pr - h * w;    K[2][1] = h + w * Pm;  K[2][2] = w * (1.0 + PE);
+    return;
+  }
   double w = m / rho, th = Th / rho, dP = or_gamma() * eos(Th) / Th;
   K[0][0] = 0.0;     K[0][1] = 1.0; K[0][2] = 0.0;
   K[1][0] = -w * w;  K[1][1] = 2 * w; K[1][2] = dP;
@@ -282,7 +329,7 @@ static void apply_L(const column_t* c, const double* q0, const double* x, double
          *dt = f + 5 * nz;
   for (int I = 0; I < nz; ++I) {
     double K[3][3];
-    flux_jacobian(q0 + 3 * I, K);
+    flux_jacobian(q0 + 3 * I, c->z[I], K);
     const double* xi = x + 3 * I;
     fr[I] = K[0][0] * xi[0] + K[0][1] * xi[1] + K[0][2] * xi[2];
     fm[I] = K[1][0] * xi[0] + K[1][1] * xi[1] + K[1][2] * xi[2];
@@ -316,7 +363,7 @@ static void assemble_band(const column_t* c, double lam, const double* q0, doubl
       for (int j = 0; j <= N; ++j) {
         int J = e * N + j;
         double K[3][3];
-        flux_jacobian(q0 + 3 * J, K);
+        flux_jacobian(q0 + 3 * J, c->z[J], K);
         double coef = lam * c->w[k] * c->D[k * (N + 1) + j] / c->M[I];
         for (int v = 0; v < 3; ++v)
           for (int u = 0; u < 3; ++u) AB(3 * I + v, 3 * J + u) += coef * K[v][u];
@@ -429,7 +476,8 @@ int or_assemble_band(int ncols, int nez, int N, const double* ztop, double lam, 
   return 0;
 }
 
-/* Reference state q_bar = (rho_bar, 0, Theta_bar) for each column. */
+/* Reference state q_bar = (rho_bar, 0, Theta_bar) for each column (set 3C:
+ * (rho_bar, 0, E_bar)). */
 int or_reference_q(int ncols, int nez, int N, const double* ztop, double* q) {
   for (int c = 0; c < ncols; ++c) {
     column_t col;
@@ -438,7 +486,7 @@ int or_reference_q(int ncols, int nez, int N, const double* ztop, double* q) {
     for (int I = 0; I < col.nz; ++I) {
       qc[3 * I] = col.rho_b[I];
       qc[3 * I + 1] = 0.0;
-      qc[3 * I + 2] = col.Theta_b[I];
+      qc[3 * I + 2] = col.X_b[I];
     }
     column_free(&col);
   }
@@ -487,7 +535,7 @@ static double scaled_norm(const column_t* c, const double* F) {
   for (int I = 0; I < c->nz; ++I) {
     double a = F[3 * I] / c->rho_b[I];
     double b = F[3 * I + 1] / (c->rho_b[I] * cs);
-    double d = F[3 * I + 2] / c->Theta_b[I];
+    double d = F[3 * I + 2] / c->X_b[I];
     s2 += a * a + b * b + d * d;
   }
   return sqrt(s2);
@@ -498,7 +546,7 @@ static double unknown_scale(const column_t* c, int i) {
   int I = i / 3, u = i - 3 * I;
   if (u == 0) return c->rho_b[I];
   if (u == 1) return c->rho_b[I] * sqrt(or_gamma() * OR_R * OR_T0);
-  return c->Theta_b[I];
+  return c->X_b[I];
 }
 
 /* Sec. 4.2.1 (NHEVI-GMRES): Jacobian-free Newton-Krylov.  Newton on
@@ -723,7 +771,7 @@ static int lhevi_step_impl(int ncols, int nez, int N, const double* ztop, int s,
     for (int I = 0; I < col.nz; ++I) {
       qbar[3 * I] = col.rho_b[I];
       qbar[3 * I + 1] = 0.0;
-      qbar[3 * I + 2] = col.Theta_b[I];
+      qbar[3 * I + 2] = col.X_b[I];
     }
     memcpy(q0, qlin ? qlin + o : (lin == 0 ? qnc : qbar), sizeof(double) * n);
     assemble_band(&col, lam, q0, ab, ldab);

@@ -753,3 +753,151 @@ def test_lhevi_ark_form_equals_direct_stage_form(name):
     assert info[0] == 0
     d = np.linalg.norm(ark - direct) / np.linalg.norm(direct - qn)
     assert d < 1e-10, d
+
+
+# --------------------------------------------------------------------------
+# Set 3C (App. A.1, Eq. set3c; reading R16): unknowns (rho, m, E)
+# --------------------------------------------------------------------------
+
+GAMMA = 1004.67 / (1004.67 - 287.17)
+CV = 1004.67 - 287.17
+G = 9.80616
+
+
+def _state_3c(nez, N, seed=0, ztop=ZTOP, amp_w=5.0, amp_t=2.0):
+    """A non-rest set-3C state built from (rho, w, T): rest density times
+    1 +- 1%, w uniform (0 at both ends), T = 300 K +- amp_t; E = rho cv T +
+    rho w^2 / 2 + rho g z (internal, kinetic, potential)."""
+    g = np.random.default_rng(seed)
+    z = oracle.column_grid(nez, N, ztop)[0]
+    rho0 = _rest(nez, N, ztop)[0].reshape(-1, 3)[:, 0]
+    rho = rho0 * (1 + 0.01 * g.uniform(-1, 1, z.size))
+    w = g.uniform(-amp_w, amp_w, z.size)
+    w[0] = w[-1] = 0.0
+    T = 300.0 + g.uniform(-amp_t, amp_t, z.size)
+    E = rho * CV * T + rho * w * w / 2 + rho * G * z
+    return np.stack([rho, rho * w, E], 1).reshape(-1)
+
+
+def test_set3c_rest_state_closed_form_and_equilibrium():
+    """The set-3C rest state is the isothermal atmosphere with E = rho cv T0 +
+    rho g z (no kinetic energy), and V of it vanishes exactly."""
+    nez, N = 8, 4
+    z = oracle.column_grid(nez, N, ZTOP)[0]
+    with oracle.equation_set(oracle.SET_3C):
+        q = _rest(nez, N)
+        v = oracle.apply_V(nez, N, ZTOP, q)
+    q3 = q[0].reshape(-1, 3)
+    rho = 1e5 / (287.17 * 300.0) * np.exp(-z * G / (287.17 * 300.0))
+    np.testing.assert_allclose(q3[:, 0], rho, rtol=1e-13)
+    np.testing.assert_allclose(q3[:, 2], rho * CV * 300.0 + rho * G * z, rtol=1e-13)
+    assert np.array_equal(v, np.zeros_like(v))
+
+
+@pytest.mark.parametrize("nez,N", [(2, 2), (8, 4), (16, 3)])
+def test_set3c_conserves_column_mass_and_total_energy(nez, N):
+    """Set 3C is in divergence form with no energy source: with m = 0 at both
+    ends the LGL column integrals of V_rho and V_E vanish (App. A.1)."""
+    _, M = oracle.column_grid(nez, N, ZTOP)
+    q = _state_3c(nez, N, seed=21)
+    with oracle.equation_set(oracle.SET_3C):
+        v = oracle.apply_V(nez, N, ZTOP, q[None])[0].reshape(-1, 3)
+    q3 = q.reshape(-1, 3)
+    assert abs(np.dot(M, v[:, 0])) < 1e-13 * np.abs(M * q3[:, 0]).sum()
+    assert abs(np.dot(M, v[:, 2])) < 1e-13 * np.abs(M * q3[:, 2]).sum()
+
+
+@pytest.mark.parametrize("nez,N", [(2, 2), (8, 4), (16, 3)])
+def test_set3c_mass_and_momentum_tendencies_equal_set2c(nez, N):
+    """The same physical state written in both sets (Theta = rho theta from the
+    same p and rho, E = p/(gamma-1) + m^2/(2 rho) + rho g z) gets the same
+    continuity and momentum tendencies: both sets carry m and m^2/rho + p."""
+    g = np.random.default_rng(22)
+    z = oracle.column_grid(nez, N, ZTOP)[0]
+    q3 = _state_3c(nez, N, seed=23).reshape(-1, 3)
+    rho, m, E = q3[:, 0], q3[:, 1], q3[:, 2]
+    p = (GAMMA - 1) * (E - m * m / (2 * rho) - rho * G * z)
+    theta = p / (rho * 287.17) * (1e5 / p) ** (287.17 / 1004.67)
+    q2 = np.stack([rho, m, rho * theta], 1).reshape(1, -1)
+    v2 = oracle.apply_V(nez, N, ZTOP, q2)[0].reshape(-1, 3)
+    with oracle.equation_set(oracle.SET_3C):
+        v3 = oracle.apply_V(nez, N, ZTOP, q3.reshape(1, -1))[0].reshape(-1, 3)
+    np.testing.assert_allclose(v3[:, 0], v2[:, 0], rtol=0, atol=1e-12 * np.abs(v2[:, 0]).max())
+    np.testing.assert_allclose(v3[:, 1], v2[:, 1], rtol=0, atol=1e-9 * np.abs(v2[:, 1]).max())
+    del g
+
+
+@pytest.mark.parametrize("nez,N", [(2, 2), (4, 4), (16, 3)])
+def test_set3c_linear_operator_is_the_frechet_derivative(nez, N):
+    """L(q0) x against central differences of the set-3C V: pins every entry
+    of the set-3C flux Jacobian (App. A.3, Eq. set3c_jacobian) and the gravity
+    coupling."""
+    q0 = _state_3c(nez, N, seed=24)
+    g = np.random.default_rng(25)
+    with oracle.equation_set(oracle.SET_3C):
+        s = oracle.scales(oracle.column_grid(nez, N, ZTOP)[0])
+        x = s * g.standard_normal(q0.size)
+        x[1] = x[-2] = 0.0
+        L = oracle.apply_L(nez, N, ZTOP, q0[None], x[None])[0]
+        eps = 1e-5
+        fd = (oracle.apply_V(nez, N, ZTOP, (q0 + eps * x)[None])[0]
+              - oracle.apply_V(nez, N, ZTOP, (q0 - eps * x)[None])[0]) / (2 * eps)
+    assert np.linalg.norm(L - fd) <= 1e-7 * np.linalg.norm(L)
+
+
+def test_set3c_hydrostatic_state_at_spectral_rate():
+    """An isothermal atmosphere at another temperature (T1 = 250 K) is in
+    hydrostatic balance, dp/dz = -rho g; written in set 3C its momentum
+    tendency is the discretisation error of that balance, which falls at a
+    spectral rate with N (pins the pressure recovered from E and the sign of
+    the gravity term)."""
+    T1 = 250.0
+    errs = []
+    for N in (2, 4, 6, 8):
+        nez = 3
+        z = oracle.column_grid(nez, N, ZTOP)[0]
+        p = 1e5 * np.exp(-z * G / (287.17 * T1))
+        rho = p / (287.17 * T1)
+        q = np.stack([rho, np.zeros_like(rho), p / (GAMMA - 1) + rho * G * z], 1).reshape(1, -1)
+        with oracle.equation_set(oracle.SET_3C):
+            v = oracle.apply_V(nez, N, ZTOP, q)[0].reshape(-1, 3)
+        errs.append(np.abs(v[:, 1]).max() / (rho.max() * G))
+        assert np.abs(v[:, 0]).max() == 0.0 and np.abs(v[:, 2]).max() == 0.0
+    assert errs[0] > 10 * errs[1] > 100 * errs[2], errs
+    assert errs[3] < 1e-8, errs
+
+
+def test_set3c_one_newton_iteration_is_the_lhevi_solve():
+    """Sec. 4.3 for set 3C: one Newton iteration on F(q) = q - Lambda V(q) - R
+    from q0 solves (I - Lambda L(q0)) q1 = R + Lambda (V(q0) - L(q0) q0)."""
+    nez, N, lam = 8, 4, 87.868
+    q0 = _state_3c(nez, N, seed=26)[None]
+    with oracle.equation_set(oracle.SET_3C):
+        R = q0 + 0.01 * oracle.scales(oracle.column_grid(nez, N, ZTOP)[0])[None] * \
+            np.random.default_rng(27).standard_normal(q0.shape)
+        R[0, 1] = R[0, -2] = 0.0
+        q1, it, st = oracle.newton(nez, N, ZTOP, lam, R, q0, rtol=0.0, max_iter=1)
+        assert it[0] == 1
+        b = R + lam * (oracle.apply_V(nez, N, ZTOP, q0) - oracle.apply_L(nez, N, ZTOP, q0, q0))
+        x, info = oracle.stage_solve(nez, N, ZTOP, lam, q0, b)
+    assert (info == 0).all()
+    np.testing.assert_allclose(q1, x, rtol=1e-12, atol=1e-12 * np.abs(q0).max())
+
+
+def test_set3c_newton_converges_quadratically():
+    nez, N, lam = 8, 4, 87.868
+    q0 = _state_3c(nez, N, seed=28, amp_w=20.0, amp_t=5.0)[None]
+    with oracle.equation_set(oracle.SET_3C):
+        s = oracle.scales(oracle.column_grid(nez, N, ZTOP)[0])
+        R = q0.copy()
+
+        def fnorm(q):
+            return np.linalg.norm((q - lam * oracle.apply_V(nez, N, ZTOP, q) - R) / s)
+        norms = [fnorm(q0)]
+        for m in range(1, 5):
+            q, it, st = oracle.newton(nez, N, ZTOP, lam, R, q0, rtol=0.0, max_iter=m)
+            norms.append(fnorm(q))
+    norms = np.array(norms) / norms[0]
+    for m in range(3):
+        assert norms[m + 1] <= 10.0 * norms[m] ** 2, norms
+    assert norms[4] < 1e-12, norms
