@@ -53,7 +53,9 @@
  *       rho g z); the flux Jacobian is that of the fluxes (m, m^2/rho + P,
  *       (E + P) m / rho), whose printed momentum-row energy entry carries a
  *       stray 1/rho.  Scales for the Newton norm: (rho_bar, rho_bar c_s,
- *       E_bar).  Selected by or_set_equation_set(1); 0 (default) is set 2C.
+ *       E_bar); the band LU solves the system equilibrated with the same
+ *       scales (E and rho differ by five orders of magnitude).  Selected by
+ *       or_set_equation_set(1); 0 (default) is set 2C.
  */
 #include <float.h>
 #include <math.h>
@@ -501,6 +503,34 @@ int or_grid(int ncols, int nez, int N, const double* ztop, double* z, double* M)
   return 0;
 }
 
+/* The band LU of a column's stage matrix, and the solve with it.  Set 3C
+ * (reading R16) is solved equilibrated, (S^-1 A S)(S^-1 x) = S^-1 b with the
+ * reference scales S = (rho_bar, rho_bar c_s, E_bar): its unknowns differ by
+ * five orders of magnitude and the unscaled band's condition number (~1e14)
+ * would put the FP64 LU's error near 1e-10; set 2C is factored as assembled. */
+static double unknown_scale(const column_t* c, int i);
+static int factor_band(const column_t* c, double lam, const double* q0, double* ab, int ldab,
+                       int* ipiv) {
+  int n = c->n, kl = 3 * (c->N + 1) - 1;
+  assemble_band(c, lam, q0, ab, ldab);
+  if (or_set) {
+    for (int j = 0; j < n; ++j) {
+      int i0 = j - kl < 0 ? 0 : j - kl, i1 = j + kl > n - 1 ? n - 1 : j + kl;
+      for (int i = i0; i <= i1; ++i)
+        ab[(size_t)j * ldab + (2 * kl + i - j)] *= unknown_scale(c, j) / unknown_scale(c, i);
+    }
+  }
+  return or_gbtrf(n, kl, kl, ab, ldab, ipiv);
+}
+static void solve_band(const column_t* c, const double* ab, int ldab, const int* ipiv, double* x) {
+  int n = c->n, kl = 3 * (c->N + 1) - 1;
+  if (or_set)
+    for (int i = 0; i < n; ++i) x[i] /= unknown_scale(c, i);
+  or_gbtrs(n, kl, kl, ab, ldab, ipiv, x);
+  if (or_set)
+    for (int i = 0; i < n; ++i) x[i] *= unknown_scale(c, i);
+}
+
 /* Sec. 4.3, Eq. (lhevi-ark-final-2): solve (I - Lambda L(q0)) x = b for each
  * column with the band LU above.  info[c] is dgbtrf's info for column c. */
 int or_stage_solve(int ncols, int nez, int N, const double* ztop, double lam, const double* q0,
@@ -513,10 +543,9 @@ int or_stage_solve(int ncols, int nez, int N, const double* ztop, double lam, co
     column_t col;
     if (column_init(&col, nez, N, ztop[c])) { bad = 1; break; }
     size_t o = (size_t)c * n;
-    assemble_band(&col, lam, q0 + o, ab, ldab);
-    info[c] = or_gbtrf(n, kl, kl, ab, ldab, ipiv);
+    info[c] = factor_band(&col, lam, q0 + o, ab, ldab, ipiv);
     memcpy(x + o, b + o, sizeof(double) * n);
-    if (info[c] == 0) or_gbtrs(n, kl, kl, ab, ldab, ipiv, x + o);
+    if (info[c] == 0) solve_band(&col, ab, ldab, ipiv, x + o);
     column_free(&col);
   }
   free(ab);
@@ -702,10 +731,9 @@ int or_newton(int ncols, int nez, int N, const double* ztop, double lam, const d
     if (f0 > OR_NEWTON_FLOOR * scaled_norm(&col, qc)) {
       status[c] = 5;
       for (int m = 1; m <= max_iter; ++m) {
-        assemble_band(&col, lam, qc, ab, ldab);
-        if (or_gbtrf(n, kl, kl, ab, ldab, ipiv) != 0) { status[c] = 4; break; }
+        if (factor_band(&col, lam, qc, ab, ldab, ipiv) != 0) { status[c] = 4; break; }
         for (int i = 0; i < n; ++i) F[i] = -F[i];
-        or_gbtrs(n, kl, kl, ab, ldab, ipiv, F);
+        solve_band(&col, ab, ldab, ipiv, F);
         for (int i = 0; i < n; ++i) qc[i] += F[i];
         const double dn = scaled_norm(&col, F);
         for (int i = 0; i < n; ++i) t[i] = qc[i] - qi[i];
@@ -774,8 +802,7 @@ static int lhevi_step_impl(int ncols, int nez, int N, const double* ztop, int s,
       qbar[3 * I + 2] = col.X_b[I];
     }
     memcpy(q0, qlin ? qlin + o : (lin == 0 ? qnc : qbar), sizeof(double) * n);
-    assemble_band(&col, lam, q0, ab, ldab);
-    info[c] = or_gbtrf(n, kl, kl, ab, ldab, ipiv);
+    info[c] = factor_band(&col, lam, q0, ab, ldab, ipiv);
     for (int i = 0; i < s; ++i) {
       double* Qi = Q + (size_t)n * i;
       if (i == 0) {
@@ -790,7 +817,7 @@ static int lhevi_step_impl(int ncols, int nez, int N, const double* ztop, int s,
           }
           Qi[r] = qnc[r] + dt * acc + wq;
         }
-        if (info[c] == 0) or_gbtrs(n, kl, kl, ab, ldab, ipiv, Qi);
+        if (info[c] == 0) solve_band(&col, ab, ldab, ipiv, Qi);
         /* Q_i = q_tt - sum_j w_ij Q_j */
         for (int r = 0; r < n; ++r) {
           double wq = 0.0;
