@@ -169,6 +169,24 @@ hevi_status hevi_stage_solve_async(hevi_ctx* ctx, const double* rhs, double* x);
  * relative error and the sweep limit (defaults 1e-11 and 10). */
 hevi_status hevi_set_refinement(hevi_ctx* ctx, double tol, int32_t max_sweeps);
 
+/* Equation set of the context's unknowns (App. A.1):
+ *   HEVI_SET_2C (default): (rho, m = rho w, Theta = rho theta), pressure from
+ *     the equation of state of set 2C;
+ *   HEVI_SET_3C: (rho, m, E) with E the total energy (internal, kinetic,
+ *     potential: E = rho (c_v T + w^2/2 + g z)), P = (gamma - 1)(E - m^2/(2 rho)
+ *     - rho g z) (Eq. set3c), in a column without horizontal momentum (an
+ *     invariant subspace of the vertical operator); the flux Jacobian is that
+ *     of Eq. set3c_jacobian restricted to it.  Set 3C runs on the FP64 path
+ *     only: HEVI_ERR_INVALID_ARG on an HEVI_FP32_IR context, and the
+ *     NHEVI-GMRES solve refuses a set-3C context.
+ * Recomputes the reference table (E_bar = P_bar / (gamma - 1) + rho_bar g z for
+ * set 3C; hevi_reference_state then writes (rho_bar, 0, E_bar)) on the
+ * context's stream; the factors of the last hevi_factor become stale.  Call it
+ * before the states of the new set are used. */
+#define HEVI_SET_2C 0
+#define HEVI_SET_3C 1
+hevi_status hevi_set_equation_set(hevi_ctx* ctx, int32_t set);
+
 /* How hevi_nhevi_step ends its Newton sequences.  on = 1 (default): after
  * each iteration the host reads the device's count of still-iterating
  * columns (a stream synchronisation) and enqueues no more iterations once it

@@ -21,6 +21,7 @@ from . import build as _build_mod
 __all__ = ["load", "Context", "HeviError", "FP64", "FP32_IR", "tableau", "Tableau"]
 
 FP64, FP32_IR = 0, 1
+SET_2C, SET_3C = 0, 1  # equation sets (hevi_set_equation_set)
 STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of device memory",
           4: "singular column", 5: "not converged", 6: "non-physical input state",
           7: "device wait past its limit"}
@@ -84,6 +85,7 @@ def load(build: bool = False):
         "hevi_reference_columns": (_I32, [_P, _I64, _I64, _P]),
         "hevi_set_column_tops": (_I32, [_P, _I64, _I64, DP]),
         "hevi_set_newton_host_check": (_I32, [_P, _I32]),
+        "hevi_set_equation_set": (_I32, [_P, _I32]),
         "hevi_autotune_solve": (_I32, [_P, _P, _P, _I32, ctypes.POINTER(_I32), DP, DP]),
         "hevi_newton_solve": (_I32, [_P, _D, _P, _P, _D, _I32]),
         "hevi_newton_solve_async": (_I32, [_P, _D, _P, _P, _D, _I32]),
@@ -362,6 +364,10 @@ class Context:
         _check(self._lib.hevi_set_column_tops(self._h, int(first), int(zt.size),
                                               zt.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
                "hevi_set_column_tops")
+
+    def hevi_set_equation_set(self, eqset: int):
+        """SET_2C (rho, m, Theta) or SET_3C (rho, m, E; FP64 contexts only)."""
+        _check(self._lib.hevi_set_equation_set(self._h, int(eqset)), "hevi_set_equation_set")
 
     def hevi_set_newton_host_check(self, on: bool):
         _check(self._lib.hevi_set_newton_host_check(self._h, 1 if on else 0),

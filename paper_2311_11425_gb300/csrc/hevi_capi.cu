@@ -857,6 +857,15 @@ hevi_status hevi_set_column_tops(hevi_ctx* c, int64_t first, int64_t count, cons
   return check_launch(c, 1);
 }
 
+hevi_status hevi_set_equation_set(hevi_ctx* c, int32_t set) {
+  if (!c || (set != HEVI_SET_2C && set != HEVI_SET_3C)) return HEVI_ERR_INVALID_ARG;
+  if (set == HEVI_SET_3C && c->prec != HEVI_FP64) return HEVI_ERR_INVALID_ARG;
+  c->v.ph.eqset = set;
+  hevi::launch_setup_ref(c->v, c->d_col_order, c->d_col_nez, c->stream);
+  c->factored = false;
+  return check_launch(c, 1);
+}
+
 hevi_status hevi_set_newton_host_check(hevi_ctx* c, int32_t on) {
   if (!c || (on != 0 && on != 1)) return HEVI_ERR_INVALID_ARG;
   c->newton_host_check = on != 0;
@@ -983,6 +992,7 @@ hevi_status hevi_newton_solve(hevi_ctx* c, double gamma_dt, double* state, const
 hevi_status hevi_newton_gmres_solve_async(hevi_ctx* c, double gamma_dt, double* state,
                                           const double* R, double eps, double rtol, double gtol,
                                           int32_t max_newton, int32_t kmax, int32_t* krylov) {
+  if (c && c->v.ph.eqset != 0) return HEVI_ERR_INVALID_ARG;  // the JFNK path is set 2C only
   if (!c || !state || !R || state == R || !(gamma_dt >= 0.0) || !(eps > 0.0) || !(rtol >= 0.0) ||
       !(gtol > 0.0) || max_newton < 0 || max_newton > 1000 || kmax < 0)
     return HEVI_ERR_INVALID_ARG;

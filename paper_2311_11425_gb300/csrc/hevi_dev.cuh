@@ -16,6 +16,51 @@ namespace hevi {
 // and uploads it in its upload function (upload_tables calls all of them).
 static __constant__ LglTables c_tab;
 
+// Height of point I of a column of nez = (nz - 1) / N elements of height dz
+// (the ends exact).
+template <int N>
+__device__ __forceinline__ double point_z(double dz, int I, int nz) {
+  if (I == 0) return 0.0;
+  if (I == nz - 1) return (double)((nz - 1) / N) * dz;
+  const int e = I / N, k = I - e * N;
+  return e * dz + (c_tab.xi[N][k] + 1.0) * 0.5 * dz;
+}
+
+// Set 3C (App. A.1, Eq. set3c, in a column without horizontal momentum):
+// from (rho, m, E) at height z, w = m / rho, the pressure perturbation
+// P - P_bar = (gamma - 1)((E - E_bar) - m w / 2 - (rho - rho_bar) g z) (the
+// differences to the reference first) and h = (E + P) / rho; false for a
+// non-physical state (rho <= 0 or P <= 0).
+__device__ __forceinline__ bool lin_coefs_3c(const Phys& ph, double rho, double m, double E,
+                                             double rho_bar, double E_bar, double P_bar, double z,
+                                             double* w, double* h, double* dP) {
+  if (!(rho > 0.0) || !isfinite(m) || !isfinite(E)) return false;
+  const double ir = rcp64(rho);
+  *w = m * ir;
+  *dP = (ph.gamma - 1.0) * ((E - E_bar) - 0.5 * m * *w - (rho - rho_bar) * ph.g * z);
+  const double P = P_bar + *dP;
+  if (!(P > 0.0)) return false;
+  *h = (E + P) * ir;
+  return true;
+}
+
+// Row v of the set-3C flux Jacobian (App. A.3, Eq. set3c_jacobian without
+// horizontal momentum) at a point with w, h = (E + P) / rho and height z:
+//   rho-flux (0, 1, 0); m-flux (-w^2 + P_rho, 2w + P_m, P_E);
+//   E-flux (w P_rho - h w, h + w P_m, w (1 + P_E)),
+// P_rho = (gamma - 1)(w^2/2 - g z), P_m = -(gamma - 1) w, P_E = gamma - 1.
+__device__ __forceinline__ void k_row_3c(const Phys& ph, int v, double w, double h, double z,
+                                         double& k0, double& k1, double& k2) {
+  const double gm = ph.gamma - 1.0, Pr = gm * (0.5 * w * w - ph.g * z), Pm = -gm * w;
+  if (v == 0) {
+    k0 = 0.0; k1 = 1.0; k2 = 0.0;
+  } else if (v == 1) {
+    k0 = -w * w + Pr; k1 = 2.0 * w + Pm; k2 = gm;
+  } else {
+    k0 = w * Pr - h * w; k1 = h + w * Pm; k2 = w * ph.gamma;
+  }
+}
+
 template <int N>
 __device__ __forceinline__ void elem_deriv(const double (&f)[N + 1][3], double (&cc)[N + 1][3]) {
   constexpr int P = (N + 1) / 2;

@@ -62,6 +62,8 @@ struct Phys {
   // FP32 constants of the equilibration scales of the FP32 path:
   // rho_bar = rho0f exp(-za z), theta_bar = T0f exp(zb z), c_s = csf
   float rho0f, za, zb, T0f, csf;
+  // equation set: 0 = set 2C (rho, m, Theta), 1 = set 3C (rho, m, E; FP64 path)
+  int eqset;
 };
 // Fill the derived fields of a Phys from T0, p0, R, cp, g (host).
 inline void phys_derive(Phys& ph);
@@ -328,6 +330,7 @@ __device__ __forceinline__ double eos_perturbation(const Phys& ph, double Theta,
 }
 
 inline void phys_derive(Phys& ph) {
+  ph.eqset = 0;
   ph.cv = ph.cp - ph.R;
   ph.gamma = ph.cp / ph.cv;
   ph.cs = std::sqrt(ph.gamma * ph.R * ph.T0);

@@ -77,10 +77,13 @@ __global__ void k_setup_ref(DevView v, const int32_t* col_order, const int32_t* 
     const double rho = ph.p0 / (ph.R * ph.T0) * exp(-z / Hs);
     const double th = ph.T0 * exp(ph.g * z / (ph.cp * ph.T0));
     const double Th = rho * th;
+    const double P = eos(ph, Th);
+    // set 3C keeps the reference energy E_bar = P_bar / (gamma - 1) + rho_bar g z
+    const double X = ph.eqset == 1 ? P / (ph.gamma - 1.0) + rho * ph.g * z : Th;
     r[3 * I + 0] = rho;
-    r[3 * I + 1] = eos(ph, Th);
-    r[3 * I + 2] = Th;
-    if (v.ithb) v.ithb[v.col_off[col] / 3 + I] = 1.0 / Th;
+    r[3 * I + 1] = P;
+    r[3 * I + 2] = X;
+    if (v.ithb) v.ithb[v.col_off[col] / 3 + I] = 1.0 / X;
   }
 }
 
@@ -171,7 +174,11 @@ __device__ __forceinline__ void assemble_row(const DevView& v, const Col& c, dou
         g = fac * c_tab.wD[N][kI * (N + 1) + j];
       const T wJ = T(lin[3 * J]), thJ = T(lin[3 * J + 1]), cJ = T(lin[3 * J + 2]);
       T kv0, kv1, kv2;
-      if (vv == 0) {
+      if (v.ph.eqset == 1) {  // set 3C: lin = (w, h, z)
+        double k0, k1, k2;
+        k_row_3c(v.ph, vv, lin[3 * J], lin[3 * J + 1], lin[3 * J + 2], k0, k1, k2);
+        kv0 = T(k0); kv1 = T(k1); kv2 = T(k2);
+      } else if (vv == 0) {
         kv0 = T(0); kv1 = T(1); kv2 = T(0);
       } else if (vv == 1) {
         kv0 = -wJ * wJ; kv1 = T(2) * wJ; kv2 = cJ;
@@ -313,7 +320,16 @@ __device__ void factor_column(const DevView& v, const TileDesc& t, int lane, dou
       rho = v.ref[a]; m = 0.0; Th = v.ref[a + 2];
     }
     double w, th, cc, dP;
-    if (!lin_coefs(ph, rho, m, Th, v.ref[a + 2], v.ref[a + 1], &w, &th, &cc, &dP)) {
+    if (ph.eqset == 1) {  // set 3C: (w, h, z)
+      const double z = point_z<N>(1.0 / (0.5 * c.s), I, c.nz);
+      double h;
+      if (!lin_coefs_3c(ph, rho, m, Th, v.ref[a], v.ref[a + 2], v.ref[a + 1], z, &w, &h, &dP)) {
+        ok = false;
+        w = h = 0.0;
+      }
+      th = h;
+      cc = z;
+    } else if (!lin_coefs(ph, rho, m, Th, v.ref[a + 2], v.ref[a + 1], &w, &th, &cc, &dP)) {
       ok = false;
       w = 0.0; th = 0.0; cc = 0.0;
     }
@@ -394,6 +410,14 @@ static void launch_factor_n(const DevView& v, double lam, const double* q0, cuda
   const int blk = pick_block(window_slots(N) * esz, 64), tiles_per_blk = blk / kTile;
   const unsigned grid = (unsigned)((v.tile_count + tiles_per_blk - 1) / tiles_per_blk);
   const int smem = window_slots(N) * blk * esz;
+  if (v.ph.eqset == 1) {
+    // set 3C: the band equilibrated with the reference scales (its unknowns
+    // differ by five orders of magnitude); the solve scales b and x to match
+    cudaFuncSetAttribute(k_factor<N, double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         smem);
+    k_factor<N, double, true><<<grid, blk, smem, st>>>(v, lam, q0);
+    return;
+  }
   cudaFuncSetAttribute(k_factor<N, double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   k_factor<N, double, false><<<grid, blk, smem, st>>>(v, lam, q0);
 }
@@ -560,11 +584,18 @@ __device__ void solve_fp64_column(const DevView& v, const TileDesc& t, int lane,
     return;
   }
   v.col_status[c.col] = HEVI_COL_OK;
-  for (int i = 0; i < c.n; ++i) y[i * stride] = b[c.off + i];
+  // set 3C factors S^-1 A S (S: rho_bar, rho_bar c_s, E_bar): y = S^-1 b, x = S y
+  const bool eq = v.ph.eqset == 1;
+  const double* ref = v.ref + c.off;
+  auto scale = [&](int i) {
+    const int P = i / 3, u = i - 3 * P;
+    return u == 0 ? ref[3 * P] : (u == 1 ? ref[3 * P] * v.ph.cs : ref[3 * P + 2]);
+  };
+  for (int i = 0; i < c.n; ++i) y[i * stride] = eq ? b[c.off + i] / scale(i) : b[c.off + i];
   for (int i = c.n; i < c.n + 2 * K; ++i) y[i * stride] = 0.0;
   forward_sweep<N, double, double>(base, lane, c.n, y, stride);
   backward_sweep<N, double, double>(base, lane, c.n, y, stride);
-  for (int i = 0; i < c.n; ++i) x[c.off + i] = y[i * stride];
+  for (int i = 0; i < c.n; ++i) x[c.off + i] = eq ? y[i * stride] * scale(i) : y[i * stride];
   v.col_iters[c.col] = 1;
 }
 
@@ -630,6 +661,18 @@ __device__ void apply_V_column(const DevView& v, const Col& c, const double* q, 
   bool ok = true;
   auto flux = [&](int I, double* f) {
     const double rho = qc[3 * I], m = qc[3 * I + 1], Th = qc[3 * I + 2];
+    if (ph.eqset == 1) {  // set 3C: fluxes (m, m^2/rho + P - P_bar, (E + P) m / rho)
+      double w, h, dP;
+      if (!lin_coefs_3c(ph, rho, m, Th, ref[3 * I], ref[3 * I + 2], ref[3 * I + 1],
+                        point_z<N>(1.0 / (0.5 * c.s), I, c.nz), &w, &h, &dP)) {
+        ok = false;
+        w = h = dP = 0.0;
+      }
+      f[0] = m;
+      f[1] = fma(m, w, dP);
+      f[2] = h * m;
+      return;
+    }
     if (!(rho > 0.0) || !(Th > 0.0)) ok = false;
     const double ir = rcp64(rho);
     f[0] = m;
@@ -664,6 +707,16 @@ __device__ void apply_L_column(const DevView& v, const Col& c, const double* x, 
   auto flux = [&](int I, double* f) {
     const double x0 = xc[3 * I], x1 = xc[3 * I + 1], x2 = xc[3 * I + 2];
     const double wI = lin[3 * I], thI = lin[3 * I + 1], cI = lin[3 * I + 2];
+    if (v.ph.eqset == 1) {  // set 3C: lin = (w, h, z)
+      f[0] = x1;
+#pragma unroll
+      for (int r = 1; r < 3; ++r) {
+        double k0, k1, k2;
+        k_row_3c(v.ph, r, wI, thI, cI, k0, k1, k2);
+        f[r] = fma(k0, x0, fma(k1, x1, k2 * x2));
+      }
+      return;
+    }
     f[0] = x1;
     f[1] = fma(-wI * wI, x0, fma(2.0 * wI, x1, cI * x2));
     f[2] = fma(-thI * wI, x0, fma(thI, x1, wI * x2));
@@ -1023,6 +1076,18 @@ __global__ void __launch_bounds__(128) k_newton_fpass(DevView v, NewtonArgs a) {
   auto flux = [&](int I, double* f) {
     const double rho = qc[3 * I], m = qc[3 * I + 1], Th = qc[3 * I + 2];
     double w, th, cc, dP;
+    if (ph.eqset == 1) {  // set 3C: E-flux (E + P) m / rho = h m
+      double h;
+      if (!lin_coefs_3c(ph, rho, m, Th, ref[3 * I], ref[3 * I + 2], ref[3 * I + 1],
+                        point_z<N>(1.0 / (0.5 * c.s), I, c.nz), &w, &h, &dP)) {
+        ok = false;
+        w = h = dP = 0.0;
+      }
+      f[0] = m;
+      f[1] = fma(m, w, dP);
+      f[2] = h * m;
+      return;
+    }
     if (!lin_coefs(ph, rho, m, Th, ref[3 * I + 2], ref[3 * I + 1], &w, &th, &cc, &dP,
                    v.ithb ? v.ithb + c.off / 3 + I : nullptr)) {
       ok = false;
