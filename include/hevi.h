@@ -176,9 +176,10 @@ hevi_status hevi_set_refinement(hevi_ctx* ctx, double tol, int32_t max_sweeps);
  *     potential: E = rho (c_v T + w^2/2 + g z)), P = (gamma - 1)(E - m^2/(2 rho)
  *     - rho g z) (Eq. set3c), in a column without horizontal momentum (an
  *     invariant subspace of the vertical operator); the flux Jacobian is that
- *     of Eq. set3c_jacobian restricted to it.  Set 3C runs on the FP64 path
- *     only: HEVI_ERR_INVALID_ARG on an HEVI_FP32_IR context, and the
- *     NHEVI-GMRES solve refuses a set-3C context.
+ *     of Eq. set3c_jacobian restricted to it.  Both precisions; the FP64 band
+ *     of set 3C is factored equilibrated with (rho_bar, rho_bar c_s, E_bar),
+ *     as the FP32 band always is.  The NHEVI-GMRES solve refuses a set-3C
+ *     context.
  * Recomputes the reference table (E_bar = P_bar / (gamma - 1) + rho_bar g z for
  * set 3C; hevi_reference_state then writes (rho_bar, 0, E_bar)) on the
  * context's stream; the factors of the last hevi_factor become stale.  Call it

@@ -613,8 +613,8 @@ hevi_status hevi_setup(hevi_ctx** out, const hevi_column_grid* grid, const hevi_
     const int64_t n = 3 * ((int64_t)t.nez * t.order + 1);
     // the FP32 solve's scratch, [row][lane]: the point coefficients of L(q0)
     // (FP64, n rows), the work vector (n + K + 1 rows, rounded to 4) and the
-    // first solution, the correction sum and the residual (n rows each)
-    y_off += (2 * n + (n + 3 * (t.order + 1) + 3) / 4 * 4 + 3 * n) * kTile;
+    // first solution, the correction sum and the residual's two parts (n rows each)
+    y_off += (2 * n + (n + 3 * (t.order + 1) + 3) / 4 * 4 + 4 * n) * kTile;
     fac_off += n * rl_of(t.order, precision) * kTile;
     scr_off += n * ur2_of(t.order) * kTile;
     if (c->order_count[t.order] == 0) c->order_begin[t.order] = (int32_t)c->h_tiles.size();
@@ -783,7 +783,7 @@ int64_t hevi_estimate_bytes(const hevi_column_grid* grid, hevi_precision precisi
     const int64_t tiles = (count[c] + kTile - 1) / kTile;
     state += n * count[c];
     ntiles += tiles;
-    ysc += tiles * (2 * n + (n + 3 * (N + 1) + 3) / 4 * 4 + 3 * n) * kTile;
+    ysc += tiles * (2 * n + (n + 3 * (N + 1) + 3) / 4 * 4 + 4 * n) * kTile;
     fac += tiles * n * rl_of(N, precision) * kTile;
     scr += tiles * n * ur2_of(N) * kTile;
   }
@@ -859,7 +859,6 @@ hevi_status hevi_set_column_tops(hevi_ctx* c, int64_t first, int64_t count, cons
 
 hevi_status hevi_set_equation_set(hevi_ctx* c, int32_t set) {
   if (!c || (set != HEVI_SET_2C && set != HEVI_SET_3C)) return HEVI_ERR_INVALID_ARG;
-  if (set == HEVI_SET_3C && c->prec != HEVI_FP64) return HEVI_ERR_INVALID_ARG;
   c->v.ph.eqset = set;
   hevi::launch_setup_ref(c->v, c->d_col_order, c->d_col_nez, c->stream);
   c->factored = false;

@@ -225,10 +225,12 @@ __device__ __forceinline__ float np_point_z(float dz, int I, int nz) {
 // conditions the FP32 factors and does not enter the FP64 residual).
 __device__ __forceinline__ void np_scales(const Phys& ph, float z, float (&s)[3]) {
   const float rho = ph.rho0f * __expf(-ph.za * z);
-  const float th = ph.T0f * __expf(ph.zb * z);
   s[0] = rho;
   s[1] = rho * ph.csf;
-  s[2] = rho * th;
+  if (ph.eqset == 1)
+    s[2] = rho * (ph.cvT0f + ph.gf * z);  // set 3C: E_bar = rho_bar (c_v T0 + g z)
+  else
+    s[2] = rho * (ph.T0f * __expf(ph.zb * z));  // Theta_bar
 }
 
 // Prefetch the line holding p into L1 (no registers held).

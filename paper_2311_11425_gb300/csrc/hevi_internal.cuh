@@ -62,6 +62,7 @@ struct Phys {
   // FP32 constants of the equilibration scales of the FP32 path:
   // rho_bar = rho0f exp(-za z), theta_bar = T0f exp(zb z), c_s = csf
   float rho0f, za, zb, T0f, csf;
+  float cvT0f, gf;  // c_v T0 and g: the set-3C energy scale rho_bar (c_v T0 + g z)
   // equation set: 0 = set 2C (rho, m, Theta), 1 = set 3C (rho, m, E; FP64 path)
   int eqset;
 };
@@ -345,6 +346,8 @@ inline void phys_derive(Phys& ph) {
   ph.za = (float)(ph.g / (ph.R * ph.T0));
   ph.zb = (float)(ph.g / (ph.cp * ph.T0));
   ph.T0f = (float)ph.T0;
+  ph.cvT0f = (float)(ph.cv * ph.T0);
+  ph.gf = (float)ph.g;
   ph.csf = (float)ph.cs;
 }
 

@@ -124,15 +124,45 @@ __device__ __forceinline__ void np_row_next(NpRowF& R, int nz, int n, const floa
   np_row_derive<N>(R, nz, n, is32);
 }
 
+// Set 3C point of the FP32 factor (App. A.1, A.3): the linearisation
+// coefficients (w, h) of q0 at height z, and the point's scaled Jacobian rows
+// ks[3 v + u] = lam_s K~_vu s_u with K~ = K T: the band is factored in the
+// variables (rho, m, E - g z rho), T the identity but for g z at (E, rho), so
+// the rho column of K gains g z times its E column and the identity part of
+// the band gains the entry g z s_rho at (E, rho) (*kz; divided by s_E in the
+// row).  False for a non-physical q0 (w = h = 0 then).
+__device__ __forceinline__ bool np_point_3c(const Phys& ph, double rho, double m, double E,
+                                          double rho_bar, double E_bar, double P_bar, double z,
+                                          float s0, float s1, float s2, float lam_s, float* ks,
+                                          float* kz, double* wh) {
+  double w, h, dP;
+  const bool ok = lin_coefs_3c(ph, rho, m, E, rho_bar, E_bar, P_bar, z, &w, &h, &dP);
+  if (!ok) w = h = 0.0;
+  const double zeta = ph.g * z;
+  for (int r = 0; r < 3; ++r) {
+    double k0, k1, k2;
+    k_row_3c(ph, r, w, h, z, k0, k1, k2);
+    ks[3 * r] = lam_s * ((float)(k0 + zeta * k2) * s0);
+    ks[3 * r + 1] = lam_s * ((float)k1 * s1);
+    ks[3 * r + 2] = lam_s * ((float)k2 * s2);
+  }
+  *kz = (float)zeta * s0;
+  wh[0] = w;
+  wh[1] = h;
+  return ok;
+}
+
 // Entry (i, col) of A_hat = S^-1 (I + Lambda Dcal K(q0) + Lambda G) S (Sec.
 // 4.2.3, App. A.3), col = 3J + u, from the column's tables
 //   KSp[9 J + 3 v + u] = Lambda (2/dz) K_vu(q0_J) s_(3J+u),  KG[J] = Lambda g s_(3J):
-//   delta + G[cls][J - I] KSp / s_i + KG / s_i [v = m, u = rho, J = I],
+//   delta + G[cls][J - I] KSp / s_i + KG / s_i [v = m, u = rho, J = I]
+//   + KZ / s_i [v = E, u = rho, J = I] (set 3C, EQ3),
 // identity rows at the ends' m unknowns, 0 outside the band or past the last
 // unknown (colok: col < n).
-template <int N>
+template <int N, bool EQ3>
 __device__ __forceinline__ float np_ent(const NpRowF& R, int col, int J, int u, bool colok,
-                                        const float* G, const float* KSp, const float* KG) {
+                                        const float* G, const float* KSp, const float* KG,
+                                        const float* KZ) {
   const int dJ = J - R.I;
   const bool live = R.live && colok;
   const bool inb = live && (unsigned)(dJ + N) <= 2u * N;
@@ -141,10 +171,11 @@ __device__ __forceinline__ float np_ent(const NpRowF& R, int col, int J, int u, 
   const float one = (col == R.i && live) ? 1.0f : 0.0f;
   float a = fmaf(inb ? g * ks : 0.0f, R.isi, one);
   if (R.v == 1 && u == 0 && dJ == 0 && live) a = fmaf(KG[J], R.isi, a);
+  if (EQ3 && R.v == 2 && u == 0 && dJ == 0 && live) a = fmaf(KZ[J], R.isi, a);
   return R.ident ? one : a;
 }
 
-template <int N>
+template <int N, bool EQ3>
 __global__ void __launch_bounds__(128) k_factor_np(DevView v, double lam, const double* q0,
                                                    int linstride) {
   using P = NpF<N>;
@@ -174,6 +205,7 @@ __global__ void __launch_bounds__(128) k_factor_np(DevView v, double lam, const 
   float* rb = ub + P::UBW;
   float* KSp = rb + P::RBW;          // per point: 9 floats
   float* KG = KSp + 3 * linstride;   // per point: gravity entry
+  float* KZ = KG + c.nz;             // per point: set 3C's E-row entry at rho (after KG)
   float* is32 = KG + linstride;      // per unknown: 1 / s
   const int n = c.n, nz = c.nz;
   float* fb = reinterpret_cast<float*>(v.fac) + t.fac_off;                   // F records
@@ -199,8 +231,18 @@ __global__ void __launch_bounds__(128) k_factor_np(DevView v, double lam, const 
       rho = v.ref[a]; m = 0.0; Th = v.ref[a + 2];
     }
     double w, th, cc, dP;
-    if (!lin_coefs(ph, rho, m, Th, v.ref[a + 2], v.ref[a + 1], &w, &th, &cc, &dP,
-                   v.ithb ? v.ithb + c.off / 3 + I : nullptr)) {
+    float* ks = KSp + 9 * I;
+    if (EQ3) {  // lin = (w, h, z)
+      const double z = point_z<N>((double)v.col_dz[c.col], I, nz);
+      double wh[2];
+      if (!np_point_3c(ph, rho, m, Th, v.ref[a], v.ref[a + 2], v.ref[a + 1], z, sc[0], sc[1],
+                       sc[2], lam_s, ks, KZ + I, wh))
+        ok = false;
+      w = wh[0];
+      th = wh[1];
+      cc = z;
+    } else if (!lin_coefs(ph, rho, m, Th, v.ref[a + 2], v.ref[a + 1], &w, &th, &cc, &dP,
+                          v.ithb ? v.ithb + c.off / 3 + I : nullptr)) {
       ok = false;
       w = th = cc = 0.0;
     }
@@ -213,11 +255,11 @@ __global__ void __launch_bounds__(128) k_factor_np(DevView v, double lam, const 
       lt[kTile] = th;
       lt[2 * kTile] = cc;
     }
+    if (EQ3) continue;
     // K(q0) at point I (App. A.3 restricted to the vertical), scaled by the
     // column scales and Lambda (2/dz): rho-flux (0, 1, 0), m-flux
     // (-w^2, 2w, c), Theta-flux (-theta w, theta, w)
     const float wf = (float)w, tf = (float)th, cf = (float)cc;
-    float* ks = KSp + 9 * I;
     ks[0] = 0.0f;
     ks[1] = lam_s * sc[1];
     ks[2] = 0.0f;
@@ -242,7 +284,7 @@ __global__ void __launch_bounds__(128) k_factor_np(DevView v, double lam, const 
   float a[WR];
 #pragma unroll
   for (int s = 0; s < WR; ++s)
-    a[s] = mine ? np_ent<N>(my, s, s / 3, s % 3, s < n, G, KSp, KG) : 0.0f;
+    a[s] = mine ? np_ent<N, EQ3>(my, s, s / 3, s % 3, s < n, G, KSp, KG, KZ) : 0.0f;
 
   // The main loop keeps, for a row, pointers to its coefficient row in G and
   // its variable's slice of KSp and its effective 1/s (0 for identity rows
@@ -285,6 +327,7 @@ __global__ void __launch_bounds__(128) k_factor_np(DevView v, double lam, const 
       if (nr.live && Jr >= ln.I - N) e = ln.gp[Jr] * ln.kp[kr] * ln.isx;
       if (diag && nr.live) e += 1.0f;
       if (nr.v == 1 && ur == 0 && Jr == ln.I && ln.isx != 0.0f) e = fmaf(KG[Jr], ln.isx, e);
+      if (EQ3 && nr.v == 2 && ur == 0 && Jr == ln.I && ln.isx != 0.0f) e = fmaf(KZ[Jr], ln.isx, e);
       rb[r] = e;
     }
     // this row's entry in the entering column (above the diagonal: neither
@@ -361,9 +404,14 @@ static void launch_factor_np_n(const DevView& v, double lam, const double* q0, i
   const int nmax = ylen - 2 * K;  // longest n of these tiles
   const int linstride = (3 * (nmax / 3) + 3) / 4 * 4;
   const int smem = (kGSzA + P::CPB * (P::fixed + 5 * linstride)) * (int)sizeof(float);
-  cudaFuncSetAttribute(k_factor_np<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  k_factor_np<N><<<(unsigned)(v.tile_count * (kTile / P::CPB)), 128, smem, st>>>(v, lam, q0,
-                                                                                linstride);
+  const unsigned grid = (unsigned)(v.tile_count * (kTile / P::CPB));
+  if (v.ph.eqset == 1) {
+    cudaFuncSetAttribute(k_factor_np<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    k_factor_np<N, true><<<grid, 128, smem, st>>>(v, lam, q0, linstride);
+  } else {
+    cudaFuncSetAttribute(k_factor_np<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    k_factor_np<N, false><<<grid, 128, smem, st>>>(v, lam, q0, linstride);
+  }
 }
 
 void launch_factor_np(const DevView& v, int order, double lam, const double* q0, int ylen,
@@ -599,21 +647,27 @@ __device__ __forceinline__ float np_backward(NpRing& rg, const float* bb, int n,
 // Refinement residual of the tile's columns (one per lane), point by point
 // through the element pass in double-float arithmetic:
 //   v' = S v (v = y, the last sweep's solution in the scaled variables;
-//   the product of two floats is exact as a double-float pair),
+//   the product of two floats is exact as a double-float pair; in set 3C
+//   v' = T S v, the band having been factored in (rho, m, E - g z rho)),
 //   r = base - A v',  A v' = v' + Lambda (Dcal[K(q0) v'] + G v'),
 // with base = b (the pair rr + zz) on the first call and the stored residual
-// rr afterwards (r_k+1 = r_k - A d_k).  Then rr = fl(r) and y = S^-1 rr, the
-// next right-hand side.  The first call keeps v in y1 (the first solution),
-// later calls add it to zz (zz = v on the call after the second sweep).  The
+// afterwards (r_k+1 = r_k - A d_k).  Then rr = fl(r) and y = S^-1 rr, the
+// next right-hand side.  The stored residual is rr alone in set 2C; in set 3C
+// it is the pair rr + rl (rl = r - fl(r)): there the first FP32 solve leaves a
+// residual of about 2^-24 |A||x| times the LU's growth, and rounding it to
+// FP32 bounds the refined solution at about 2^-48 |A||x| times that growth
+// times kappa, past 1e-10 on the worst columns.  The first call keeps v in y1 (the first solution),
+// later calls add it to zz (zz = v on the call after the second sweep; in set
+// 3C that call makes (y1, zz) the normalised pair of y1 + v instead).  The
 // point coefficients of L(q0) are read from the tile's scratch (one contiguous
 // line per row for the warp).  Writes are predicated on w (the lanes whose
 // column goes on).
 template <int N>
 __device__ void np_residual(const double* lint, int nez, const Phys& ph, float dzf, double cs,
                             double lam, int sweep, float* y, float* y1, float* zz, float* rr,
-                            float2* slots, int lane, bool w) {
+                            float* rl, float2* slots, int lane, bool w) {
   const int nz = nez * N + 1;
-  const bool first = sweep == 1;
+  const bool first = sweep == 1, eq3 = ph.eqset == 1;
   const double* lc0 = lint + lane;
   const df lamd = df_from_double(lam), gd = df_from_double(ph.g), csd = df_from_double(cs);
   auto scaled = [&](int I, float (&v)[3], df (&xp)[3], float (&sc)[3]) {
@@ -624,6 +678,8 @@ __device__ void np_residual(const double* lint, int nez, const Phys& ph, float d
       const float p = sc[u] * v[u];
       xp[u] = {p, fmaf(sc[u], v[u], -p)};
     }
+    if (eq3)  // set 3C: x = T S v, E = (E - g z rho) + g z rho
+      xp[2] = df_fma(df_mul(gd, df_from_double(lc0[(int64_t)(3 * I + 2) * kTile])), xp[0], xp[2]);
   };
   auto flux = [&](int I, df* f) {
     const double* lc = lc0 + (int64_t)(3 * I) * kTile;
@@ -646,15 +702,36 @@ __device__ void np_residual(const double* lint, int nez, const Phys& ph, float d
 #pragma unroll
       for (int u = 0; u < 3; ++u) {
         const int i = (3 * I + u) * kTile;
-        if (first)
+        if (first) {
           y1[i] = v[u];
-        else
+        } else if (sweep == 2 && eq3) {
+          // set 3C: the first FP32 solve is poorer there, so the first
+          // correction can be a sizeable part of y1, and zz rounded to FP32
+          // would hold x to only 2^-24 of it; y1 + zz becomes a normalised
+          // pair, so the later corrections add to a zz below ulp(y1)
+          const df p2 = df_two_sum(y1[i], v[u]);
+          y1[i] = p2.hi;
+          zz[i] = p2.lo;
+        } else {
           zz[i] = sweep == 2 ? v[u] : zz[i] + v[u];
+        }
       }
     }
     const df wI = df_from_double(lc[0]), thI = df_from_double(lc[kTile]),
              cI = df_from_double(lc[2 * kTile]);
     f[0] = xp[1];
+    if (ph.eqset == 1) {  // set 3C: lin = (w, h, z); rows of the flux Jacobian
+      const df gm = df_from_double(ph.gamma - 1.0);
+      const df w2 = df_mul(wI, wI);
+      const df Pr = df_mul(gm, df_sub(df{0.5f * w2.hi, 0.5f * w2.lo}, df_mul(gd, cI)));
+      const df Pm = df_mul(gm, df{-wI.hi, -wI.lo});
+      const df k10 = df_add(df{-w2.hi, -w2.lo}, Pr), k11 = df_add(df{2.0f * wI.hi, 2.0f * wI.lo}, Pm);
+      const df k20 = df_mul(wI, df_sub(Pr, thI)), k21 = df_fma(wI, Pm, thI);
+      const df k22 = df_mul(wI, df_from_double(ph.gamma));
+      f[1] = df_fma(k10, xp[0], df_fma(k11, xp[1], df_mul(gm, xp[2])));
+      f[2] = df_fma(k20, xp[0], df_fma(k21, xp[1], df_mul(k22, xp[2])));
+      return;
+    }
     // f1 = -w^2 rho + 2 w m + c Theta,  f2 = -theta w rho + theta m + w Theta
     f[1] = df_sub(df_fma({2.0f * wI.hi, 2.0f * wI.lo}, xp[1], df_mul(cI, xp[2])),
                   df_mul(df_mul(wI, wI), xp[0]));
@@ -667,7 +744,7 @@ __device__ void np_residual(const double* lint, int nez, const Phys& ph, float d
 #pragma unroll
     for (int u = 0; u < 3; ++u) {
       const int i = (3 * I + u) * kTile;
-      const df base = first ? df{rr[i], zz[i]} : df{rr[i], 0.0f};
+      const df base = first ? df{rr[i], zz[i]} : df{rr[i], eq3 ? rl[i] : 0.0f};
       df r;
       if (u == 1 && (I == 0 || I == nz - 1)) {
         r = df_sub(base, xp[1]);  // identity rows: w = 0 at the ends
@@ -679,6 +756,7 @@ __device__ void np_residual(const double* lint, int nez, const Phys& ph, float d
       if (w) {
         const float rf = __fadd_rn(r.hi, r.lo);
         rr[i] = rf;
+        if (eq3) rl[i] = __fadd_rn(__fsub_rn(r.hi, rf), r.lo);
         y[i] = rf * (1.0f / sc[u]);
       }
     }
@@ -691,8 +769,8 @@ __device__ void np_residual(const double* lint, int nez, const Phys& ph, float d
 // element pass of the residual parks its slots in the ring's memory (the ring
 // is idle between sweeps).  The tile's vectors live in its global scratch,
 // [row][lane]: the work vector y (n + K + 1 rows, the rows past n zero), the
-// first sweep's solution y1, the sum zz of the later corrections and the
-// stored residual rr; x = S (y1 + zz).
+// first sweep's solution y1, the sum zz of the later corrections, the
+// stored residual rr and its low part rl (set 3C); x = S (y1 + zz).
 struct NpWarpMem {
   float2* slots;
 };
@@ -721,6 +799,8 @@ __device__ void np_solve_tile(const DevView& v, const TileDesc& t, int lane, dou
   float* y1 = y + (int64_t)yr * kTile;
   float* zz = y1 + (int64_t)n * kTile;
   float* rr = zz + (int64_t)n * kTile;
+  float* rl = rr + (int64_t)n * kTile;
+  const bool eq3 = v.ph.eqset == 1;
   Col c{};
   bool active = false;
   if (valid) {
@@ -787,8 +867,13 @@ __device__ void np_solve_tile(const DevView& v, const TileDesc& t, int lane, dou
           status = HEVI_COL_OK;
         }
       } else {
-        const double pred = dn * (dn / dprev);  // error left after applying d
-        if (dn <= tol * xnorm || pred <= tol * xnorm) {
+        // error left after applying d, from the last contraction; in set 3C
+        // only from the third sweep on: there the first ratio |d_2| / |y_1|
+        // can understate the contraction of the later corrections (whose
+        // right-hand sides are rounding residuals, not the smooth b), and a
+        // prediction from it stopped columns at 1e-10 after two sweeps
+        const double pred = dn * (dn / dprev);
+        if (dn <= tol * xnorm || (pred <= tol * xnorm && (k > 2 || !eq3))) {
           stop = true;
           status = HEVI_COL_OK;
         } else if (dn > 0.5 * dprev) {
@@ -831,7 +916,7 @@ __device__ void np_solve_tile(const DevView& v, const TileDesc& t, int lane, dou
     }
     // the columns that go on: r = base - A S y, y = S^-1 r
     if (rg.ok && __any_sync(FULL, more))
-      np_residual<N>(lint, t.nez, v.ph, dzf, cs, lam, k, y, y1, zz, rr, wm.slots, lane, more);
+      np_residual<N>(lint, t.nez, v.ph, dzf, cs, lam, k, y, y1, zz, rr, rl, wm.slots, lane, more);
     if (!rg.ok) {  // a copy did not arrive within the wait limit
       np_reset<N>(rg, lane);
       if (active) {
@@ -844,9 +929,11 @@ __device__ void np_solve_tile(const DevView& v, const TileDesc& t, int lane, dou
     }
     __syncwarp();
   }
-  // x = S (y1 + zz), written by each lane into its own column
+  // x = S (y1 + zz) (set 3C: T S (y1 + zz)), written by each lane into its own column
   if (ran) {
     double* xc = x + c.off;
+    const df gd3 = df_from_double(v.ph.g);
+    df x0 = {0.0f, 0.0f};
     for (int I0 = 0; I0 < nz; I0 += kPts) {
       float a1[3 * kPts], a2[3 * kPts];
 #pragma unroll
@@ -864,7 +951,11 @@ __device__ void np_solve_tile(const DevView& v, const TileDesc& t, int lane, dou
 #pragma unroll
           for (int u = 0; u < 3; ++u) {
             // S (y1 + zz) as a double-float pair on the FP32 pipes, one FP64 add
-            const df xi = df_mul(df_two_sum(a1[3 * p + u], a2[3 * p + u]), df{sc[u], 0.0f});
+            // (set 3C: T S (y1 + zz), E gaining g z rho)
+            df xi = df_mul(df_two_sum(a1[3 * p + u], a2[3 * p + u]), df{sc[u], 0.0f});
+            if (u == 0) x0 = xi;
+            if (u == 2 && eq3)
+              xi = df_fma(df_mul(gd3, df_from_double(lint[(int64_t)(3 * I + 2) * kTile + lane])), x0, xi);
             xc[3 * I + u] = (double)xi.hi + (double)xi.lo;
           }
         }
@@ -1069,8 +1160,21 @@ __global__ void __launch_bounds__(128) k_apply_rhs_df(DevView v, const double* Q
       const df ir = df_add_f(df_mul(df{r0, 0.0f}, ee), r0);
       const df w = df_mul(md, ir);
       f[0] = md;
-      f[1] = df_add(df_mul(md, w), eos_perturbation_df(ph, dTh, ithb, Pb));
-      f[2] = df_mul(T, w);
+      if (ph.eqset == 1) {
+        // set 3C: P - P_bar = (gamma - 1)((E - E_bar) - m w / 2 - (rho - rho_bar) g z),
+        // fluxes (m, m w + P - P_bar, (E + P) w)
+        const double z = point_z<N>(1.0 / (0.5 * c.s), I, c.nz);
+        const df gm = df_from_double(ph.gamma - 1.0);
+        const df mw2 = df_mul(md, w);
+        const df dP = df_mul(gm, df_sub(df_sub(df_from_double(dTh), df{0.5f * mw2.hi, 0.5f * mw2.lo}),
+                                        df_from_double((rho - rb) * ph.g * z)));
+        if (!((float)Pb + dP.hi > 0.0f)) ok = false;
+        f[1] = df_add(mw2, dP);
+        f[2] = df_mul(df_add(df_from_double(Th + Pb), dP), w);
+      } else {
+        f[1] = df_add(df_mul(md, w), eos_perturbation_df(ph, dTh, ithb, Pb));
+        f[2] = df_mul(T, w);
+      }
     }
     // this lane's row of the element derivative from its element's fluxes
     const int base = (lane_ok ? el : 0) * P;
