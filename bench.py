@@ -72,11 +72,11 @@ def factor_flops(n=NUNK, k=K_BAND):
 # capture of `python bench.py --ncu-case solve|factor` (the summaries under
 # profiles/ give the commands), valid only for the kernel source they were
 # taken from: the SHA-256 of the kernel file at capture time.
-_NP_SHA = "26810b64c1f04e93d98c705d07b063c8370a21882001b0dcce725dee59c87b64"
+_NP_SHA = "9808ebdebcffd291717b9ca98b41b4fa856e51e0b22c67446e56982c601db59f"
 NCU_TRAFFIC = {
-    "k_solve_np": {"bytes": 3.791e9, "sha256": _NP_SHA},      # 5.334 TB/s x 0.711 ms
-    "k_factor_np": {"bytes": 1.833e9, "sha256": _NP_SHA},     # 1.728 TB/s x 1.060 ms
-    "k_apply_rhs_df": {"bytes": 0.352e9, "sha256": _NP_SHA},  # 1.396 TB/s x 0.252 ms
+    "k_solve_np": {"bytes": 3.793e9, "sha256": _NP_SHA},      # 5.160 TB/s x 0.735 ms
+    "k_factor_np": {"bytes": 1.833e9, "sha256": _NP_SHA},     # 1.730 TB/s x 1.059 ms
+    "k_apply_rhs_df": {"bytes": 0.351e9, "sha256": _NP_SHA},  # 1.393 TB/s x 0.252 ms
 }
 KERNEL_SOURCE = os.path.join(ROOT, "paper_2311_11425_gb300", "csrc", "hevi_np.cu")
 

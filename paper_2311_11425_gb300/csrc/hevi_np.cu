@@ -1107,7 +1107,7 @@ __device__ __forceinline__ df eos_perturbation_df(const Phys& ph, double dTh, do
 // first element of a round, the last row carried from the previous round)
 // and scale by (2/dz) / W_I; every point's output is written by one lane.
 // Loads and stores of a round touch consecutive points of the column.
-template <int N>
+template <int N, bool EQ3>
 __global__ void __launch_bounds__(128) k_apply_rhs_df(DevView v, const double* Q, const double* H,
                                                       double* S) {
   constexpr int P = N + 1;      // lanes per element
@@ -1160,7 +1160,7 @@ __global__ void __launch_bounds__(128) k_apply_rhs_df(DevView v, const double* Q
       const df ir = df_add_f(df_mul(df{r0, 0.0f}, ee), r0);
       const df w = df_mul(md, ir);
       f[0] = md;
-      if (ph.eqset == 1) {
+      if (EQ3) {
         // set 3C: P - P_bar = (gamma - 1)((E - E_bar) - m w / 2 - (rho - rho_bar) g z),
         // fluxes (m, m w + P - P_bar, (E + P) w)
         const double z = point_z<N>(1.0 / (0.5 * c.s), I, c.nz);
@@ -1233,15 +1233,25 @@ __global__ void __launch_bounds__(128) k_apply_rhs_df(DevView v, const double* Q
   if (__any_sync(0xffffffffu, !ok) && lane == 0) fail(v, c.col, HEVI_COL_BAD_INPUT);
 }
 
+template <int N>
+void launch_apply_df_n(bool eq3, unsigned grid, cudaStream_t st, const DevView& v, const double* Q,
+                       const double* H, double* S) {
+  if (eq3)
+    k_apply_rhs_df<N, true><<<grid, 128, 0, st>>>(v, Q, H, S);
+  else
+    k_apply_rhs_df<N, false><<<grid, 128, 0, st>>>(v, Q, H, S);
+}
+
 void launch_apply_rhs_df(const DevView& v, int order, const double* Q, const double* H, double* S,
                          cudaStream_t st) {
   const unsigned grid = (unsigned)(v.tile_count * (kTile / 4));  // a warp per column slot
+  const bool e3 = v.ph.eqset == 1;
   switch (order) {
-    case 1: k_apply_rhs_df<1><<<grid, 128, 0, st>>>(v, Q, H, S); break;
-    case 2: k_apply_rhs_df<2><<<grid, 128, 0, st>>>(v, Q, H, S); break;
-    case 3: k_apply_rhs_df<3><<<grid, 128, 0, st>>>(v, Q, H, S); break;
-    case 4: k_apply_rhs_df<4><<<grid, 128, 0, st>>>(v, Q, H, S); break;
-    case 5: k_apply_rhs_df<5><<<grid, 128, 0, st>>>(v, Q, H, S); break;
+    case 1: launch_apply_df_n<1>(e3, grid, st, v, Q, H, S); break;
+    case 2: launch_apply_df_n<2>(e3, grid, st, v, Q, H, S); break;
+    case 3: launch_apply_df_n<3>(e3, grid, st, v, Q, H, S); break;
+    case 4: launch_apply_df_n<4>(e3, grid, st, v, Q, H, S); break;
+    case 5: launch_apply_df_n<5>(e3, grid, st, v, Q, H, S); break;
     default: break;
   }
 }
