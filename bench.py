@@ -72,13 +72,30 @@ def factor_flops(n=NUNK, k=K_BAND):
 # capture of `python bench.py --ncu-case solve|factor` (the summaries under
 # profiles/ give the commands), valid only for the kernel source they were
 # taken from: the SHA-256 of the kernel file at capture time.
-_NP_SHA = "9808ebdebcffd291717b9ca98b41b4fa856e51e0b22c67446e56982c601db59f"
+_NP_SHA = "6e02d2a6011daa9e3cee6e90874fa8398b053bfdaa0e6187b0396706b5ed38b6"
 NCU_TRAFFIC = {
-    "k_solve_np": {"bytes": 3.793e9, "sha256": _NP_SHA},      # 5.160 TB/s x 0.735 ms
-    "k_factor_np": {"bytes": 1.833e9, "sha256": _NP_SHA},     # 1.730 TB/s x 1.059 ms
-    "k_apply_rhs_df": {"bytes": 0.351e9, "sha256": _NP_SHA},  # 1.393 TB/s x 0.252 ms
+    "k_solve_np": {"bytes": 3.792e9, "sha256": _NP_SHA},      # 5.212 TB/s x 0.728 ms
+    "k_factor_np": {"bytes": 1.833e9, "sha256": _NP_SHA},     # 1.731 TB/s x 1.059 ms
+    # k_apply_rhs_df: its passes differ (the stage combinations fold in a
+    # different number of vectors); the capture covers the first pass only,
+    # so no per-launch average is recorded
 }
 KERNEL_SOURCE = os.path.join(ROOT, "paper_2311_11425_gb300", "csrc", "hevi_np.cu")
+
+
+def apply_bytes_fused(s):
+    """Algorithmic bytes per column of one tendency pass of an s-stage LHEVI
+    step with the stage combinations folded in, averaged over the s passes.
+    Every pass reads H, the reference (rho_bar, P_bar, Theta_bar: one vector)
+    and 1/Theta_bar (one double per point).  Pass 0 reads q^n and writes S_0
+    and the next right-hand side; pass i (0 < i < s-1) reads q_tt, the i
+    earlier Q_j and S_j and q^n and writes Q_i, S_i and the next right-hand
+    side; the last pass reads q_tt, the Q_j and S_j before it and q^n and
+    writes q^{n+1}.  Vectors of NUNK doubles."""
+    vecs = 2 + 3                                    # pass 0: H, ref; q^n, S_0, rhs
+    vecs += sum(2 + 5 + 2 * i for i in range(1, s - 1))
+    vecs += 2 + 3 + 2 * (s - 1)
+    return (vecs / s * NUNK + NZ) * 8
 
 
 def ncu_traffic(kernel):
@@ -430,15 +447,14 @@ def gpu_arm(args, rank, world, local_rank, pool, cores):
                     "peak_source": "measured (cuBLAS SGEMM, TF32 off)",
                     "algorithmic_flops_per_launch": factor_flops() * NCOLS, "avg_launch_ms": avg}
         if kind == "apply":
-            # S(Q) = H + V(Q): reads Q, H and the reference (rho_bar, P_bar,
-            # Theta_bar) and 1/Theta_bar, writes S
-            b = (4 * NUNK + NZ) * 8
-            ach = b * NCOLS / (avg * 1e-3) / 1e9
-            return {"kernel": "k_apply_rhs_df<4> (apply, double-float)", "bound": "hbm",
+            b = apply_bytes_fused(STAGES + 1) * NCOLS
+            ach = b / (avg * 1e-3) / 1e9
+            return {"kernel": "k_apply_rhs_df<4> (tendency pass with the stage combinations)",
+                    "bound": "hbm",
                     "achieved": ach,
                     "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": ach / pk["hbm_gbs"],
                     "traffic": ncu_traffic("k_apply_rhs_df"), "peak_source": pk["source"],
-                    "algorithmic_bytes_per_launch": b * NCOLS, "avg_launch_ms": avg}
+                    "algorithmic_bytes_per_launch": b, "avg_launch_ms": avg}
         return {"kernel": kind, "bound": None, "achieved": None, "peak": None, "unit": None,
                 "frac": None, "traffic": None, "avg_launch_ms": avg}
 

@@ -197,6 +197,17 @@ hevi_status hevi_set_equation_set(hevi_ctx* ctx, int32_t set);
  * blocks the calling thread.  Results are the same either way. */
 hevi_status hevi_set_newton_host_check(hevi_ctx* ctx, int32_t on);
 
+/* How hevi_lhevi_step sequences an HEVI_FP32_IR step (Sec. 4.3, Eq.
+ * lhevi-ark-final-3).  on = 1 (default): each stage's combinations (the stage
+ * value Q_i from the solve's result, the next stage's right-hand side, and
+ * q^{n+1} after the last stage) are formed inside the tendency pass of that
+ * stage, so a step launches no combination kernel (equation set 2C; a
+ * set-3C context and an HEVI_FP64 context always use separate combination
+ * launches).  on = 0: separate combination launches.  Both evaluate the same
+ * FMA chains in the same order and give the same bits.  HEVI_ERR_INVALID_ARG
+ * for on outside {0, 1}. */
+hevi_status hevi_set_fused_stages(hevi_ctx* ctx, int32_t on);
+
 /* Resident warps per SM of the HEVI_FP32_IR stage solve (1 .. 32; 0 restores
  * the default).  The solve is ONE persistent launch over the tiles of every
  * polynomial order of the context: each warp takes the next tile of 32

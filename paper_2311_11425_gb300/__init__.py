@@ -85,6 +85,7 @@ def load(build: bool = False):
         "hevi_reference_columns": (_I32, [_P, _I64, _I64, _P]),
         "hevi_set_column_tops": (_I32, [_P, _I64, _I64, DP]),
         "hevi_set_newton_host_check": (_I32, [_P, _I32]),
+        "hevi_set_fused_stages": (_I32, [_P, _I32]),
         "hevi_set_equation_set": (_I32, [_P, _I32]),
         "hevi_autotune_solve": (_I32, [_P, _P, _P, _I32, ctypes.POINTER(_I32), DP, DP]),
         "hevi_newton_solve": (_I32, [_P, _D, _P, _P, _D, _I32]),
@@ -372,6 +373,9 @@ class Context:
     def hevi_set_newton_host_check(self, on: bool):
         _check(self._lib.hevi_set_newton_host_check(self._h, 1 if on else 0),
                "hevi_set_newton_host_check")
+
+    def hevi_set_fused_stages(self, on: bool):
+        _check(self._lib.hevi_set_fused_stages(self._h, 1 if on else 0), "hevi_set_fused_stages")
 
     def hevi_factor(self, gamma_dt: float, lin_state=None):
         p = None if lin_state is None else self._v(lin_state)

@@ -380,10 +380,35 @@ void launch_apply(const DevView& v, int order, const double* x, double* y, int n
                   cudaStream_t st);
 void launch_apply_stage(const DevView& v, int order, const double* Q, const double* H, double* E,
                         double* LQ, cudaStream_t st);
+// The stage combinations an LHEVI step folds into the tendency pass of stage
+// i (Sec. 4.3, Eq. lhevi-ark-final-3), every vector in the state layout.  With
+// qtt set, the stage value is formed at each point as
+//   Q_i = qtt + sum_t cq[t] q[t]
+// (and stored to qout when set) instead of being read from Q.  With rout
+// set, after S_i = H + V(Q_i) the pass writes
+//   rout = rbase + sum_t cr[t] r[t] (+ cs S_i if has_s) (+ cqs Q_i if has_q),
+// each sum an FMA chain in this order, as the stand-alone combination kernel
+// evaluates it, so the fused step gives the same bits as the unfused one.
+constexpr int kFuseQ = 8, kFuseR = 16;
+struct StageFuse {
+  const double* qtt = nullptr;
+  int nq = 0;
+  const double* q[kFuseQ] = {};
+  double cq[kFuseQ] = {};
+  double* qout = nullptr;
+  const double* rbase = nullptr;
+  double* rout = nullptr;
+  int nr = 0;
+  const double* r[kFuseR] = {};
+  double cr[kFuseR] = {};
+  int has_s = 0, has_q = 0;
+  double cs = 0.0, cqs = 0.0;
+};
 // S = H + V(Q) in double-float arithmetic (hevi_np.cu): the FP32 path's
-// explicit tendency.
+// explicit tendency; with fz (may be null) also the stage combinations above.
+// S may be null when only rout is wanted.
 void launch_apply_rhs_df(const DevView& v, int order, const double* Q, const double* H, double* S,
-                         cudaStream_t st);
+                         cudaStream_t st, const StageFuse* fz = nullptr);
 void launch_apply_rhs(const DevView& v, int order, const double* Q, const double* H, double* S,
                       cudaStream_t st);
 // The fused one-column-per-thread Newton kernel (the allocation-free entry

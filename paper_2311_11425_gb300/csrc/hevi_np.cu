@@ -1107,9 +1107,32 @@ __device__ __forceinline__ df eos_perturbation_df(const Phys& ph, double dTh, do
 // first element of a round, the last row carried from the previous round)
 // and scale by (2/dz) / W_I; every point's output is written by one lane.
 // Loads and stores of a round touch consecutive points of the column.
+// acc[u] = fma(c[t], v[t][g0 + u], acc[u]) for t = 0 .. n-1 in order (u = 0..2);
+// the loads of two terms are issued before their FMAs, so their latencies
+// overlap (n is uniform across the warp).
+template <int MAXT>
+__device__ __forceinline__ void fuse_chain(int n, const double* const (&v)[MAXT],
+                                           const double (&c)[MAXT], int64_t g0, double (&acc)[3]) {
+#pragma unroll
+  for (int t0 = 0; t0 < MAXT; t0 += 2) {
+    if (t0 < n) {
+      double x[2][3];
+#pragma unroll
+      for (int d = 0; d < 2; ++d)
+#pragma unroll
+        for (int u = 0; u < 3; ++u) x[d][u] = t0 + d < n ? v[t0 + d][g0 + u] : 0.0;
+#pragma unroll
+      for (int d = 0; d < 2; ++d)
+        if (t0 + d < n)
+#pragma unroll
+          for (int u = 0; u < 3; ++u) acc[u] = fma(c[t0 + d], x[d][u], acc[u]);
+    }
+  }
+}
+
 template <int N, bool EQ3>
 __global__ void __launch_bounds__(128) k_apply_rhs_df(DevView v, const double* Q, const double* H,
-                                                      double* S) {
+                                                      double* S, StageFuse fz) {
   constexpr int P = N + 1;      // lanes per element
   constexpr int EPR = 32 / P;   // elements per round
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -1133,11 +1156,9 @@ __global__ void __launch_bounds__(128) k_apply_rhs_df(DevView v, const double* Q
   const df sc_sh = df_mul(cs, df{0.5f * iw0.hi, 0.5f * iw0.lo});      // shared point
   const df sc_end = df_mul(cs, iw0);                                  // bottom, top
   const df gd = df_from_double(ph.g);
-  const double* qc = Q + c.off;
   const double* ref = v.ref + c.off;
   const double* ith = v.ithb + c.off / 3;
   const double* hc = H + c.off;
-  double* sc = S + c.off;
   bool ok = true;
   df carry[3] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
   for (int e0 = 0; e0 < c.nez; e0 += EPR) {
@@ -1146,9 +1167,27 @@ __global__ void __launch_bounds__(128) k_apply_rhs_df(DevView v, const double* Q
     const int I = e * N + k;
     df f[3] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
     double rho = 0.0, dTh = 0.0, ithb = 0.0, Pb = 0.0, rb = 0.0;
+    double q[3] = {0.0, 0.0, 0.0};   // Q_i at point I
+    double rp[3] = {0.0, 0.0, 0.0};  // memory part of the next right-hand side at point I
     if (act) {
-      rho = qc[3 * I];
-      const double m = qc[3 * I + 1], Th = qc[3 * I + 2];
+      const int64_t g0 = c.off + 3 * I;
+      if (fz.qtt) {  // Q_i = qtt + sum_t cq[t] q[t]
+#pragma unroll
+        for (int u = 0; u < 3; ++u) q[u] = fz.qtt[g0 + u];
+        fuse_chain<kFuseQ>(fz.nq, fz.q, fz.cq, g0, q);
+      } else {
+#pragma unroll
+        for (int u = 0; u < 3; ++u) q[u] = Q[g0 + u];
+      }
+      if (fz.rout && (k < N || e == c.nez - 1)) {
+        // the memory terms of the right-hand side at the point this lane
+        // writes (the chain's first part: rbase, then the r[t] in order)
+#pragma unroll
+        for (int u = 0; u < 3; ++u) rp[u] = fz.rbase[g0 + u];
+        fuse_chain<kFuseR>(fz.nr, fz.r, fz.cr, g0, rp);
+      }
+      rho = q[0];
+      const double m = q[1], Th = q[2];
       rb = ref[3 * I];
       Pb = ref[3 * I + 1];
       dTh = Th - ref[3 * I + 2];
@@ -1226,7 +1265,16 @@ __global__ void __launch_bounds__(128) k_apply_rhs_df(DevView v, const double* Q
           val = df_sub(df_from_double(hc[i]), D[u]);
           if (u == 1) val = df_sub(val, df_mul(gd, df_from_double(rho - rb)));
         }
-        sc[i] = df_to_double(val);
+        const double sv = df_to_double(val);
+        const int64_t gi = c.off + i;
+        if (S) S[gi] = sv;
+        if (fz.qout) fz.qout[gi] = q[u];
+        if (fz.rout) {
+          double rs = rp[u];
+          if (fz.has_s) rs = fma(fz.cs, sv, rs);
+          if (fz.has_q) rs = fma(fz.cqs, q[u], rs);
+          fz.rout[gi] = rs;
+        }
       }
     }
   }
@@ -1235,23 +1283,24 @@ __global__ void __launch_bounds__(128) k_apply_rhs_df(DevView v, const double* Q
 
 template <int N>
 void launch_apply_df_n(bool eq3, unsigned grid, cudaStream_t st, const DevView& v, const double* Q,
-                       const double* H, double* S) {
+                       const double* H, double* S, const StageFuse& fz) {
   if (eq3)
-    k_apply_rhs_df<N, true><<<grid, 128, 0, st>>>(v, Q, H, S);
+    k_apply_rhs_df<N, true><<<grid, 128, 0, st>>>(v, Q, H, S, fz);
   else
-    k_apply_rhs_df<N, false><<<grid, 128, 0, st>>>(v, Q, H, S);
+    k_apply_rhs_df<N, false><<<grid, 128, 0, st>>>(v, Q, H, S, fz);
 }
 
 void launch_apply_rhs_df(const DevView& v, int order, const double* Q, const double* H, double* S,
-                         cudaStream_t st) {
+                         cudaStream_t st, const StageFuse* fzp) {
+  const StageFuse fz = fzp ? *fzp : StageFuse{};
   const unsigned grid = (unsigned)(v.tile_count * (kTile / 4));  // a warp per column slot
   const bool e3 = v.ph.eqset == 1;
   switch (order) {
-    case 1: launch_apply_df_n<1>(e3, grid, st, v, Q, H, S); break;
-    case 2: launch_apply_df_n<2>(e3, grid, st, v, Q, H, S); break;
-    case 3: launch_apply_df_n<3>(e3, grid, st, v, Q, H, S); break;
-    case 4: launch_apply_df_n<4>(e3, grid, st, v, Q, H, S); break;
-    case 5: launch_apply_df_n<5>(e3, grid, st, v, Q, H, S); break;
+    case 1: launch_apply_df_n<1>(e3, grid, st, v, Q, H, S, fz); break;
+    case 2: launch_apply_df_n<2>(e3, grid, st, v, Q, H, S, fz); break;
+    case 3: launch_apply_df_n<3>(e3, grid, st, v, Q, H, S, fz); break;
+    case 4: launch_apply_df_n<4>(e3, grid, st, v, Q, H, S, fz); break;
+    case 5: launch_apply_df_n<5>(e3, grid, st, v, Q, H, S, fz); break;
     default: break;
   }
 }

@@ -92,6 +92,36 @@ def test_lhevi_graph_bitwise_equal_to_steps(hv, prec):
     ctx.close()
 
 
+@pytest.mark.parametrize("name,rest", [
+    ("ARK2", False), ("ARK3", False), ("ARK3", True), ("ARK4", False), ("ARS3", False)])
+def test_fused_stage_combinations_bitwise(hv, name, rest):
+    """An FP32 LHEVI step with the stage combinations folded into the
+    tendency passes (the default in set 2C) equals the step with separate
+    combination launches bit for bit: three size classes of three orders, a
+    perturbed state, the seeded tendency, the Jacobian about the state or
+    about rest.  The fused step launches fewer kernels."""
+    import torch
+    ctx, H = _mixed_ctx(hv, hv.FP32_IR)
+    tab = hv.tableau(name)
+    q0 = ctx.hevi_reference_state()
+    g = torch.Generator(device="cuda").manual_seed(5)
+    q0 = q0 * (1 + 1e-3 * torch.randn(q0.shape, generator=g, device="cuda", dtype=q0.dtype))
+    l0 = ctx.launch_count
+    fused = ctx.hevi_lhevi_step(tab, 300.0, q0, H, lin_about_rest=rest)
+    ctx.hevi_sync()
+    l1 = ctx.launch_count
+    ctx.hevi_set_fused_stages(False)
+    plain = ctx.hevi_lhevi_step(tab, 300.0, q0, H, lin_about_rest=rest)
+    ctx.hevi_sync()
+    assert 0 < l1 - l0 < ctx.launch_count - l1
+    st, _ = ctx.hevi_column_status()
+    assert bool((st == 0).all())
+    assert bool(torch.isfinite(fused).all())
+    assert bool((fused == plain).all())
+    assert float((fused - q0).abs().max()) > 0.0
+    ctx.close()
+
+
 def test_nhevi_graph_bitwise_equal_to_steps(hv):
     ctx, H = _mixed_ctx(hv, hv.FP32_IR, ncols=64, seed=32)
     tab = hv.tableau("ARK2")
