@@ -93,14 +93,15 @@ def _load():
     return _lib
 
 
-SET_2C, SET_3C = 0, 1
+SET_2C, SET_3C, SET_2NC = 0, 1, 2
 
 
 @contextlib.contextmanager
 def equation_set(s: int):
     """Run the oracle calls inside the block with equation set s (SET_2C:
     unknowns rho, m, Theta; SET_3C: rho, m, E, total energy, App. A.1 and
-    reading R16 of the C source); set 2C again afterwards."""
+    reading R16 of the C source; SET_2NC: rho, w, theta, the advective set of
+    Sec. 2.1, reading R17); set 2C again afterwards."""
     lib = _load()
     if lib.or_set_equation_set(int(s)):
         raise ValueError(f"unknown equation set {s}")

@@ -56,6 +56,22 @@
  *       E_bar); the band LU solves the system equilibrated with the same
  *       scales (E and rho differ by five orders of magnitude).  Selected by
  *       or_set_equation_set(1); 0 (default) is set 2C.
+ *   R17 set 2NC (Sec. 2.1, Eq. set2nc) in the same column, unknowns (rho, w,
+ *       theta): zero horizontal velocity is invariant under the vertical
+ *       operator.  V follows Eq. (hevi/vertical_operators) with the reference
+ *       subtracted as in R2,
+ *         V_rho = -Dcal[rho w],
+ *         V_w   = -(w Dcal[w] + (Dcal[P - P_bar] + g (rho - rho_bar)) / rho),
+ *         V_th  = -w Dcal[theta],
+ *       P = EOS(rho theta), V_w = 0 at both ends (R3).  With w = 0 at both
+ *       ends the weak-form continuity derivative of Sec. 4.2.3 equals the
+ *       strong form after DSS (the element boundary terms cancel in pairs and
+ *       vanish at the ends), so Dcal serves all three equations.  L is the
+ *       Frechet derivative of this V (the printed K_2NC is not: its advection
+ *       and pressure entries put the point-j factor where the derivative has
+ *       the point-i one); the band is A = I - Lambda L assembled column by
+ *       column from L applied to unit vectors.  Scales (rho_bar, c_s,
+ *       theta_bar).  Selected by or_set_equation_set(2).
  */
 #include <float.h>
 #include <math.h>
@@ -163,10 +179,10 @@ int or_column_grid(int nez, int N, double ztop, double* z, double* M) {
 }
 
 /* The equation set of every call: 0 = set 2C (unknowns rho, m, Theta),
- * 1 = set 3C (rho, m, E; reading R16). */
+ * 1 = set 3C (rho, m, E; reading R16), 2 = set 2NC (rho, w, theta; R17). */
 static int or_set = 0;
 int or_set_equation_set(int s) {
-  if (s != 0 && s != 1) return 1;
+  if (s != 0 && s != 1 && s != 2) return 1;
   or_set = s;
   return 0;
 }
@@ -189,7 +205,8 @@ void or_reference_state(int nz, const double* z, double* rho, double* theta, dou
 }
 
 /* Scales used for the Newton norm (reading R7): rho_bar, rho_bar * c_s and
- * Theta_bar at each point, with c_s = sqrt(gamma R T0). */
+ * Theta_bar at each point, with c_s = sqrt(gamma R T0); set 3C: E_bar for the
+ * third; set 2NC: c_s and theta_bar for the second and third. */
 void or_scales(int nz, const double* z, double* s) {
   double* rho = (double*)malloc(sizeof(double) * 4 * nz);
   double *th = rho + nz, *Th = th + nz, *P = Th + nz;
@@ -197,8 +214,10 @@ void or_scales(int nz, const double* z, double* s) {
   double cs = sqrt(or_gamma() * OR_R * OR_T0);
   for (int I = 0; I < nz; ++I) {
     s[3 * I + 0] = rho[I];
-    s[3 * I + 1] = rho[I] * cs;
-    s[3 * I + 2] = or_set ? P[I] / (or_gamma() - 1.0) + rho[I] * OR_G * z[I] : Th[I];
+    s[3 * I + 1] = or_set == 2 ? cs : rho[I] * cs;
+    s[3 * I + 2] = or_set == 1   ? P[I] / (or_gamma() - 1.0) + rho[I] * OR_G * z[I]
+                   : or_set == 2 ? th[I]
+                                 : Th[I];
   }
   free(rho);
 }
@@ -215,7 +234,7 @@ typedef struct {
   double* M;   /* nz */
   double *rho_b, *theta_b, *Theta_b, *P_b;
   double* E_b;  /* set 3C reference energy P_bar / (gamma - 1) + rho_bar g z */
-  double* X_b;  /* reference value of the third unknown: Theta_b (2C) or E_b (3C) */
+  double* X_b;  /* reference value of the third unknown: Theta_b (2C), E_b (3C), theta_b (2NC) */
 } column_t;
 
 static int column_init(column_t* c, int nez, int N, double ztop) {
@@ -234,7 +253,7 @@ static int column_init(column_t* c, int nez, int N, double ztop) {
   c->E_b = c->P_b + c->nz;
   for (int I = 0; I < c->nz; ++I)
     c->E_b[I] = c->P_b[I] / (or_gamma() - 1.0) + c->rho_b[I] * OR_G * c->z[I];
-  c->X_b = or_set ? c->E_b : c->Theta_b;
+  c->X_b = or_set == 1 ? c->E_b : (or_set == 2 ? c->theta_b : c->Theta_b);
   return 0;
 }
 static void column_free(column_t* c) { free(c->D); }
@@ -261,7 +280,12 @@ static void dss_derivative(const column_t* c, const double* f, double* out) {
  *   V_m     = -Dcal[m^2/rho + P(Theta) - P_bar] - g (rho - rho_bar)
  *   V_Theta = -Dcal[Theta m / rho]
  * with readings R2 (reference subtraction) and R3 (V_m = 0 at both ends). */
+static void apply_V_2nc(const column_t* c, const double* q, double* v);
 static void apply_V(const column_t* c, const double* q, double* v) {
+  if (or_set == 2) {
+    apply_V_2nc(c, q, v);
+    return;
+  }
   int nz = c->nz;
   double* f = (double*)malloc(sizeof(double) * 6 * nz);
   double *fr = f, *fm = f + nz, *ft = f + 2 * nz, *dr = f + 3 * nz, *dm = f + 4 * nz,
@@ -269,7 +293,7 @@ static void apply_V(const column_t* c, const double* q, double* v) {
   for (int I = 0; I < nz; ++I) {
     double rho = q[3 * I], m = q[3 * I + 1], Th = q[3 * I + 2];
     fr[I] = m;
-    if (or_set) {
+    if (or_set == 1) {
       /* set 3C (R16): Th holds E; P - P_bar from the differences to the reference */
       double E = Th;
       double dP = (or_gamma() - 1.0) *
@@ -294,6 +318,85 @@ static void apply_V(const column_t* c, const double* q, double* v) {
   free(f);
 }
 
+/* Set 2NC (reading R17), unknowns (rho, w, theta):
+ *   V_rho = -Dcal[rho w]
+ *   V_w   = -( w Dcal[w] + (Dcal[P - P_bar] + g (rho - rho_bar)) / rho ),  P = EOS(rho theta)
+ *   V_th  = -w Dcal[theta]
+ * and V_w = 0 at both ends (R3). */
+static void apply_V_2nc(const column_t* c, const double* q, double* v) {
+  int nz = c->nz;
+  double* f = (double*)malloc(sizeof(double) * 8 * nz);
+  double *fr = f, *fw = f + nz, *fp = f + 2 * nz, *ft = f + 3 * nz;
+  double *dr = f + 4 * nz, *dw = f + 5 * nz, *dp = f + 6 * nz, *dt = f + 7 * nz;
+  for (int I = 0; I < nz; ++I) {
+    double rho = q[3 * I], w = q[3 * I + 1], th = q[3 * I + 2];
+    fr[I] = rho * w;
+    fw[I] = w;
+    fp[I] = eos(rho * th) - c->P_b[I];
+    ft[I] = th;
+  }
+  dss_derivative(c, fr, dr);
+  dss_derivative(c, fw, dw);
+  dss_derivative(c, fp, dp);
+  dss_derivative(c, ft, dt);
+  for (int I = 0; I < nz; ++I) {
+    double rho = q[3 * I], w = q[3 * I + 1];
+    v[3 * I + 0] = -dr[I];
+    v[3 * I + 1] = -(w * dw[I] + (dp[I] + OR_G * (rho - c->rho_b[I])) / rho);
+    v[3 * I + 2] = -w * dt[I];
+  }
+  v[1] = 0.0;
+  v[3 * (nz - 1) + 1] = 0.0;
+  free(f);
+}
+
+/* Set 2NC (reading R17): L = dV/dq at q0 = (rho0, w0, theta0) applied to
+ * x = (r, u, t), with P0 = EOS(rho0 theta0), P_rho = gamma P0 / rho0,
+ * P_theta = gamma P0 / theta0 and X0 = Dcal[P0 - P_bar] + g (rho0 - rho_bar):
+ *   L_rho = -Dcal[w0 r + rho0 u]
+ *   L_w   = -( u Dcal[w0] + w0 Dcal[u] - r X0 / rho0^2
+ *              + (Dcal[P_rho r + P_theta t] + g r) / rho0 )
+ *   L_th  = -( u Dcal[theta0] + w0 Dcal[t] )
+ * and L_w = 0 at both ends (R3). */
+static void apply_L_2nc(const column_t* c, const double* q0, const double* x, double* y) {
+  int nz = c->nz;
+  double* f = (double*)malloc(sizeof(double) * 14 * nz);
+  double *fr = f, *fu = f + nz, *fp = f + 2 * nz, *ft = f + 3 * nz;
+  double *gw = f + 4 * nz, *gp = f + 5 * nz, *gt = f + 6 * nz;
+  double *dr = f + 7 * nz, *du = f + 8 * nz, *dp = f + 9 * nz, *dt = f + 10 * nz;
+  double *Dw0 = f + 11 * nz, *Dp0 = f + 12 * nz, *Dt0 = f + 13 * nz;
+  for (int I = 0; I < nz; ++I) {
+    double r0 = q0[3 * I], w0 = q0[3 * I + 1], t0 = q0[3 * I + 2];
+    double P0 = eos(r0 * t0);
+    double r = x[3 * I], u = x[3 * I + 1], t = x[3 * I + 2];
+    fr[I] = w0 * r + r0 * u;
+    fu[I] = u;
+    fp[I] = or_gamma() * P0 / r0 * r + or_gamma() * P0 / t0 * t;
+    ft[I] = t;
+    gw[I] = w0;
+    gp[I] = P0 - c->P_b[I];
+    gt[I] = t0;
+  }
+  dss_derivative(c, fr, dr);
+  dss_derivative(c, fu, du);
+  dss_derivative(c, fp, dp);
+  dss_derivative(c, ft, dt);
+  dss_derivative(c, gw, Dw0);
+  dss_derivative(c, gp, Dp0);
+  dss_derivative(c, gt, Dt0);
+  for (int I = 0; I < nz; ++I) {
+    double r0 = q0[3 * I], w0 = q0[3 * I + 1];
+    double r = x[3 * I], u = x[3 * I + 1];
+    double X0 = Dp0[I] + OR_G * (r0 - c->rho_b[I]);
+    y[3 * I + 0] = -dr[I];
+    y[3 * I + 1] = -(u * Dw0[I] + w0 * du[I] - r * X0 / (r0 * r0) + (dp[I] + OR_G * r) / r0);
+    y[3 * I + 2] = -(u * Dt0[I] + w0 * dt[I]);
+  }
+  y[1] = 0.0;
+  y[3 * (nz - 1) + 1] = 0.0;
+  free(f);
+}
+
 /* App. A.3, Eq. (set2c_jacobian) restricted to the vertical (zeta_x = zeta_y
  * = 0, zeta_z = 1 after the metric cancellation above): the 3x3 flux
  * Jacobian at a point, rows = flux of (rho, m, Theta), columns = d/d(rho, m,
@@ -303,7 +406,7 @@ static void apply_V(const column_t* c, const double* q, double* v) {
  *   Theta-flux : ( -theta w, theta,  w  )       (reading R5) */
 static void flux_jacobian(const double* q, double z, double K[3][3]) {
   double rho = q[0], m = q[1], Th = q[2];
-  if (or_set) {
+  if (or_set == 1) {
     /* set 3C (R16): fluxes (m, m^2/rho + P, (E + P) m / rho), P = (gamma - 1)
      * (E - m^2/(2 rho) - rho g z): with w = m/rho, h = (E + P)/rho,
      *   dP/drho = (gamma - 1)(w^2/2 - g z), dP/dm = -(gamma - 1) w, dP/dE = gamma - 1 */
@@ -325,6 +428,10 @@ static void flux_jacobian(const double* q, double z, double K[3][3]) {
  *   (L x) = -Dcal[K(q0) x] - G x,   G[m, rho] = g   (reading R4),
  * and (L x)_m = 0 at both ends (reading R3). */
 static void apply_L(const column_t* c, const double* q0, const double* x, double* y) {
+  if (or_set == 2) {
+    apply_L_2nc(c, q0, x, y);
+    return;
+  }
   int nz = c->nz;
   double* f = (double*)malloc(sizeof(double) * 6 * nz);
   double *fr = f, *fm = f + nz, *ft = f + 2 * nz, *dr = f + 3 * nz, *dm = f + 4 * nz,
@@ -359,6 +466,22 @@ static void assemble_band(const column_t* c, double lam, const double* q0, doubl
   int N = c->N, n = c->n, kl = 3 * (N + 1) - 1, ku = kl;
   memset(ab, 0, sizeof(double) * (size_t)ldab * n);
 #define AB(i, j) ab[(size_t)(j) * ldab + (kl + ku + (i) - (j))]
+  if (or_set == 2) {
+    /* set 2NC (R17): column j of A = I - Lambda L is e_j - Lambda L e_j; L
+     * couples the points of one element only, so the column lies in the band */
+    double* e = (double*)calloc((size_t)n, sizeof(double));
+    double* y = (double*)malloc(sizeof(double) * n);
+    for (int j = 0; j < n; ++j) {
+      e[j] = 1.0;
+      apply_L(c, q0, e, y);
+      e[j] = 0.0;
+      int i0 = j - ku < 0 ? 0 : j - ku, i1 = j + kl > n - 1 ? n - 1 : j + kl;
+      for (int i = i0; i <= i1; ++i) AB(i, j) = (i == j ? 1.0 : 0.0) - lam * y[i];
+    }
+    free(e);
+    free(y);
+    return;
+  }
   for (int e = 0; e < c->nez; ++e) {
     for (int k = 0; k <= N; ++k) {
       int I = e * N + k;
@@ -507,7 +630,8 @@ int or_grid(int ncols, int nez, int N, const double* ztop, double* z, double* M)
  * (reading R16) is solved equilibrated, (S^-1 A S)(S^-1 x) = S^-1 b with the
  * reference scales S = (rho_bar, rho_bar c_s, E_bar): its unknowns differ by
  * five orders of magnitude and the unscaled band's condition number (~1e14)
- * would put the FP64 LU's error near 1e-10; set 2C is factored as assembled. */
+ * would put the FP64 LU's error near 1e-10; set 2NC likewise with (rho_bar,
+ * c_s, theta_bar); set 2C is factored as assembled. */
 static double unknown_scale(const column_t* c, int i);
 static int factor_band(const column_t* c, double lam, const double* q0, double* ab, int ldab,
                        int* ipiv) {
@@ -563,18 +687,19 @@ static double scaled_norm(const column_t* c, const double* F) {
   double s2 = 0.0, cs = sqrt(or_gamma() * OR_R * OR_T0);
   for (int I = 0; I < c->nz; ++I) {
     double a = F[3 * I] / c->rho_b[I];
-    double b = F[3 * I + 1] / (c->rho_b[I] * cs);
+    double b = F[3 * I + 1] / (or_set == 2 ? cs : c->rho_b[I] * cs);
     double d = F[3 * I + 2] / c->X_b[I];
     s2 += a * a + b * b + d * d;
   }
   return sqrt(s2);
 }
 
-/* Reference scale of unknown i (rho_bar, rho_bar c_s, Theta_bar at point i/3). */
+/* Reference scale of unknown i (rho_bar, rho_bar c_s, Theta_bar at point i/3;
+ * set 3C: E_bar third; set 2NC: c_s second, theta_bar third). */
 static double unknown_scale(const column_t* c, int i) {
   int I = i / 3, u = i - 3 * I;
   if (u == 0) return c->rho_b[I];
-  if (u == 1) return c->rho_b[I] * sqrt(or_gamma() * OR_R * OR_T0);
+  if (u == 1) return (or_set == 2 ? 1.0 : c->rho_b[I]) * sqrt(or_gamma() * OR_R * OR_T0);
   return c->X_b[I];
 }
 

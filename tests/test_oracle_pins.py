@@ -927,3 +927,220 @@ def test_set3c_stage_solve_matches_refined_dense_solve(nez, N):
         y = y + np.linalg.solve(As, r.astype(np.float64))
     ref = y * s
     assert np.linalg.norm(x[0] - ref) / np.linalg.norm(ref) < 1e-12
+
+
+# --------------------------------------------------------------------------
+# Set 2NC (Sec. 2.1, Eq. set2nc; reading R17 of the C source): unknowns
+# (rho, w, theta) in the column, advective momentum and theta equations.
+# --------------------------------------------------------------------------
+
+RGAS, CPH = 287.17, 1004.67
+
+
+def _state_2nc(nez, N, seed=0, ztop=ZTOP, amp_w=5.0, amp_t=2.0):
+    """A non-rest set-2NC state: rest density times 1 +- 1%, w uniform (0 at
+    both ends), theta = theta_bar +- amp_t."""
+    g = np.random.default_rng(seed)
+    z = oracle.column_grid(nez, N, ztop)[0]
+    with oracle.equation_set(oracle.SET_2NC):
+        qr = oracle.reference_q(nez, N, ztop, 1)[0].reshape(-1, 3)
+    rho = qr[:, 0] * (1 + 0.01 * g.uniform(-1, 1, z.size))
+    w = g.uniform(-amp_w, amp_w, z.size)
+    w[0] = w[-1] = 0.0
+    th = qr[:, 2] + g.uniform(-amp_t, amp_t, z.size)
+    return np.stack([rho, w, th], 1).reshape(-1)
+
+
+def _smooth_2nc(nez, N, ztop=ZTOP):
+    """A smooth non-rest state: every field a few sine or cosine waves over
+    the column (w = 0 at both ends)."""
+    z = oracle.column_grid(nez, N, ztop)[0]
+    with oracle.equation_set(oracle.SET_2NC):
+        qr = oracle.reference_q(nez, N, ztop, 1)[0].reshape(-1, 3)
+    s = z / ztop
+    rho = qr[:, 0] * (1 + 0.01 * np.cos(np.pi * s))
+    w = 3.0 * np.sin(np.pi * s) + np.sin(3 * np.pi * s)
+    th = qr[:, 2] * (1 + 0.005 * np.sin(2 * np.pi * s))
+    return np.stack([rho, w, th], 1).reshape(-1)
+
+
+def test_set2nc_rest_state_closed_form_and_equilibrium():
+    """The set-2NC rest state is the isothermal atmosphere (rho_bar, 0,
+    theta_bar = T0 exp(g z / (cp T0))), and V of it vanishes exactly."""
+    nez, N = 8, 4
+    z = oracle.column_grid(nez, N, ZTOP)[0]
+    with oracle.equation_set(oracle.SET_2NC):
+        q = _rest(nez, N)
+        v = oracle.apply_V(nez, N, ZTOP, q)
+        s = oracle.scales(z)
+    q3 = q[0].reshape(-1, 3)
+    rho = 1e5 / (RGAS * 300.0) * np.exp(-z * G / (RGAS * 300.0))
+    np.testing.assert_allclose(q3[:, 0], rho, rtol=1e-13)
+    assert np.array_equal(q3[:, 1], np.zeros_like(z))
+    np.testing.assert_allclose(q3[:, 2], 300.0 * np.exp(G * z / (CPH * 300.0)), rtol=1e-13)
+    assert np.array_equal(v, np.zeros_like(v))
+    cs = np.sqrt(GAMMA * RGAS * 300.0)
+    np.testing.assert_allclose(s.reshape(-1, 3), np.stack([rho, np.full_like(z, cs), q3[:, 2]], 1),
+                               rtol=1e-13)
+
+
+@pytest.mark.parametrize("nez,N", [(2, 2), (8, 4), (16, 3)])
+def test_set2nc_conserves_column_mass(nez, N):
+    """The continuity equation keeps its flux form in set 2NC: with w = 0 at
+    both ends the LGL column integral of V_rho vanishes."""
+    _, M = oracle.column_grid(nez, N, ZTOP)
+    q = _state_2nc(nez, N, seed=41)
+    with oracle.equation_set(oracle.SET_2NC):
+        v = oracle.apply_V(nez, N, ZTOP, q[None])[0].reshape(-1, 3)
+    q3 = q.reshape(-1, 3)
+    assert abs(np.dot(M, v[:, 0])) < 1e-13 * np.abs(M * q3[:, 0] * q3[:, 1]).sum()
+
+
+@pytest.mark.parametrize("nez,N", [(2, 2), (8, 4), (16, 3)])
+def test_set2nc_continuity_tendency_equals_set2c(nez, N):
+    """The same physical state written in sets 2C (rho, rho w, rho theta) and
+    2NC (rho, w, theta) gets the same continuity tendency: both take Dcal of
+    the mass flux rho w."""
+    q = _state_2nc(nez, N, seed=42).reshape(-1, 3)
+    rho, w, th = q[:, 0], q[:, 1], q[:, 2]
+    q2 = np.stack([rho, rho * w, rho * th], 1).reshape(1, -1)
+    v2 = oracle.apply_V(nez, N, ZTOP, q2)[0].reshape(-1, 3)
+    with oracle.equation_set(oracle.SET_2NC):
+        vn = oracle.apply_V(nez, N, ZTOP, q.reshape(1, -1))[0].reshape(-1, 3)
+    np.testing.assert_allclose(vn[:, 0], v2[:, 0], rtol=0, atol=1e-13 * np.abs(v2[:, 0]).max())
+
+
+def test_set2nc_momentum_and_theta_match_set2c_at_spectral_rate():
+    """Sets 2C and 2NC are the same equations written with and without the
+    product rule: d(rho w)/dt = rho dw/dt + w drho/dt and d(rho theta)/dt =
+    rho dtheta/dt + theta drho/dt.  On a smooth state the discrete tendencies
+    satisfy these identities up to the product-rule error of the derivative,
+    which falls at a spectral rate with N (pins the advection, pressure and
+    gravity terms of V_w and the advection of theta)."""
+    em, et = [], []
+    for N in (2, 4, 6, 8):
+        nez = 6
+        q = _smooth_2nc(nez, N).reshape(-1, 3)
+        rho, w, th = q[:, 0], q[:, 1], q[:, 2]
+        q2 = np.stack([rho, rho * w, rho * th], 1).reshape(1, -1)
+        v2 = oracle.apply_V(nez, N, ZTOP, q2)[0].reshape(-1, 3)
+        with oracle.equation_set(oracle.SET_2NC):
+            vn = oracle.apply_V(nez, N, ZTOP, q.reshape(1, -1))[0].reshape(-1, 3)
+        dm = rho * vn[:, 1] + w * vn[:, 0]
+        dT = rho * vn[:, 2] + th * vn[:, 0]
+        em.append(np.abs(dm - v2[:, 1])[1:-1].max() / np.abs(v2[:, 1]).max())
+        et.append(np.abs(dT - v2[:, 2]).max() / np.abs(v2[:, 2]).max())
+    for e in (em, et):
+        assert e[0] > 10 * e[1] > 100 * e[2] > 1000 * e[3], e
+        assert e[3] < 1e-7, e
+
+
+@pytest.mark.parametrize("nez,N", [(2, 2), (4, 4), (16, 3)])
+def test_set2nc_linear_operator_is_the_frechet_derivative(nez, N):
+    """L(q0) x against central differences of the set-2NC V: pins the
+    Frechet derivative, its point-local terms (w' dw0/dz, w' dtheta0/dz, the
+    1/rho factor of the pressure and gravity terms) included.  L couples the
+    points of one element only, and neither the continuity nor the theta row
+    sees the other end's theta or rho, so A = I - Lambda L lies within
+    k_l = k_u = 3N + 1, one inside the 3(N+1) - 1 of the band storage."""
+    q0 = _state_2nc(nez, N, seed=43)
+    g = np.random.default_rng(44)
+    with oracle.equation_set(oracle.SET_2NC):
+        s = oracle.scales(oracle.column_grid(nez, N, ZTOP)[0])
+        x = s * g.standard_normal(q0.size)
+        x[1] = x[-2] = 0.0
+        L = oracle.apply_L(nez, N, ZTOP, q0[None], x[None])[0]
+        eps = 1e-5
+        fd = (oracle.apply_V(nez, N, ZTOP, (q0 + eps * x)[None])[0]
+              - oracle.apply_V(nez, N, ZTOP, (q0 - eps * x)[None])[0]) / (2 * eps)
+        n, kl = q0.size, 3 * (N + 1) - 1
+        Ld = np.stack([oracle.apply_L(nez, N, ZTOP, q0[None], np.eye(n)[j][None])[0]
+                       for j in range(n)], 1)
+    assert np.linalg.norm(L - fd) <= 1e-7 * np.linalg.norm(L)
+    i, j = np.indices(Ld.shape)
+    assert np.abs(Ld[np.abs(i - j) >= kl]).max() == 0.0
+    assert np.abs(Ld[i - j == kl - 1]).max() > 0.0 and np.abs(Ld[j - i == kl - 1]).max() > 0.0
+
+
+def test_set2nc_hydrostatic_state_at_spectral_rate():
+    """An isothermal atmosphere at T1 = 250 K, written as (rho, 0, theta), is
+    in hydrostatic balance; its set-2NC momentum tendency is the discretisation
+    error of dp/dz = -rho g divided by rho, which falls at a spectral rate with
+    N (pins the EOS, the 1/rho factor and the sign of the gravity term)."""
+    T1 = 250.0
+    errs = []
+    for N in (2, 4, 6, 8):
+        nez = 3
+        z = oracle.column_grid(nez, N, ZTOP)[0]
+        p = 1e5 * np.exp(-z * G / (RGAS * T1))
+        rho = p / (RGAS * T1)
+        th = T1 * (1e5 / p) ** (RGAS / CPH)
+        q = np.stack([rho, np.zeros_like(rho), th], 1).reshape(1, -1)
+        with oracle.equation_set(oracle.SET_2NC):
+            v = oracle.apply_V(nez, N, ZTOP, q)[0].reshape(-1, 3)
+        errs.append(np.abs(v[:, 1]).max() / G)
+        assert np.abs(v[:, 0]).max() == 0.0 and np.abs(v[:, 2]).max() == 0.0
+    assert errs[0] > 10 * errs[1] > 100 * errs[2] > 1000 * errs[3], errs
+    assert errs[3] < 1e-7, errs
+
+
+def test_set2nc_one_newton_iteration_is_the_lhevi_solve():
+    """Sec. 4.3 for set 2NC: one Newton iteration on F(q) = q - Lambda V(q) -
+    R from q0 solves (I - Lambda L(q0)) q1 = R + Lambda (V(q0) - L(q0) q0)."""
+    nez, N, lam = 8, 4, 87.868
+    q0 = _state_2nc(nez, N, seed=45)[None]
+    with oracle.equation_set(oracle.SET_2NC):
+        R = q0 + 0.01 * oracle.scales(oracle.column_grid(nez, N, ZTOP)[0])[None] * \
+            np.random.default_rng(46).standard_normal(q0.shape)
+        R[0, 1] = R[0, -2] = 0.0
+        q1, it, st = oracle.newton(nez, N, ZTOP, lam, R, q0, rtol=0.0, max_iter=1)
+        assert it[0] == 1
+        b = R + lam * (oracle.apply_V(nez, N, ZTOP, q0) - oracle.apply_L(nez, N, ZTOP, q0, q0))
+        x, info = oracle.stage_solve(nez, N, ZTOP, lam, q0, b)
+    assert (info == 0).all()
+    np.testing.assert_allclose(q1, x, rtol=1e-12, atol=1e-12 * np.abs(q0).max())
+
+
+def test_set2nc_newton_converges_quadratically():
+    nez, N, lam = 8, 4, 87.868
+    q0 = _state_2nc(nez, N, seed=47, amp_w=20.0, amp_t=5.0)[None]
+    with oracle.equation_set(oracle.SET_2NC):
+        s = oracle.scales(oracle.column_grid(nez, N, ZTOP)[0])
+        R = q0.copy()
+
+        def fnorm(q):
+            return np.linalg.norm((q - lam * oracle.apply_V(nez, N, ZTOP, q) - R) / s)
+        norms = [fnorm(q0)]
+        for m in range(1, 5):
+            q, it, st = oracle.newton(nez, N, ZTOP, lam, R, q0, rtol=0.0, max_iter=m)
+            norms.append(fnorm(q))
+    norms = np.array(norms) / norms[0]
+    for m in range(3):
+        assert norms[m + 1] <= 10.0 * norms[m] ** 2, norms
+    assert norms[4] < 1e-12, norms
+
+
+@pytest.mark.parametrize("nez,N", [(8, 4), (24, 4)])
+def test_set2nc_stage_solve_matches_refined_dense_solve(nez, N):
+    """The set-2NC stage solve (band LU of the equilibrated system) against a
+    dense LAPACK solve of the same matrix (numpy, equilibrated) refined three
+    times with residuals in extended precision: 1e-12."""
+    lam = 87.868
+    q0 = _state_2nc(nez, N, seed=48)[None]
+    kl = 3 * (N + 1) - 1
+    with oracle.equation_set(oracle.SET_2NC):
+        s = oracle.scales(oracle.column_grid(nez, N, ZTOP)[0])
+        b = q0 + 1e-2 * s * np.random.default_rng(49).standard_normal(q0.shape)
+        b[0, 1] = b[0, -2] = 0.0
+        x, info = oracle.stage_solve(nez, N, ZTOP, lam, q0, b)
+        ab = oracle.assemble_band(nez, N, ZTOP, lam, q0)
+    assert (info == 0).all()
+    A = oracle.band_to_dense(ab[0] if ab.ndim == 3 else ab, kl, kl)
+    As = A * s[None, :] / s[:, None]
+    bs = b[0] / s
+    y = np.linalg.solve(As, bs)
+    for _ in range(3):
+        r = (bs.astype(np.longdouble) - As.astype(np.longdouble) @ y.astype(np.longdouble))
+        y = y + np.linalg.solve(As, r.astype(np.float64))
+    ref = y * s
+    assert np.linalg.norm(x[0] - ref) / np.linalg.norm(ref) < 1e-12
