@@ -180,12 +180,24 @@ hevi_status hevi_set_refinement(hevi_ctx* ctx, double tol, int32_t max_sweeps);
  *     of set 3C is factored equilibrated with (rho_bar, rho_bar c_s, E_bar),
  *     as the FP32 band always is.  The NHEVI-GMRES solve refuses a set-3C
  *     context.
+ *   HEVI_SET_2NC: (rho, w, theta), the advective set of Sec. 2.1 (Eq. set2nc)
+ *     in the same column: V_rho = -Dcal[rho w], V_w = -(w Dcal w + (Dcal[P -
+ *     P_bar] + g (rho - rho_bar)) / rho), V_theta = -w Dcal theta; its Jacobian
+ *     is the Frechet derivative of that V, with terms local to each point
+ *     (w' Dcal w0, w' Dcal theta0, the 1/rho0 factor), factored equilibrated
+ *     with (rho_bar, c_s, theta_bar).  HEVI_FP64 contexts only (an
+ *     HEVI_FP32_IR context returns HEVI_ERR_INVALID_ARG); the first selection
+ *     allocates 6 doubles per point of coefficient scratch
+ *     (HEVI_ERR_OOM if that fails).  The NHEVI-GMRES solve refuses a
+ *     set-2NC context too.
  * Recomputes the reference table (E_bar = P_bar / (gamma - 1) + rho_bar g z for
- * set 3C; hevi_reference_state then writes (rho_bar, 0, E_bar)) on the
- * context's stream; the factors of the last hevi_factor become stale.  Call it
- * before the states of the new set are used. */
+ * set 3C, theta_bar for set 2NC; hevi_reference_state then writes (rho_bar, 0,
+ * E_bar) or (rho_bar, 0, theta_bar)) on the context's stream; the factors of
+ * the last hevi_factor become stale.  Call it before the states of the new set
+ * are used. */
 #define HEVI_SET_2C 0
 #define HEVI_SET_3C 1
+#define HEVI_SET_2NC 2
 hevi_status hevi_set_equation_set(hevi_ctx* ctx, int32_t set);
 
 /* How hevi_nhevi_step ends its Newton sequences.  on = 1 (default): after

@@ -21,7 +21,7 @@ from . import build as _build_mod
 __all__ = ["load", "Context", "HeviError", "FP64", "FP32_IR", "tableau", "Tableau"]
 
 FP64, FP32_IR = 0, 1
-SET_2C, SET_3C = 0, 1  # equation sets (hevi_set_equation_set)
+SET_2C, SET_3C, SET_2NC = 0, 1, 2  # equation sets (hevi_set_equation_set)
 STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of device memory",
           4: "singular column", 5: "not converged", 6: "non-physical input state",
           7: "device wait past its limit"}

@@ -859,7 +859,15 @@ hevi_status hevi_set_column_tops(hevi_ctx* c, int64_t first, int64_t count, cons
 }
 
 hevi_status hevi_set_equation_set(hevi_ctx* c, int32_t set) {
-  if (!c || (set != HEVI_SET_2C && set != HEVI_SET_3C)) return HEVI_ERR_INVALID_ARG;
+  if (!c || (set != HEVI_SET_2C && set != HEVI_SET_3C && set != HEVI_SET_2NC))
+    return HEVI_ERR_INVALID_ARG;
+  if (set == HEVI_SET_2NC) {
+    if (c->prec != HEVI_FP64) return HEVI_ERR_INVALID_ARG;
+    if (!c->v.lin2) {
+      const hevi_status s = c->alloc(&c->v.lin2, 2 * (size_t)c->state_size);
+      if (s != HEVI_OK) return s;
+    }
+  }
   c->v.ph.eqset = set;
   hevi::launch_setup_ref(c->v, c->d_col_order, c->d_col_nez, c->stream);
   c->factored = false;

@@ -61,11 +61,11 @@ __device__ __forceinline__ void k_row_3c(const Phys& ph, int v, double w, double
   }
 }
 
-template <int N>
-__device__ __forceinline__ void elem_deriv(const double (&f)[N + 1][3], double (&cc)[N + 1][3]) {
+template <int N, int NC>
+__device__ __forceinline__ void elem_deriv(const double (&f)[N + 1][NC], double (&cc)[N + 1][NC]) {
   constexpr int P = (N + 1) / 2;
 #pragma unroll
-  for (int v = 0; v < 3; ++v) {
+  for (int v = 0; v < NC; ++v) {
     double e[P], o[P];
 #pragma unroll
     for (int j = 0; j < P; ++j) {

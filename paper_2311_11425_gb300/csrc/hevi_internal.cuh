@@ -121,6 +121,8 @@ struct DevView {
   const double* ref;        // state layout: (rho_bar, P_bar, Theta_bar) per point
   double* ithb;             // per point (index off/3 + I): 1 / Theta_bar, or null
   double* lin;              // state layout: (w0, theta0, c0 = gamma P0 / Theta0)
+  double* lin2;             // set 2NC only, 6 per point at 2 off + 6 I: (P_rho, P_theta,
+                            // Dcal w0, Dcal[P0 - P_bar] + g (rho0 - rho_bar), Dcal theta0, 0)
   const TileDesc* tiles;
   int32_t ntiles;
   int32_t tile_begin;       // tiles [tile_begin, tile_begin + tile_count) of one order, or
@@ -157,56 +159,56 @@ __device__ __forceinline__ double wsum(const double* w, int I, int nz) {
 }
 
 // Element pass: visits the elements of a column bottom to top, asks `flux`
-// for the 3 flux components at every point (once per point, in increasing
+// for the NC (default 3) flux components at every point (once per point, in increasing
 // order), forms the strong-form element derivative weighted by the LGL
 // weights, sums the two contributions of shared points (DSS), and hands each
 // completed point I to `out` with D_I = (Dcal f)_I =
 // (1/M_I) sum_{(e,k)->I} w_k J_e (dxi/dz) sum_j Dhat_kj f_(e,j)   (Sec. 3).
 // `out(I, D)` is called in increasing I, always after flux(J) for every J
 // of the element holding I.
-// Weighted element derivative cc[k] = sum_j w_k Dhat_kj f_j (3 components)
+// Weighted element derivative cc[k] = sum_j w_k Dhat_kj f_j (NC components)
 // in the even-odd form; reads the tables from constant memory.
-template <int N>
-__device__ __forceinline__ void elem_deriv(const double (&f)[N + 1][3], double (&cc)[N + 1][3]);
+template <int N, int NC>
+__device__ __forceinline__ void elem_deriv(const double (&f)[N + 1][NC], double (&cc)[N + 1][NC]);
 
-template <int N, class FluxF, class OutF>
+template <int N, int NC = 3, class FluxF, class OutF>
 __device__ __forceinline__ void element_pass(const Col& c, const double* w, const double* iw,
                                              FluxF&& flux, OutF&& out) {
   (void)w;
-  double f[N + 1][3];
-  double carry[3] = {0.0, 0.0, 0.0};
+  double f[N + 1][NC];
+  double carry[NC] = {};
   flux(0, f[0]);
   for (int e = 0; e < c.nez; ++e) {
     const int I0 = e * N;
 #pragma unroll
     for (int k = 1; k <= N; ++k) flux(I0 + k, f[k]);
-    double cc[N + 1][3];
-    elem_deriv<N>(f, cc);
+    double cc[N + 1][NC];
+    elem_deriv<N, NC>(f, cc);
     {
-      double D[3];
+      double D[NC];
       const double sc = c.s * (e == 0 ? iw[0] : 0.5 * iw[0]);
 #pragma unroll
-      for (int v = 0; v < 3; ++v) D[v] = (carry[v] + cc[0][v]) * sc;
+      for (int v = 0; v < NC; ++v) D[v] = (carry[v] + cc[0][v]) * sc;
       out(I0, D);
     }
 #pragma unroll
     for (int k = 1; k < N; ++k) {
-      double D[3];
+      double D[NC];
       const double sc = c.s * iw[k];
 #pragma unroll
-      for (int v = 0; v < 3; ++v) D[v] = cc[k][v] * sc;
+      for (int v = 0; v < NC; ++v) D[v] = cc[k][v] * sc;
       out(I0 + k, D);
     }
 #pragma unroll
-    for (int v = 0; v < 3; ++v) {
+    for (int v = 0; v < NC; ++v) {
       carry[v] = cc[N][v];
       f[0][v] = f[N][v];
     }
   }
-  double D[3];
+  double D[NC];
   const double sc = c.s * iw[0];
 #pragma unroll
-  for (int v = 0; v < 3; ++v) D[v] = carry[v] * sc;
+  for (int v = 0; v < NC; ++v) D[v] = carry[v] * sc;
   out(c.nz - 1, D);
 }
 

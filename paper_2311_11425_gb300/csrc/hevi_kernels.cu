@@ -78,8 +78,11 @@ __global__ void k_setup_ref(DevView v, const int32_t* col_order, const int32_t* 
     const double th = ph.T0 * exp(ph.g * z / (ph.cp * ph.T0));
     const double Th = rho * th;
     const double P = eos(ph, Th);
-    // set 3C keeps the reference energy E_bar = P_bar / (gamma - 1) + rho_bar g z
-    const double X = ph.eqset == 1 ? P / (ph.gamma - 1.0) + rho * ph.g * z : Th;
+    // set 3C keeps the reference energy E_bar = P_bar / (gamma - 1) + rho_bar g z,
+    // set 2NC the potential temperature theta_bar
+    const double X = ph.eqset == 1 ? P / (ph.gamma - 1.0) + rho * ph.g * z
+                     : ph.eqset == 2 ? th
+                                     : Th;
     r[3 * I + 0] = rho;
     r[3 * I + 1] = P;
     r[3 * I + 2] = X;
@@ -145,11 +148,16 @@ __device__ __forceinline__ void assemble_row(const DevView& v, const Col& c, dou
   const double* lin = v.lin + c.off;
   const double* ref = v.ref + c.off;
   const double cs = v.ph.cs;
-  auto scale = [&](int idx) -> double {  // S entry of unknown idx
+  const bool nc = v.ph.eqset == 2;
+  auto scale = [&](int idx) -> double {  // S entry of unknown idx (set 2NC: c_s for w)
     const int P = idx / 3, u = idx - 3 * P;
     const double rb = ref[3 * P];
-    return u == 0 ? rb : (u == 1 ? rb * cs : ref[3 * P + 2]);
+    return u == 0 ? rb : (u == 1 ? (nc ? cs : rb * cs) : ref[3 * P + 2]);
   };
+  // set 2NC: lin = (w0, rho0, theta0), lin2 = (P_rho, P_theta, Dcal w0, X0, Dcal theta0);
+  // the w- and theta-rows carry coefficients of the row's own point
+  const double* l2 = nc ? v.lin2 + 2 * c.off : nullptr;
+  const double irI = nc ? 1.0 / lin[3 * I + 1] : 0.0, w0I = nc ? lin[3 * I] : 0.0;
   const T inv_si = SCALED ? T(1.0 / scale(i)) : T(1);
   const T fac = T(lam * c.s / wsum<N>(w, I, c.nz));
   // elements containing point I and I's local index in each
@@ -178,6 +186,14 @@ __device__ __forceinline__ void assemble_row(const DevView& v, const Col& c, dou
         double k0, k1, k2;
         k_row_3c(v.ph, vv, lin[3 * J], lin[3 * J + 1], lin[3 * J + 2], k0, k1, k2);
         kv0 = T(k0); kv1 = T(k1); kv2 = T(k2);
+      } else if (nc) {  // set 2NC: Dcal_IJ times these, the w-, theta-rows scaled at I
+        if (vv == 0) {
+          kv0 = T(lin[3 * J]); kv1 = T(lin[3 * J + 1]); kv2 = T(0);
+        } else if (vv == 1) {
+          kv0 = T(l2[6 * J] * irI); kv1 = T(w0I); kv2 = T(l2[6 * J + 1] * irI);
+        } else {
+          kv0 = T(0); kv1 = T(0); kv2 = T(w0I);
+        }
       } else if (vv == 0) {
         kv0 = T(0); kv1 = T(1); kv2 = T(0);
       } else if (vv == 1) {
@@ -197,7 +213,22 @@ __device__ __forceinline__ void assemble_row(const DevView& v, const Col& c, dou
     }
   }
   row[slot(i) * stride] += T(1);
-  if (vv == 1) {
+  if (nc) {  // set 2NC: the point-local terms of the derivative (gravity among them)
+    if (vv == 1) {
+      T gr = T(lam * (v.ph.g * irI - l2[6 * I + 3] * irI * irI));
+      T gw = T(lam * l2[6 * I + 2]);
+      if (SCALED) {
+        gr *= T(scale(i - 1)) * inv_si;
+        gw *= T(scale(i)) * inv_si;
+      }
+      row[slot(i - 1) * stride] += gr;
+      row[slot(i) * stride] += gw;
+    } else if (vv == 2) {
+      T gw = T(lam * l2[6 * I + 4]);
+      if (SCALED) gw *= T(scale(i - 1)) * inv_si;
+      row[slot(i - 1) * stride] += gw;
+    }
+  } else if (vv == 1) {
     T gg = T(lam * v.ph.g);
     if (SCALED) gg *= T(scale(i - 1)) * inv_si;
     row[slot(i - 1) * stride] += gg;
@@ -299,6 +330,14 @@ __device__ int band_lu(const DevView& v, const Col& c, double lam, T* win, int s
   return info;
 }
 
+// Set 2NC: P(rho theta) - P_bar at a point, ref = (rho_bar, P_bar, theta_bar)
+// there.  Both products are rounded as written (never fused into a
+// multiply-add with the subtraction inside), so that the rest state gives
+// exactly zero.
+__device__ __forceinline__ double dp_2nc(const Phys& ph, double rho, double th, const double* ref) {
+  return eos_perturbation(ph, __dmul_rn(rho, th), __dmul_rn(ref[0], ref[2]), ref[1]);
+}
+
 // ---------------------------------------------------------------------------
 // Factor kernel: linearisation coefficients, assembly, band LU, records out.
 // ---------------------------------------------------------------------------
@@ -320,6 +359,18 @@ __device__ void factor_column(const DevView& v, const TileDesc& t, int lane, dou
       rho = v.ref[a]; m = 0.0; Th = v.ref[a + 2];
     }
     double w, th, cc, dP;
+    if (ph.eqset == 2) {  // set 2NC: lin = (w0, rho0, theta0); lin2[0..1] = (P_rho, P_theta)
+      if (!(rho > 0.0) || !(Th > 0.0) || !isfinite(m)) ok = false;
+      const double P = v.ref[a + 1] + dp_2nc(ph, rho, Th, v.ref + a);
+      double* l2 = v.lin2 + 2 * a;
+      l2[0] = ph.gamma * P / rho;
+      l2[1] = ph.gamma * P / Th;
+      l2[5] = 0.0;
+      v.lin[a] = m;
+      v.lin[a + 1] = rho;
+      v.lin[a + 2] = Th;
+      continue;
+    }
     if (ph.eqset == 1) {  // set 3C: (w, h, z)
       const double z = point_z<N>(1.0 / (0.5 * c.s), I, c.nz);
       double h;
@@ -336,6 +387,23 @@ __device__ void factor_column(const DevView& v, const TileDesc& t, int lane, dou
     v.lin[a] = w;
     v.lin[a + 1] = th;
     v.lin[a + 2] = cc;
+  }
+  if (ph.eqset == 2) {  // set 2NC: the derivatives of q0 its Jacobian needs at each point
+    const double* lc = v.lin + c.off;
+    const double* ref = v.ref + c.off;
+    double* l2 = v.lin2 + 2 * c.off;
+    auto flux = [&](int I, double* f) {
+      const double rho = lc[3 * I + 1], th = lc[3 * I + 2];
+      f[0] = lc[3 * I];
+      f[1] = dp_2nc(ph, rho, th, ref + 3 * I);
+      f[2] = th;
+    };
+    auto out = [&](int I, const double* D) {
+      l2[6 * I + 2] = D[0];
+      l2[6 * I + 3] = D[1] + ph.g * (lc[3 * I + 1] - ref[3 * I]);
+      l2[6 * I + 4] = D[2];
+    };
+    element_pass<N>(c, c_tab.w[N], c_tab.iw[N], flux, out);
   }
   T* base = reinterpret_cast<T*>(v.fac) + t.fac_off;
   constexpr int FR = Band<N>::FR;
@@ -410,9 +478,9 @@ static void launch_factor_n(const DevView& v, double lam, const double* q0, cuda
   const int blk = pick_block(window_slots(N) * esz, 64), tiles_per_blk = blk / kTile;
   const unsigned grid = (unsigned)((v.tile_count + tiles_per_blk - 1) / tiles_per_blk);
   const int smem = window_slots(N) * blk * esz;
-  if (v.ph.eqset == 1) {
-    // set 3C: the band equilibrated with the reference scales (its unknowns
-    // differ by five orders of magnitude); the solve scales b and x to match
+  if (v.ph.eqset != 0) {
+    // sets 3C and 2NC: the band equilibrated with the reference scales (their
+    // unknowns differ by orders of magnitude); the solve scales b and x to match
     cudaFuncSetAttribute(k_factor<N, double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          smem);
     k_factor<N, double, true><<<grid, blk, smem, st>>>(v, lam, q0);
@@ -584,12 +652,13 @@ __device__ void solve_fp64_column(const DevView& v, const TileDesc& t, int lane,
     return;
   }
   v.col_status[c.col] = HEVI_COL_OK;
-  // set 3C factors S^-1 A S (S: rho_bar, rho_bar c_s, E_bar): y = S^-1 b, x = S y
-  const bool eq = v.ph.eqset == 1;
+  // sets 3C and 2NC factor S^-1 A S (S: rho_bar, rho_bar c_s or, in set 2NC, c_s,
+  // and the third unknown's reference): y = S^-1 b, x = S y
+  const bool eq = v.ph.eqset != 0, nc = v.ph.eqset == 2;
   const double* ref = v.ref + c.off;
   auto scale = [&](int i) {
     const int P = i / 3, u = i - 3 * P;
-    return u == 0 ? ref[3 * P] : (u == 1 ? ref[3 * P] * v.ph.cs : ref[3 * P + 2]);
+    return u == 0 ? ref[3 * P] : (u == 1 ? (nc ? v.ph.cs : ref[3 * P] * v.ph.cs) : ref[3 * P + 2]);
   };
   for (int i = 0; i < c.n; ++i) y[i * stride] = eq ? b[c.off + i] / scale(i) : b[c.off + i];
   for (int i = c.n; i < c.n + 2 * K; ++i) y[i * stride] = 0.0;
@@ -659,6 +728,39 @@ __device__ void apply_V_column(const DevView& v, const Col& c, const double* q, 
   const double* ref = v.ref + c.off;
   const double* qc = q + c.off;
   bool ok = true;
+  if (ph.eqset == 2) {
+    // set 2NC, unknowns (rho, w, theta):  V_rho = -Dcal[rho w],
+    // V_w = -(w Dcal[w] + (Dcal[P - P_bar] + g (rho - rho_bar)) / rho), V_theta = -w Dcal[theta]
+    auto flux4 = [&](int I, double* f) {
+      const double rho = qc[3 * I], w = qc[3 * I + 1], th = qc[3 * I + 2];
+      if (!(rho > 0.0) || !(th > 0.0)) ok = false;
+      f[0] = rho * w;
+      f[1] = w;
+      f[2] = dp_2nc(ph, rho, th, ref + 3 * I);
+      f[3] = th;
+    };
+    auto o4 = [&](int I, const double* D) {
+      const double rho = qc[3 * I], w = qc[3 * I + 1];
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        const int64_t i = c.off + 3 * I + u;
+        double val;
+        if (u == 0)
+          val = -D[0];
+        else if (u == 1)
+          val = (I == 0 || I == c.nz - 1) ? 0.0
+                                          : -(w * D[1] + (D[2] + ph.g * (rho - ref[3 * I])) / rho);
+        else
+          val = -(w * D[3]);
+        if (add) val += add[i];
+        if (sub) val -= sub[i];
+        out[i] = val;
+      }
+    };
+    element_pass<N, 4>(c, c_tab.w[N], c_tab.iw[N], flux4, o4);
+    if (!ok && report) fail(v, c.col, HEVI_COL_BAD_INPUT);
+    return;
+  }
   auto flux = [&](int I, double* f) {
     const double rho = qc[3 * I], m = qc[3 * I + 1], Th = qc[3 * I + 2];
     if (ph.eqset == 1) {  // set 3C: fluxes (m, m^2/rho + P - P_bar, (E + P) m / rho)
@@ -704,6 +806,34 @@ __device__ void apply_L_column(const DevView& v, const Col& c, const double* x, 
   const double* lin = v.lin + c.off;
   const double* xc = x + c.off;
   const double g = v.ph.g;
+  if (v.ph.eqset == 2) {
+    // set 2NC: the Frechet derivative of V at q0 (lin = (w0, rho0, theta0), lin2 =
+    // (P_rho, P_theta, Dcal w0, X0, Dcal theta0)) applied to x = (r, u, t):
+    //   L_rho = -Dcal[w0 r + rho0 u],
+    //   L_w   = -(u Dcal w0 + w0 Dcal u - r X0 / rho0^2 + (Dcal[P_rho r + P_theta t] + g r) / rho0),
+    //   L_theta = -(u Dcal theta0 + w0 Dcal t)
+    const double* l2 = v.lin2 + 2 * c.off;
+    auto flux4 = [&](int I, double* f) {
+      const double r = xc[3 * I], u = xc[3 * I + 1], t = xc[3 * I + 2];
+      f[0] = lin[3 * I] * r + lin[3 * I + 1] * u;
+      f[1] = u;
+      f[2] = l2[6 * I] * r + l2[6 * I + 1] * t;
+      f[3] = t;
+    };
+    auto o4 = [&](int I, const double* D) {
+      const int64_t a = c.off + 3 * I;
+      const double r = xc[3 * I], u = xc[3 * I + 1];
+      const double w0 = lin[3 * I], r0 = lin[3 * I + 1];
+      out[a] = -D[0];
+      out[a + 1] = (I == 0 || I == c.nz - 1)
+                       ? 0.0
+                       : -(u * l2[6 * I + 2] + w0 * D[1] - r * l2[6 * I + 3] / (r0 * r0) +
+                           (D[2] + g * r) / r0);
+      out[a + 2] = -(u * l2[6 * I + 4] + w0 * D[3]);
+    };
+    element_pass<N, 4>(c, c_tab.w[N], c_tab.iw[N], flux4, o4);
+    return;
+  }
   auto flux = [&](int I, double* f) {
     const double x0 = xc[3 * I], x1 = xc[3 * I + 1], x2 = xc[3 * I + 2];
     const double wI = lin[3 * I], thI = lin[3 * I + 1], cI = lin[3 * I + 2];
@@ -1048,10 +1178,11 @@ __global__ void __launch_bounds__(128) k_newton_fpass(DevView v, NewtonArgs a) {
   // 1/Theta_bar in FP32; F itself is FP64.
   const float ics = 1.0f / ph.csf;
   auto f32 = [](double x) { return df_from_double(x).hi; };
+  const bool nc = ph.eqset == 2;  // set 2NC: w is scaled by c_s alone
   auto inv_scales = [&](int I, float (&is)[3]) {
     const float ir = __frcp_rn(f32(ref[3 * I]));
     is[0] = ir;
-    is[1] = ir * ics;
+    is[1] = nc ? ics : ir * ics;
     is[2] = v.ithb ? f32(v.ithb[c.off / 3 + I]) : __frcp_rn(f32(ref[3 * I + 2]));
   };
   float dn2 = 0.0f;
@@ -1120,7 +1251,50 @@ __global__ void __launch_bounds__(128) k_newton_fpass(DevView v, NewtonArgs a) {
       un2 = fmaf(su, su, un2);
     }
   };
-  element_pass<N>(c, c_tab.w[N], c_tab.iw[N], flux, out);
+  if (nc) {
+    // set 2NC: V_rho = -Dcal[rho w], V_w = -(w Dcal[w] + (Dcal[P - P_bar] + g (rho -
+    // rho_bar)) / rho), V_theta = -w Dcal[theta]
+    auto flux4 = [&](int I, double* f) {
+      const double rho = qc[3 * I], w = qc[3 * I + 1], th = qc[3 * I + 2];
+      if (!(rho > 0.0) || !(th > 0.0)) ok = false;
+      f[0] = rho * w;
+      f[1] = w;
+      f[2] = dp_2nc(ph, rho, th, ref + 3 * I);
+      f[3] = th;
+    };
+    auto out4 = [&](int I, const double* D) {
+      float is[3];
+      inv_scales(I, is);
+      const double rho = qc[3 * I], w = qc[3 * I + 1];
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        const int i = 3 * I + u;
+        double F;
+        if (u == 1 && (I == 0 || I == c.nz - 1)) {
+          F = qc[i] - Rc[i];
+        } else {
+          // F = q - Lambda V - R with -V as below
+          double vterm;
+          if (u == 0)
+            vterm = D[0];
+          else if (u == 1)
+            vterm = w * D[1] + (D[2] + ph.g * (rho - ref[3 * I])) / rho;
+          else
+            vterm = w * D[3];
+          F = fma(a.lam, vterm, qc[i]) - Rc[i];
+        }
+        rc[i] = -F;
+        const float isc = is[u];
+        const float sF = f32(F) * isc, sq = f32(qc[i]) * isc, su = f32(qc[i] - q0c[i]) * isc;
+        fn2 = fmaf(sF, sF, fn2);
+        qn2 = fmaf(sq, sq, qn2);
+        un2 = fmaf(su, su, un2);
+      }
+    };
+    element_pass<N, 4>(c, c_tab.w[N], c_tab.iw[N], flux4, out4);
+  } else {
+    element_pass<N>(c, c_tab.w[N], c_tab.iw[N], flux, out);
+  }
   const double fn = sqrt((double)fn2), qn = sqrt((double)qn2), un = sqrt((double)un2);
   const double floor_ok = kNewtonFloor * qn;
   int cv = 0, st = HEVI_COL_OK;
