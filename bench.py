@@ -515,6 +515,7 @@ def gpu_arm(args, rank, world, local_rank, pool, cores):
     if world == 1 and not args.no_extra:
         line["stage_latency_1538"] = stage_latency(args)
         line["nhevi_lu"] = nhevi_lu_run(args)
+        line["equation_sets"] = equation_sets_run(args)
         line["batched"] = batched_run(args)
         line["nhevi_gmres_vs_lu"] = gmres_run(args)
         line["serving"] = serving_run(args)
@@ -759,6 +760,58 @@ def stage_latency(args):
                      "factor_and_solve_wall_p50_us": float(np.percentile(fwall, 50))}
         ctx.close()
     torch.cuda.empty_cache()
+    return out
+
+
+def equation_sets_run(args, steps=10, warmup=3):
+    """The headline step (LHEVI-PS ARK3, 86,402 columns of (10, 4), 30 km,
+    dt = 300 s) in equation sets 3C (rho, m, E) and 2NC (rho, w, theta), from
+    each set's rest state plus the increment of ``hevi_inputs.state_increment``
+    written in that set's unknowns (w' and a 1 K Gaussian: m' = rho' w', E' =
+    cv rho' T' in set 3C; w' and theta' themselves in set 2NC), H = 0.  Set 3C
+    on both precisions, set 2NC on the FP64 path (the one it has)."""
+    import numpy as np
+    import torch
+    import hevi_inputs
+    import paper_2311_11425_gb300 as hv
+    cv = 1004.67 - 287.17
+    g = hevi_inputs.rng(7)
+    zt = np.full(NCOLS, 30e3)
+    dq = hevi_inputs.state_increment(g, NEZ, ORDER, zt).reshape(NCOLS, -1, 3)
+    amp = hevi_inputs.density_like(np.arange(NZ) / (NZ - 1), zt)
+    tab = hv.tableau("ARK3")
+    out = {}
+    for name, eq, prec in (("3C_FP32_IR", hv.SET_3C, hv.FP32_IR), ("3C_FP64", hv.SET_3C, hv.FP64),
+                           ("2NC_FP64", hv.SET_2NC, hv.FP64)):
+        inc = dq.copy()
+        if eq == hv.SET_3C:
+            inc[:, :, 2] *= cv  # rho' T' -> cv rho' T'
+        else:
+            inc[:, :, 1] /= amp  # m' -> w'
+            inc[:, :, 2] /= amp  # Theta' -> theta'
+        stream = torch.cuda.current_stream()
+        ctx = hv.Context([(NEZ, ORDER)], 30e3, ncols=NCOLS, precision=prec, stream=stream)
+        ctx.hevi_set_equation_set(eq)
+        q0 = ctx.hevi_reference_state() + torch.from_numpy(inc.reshape(-1)).cuda()
+        H = torch.zeros_like(q0)
+        qa, qb = q0.clone(), torch.empty_like(q0)
+        qa, qb = run_steps(ctx, tab, qa, qb, H, warmup)
+        ctx.hevi_sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        qa, qb = run_steps(ctx, tab, qa, qb, H, steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        st, it = ctx.hevi_column_status()
+        out[name] = {"value": STAGES * NCOLS / (ms * 1e-3), "unit": "column-solves/s",
+                     "ms_per_step": ms, "status_ok": bool((st == 0).all()),
+                     "state_finite": bool(torch.isfinite(qa).all()),
+                     "ir_sweeps_mean": float(it.float().mean()) if prec == hv.FP32_IR else None}
+        del ctx, q0, H, qa, qb
+        torch.cuda.empty_cache()
+    out["workload"] = ("the headline step (LHEVI-PS ARK3, 86402 columns of (10, 4), 30 km, dt = 300 s) "
+                       "in sets 3C and 2NC from rest plus the seeded w' and 1 K Gaussian, H = 0")
     return out
 
 
