@@ -118,9 +118,11 @@ struct DevView {
   const int64_t* col_off;   // [ncols + 1] state offsets
   const int32_t* perm;      // [ncols] class-sorted column index
   const double* col_dz;     // [ncols] element height
-  const double* ref;        // state layout: (rho_bar, P_bar, Theta_bar) per point
-  double* ithb;             // per point (index off/3 + I): 1 / Theta_bar, or null
-  double* lin;              // state layout: (w0, theta0, c0 = gamma P0 / Theta0)
+  const double* ref;        // state layout: (rho_bar, P_bar, X) per point, X = Theta_bar (set
+                            // 2C), E_bar (3C) or theta_bar (2NC)
+  double* ithb;             // per point (index off/3 + I): 1 / X (X as in ref), or null
+  double* lin;              // state layout: set 2C (w0, theta0, c0 = gamma P0 / Theta0),
+                            // set 3C (w0, h0, z), set 2NC (w0, rho0, theta0)
   double* lin2;             // set 2NC only, 6 per point at 2 off + 6 I: (P_rho, P_theta,
                             // Dcal w0, Dcal[P0 - P_bar] + g (rho0 - rho_bar), Dcal theta0, 0)
   const TileDesc* tiles;
