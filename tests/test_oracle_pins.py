@@ -1144,3 +1144,27 @@ def test_set2nc_stage_solve_matches_refined_dense_solve(nez, N):
         y = y + np.linalg.solve(As, r.astype(np.float64))
     ref = y * s
     assert np.linalg.norm(x[0] - ref) / np.linalg.norm(ref) < 1e-12
+
+
+@pytest.mark.parametrize("eqset", ["SET_3C", "SET_2NC"])
+def test_newton_gmres_reaches_the_lu_root_in_sets_3c_and_2nc(eqset):
+    """The oracle's JFNK-GMRES (Sec. 4.2.1) works from V alone, so it serves
+    every equation set: with a small Frechet perturbation and tight
+    tolerances it finds the Newton-LU root in sets 3C and 2NC as in set 2C
+    (an independent check of each set's analytic Jacobian, which only the
+    LU path uses)."""
+    nez, N = 8, 4
+    lam = tableaux.ARK2.gamma * 300.0
+    q0 = (_state_3c(nez, N, seed=61, amp_w=1.0, amp_t=0.5) if eqset == "SET_3C"
+          else _state_2nc(nez, N, seed=61, amp_w=1.0, amp_t=0.5))[None]
+    n = q0.shape[1]
+    with oracle.equation_set(getattr(oracle, eqset)):
+        s = oracle.scales(oracle.column_grid(nez, N, ZTOP)[0])
+        R = q0 + 1e-3 * s[None] * np.random.default_rng(62).standard_normal(q0.shape)
+        R[0, 1] = R[0, -2] = 0.0
+        q, it, kit, st = oracle.newton_gmres(nez, N, ZTOP, lam, R, q0, eps=1e-7, rtol=1e-12,
+                                             gtol=1e-12)
+        qr, _, str_ = oracle.newton(nez, N, ZTOP, lam, R, q0, rtol=1e-12)
+    assert st[0] == 0 and str_[0] == 0
+    assert np.linalg.norm((q - qr)[0] / s) < 1e-9 * np.linalg.norm((qr - q0)[0] / s)
+    assert 1 <= it[0] <= 8 and it[0] <= kit[0] <= it[0] * n
